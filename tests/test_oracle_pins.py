@@ -1,0 +1,530 @@
+"""Pins of the FP64 oracle to things other than itself: closed forms, hand-reduced special cases
+of the paper's equations, invariants, brute force and finite differences.
+
+Each pin is chosen so that a plausible mistake in the oracle (a dropped term, a wrong sign, a
+transposed operand, a wrong index) changes the checked value.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import worlds as Wd
+from paper_2603_12185_gb300 import scenes as S
+
+G = 9.81
+DT = 0.002
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------------------------------
+# Eq. r_scaling: the MuJoCo solimp gap scaling
+# ------------------------------------------------------------------------------------------
+def test_solimp_r_table(oracle):
+    """Values worked by hand from Eq. r_scaling with (0.9, 0.95, 0.001, 0.5, 2) -- see
+    tests/golden/solimp_r.json for the arithmetic."""
+    g = json.load(open(os.path.join(GOLDEN, "solimp_r.json")))
+    for aphi, r in zip(g["abs_phi"], g["r"]):
+        assert oracle.solimp_r(aphi, g["solimp"]) == pytest.approx(r, abs=1e-15)
+
+
+# ------------------------------------------------------------------------------------------
+# closed forms without contact
+# ------------------------------------------------------------------------------------------
+def test_free_flight_projectile(oracle):
+    """Semi-implicit Euler under gravity: v_n = v0 + n g dt, x_n = x0 + n dt v0 + g dt^2 n(n+1)/2."""
+    d = Wd.sphere_on_plane()
+    p = Wd.params()
+    x0, v0, w = np.array([0.1, -0.2, 50.0]), np.array([1.0, 2.0, 3.0]), np.array([0.3, -0.2, 0.5])
+    q, v = Wd.free_state(x0, lin=v0, ang=w)
+    n = 200
+    q, v, nc = oracle.step(d, p, DT, n, q, v)
+    g = np.array([0, 0, -G])
+    assert nc == 0
+    np.testing.assert_allclose(v[:3], v0 + n * g * DT, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(q[:3], x0 + n * DT * v0 + g * DT * DT * n * (n + 1) / 2, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(v[3:], w, atol=1e-14)  # isotropic body: no gyroscopic torque
+
+
+def test_isotropic_spin_is_exact(oracle):
+    """Torque-free isotropic body: body-frame omega is constant and the exponential-map update
+    composes to q_n = q0 (x) (cos(n|w|dt/2), sin(n|w|dt/2) w/|w|)."""
+    d = Wd.sphere_on_plane()
+    p = Wd.params(gravity=(0.0, 0.0, 0.0))
+    q0 = S.quat_about((1, 2, 3), 0.7)
+    w = np.array([2.0, -1.0, 0.5])
+    q, v = Wd.free_state((0, 0, 10.0), quat=q0, ang=w)
+    n = 500
+    q, v, _ = oracle.step(d, p, DT, n, q, v)
+    ang = np.linalg.norm(w) * n * DT
+    dq = np.concatenate([[np.cos(ang / 2)], np.sin(ang / 2) * w / np.linalg.norm(w)])
+    a, b = q0, dq
+    expect = np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                       a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                       a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                       a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+    np.testing.assert_allclose(q[3:], expect, atol=1e-12)
+
+
+def test_torque_free_asymmetric_body_conserves_world_angular_momentum(oracle):
+    """The gyroscopic bias w x I w (sign and frame) keeps the world-frame angular momentum
+    R I w fixed up to the O(dt) error of explicit integration; a flipped sign or a world-frame
+    inertia drifts it at O(1)."""
+    inertia = np.array([1e-3, 2e-3, 3.5e-3])
+    d = Wd.world([dict(mass=1.0, inertia=inertia)], [dict(type=S.SPHERE, body=0, size=(0.05, 0, 0))])
+    p = Wd.params(gravity=(0.0, 0.0, 0.0))
+    q, v = Wd.free_state((0, 0, 0), quat=S.quat_about((0.3, 1, 0.2), 0.4), ang=(0.4, 3.0, 0.2))
+
+    def Lworld(q, v):
+        _, _, poses = oracle.dynamics(d, (0, 0, 0), q, v)
+        R = poses[0, 3:12].reshape(3, 3)
+        return R @ (inertia * v[3:])
+
+    L0 = Lworld(q, v)
+    q1, v1, _ = oracle.step(d, p, 1e-4, 5000, q, v)
+    assert np.linalg.norm(Lworld(q1, v1) - L0) < 2e-3 * np.linalg.norm(L0)
+
+
+# ------------------------------------------------------------------------------------------
+# the worked single-contact step: the general dense-Jacobian path must reduce to scalar
+# arithmetic of Eqs. smooth_vel, tilde_defs, cf_wrench, k_d_setting, r_scaling, vel_correction
+# ------------------------------------------------------------------------------------------
+def _sphere_plane_by_hand(v0x):
+    """Sphere r=0.05, m=1, I=1e-3 on the plane z=0 (t1=x, t2=y), centre height 0.048 (phi=-2 mm),
+    linear velocity (v0x, 0, 0), 4 facets {+t1,+t2,-t1,-t2}, mu=0.5, k=0.1, d=0.001, dt=2 ms."""
+    r, m, I, mu, k, dd, phi = 0.05, 1.0, 1e-3, 0.5, 0.1, 0.001, -0.002
+    vz = -G * DT                             # Eq. smooth_vel: contact-free velocity
+    lever = np.array([0.0, 0.0, -(r + phi / 2)])  # midpoint of surface points minus the centre
+    rr = 0.95                                # |phi|/w = 2 -> clamped to 1 -> r_max
+    trace = 3 / m + (lever @ lever) * 3 / I - (lever @ lever) / I   # 3/m + |l|^2 tr(I^-1) - l^T I^-1 l
+    Mphi = rr / (1 - rr) / trace
+    d_dirs = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    lam = []
+    for dx, dy in d_dirs:
+        s = vz - mu * (dx * v0x + dy * 0.0)  # J~ v_s = J_n v - mu d^T J_t v
+        lam.append(max(0.0, -k * Mphi * (s * DT + phi) - dd * Mphi * s))
+    f = np.array([-mu * sum(l * dx for l, (dx, dy) in zip(lam, d_dirs)),
+                  -mu * sum(l * dy for l, (dx, dy) in zip(lam, d_dirs)), sum(lam)])
+    torque = np.cross(lever, f)
+    v = np.array([v0x, 0, vz]) + f / m
+    w = torque / I
+    return Mphi, lam, v, w
+
+
+@pytest.mark.parametrize("v0x", [0.0, 0.1])
+def test_worked_single_contact_step(oracle, v0x):
+    d = Wd.sphere_on_plane()
+    p = Wd.params(n_t=4)
+    q, v = Wd.free_state((0, 0, 0.048), lin=(v0x, 0, 0))
+    rec = oracle.step_record(d, p, DT, q, v)
+    Mphi, lam, v_exp, w_exp = _sphere_plane_by_hand(v0x)
+    assert len(rec["contacts"]) == 1
+    c = rec["contacts"][0]
+    assert c["phi"] == pytest.approx(-0.002, abs=1e-15)
+    np.testing.assert_allclose(c["pos"], [0, 0, -0.001], atol=1e-15)
+    assert c["mphi"] == pytest.approx(Mphi, rel=1e-12)
+    assert c["lam_sum"] == pytest.approx(sum(lam), rel=1e-12)
+    np.testing.assert_allclose(rec["v"][:3], v_exp, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][3:], w_exp, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["q"][:3], np.array([0, 0, 0.048]) + DT * v_exp, rtol=1e-12, atol=1e-15)
+    if v0x == 0.0:
+        assert sum(lam) == pytest.approx(4 * Mphi * 0.000223544, rel=1e-9)  # printed digits of the hand sum
+
+
+def test_rest_penetration_fixed_point(oracle):
+    """A sphere at rest settles where the F facet impulses carry its weight:
+    F M(phi) (k (g dt^2 + |phi|) + d g dt) = m g dt (all facets see s = -g dt), with M(phi) at
+    r_max and the lever arm r - |phi|/2 of the midpoint contact."""
+    r, m, I, k, dd = 0.05, 1.0, 1e-3, 0.1, 0.001
+    for nt, ntor, nrol in [(4, 0, 0), (8, 2, 8)]:
+        F = nt + ntor + nrol
+        lo, hi = 1e-3, 0.04
+        for _ in range(200):  # bisection on the balance residual
+            a = 0.5 * (lo + hi)
+            lev = r - a / 2
+            Mp = 19.0 / (3 / m + 2 * lev * lev / I)
+            res = F * Mp * (k * (G * DT * DT + a) + dd * G * DT) - m * G * DT
+            lo, hi = (a, hi) if res < 0 else (lo, a)
+        d = Wd.sphere_on_plane(mu=(0.5, 0.005, 0.005))
+        q, v = Wd.free_state((0, 0, 0.05))
+        q, v, _ = oracle.step(d, Wd.params(n_t=nt, n_tor=ntor, n_rol=nrol), DT, 6000, q, v)
+        assert r - q[2] == pytest.approx(0.5 * (lo + hi), rel=1e-6)
+        assert np.abs(v).max() < 1e-9
+
+
+# ------------------------------------------------------------------------------------------
+# invariants
+# ------------------------------------------------------------------------------------------
+def test_sphere_sphere_conserves_momentum(oracle):
+    """Equal and opposite J^T lambda: linear and angular momentum (about the origin) of two
+    colliding spheres are conserved without gravity, including an oblique, spinning impact
+    through the 6D cone."""
+    d = Wd.world([dict(mass=1.0, inertia=(1e-3,) * 3), dict(mass=2.0, inertia=(3e-3,) * 3)],
+                 [dict(type=S.SPHERE, body=0, size=(0.05, 0, 0), mu=(0.8, 0.005, 0.005)),
+                  dict(type=S.SPHERE, body=1, size=(0.06, 0, 0), mu=(0.8, 0.005, 0.005))])
+    p = Wd.params(gravity=(0.0, 0.0, 0.0), n_t=8, n_tor=2, n_rol=8)
+    qa, va = Wd.free_state((-0.2, 0.01, 0.02), quat=S.quat_about((1, 0, 0), 0.3), lin=(1.0, 0, 0), ang=(0, 5, 1))
+    qb, vb = Wd.free_state((0.2, -0.01, 0.0), lin=(-0.5, 0.1, 0), ang=(3, 0, -2))
+    q, v = np.concatenate([qa, qb]), np.concatenate([va, vb])
+    m = np.array([1.0, 2.0])
+    inert = [np.full(3, 1e-3), np.full(3, 3e-3)]
+
+    def momenta(q, v):
+        _, _, poses = oracle.dynamics(d, (0, 0, 0), q, v)
+        P = sum(m[i] * v[6 * i:6 * i + 3] for i in range(2))
+        L = sum(np.cross(q[7 * i:7 * i + 3], m[i] * v[6 * i:6 * i + 3])
+                + poses[i, 3:12].reshape(3, 3) @ (inert[i] * v[6 * i + 3:6 * i + 6]) for i in range(2))
+        return P, L
+
+    P0, L0 = momenta(q, v)
+    total = 0
+    for _ in range(60):
+        q, v, nc = oracle.step(d, p, DT, 10, q, v)
+        total += nc
+    P1, L1 = momenta(q, v)
+    assert total > 0
+    np.testing.assert_allclose(P1, P0, atol=1e-13)
+    np.testing.assert_allclose(L1, L0, atol=1e-12)
+
+
+def _pile_record(oracle, nbody=16, seed=3, settle=150):
+    b = S.make_pile(1, nbody, seed=seed)
+    d = b.world(0)
+    q, v, _ = oracle.step(d, b.params, b.dt, settle, b.q0[0], b.v0[0])
+    return b, d, q, v, oracle.step_record(d, b.params, b.dt, q, v)
+
+
+def test_facet_impulses_stay_in_the_primal_cone(oracle):
+    """lambda_j >= 0 for every facet, so the resultant satisfies Eq. primal_cone: the tangential
+    part lies in mu N_t conv{d_j} (within mu N_t), torsion within mu_tor N_tor, rolling within
+    mu_rol N_rol, with N_s the normal impulse of subspace s (all <= the total N)."""
+    b, d, q, v, rec = _pile_record(oracle)
+    assert len(rec["contacts"]) > 5
+    mu = S.PILE_MU
+    for c in rec["contacts"]:
+        w = c["wrench"]
+        assert w[0] >= 0.0
+        assert np.hypot(w[1], w[2]) <= mu[0] * w[0] * (1 + 1e-12) + 1e-18
+        assert abs(w[3]) <= mu[1] * w[0] * (1 + 1e-12) + 1e-18
+        assert np.hypot(w[4], w[5]) <= mu[2] * w[0] * (1 + 1e-12) + 1e-18
+        assert c["nfacet"] == 18 and 0 <= c["nactive"] <= 18
+        # the frame is orthonormal and right handed
+        fr = np.stack([c["normal"], c["t1"], c["t2"]])
+        np.testing.assert_allclose(fr @ fr.T, np.eye(3), atol=1e-12)
+        assert np.linalg.det(np.stack([c["t1"], c["t2"], c["normal"]])) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_four_facet_friction_polytope(oracle):
+    """With facets {+-t1, +-t2}: |F_t1| + |F_t2| <= mu N (the 1-norm ball of the pyramid)."""
+    d = Wd.sphere_on_plane()
+    q, v = Wd.free_state((0, 0, 0.047), lin=(0.3, -0.7, 0.1), ang=(2, 1, 0))
+    rec = oracle.step_record(d, Wd.params(n_t=4), DT, q, v)
+    w = rec["contacts"][0]["wrench"]
+    assert abs(w[1]) + abs(w[2]) <= 0.5 * w[0] * (1 + 1e-12)
+    assert abs(w[1]) + abs(w[2]) > 0.1 * w[0]
+
+
+def test_permutation_invariance(oracle):
+    """Decoupling across contacts: relabelling the bodies (and with them every contact) changes
+    the next state only at rounding level."""
+    b, d, q, v, _ = _pile_record(oracle, settle=120)
+    n = len(d["body_parent"])
+    perm = np.random.default_rng(0).permutation(n)
+    d2 = {k: np.array(x) for k, x in d.items()}
+    for k in ("body_mass", "body_inertia"):
+        d2[k] = d[k][perm]
+    for k in ("geom_type", "geom_size", "geom_pos", "geom_quat", "geom_mu"):
+        d2[k][:n] = d[k][:n][perm]
+    q2 = q.reshape(n, 7)[perm].reshape(-1)
+    v2 = v.reshape(n, 6)[perm].reshape(-1)
+    qa, va, _ = oracle.step(d, b.params, b.dt, 1, q, v)
+    qb, vb, _ = oracle.step(d2, b.params, b.dt, 1, q2, v2)
+    np.testing.assert_allclose(vb.reshape(n, 6), va.reshape(n, 6)[perm], rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(qb.reshape(n, 7), qa.reshape(n, 7)[perm], rtol=1e-12, atol=1e-14)
+
+
+def test_stick_slip_switches_at_tan_theta_equal_mu(oracle):
+    """A non-rotating block on an incline with the 4-facet cone aligned with the slope: below
+    tan(theta) = mu the slide settles to a bounded (viscous) terminal speed; above it, only the
+    downhill facet stays active and the acceleration approaches Coulomb's g(sin - mu cos)."""
+    mu = 0.5
+    res = {}
+    for ratio in (0.8, 1.2):
+        th = np.arctan(ratio * mu)
+        pq = S.quat_about((0, 1, 0), th)
+        d = Wd.world([dict(mass=1.0, inertia=(1e9,) * 3)],
+                     [dict(type=S.PLANE, body=-1, quat=pq, mu=(mu, 0, 0)),
+                      dict(type=S.SPHERE, body=0, size=(0.05, 0, 0), mu=(mu, 0, 0))])
+        slope = np.array([np.cos(th), 0, -np.sin(th)])
+        q, v = Wd.free_state(0.05 * np.array([np.sin(th), 0, np.cos(th)]))
+        speeds = []
+        for _ in range(10):
+            q, v, _ = oracle.step(d, Wd.params(n_t=4), DT, 1000, q, v)
+            speeds.append(v[:3] @ slope)
+        res[ratio] = (np.array(speeds), G * (np.sin(th) - mu * np.cos(th)))
+    sp, _ = res[0.8]
+    assert abs(sp[-1] - sp[-2]) < 0.02 * abs(sp[-1])          # terminal speed reached
+    sp, coulomb = res[1.2]
+    acc = (sp[-1] - sp[-5]) / 8.0
+    assert acc == pytest.approx(coulomb, rel=0.08)
+
+
+# ------------------------------------------------------------------------------------------
+# rigid-body dynamics: kinematics, inertia, bias, factorisation
+# ------------------------------------------------------------------------------------------
+def _planar_arm(l1=0.3, l2=0.2):
+    """Two hinges about the world y axis; link 1 from the origin along +x, link 2 along +x."""
+    bodies = [dict(parent=-1, jnt=S.HINGE, axis=(0, 1, 0), ipos=(l1 / 2, 0, 0), mass=1.3, inertia=(1e-3, 8e-3, 9e-3),
+                   damping=0.1),
+              dict(parent=0, jnt=S.HINGE, pos=(l1, 0, 0), axis=(0, 1, 0), ipos=(l2 / 2, 0, 0), mass=0.7,
+                   inertia=(5e-4, 3e-3, 3.2e-3), damping=0.1)]
+    return Wd.world(bodies, [dict(type=S.CAPSULE, body=0, pos=(l1 / 2, 0, 0), size=(0.02, 0.1, 0))])
+
+
+def test_forward_kinematics_planar_arm(oracle):
+    """Closed form of a planar two-link arm: a rotation by +a about +y takes x to (cos a, 0, -sin a)."""
+    l1, l2 = 0.3, 0.2
+    d = _planar_arm(l1, l2)
+    a1, a2 = 0.4, -1.1
+    _, _, poses = oracle.dynamics(d, (0, 0, -G), np.array([a1, a2]), np.zeros(2))
+    e = lambda a: np.array([np.cos(a), 0, -np.sin(a)])
+    np.testing.assert_allclose(poses[1, :3], l1 * e(a1), atol=1e-14)
+    np.testing.assert_allclose(poses[1, 12:15], l1 * e(a1) + l2 / 2 * e(a1 + a2), atol=1e-14)
+
+
+def _kinetic_fd(oracle, d, q, h=1e-6):
+    """M by polarisation of the kinetic energy, with body velocities from central differences of
+    the forward kinematics (hinge worlds: q + h v is a valid perturbation)."""
+    nv = len(q)
+    mass, inert = d["body_mass"], d["body_inertia"]
+
+    def T(vel):
+        _, _, pp = oracle.dynamics(d, (0, 0, 0), q + h * vel, np.zeros(nv))
+        _, _, pm = oracle.dynamics(d, (0, 0, 0), q - h * vel, np.zeros(nv))
+        e = 0.0
+        for b in range(len(mass)):
+            vc = (pp[b, 12:15] - pm[b, 12:15]) / (2 * h)
+            Rp, Rm = pp[b, 3:12].reshape(3, 3), pm[b, 3:12].reshape(3, 3)
+            W = (Rp - Rm) / (2 * h) @ ((Rp + Rm) / 2).T      # skew(omega_world)
+            w = np.array([W[2, 1], W[0, 2], W[1, 0]])
+            R = (Rp + Rm) / 2
+            e += 0.5 * mass[b] * vc @ vc + 0.5 * w @ (R @ np.diag(inert[b]) @ R.T) @ w
+        return e
+
+    M = np.zeros((nv, nv))
+    I = np.eye(nv)
+    for i in range(nv):
+        for j in range(nv):
+            M[i, j] = T(I[i] + I[j]) - T(I[i]) - T(I[j])
+    return M
+
+
+def test_mass_matrix_matches_kinetic_energy(oracle):
+    for d, q in [(_planar_arm(), np.array([0.4, -1.1])),
+                 (S.hand_template(seed=2).__dict__, None)]:
+        if q is None:
+            t = S.hand_template(seed=2)
+            d = {k: getattr(t, k) for k in t.__dataclass_fields__ if k not in ("name", "pile")}
+            # fingers only: drop the free cube (its quasi-velocity is not a q-derivative)
+            keep = np.arange(1, t.nbody)
+            d = {k: (v[keep] if k.startswith("body_") else v) for k, v in d.items()}
+            d["body_parent"] = np.where(d["body_parent"] > 0, d["body_parent"] - 1, -1).astype(np.int32)
+            d["geom_body"] = np.where(d["geom_body"] > 0, d["geom_body"] - 1, -1).astype(np.int32)
+            d["geom_type"] = np.where(d["geom_body"] >= 0, d["geom_type"], S.PLANE).astype(np.int32)
+            q = np.random.default_rng(1).uniform(-0.5, 0.5, 16)
+        M, _, _ = oracle.dynamics(d, (0, 0, -G), q, np.zeros(len(q)))
+        Mfd = _kinetic_fd(oracle, d, q)
+        np.testing.assert_allclose(M, Mfd, rtol=1e-6, atol=1e-9 * np.abs(M).max())
+        np.testing.assert_allclose(M, M.T, atol=1e-16)
+
+
+def test_bias_forces_match_euler_lagrange(oracle):
+    """c(q, v) = Mdot v - dT/dq + dV/dq (Euler-Lagrange with zero joint acceleration), each term
+    by central differences of the (separately pinned) inertia and of the potential sum m g z."""
+    d = _planar_arm()
+    q, v = np.array([0.4, -1.1]), np.array([1.7, -2.3])
+    h = 1e-6
+    M = lambda qq: oracle.dynamics(d, (0, 0, -G), qq, v)[0]
+    Mdot = (M(q + h * v) - M(q - h * v)) / (2 * h)
+    dT = np.array([(0.5 * v @ M(q + h * e) @ v - 0.5 * v @ M(q - h * e) @ v) / (2 * h) for e in np.eye(2)])
+
+    def V(qq):
+        _, _, p = oracle.dynamics(d, (0, 0, -G), qq, v)
+        return sum(d["body_mass"][b] * G * p[b, 14] for b in range(2))
+
+    dV = np.array([(V(q + h * e) - V(q - h * e)) / (2 * h) for e in np.eye(2)])
+    _, c, _ = oracle.dynamics(d, (0, 0, -G), q, v)
+    np.testing.assert_allclose(c, Mdot @ v - dT + dV, rtol=1e-7, atol=1e-9)
+
+
+def test_cholesky_matches_numpy(oracle):
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((7, 7))
+    A = A @ A.T + 0.1 * np.eye(7)
+    np.testing.assert_allclose(oracle.cholesky(A), np.linalg.cholesky(A), rtol=1e-12, atol=1e-14)
+
+
+def test_implicit_damping_smooth_velocity(oracle):
+    """Eq. smooth_vel with implicit damping on a single hinge without gravity: the rate decays
+    as v1 = v0 (I - 0) / (I + dt b) ... i.e. (M + dt b) v1 = M v0 for M = const."""
+    d = Wd.world([dict(parent=-1, jnt=S.HINGE, axis=(0, 0, 1), mass=1.0, inertia=(1e-2, 1e-2, 2e-2), damping=0.3)],
+                 [dict(type=S.SPHERE, body=0, size=(0.01, 0, 0))])
+    q, v, _ = oracle.step(d, Wd.params(gravity=(0.0, 0.0, 0.0)), DT, 1, np.zeros(1), np.array([2.0]))
+    assert v[0] == pytest.approx(2.0 * 2e-2 / (2e-2 + DT * 0.3), rel=1e-14)
+    assert q[0] == pytest.approx(DT * v[0], rel=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# narrowphase against brute force
+# ------------------------------------------------------------------------------------------
+def _box_sdf(x, half):
+    qd = np.abs(x) - half
+    return np.linalg.norm(np.maximum(qd, 0), axis=-1) + np.minimum(qd.max(axis=-1), 0)
+
+
+def test_capsule_box_minimiser_brute_force(oracle):
+    """The exact piecewise minimiser of the box SDF along the segment agrees with a dense grid."""
+    rng = np.random.default_rng(5)
+    half = np.array([0.03, 0.04, 0.05])
+    for _ in range(300):
+        w = rng.standard_normal(3)
+        w /= np.linalg.norm(w)
+        x0 = rng.uniform(-0.12, 0.12, 3)
+        h = rng.uniform(0.01, 0.06)
+        t = oracle.capsule_box_param(x0, w, h, half)
+        grid = np.linspace(-h, h, 200001)
+        f = _box_sdf(x0[None] + grid[:, None] * w[None], half)
+        ft = _box_sdf((x0 + t * w)[None], half)[0]
+        assert -h - 1e-15 <= t <= h + 1e-15
+        assert ft <= f.min() + 1e-9
+
+
+def _two_body_contact(oracle, ga, gb, qa, qb):
+    d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(ga, body=0), dict(gb, body=1)])
+    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=1.0), DT, np.concatenate([qa, qb]),
+                             np.zeros(12))
+    return rec["contacts"]
+
+
+def _surface_points(g, q, n=60000, rng=None):
+    """Dense samples of a geom's surface in world coordinates."""
+    rng = rng or np.random.default_rng(0)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = g["size"][0]
+    if g["type"] == S.SPHERE:
+        pts = r * u
+    elif g["type"] == S.CAPSULE:
+        t = rng.uniform(-1, 1, n)
+        core = np.zeros((n, 3))
+        core[:, 2] = t * g["size"][1]
+        pts = core + r * u
+        keep = np.abs(pts[:, 2]) >= 0  # core + sphere shell: the outer envelope is the capsule surface
+        pts = pts[keep]
+    else:
+        half = np.array(g["size"])
+        face = rng.integers(0, 3, n)
+        pts = rng.uniform(-1, 1, (n, 3)) * half
+        sgn = np.where(rng.random(n) < 0.5, -1, 1)
+        pts[np.arange(n), face] = sgn * half[face]
+    w, x, y, z = q[3:]
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    return q[:3] + pts @ R.T
+
+
+def _inside(g, q, pts):
+    w, x, y, z = q[3:]
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    l = (pts - q[:3]) @ R
+    if g["type"] == S.SPHERE:
+        return np.linalg.norm(l, axis=1) < g["size"][0]
+    if g["type"] == S.CAPSULE:
+        t = np.clip(l[:, 2], -g["size"][1], g["size"][1])
+        return np.hypot(np.hypot(l[:, 0], l[:, 1]), l[:, 2] - t) < g["size"][0]
+    return np.all(np.abs(l) < np.array(g["size"]), axis=1)
+
+
+@pytest.mark.parametrize("ta,tb", [(S.SPHERE, S.SPHERE), (S.SPHERE, S.CAPSULE), (S.CAPSULE, S.SPHERE),
+                                   (S.CAPSULE, S.CAPSULE), (S.SPHERE, S.BOX), (S.CAPSULE, S.BOX), (S.BOX, S.CAPSULE)])
+def test_narrowphase_distance_brute_force(oracle, ta, tb):
+    """Separated pairs: phi equals the minimum distance between dense surface samples; the
+    normal is the unit vector between the surface points and points from B to A."""
+    rng = np.random.default_rng(ta * 10 + tb)
+    size = {S.SPHERE: (0.04, 0, 0), S.CAPSULE: (0.03, 0.05, 0), S.BOX: (0.03, 0.04, 0.05)}
+    done = 0
+    for trial in range(40):
+        qa = np.concatenate([rng.uniform(-0.02, 0.02, 3), S.random_quats(rng, 1)[0]])
+        qb = np.concatenate([rng.uniform(-0.02, 0.02, 3) + rng.standard_normal(3) / 6, S.random_quats(rng, 1)[0]])
+        ga, gb = dict(type=ta, size=size[ta]), dict(type=tb, size=size[tb])
+        cs = _two_body_contact(oracle, ga, gb, qa, qb)
+        assert len(cs) == 1
+        c = cs[0]
+        if c["phi"] < 0.005:
+            continue
+        pa, pb = _surface_points(ga, qa, rng=rng), _surface_points(gb, qb, rng=rng)
+        from scipy.spatial import cKDTree
+        dist, _ = cKDTree(pb).query(pa)
+        assert c["phi"] <= dist.min() + 1e-9           # no pair of surface points is closer
+        assert c["phi"] >= dist.min() - 3e-3           # ... up to the sampling resolution
+        sa = c["pos"] + c["phi"] / 2 * c["normal"]     # surface point of A (n points from B to A)
+        sb = c["pos"] - c["phi"] / 2 * c["normal"]     # surface point of B
+        assert np.linalg.norm(sa - sb) == pytest.approx(c["phi"], rel=1e-12)
+        assert _inside(ga, qa, (sa + 1e-4 * c["normal"])[None])[0]
+        assert not _inside(ga, qa, (sa - 1e-4 * c["normal"])[None])[0]
+        assert _inside(gb, qb, (sb - 1e-4 * c["normal"])[None])[0]
+        assert not _inside(gb, qb, (sb + 1e-4 * c["normal"])[None])[0]
+        done += 1
+        if done >= 6:
+            break
+    assert done >= 3
+
+
+def test_box_plane_corners_and_capsule_plane_endpoints(oracle):
+    """Box-plane emits every corner below the margin; capsule-plane both end spheres."""
+    d = Wd.world([dict(mass=1.0), dict(mass=1.0)],
+                 [dict(type=S.PLANE, body=-1), dict(type=S.BOX, body=0, size=(0.03, 0.04, 0.05)),
+                  dict(type=S.CAPSULE, body=1, size=(0.02, 0.06, 0))])
+    tilt = S.quat_about((1, 0, 0), 0.3)
+    qa, _ = Wd.free_state((0, 0, 0.01), quat=tilt)
+    qb, _ = Wd.free_state((1.0, 0, 0.015), quat=S.quat_about((0, 1, 0), np.pi / 2 - 0.05))
+    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0)), DT, np.concatenate([qa, qb]), np.zeros(12))
+    box = [c for c in rec["contacts"] if c["body_a"] == 0]
+    caps = [c for c in rec["contacts"] if c["body_a"] == 1]
+    R = np.array(oracle.dynamics(d, (0, 0, 0), np.concatenate([qa, qb]), np.zeros(12))[2][0, 3:12]).reshape(3, 3)
+    corners = [np.array([0, 0, 0.01]) + R @ (np.array([sx, sy, sz]) * [0.03, 0.04, 0.05])
+               for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+    below = sorted(c[2] for c in corners if c[2] < 0)
+    assert sorted(c["phi"] for c in box) == pytest.approx(below, abs=1e-15)
+    assert len(caps) == 2
+    ends_z = sorted(0.015 + s * 0.06 * np.sin(0.05) for s in (-1, 1))
+    assert sorted(c["phi"] for c in caps) == pytest.approx([z - 0.02 for z in ends_z], abs=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# reference gradient: forward-mode duals against central differences
+# ------------------------------------------------------------------------------------------
+def test_dual_gradient_matches_finite_differences(oracle):
+    b = S.make_hand(2, seed=4)
+    d = b.world(0)
+    nv = len(b.v0[0])
+    T = 20
+    rng = np.random.default_rng(0)
+    tau = np.zeros((T, nv))
+    tau[:, 6:] = rng.normal(0, 0.05, (T, 16))
+    dv0 = np.zeros(nv)
+    dv0[6:] = rng.standard_normal(16)
+    dtau = np.zeros((T, nv))
+    dtau[:, 6:] = rng.standard_normal((T, 16))
+    tp, tq = np.array([0.0, 0.0, 0.05]), S.quat_about((0, 0, 1), 0.5)
+    args = lambda eps: (d, b.params, b.dt, b.q0[0], b.v0[0] + eps * dv0, tau + eps * dtau, np.zeros(len(b.q0[0])),
+                        dv0, dtau, 0, tp, tq)
+    L, dL = oracle.rollout_loss_dir(*args(0.0))
+    h = 1e-6
+    Lp, _ = oracle.rollout_loss_dir(*args(h))
+    Lm, _ = oracle.rollout_loss_dir(*args(-h))
+    assert dL == pytest.approx((Lp - Lm) / (2 * h), rel=1e-5, abs=1e-9)
