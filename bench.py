@@ -1,0 +1,317 @@
+"""Benchmark of the batched ComFree step on GB300.
+
+Workload (dense-contact scaling): 4096 walled bins, each with 256 free bodies (seeded 50/50
+sphere/capsule mix, density 1000), 6D cone with 8 tangential + 2 torsional + 8 rolling facets,
+mu = 0.8, dt = 2 ms, a 1000-step drop episode.  One bench "step" is one simulation step of all
+4096 worlds (one launch of the fused step kernel).  The timed K steps are the last K steps of
+the episode (the settled, densest part); the steps before them run untimed.  The same run also
+measures 16- and 64-body bins (4096 worlds each) for the contacts/world sweep.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank simulates its own 4096 worlds (weak
+scaling, no collective on the data path; the timing barrier and max use torch.distributed).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EPISODE = 1000
+WORLDS = 4096
+BODIES = 256
+SWEEP = (16, 64)
+BYTES_PER_BODY = (7 + 6) * 4 * 2 + 8 * 4   # q, v read + written, 8-float parameter block read
+METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--worlds", type=int, default=WORLDS)
+    ap.add_argument("--bodies", type=int, default=BODIES)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, max clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for n, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    n = int(os.environ.get("WORLD_SIZE", "1"))
+    if n > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist.get_rank(), n, local
+    return 0, 1, 0
+
+
+def barrier_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_pile(nbody, nworld, steps, warmup, rank, timed_events=True, flush=None):
+    """Simulate the episode; time the last `steps` steps with CUDA events on the launch stream,
+    flushing L2 (256 MB write) between timed steps outside the timed intervals."""
+    import torch
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import scenes as S
+    sb = S.make_pile(nworld, nbody, seed=1000 + rank)
+    model, b = CF.from_scenes(sb)
+    b.autotune(sb.dt)
+    stream = torch.cuda.current_stream()
+    preroll = max(warmup, EPISODE - steps)
+    for _ in range(preroll):
+        b.step(sb.dt, 1)
+    torch.cuda.synchronize()
+    counts = torch.zeros(nworld, dtype=torch.int32, device="cuda")
+    contact_sum = torch.zeros(nworld, dtype=torch.int64, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.add_(1.0)
+        ev[i][0].record(stream)
+        b.step(sb.dt, 1)
+        ev[i][1].record(stream)
+        b.contact_counts_device(counts)
+        contact_sum += counts
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(c) for a, c in ev]
+    st, _ = b.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the episode")
+    return dict(ms=float(np.sum(times)), per_launch_ms=float(np.mean(times)), steps=steps, preroll=preroll,
+                contacts=int(contact_sum.sum().item()), worlds=nworld, bodies=nbody, sb=sb, batch=b, model=model)
+
+
+def run_e2e(res, steps):
+    """Same workload through the C ABI with pinned host buffers: per step the state goes
+    host -> device, one step, device -> host (the copies are inside the timed region)."""
+    import torch
+    b = res["batch"]
+    q, v = b.get_state()
+    hq = torch.empty(b.total_nq, dtype=torch.float32, pin_memory=True)
+    hv = torch.empty(b.total_nv, dtype=torch.float32, pin_memory=True)
+    hq.copy_(q.cpu())
+    hv.copy_(v.cpu())
+    dt = res["sb"].dt
+    # warm-up
+    b.set_state(hq, hv)
+    b.step(dt, 1)
+    b.get_state(hq, hv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.set_state(hq, hv)          # host -> device (synchronous copy of pinned buffers)
+        b.step(dt, 1)
+        b.get_state(hq, hv)          # device -> host, synchronises and checks device status
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nbytes = (b.total_nq + b.total_nv) * 4
+    return dict(value=res["worlds"] * steps / sec, h2d=nbytes, d2h=nbytes)
+
+
+def cpu_baseline(nbody, rank, budget_s=20.0, reference=False):
+    """The FP64 oracle as it stands, OpenMP over the host cores, on a bounded sample: the first
+    worlds of the same seeded workload, from their initial state."""
+    from oracle import oracle as O
+    from paper_2603_12185_gb300 import scenes as S
+    nw = 16
+    sb = S.make_pile(nw, nbody, seed=1000 + rank)
+    runner = O.BatchRunner([sb.world(w) for w in range(nw)], sb.params)
+    q = np.concatenate([np.asarray(x, np.float64) for x in sb.q0])
+    v = np.concatenate([np.asarray(x, np.float64) for x in sb.v0])
+    cores = O.max_threads()
+    steps, done, t_total, contacts = 2, 0, 0.0, 0
+    while t_total < budget_s:
+        t0 = time.perf_counter()
+        c = runner.run(q, v, sb.dt, steps)
+        t_total += time.perf_counter() - t0
+        done += steps
+        contacts += int(c.sum())
+        if t_total < budget_s / 4:
+            steps *= 2
+    ws = nw * done / t_total
+    return dict(value=ws, unit="world-steps/s", cores=cores, kind="oracle",
+                sample=f"{nw} worlds x {nbody} bodies of the same seeded workload, steps 1..{done} of the episode "
+                       f"from the initial state (FP64, {cores} OpenMP threads, {t_total:.1f} s)",
+                contacts_per_s=contacts / t_total, seconds=t_total, steps=done)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+        cb = cpu_baseline(args.bodies, 0, budget_s=max(10.0, min(60.0, 3.0 * (args.steps + args.warmup))),
+                          reference=True)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "world-steps/s",
+                "n_gpus": args.gpus, "steps": cb["steps"], "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / cb["steps"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"pile_{args.worlds}x{args.bodies}", "worlds_sampled": 16,
+                           "bodies_per_world": args.bodies},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "world-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2603_12185_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    # sweep: smaller bins first (each also a warm-up of the library)
+    sweep = {}
+    if not args.no_sweep:
+        for n in SWEEP:
+            r = run_pile(n, args.worlds, min(args.steps, 100), args.warmup, rank, flush=flush)
+            sec = barrier_max(r["ms"] / 1e3, world)
+            sweep[str(n)] = {"world_steps_per_s": world * r["worlds"] * r["steps"] / sec,
+                             "contacts_per_s": barrier_sum(r["contacts"], world) / sec,
+                             "contacts_per_world": r["contacts"] / (r["worlds"] * r["steps"]),
+                             "ms_per_step": 1e3 * sec / r["steps"]}
+            del r
+
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    res = run_pile(args.bodies, args.worlds, args.steps, args.warmup, rank, flush=flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = barrier_max(res["ms"] / 1e3, world)
+    total_contacts = barrier_sum(res["contacts"], world)
+    value = world * res["worlds"] * res["steps"] / sec
+    e2e = run_e2e(res, args.e2e_steps)
+    e2e_v = barrier_sum(e2e["value"], world) if world > 1 else e2e["value"]
+
+    pk, src = peaks()
+    launch_s = res["per_launch_ms"] / 1e3
+    alg_bytes = res["worlds"] * res["bodies"] * BYTES_PER_BODY
+    achieved = alg_bytes / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk and src,
+                "kernel": "cf::step_kernel", "algorithmic_bytes_per_launch": alg_bytes}
+    line = {"metric": METRIC, "value": value, "unit": "world-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec / res["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"pile_{res['worlds']}x{res['bodies']}", "worlds_per_gpu": res["worlds"],
+                       "bodies_per_world": res["bodies"], "facets_per_contact": 18, "dt": 0.002,
+                       "episode_steps": EPISODE, "timed_steps": f"last {res['steps']} of the episode",
+                       "preroll_untimed": res["preroll"], "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "contacts_per_s": total_contacts / sec,
+            "contacts_per_world": res["contacts"] / (res["worlds"] * res["steps"]),
+            "sweep_bodies": sweep,
+            "roofline": roofline,
+            "e2e": {"value": e2e_v, "unit": "world-steps/s", "h2d_bytes_per_step": e2e["h2d"],
+                    "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": res["steps"],
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(args.bodies, rank)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

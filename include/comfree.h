@@ -1,0 +1,204 @@
+/*
+ * comfree.h -- C ABI of libcomfree, the GB300 (sm_103a) batched ComFree contact step.
+ *
+ * The library advances thousands of independent rigid-body worlds with the
+ * complementarity-free contact model of ComFree-Sim (arxiv 2603.12185): a contact-free
+ * velocity prediction (Eq. smooth_vel), closed-form impulses on the facets of the polyhedral
+ * dual friction cone (Eqs. dual_polyhedral, tilde_defs, cf_wrench) with the heuristic
+ * impedance (Eqs. k_d_setting, r_scaling), the J~^T lambda scatter and M^-1 correction
+ * (Eq. vel_correction, Algorithm 1 Kernels I-IV), followed by semi-implicit integration.
+ *
+ * Conventions
+ *   - Ownership: model and batch handles belong to the library (create/destroy pairs).  All
+ *     device memory belongs to the caller: cf_batch_create receives a caller-allocated device
+ *     workspace (e.g. a torch uint8 tensor) and the library never calls cudaMalloc for it.
+ *     Pointers passed to a call are borrowed for the duration of that call only.
+ *   - Precision: state, controls and model quantities are FP32 on the device; the model
+ *     description is read in FP64 on the host and rounded once.
+ *   - State layout: world-major and contiguous.  World w owns nq(scene) floats of q and
+ *     nv(scene) floats of v, in world order.  Per body: a free body holds q = (x, y, z, qw, qx,
+ *     qy, qz) and v = (world linear velocity, body-frame angular velocity); a hinge holds its
+ *     angle and rate.  Bodies appear in scene order.
+ *   - Streams: every device operation is enqueued on the stream passed in (a cudaStream_t
+ *     handed over as void*; NULL = legacy default stream).  Host-pointer variants synchronise
+ *     that stream before returning.
+ *   - Errors: no exception crosses the ABI; every call returns a cf_status.  cf_last_error()
+ *     gives a thread-local human-readable message for the most recent failure.  Device-side
+ *     conditions (non-finite state, contact-capture overflow, a bounded wait that gave up) are
+ *     latched into per-world flags and an error word in the workspace and reported by the next
+ *     call that synchronises (cf_batch_status, cf_get_state with host buffers).
+ */
+#ifndef COMFREE_H
+#define COMFREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CF_OK = 0,
+  CF_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, index or description            */
+  CF_ERR_OUT_OF_MEMORY = 2,    /* host allocation failed / workspace too small        */
+  CF_ERR_CUDA = 3,             /* a CUDA runtime call failed (message in cf_last_error) */
+  CF_ERR_CONTACT_OVERFLOW = 4, /* contact capture buffer full for some world          */
+  CF_ERR_NONFINITE = 5,        /* a world produced a NaN/Inf state                    */
+  CF_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                       */
+  CF_ERR_UNSUPPORTED = 7       /* a valid but unsupported request                     */
+} cf_status;
+
+/* per-world flag bits (cf_batch_status) */
+#define CF_FLAG_NONFINITE 1
+#define CF_FLAG_CONTACT_OVERFLOW 2
+#define CF_FLAG_TIMEOUT 4
+
+/* geom and joint kinds */
+#define CF_GEOM_PLANE 0   /* static only; the plane through pos with normal = local +z   */
+#define CF_GEOM_SPHERE 1  /* size[0] = radius                                           */
+#define CF_GEOM_CAPSULE 2 /* size[0] = radius, size[1] = half length along local z      */
+#define CF_GEOM_BOX 3     /* size = half extents                                        */
+#define CF_JOINT_FREE 0
+#define CF_JOINT_HINGE 1
+
+typedef struct cf_model cf_model;
+typedef struct cf_batch cf_batch;
+
+/* One scene template.  Bodies form a forest in topological order (parent < child): either a
+ * free body with no children (its body frame at its centre of mass), or a fixed-base tree of
+ * hinges whose bodies are contiguous.  Arrays are host pointers, FP64, read during
+ * cf_model_create only.  `pile` != 0 declares the layout "body i is free and carries geom i at
+ * its origin; geoms nbody.. are static planes"; only such scenes accept per-world overrides. */
+typedef struct {
+  int32_t nbody, ngeom;
+  const int32_t* body_parent;   /* [nbody] parent body or -1                              */
+  const int32_t* body_jnt;      /* [nbody] CF_JOINT_*                                     */
+  const double* body_pos;       /* [nbody][3] hinge frame origin in the parent frame      */
+  const double* body_quat;      /* [nbody][4] hinge frame orientation in the parent frame */
+  const double* body_axis;      /* [nbody][3] hinge axis in the body frame                */
+  const double* body_ipos;      /* [nbody][3] centre of mass in the body frame            */
+  const double* body_mass;      /* [nbody]                                                */
+  const double* body_inertia;   /* [nbody][3] principal inertia about the centre of mass  */
+  const double* body_damping;   /* [nbody] hinge damping (implicit)                       */
+  const int32_t* geom_type;     /* [ngeom] CF_GEOM_*                                      */
+  const int32_t* geom_body;     /* [ngeom] body or -1 (static)                            */
+  const double* geom_pos;       /* [ngeom][3] in the body frame (world if static)         */
+  const double* geom_quat;      /* [ngeom][4]                                             */
+  const double* geom_size;      /* [ngeom][3]                                             */
+  const double* geom_mu;        /* [ngeom][3] tangential, torsional, rolling coefficients */
+  int32_t pile;
+} cf_scene_desc;
+
+/* Global model parameters (one set per model). */
+typedef struct {
+  int32_t nscene;
+  const cf_scene_desc* scenes;
+  double gravity[3];
+  double k_user, d_user;   /* Eq. k_d_setting global impedance                           */
+  double solimp[5];        /* Eq. r_scaling (r_min, r_max, width, midpoint, power)        */
+  double margin;           /* contact when the signed gap phi < margin                   */
+  int32_t n_t, n_tor, n_rol; /* facets per subspace (Eq. tilde_defs); n_tor in {0, 2},
+                                n_t and n_rol in {0, 2..16} (symmetric unit directions)  */
+  int32_t trace_mode;      /* 0: M(phi) with tr(J_i M~^-1 J_i^T) of body i's translational
+                              point Jacobian; 1: 1/m_i per body                         */
+} cf_model_desc;
+
+/* Validate a description and build the host model.  Errors: CF_ERR_INVALID_ARGUMENT for a
+ * malformed description (index out of range, non-topological parents, non-positive mass or
+ * inertia, a plane attached to a body, bad facet counts), CF_ERR_UNSUPPORTED for structures
+ * outside the forest rules above, CF_ERR_OUT_OF_MEMORY. */
+cf_status cf_model_create(const cf_model_desc* desc, cf_model** out);
+void cf_model_destroy(cf_model* model);
+
+/* per-model sizes of one scene: nq, nv, nu (actuated hinge DoFs), nbody, ngeom */
+cf_status cf_scene_sizes(const cf_model* model, int32_t scene, int32_t sizes[5]);
+
+/* Batch options. */
+typedef struct {
+  int32_t max_ctrl_steps;  /* capacity T of the control sequence [T][sum nu] (>= 1)       */
+  int32_t contact_capture; /* per-world capacity of the contact record buffer (0 = off)   */
+  int32_t grad_steps;      /* capacity (steps) of the adjoint tape; 0 = no cf_step_grad    */
+  int32_t grad_ckpt;       /* checkpoint interval of the adjoint (>= 1)                   */
+} cf_batch_opts;
+
+/* Device bytes the caller must provide for a batch of n_worlds worlds whose scene indices are
+ * scene_of_world[n_worlds] (host).  world_params may be NULL for the size query. */
+cf_status cf_batch_workspace_bytes(const cf_model* model, int32_t n_worlds, const int32_t* scene_of_world,
+                                   const cf_batch_opts* opts, size_t* bytes);
+
+/* Create a batch inside the caller's device workspace (at least cf_batch_workspace_bytes,
+ * 256-byte aligned).  world_params (host, nullable) holds, in world order, one block of 8
+ * floats per body for every world of a pile scene: mass, I1, I2, I3, geom type (sphere or
+ * capsule), size0, size1, size2; worlds of other scenes contribute nothing.  NULL keeps the
+ * scene defaults.  The initial state is the scene's zero state (identity poses) until
+ * cf_set_state.  The workspace must outlive the batch.  Synchronises `stream`. */
+cf_status cf_batch_create(const cf_model* model, int32_t n_worlds, const int32_t* scene_of_world,
+                          const float* world_params, const cf_batch_opts* opts, void* device_workspace,
+                          size_t workspace_bytes, void* stream, cf_batch** out);
+void cf_batch_destroy(cf_batch* batch);
+
+/* total floats of q, v and actuated controls over all worlds */
+cf_status cf_batch_sizes(const cf_batch* batch, int64_t* total_nq, int64_t* total_nv, int64_t* total_nu);
+
+/* Copy the full state in (set) or out (get).  q[total_nq], v[total_nv]; on_device != 0 means
+ * device pointers (asynchronous on `stream`), else host pointers (the call synchronises and,
+ * for get, reports latched device errors). */
+cf_status cf_set_state(cf_batch* batch, const float* q, const float* v, int32_t on_device, void* stream);
+cf_status cf_get_state(const cf_batch* batch, float* q, float* v, int32_t on_device, void* stream);
+
+/* Control sequence: tau[T][total_nu] generalised forces of the actuated hinges (world order,
+ * then hinge order), 1 <= T <= max_ctrl_steps.  Step s of a cf_step call uses slice
+ * min(s, T - 1); free bodies are unactuated. */
+cf_status cf_set_ctrl(cf_batch* batch, const float* tau, int32_t T, int32_t on_device, void* stream);
+
+/* Advance worlds nsteps steps of length dt (one launch; the state stays on chip across the
+ * nsteps).  worlds: NULL = all, else a host list of n distinct world indices.  Errors:
+ * CF_ERR_INVALID_ARGUMENT (dt <= 0, nsteps < 1, bad index), CF_ERR_CUDA (launch failure). */
+cf_status cf_step(cf_batch* batch, const int32_t* worlds, int32_t n, float dt, int32_t nsteps, void* stream);
+
+/* Per-world number of contacts (phi < margin) detected in the last step of the last cf_step,
+ * counts[n_worlds] (device or host per on_device). */
+cf_status cf_get_contact_counts(const cf_batch* batch, int32_t* counts, int32_t on_device, void* stream);
+
+/* One captured contact (contact_capture > 0): geoms (a, b) with a the geom the normal points
+ * to, sub = contact index within the pair (capsule end / box corner), phi, point, normal,
+ * the summed facet impulse (lambda dt) and M(phi). */
+typedef struct {
+  int32_t geom_a, geom_b, sub, pad;
+  float phi, pos[3], normal[3], lam_sum, mphi, pad2[3];
+} cf_contact;
+
+/* Copy the contacts captured in the last step: out[n_worlds][capacity], counts[n_worlds]
+ * (host).  Order within a world is unspecified.  CF_ERR_CONTACT_OVERFLOW if a world had more
+ * contacts than the capacity (the first `capacity` are kept).  Synchronises. */
+cf_status cf_get_contacts(const cf_batch* batch, cf_contact* out, int32_t* counts, void* stream);
+
+/* Synchronise and report the latched device error word; flags[n_worlds] (host, nullable)
+ * receives the per-world CF_FLAG_* bits.  clear != 0 resets them. */
+cf_status cf_batch_status(cf_batch* batch, int32_t* flags, int32_t clear, void* stream);
+
+/* Pick warps-per-world for every scene class of the batch by timing candidate launch shapes
+ * on the batch itself (the state is saved and restored).  chosen[nscene] (host, nullable)
+ * receives the warps per world.  Synchronises. */
+cf_status cf_batch_autotune(cf_batch* batch, float dt, void* stream, int32_t* chosen);
+/* Set warps-per-world of one scene class explicitly (1, 2, 4 or 8). */
+cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
+
+/* Reverse-mode gradient of a T-step rollout from the current state with the current control
+ * sequence (T <= min(grad_steps, max_ctrl_steps); step s uses control slice s).  Given the
+ * cotangents of the final state dL_dqT[total_nq], dL_dvT[total_nv] (device), writes
+ * dL_dq0[total_nq], dL_dv0[total_nv] and dL_dtau[T][total_nu] (device).  The forward state is
+ * recomputed from checkpoints every grad_ckpt steps.  The batch state is left at the rollout's
+ * final state.  Errors: CF_ERR_UNSUPPORTED for scenes outside the differentiable set (hinge
+ * trees and free bodies with sphere/capsule/box/plane geoms), CF_ERR_INVALID_ARGUMENT. */
+cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
+                       float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);
+
+const char* cf_status_string(cf_status status);
+const char* cf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COMFREE_H */

@@ -105,7 +105,7 @@ typedef struct {
 
 /* one detected contact, for tests */
 typedef struct {
-  int geom_a, geom_b, body_a, body_b;
+  int geom_a, geom_b, body_a, body_b, sub;
   double phi, pos[3], normal[3], t1[3], t2[3];
   double trace_a, trace_b, r, mphi;
   double lam_sum;        /* sum of facet impulses (lambda dt)              */
@@ -453,7 +453,7 @@ static void solve_all(const Structure& st, const std::vector<std::vector<S>>& L,
  * penetration); the contact point is the midpoint of the two surface points.
  * ---------------------------------------------------------------------------------------- */
 template <class S> struct GeomPose { V3<S> c; M3<S> R; };
-template <class S> struct RawContact { S phi; V3<S> p, n; };
+template <class S> struct RawContact { S phi; V3<S> p, n; int sub = 0; };
 
 template <class S>
 static void sphere_sphere(const V3<S>& ca, S ra, const V3<S>& cb, S rb, std::vector<RawContact<S>>& out) {
@@ -791,6 +791,7 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
       } else {
         continue; /* box-box: not a supported pair */
       }
+      for (size_t ri = 0; ri < raw.size(); ++ri) raw[ri].sub = (int)ri;
       for (RawContact<S>& k : raw) {
         if (!(val(k.phi) < margin)) continue;
         int ba = w->geom_body[ga], bb = w->geom_body[gb];
@@ -874,7 +875,7 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           facet(2, S(std::cos(th)), S(std::sin(th)));
         }
         if (rec) {
-          rc.geom_a = ga; rc.geom_b = gb; rc.body_a = ba; rc.body_b = bb;
+          rc.geom_a = ga; rc.geom_b = gb; rc.body_a = ba; rc.body_b = bb; rc.sub = k.sub;
           rc.phi = val(k.phi);
           rc.pos[0] = val(k.p.x); rc.pos[1] = val(k.p.y); rc.pos[2] = val(k.p.z);
           rc.normal[0] = val(k.n.x); rc.normal[1] = val(k.n.y); rc.normal[2] = val(k.n.z);

@@ -50,7 +50,7 @@ class OParams(C.Structure):
 
 class OContact(C.Structure):
     _fields_ = [("geom_a", C.c_int), ("geom_b", C.c_int), ("body_a", C.c_int), ("body_b", C.c_int),
-                ("phi", C.c_double), ("pos", C.c_double * 3), ("normal", C.c_double * 3),
+                ("sub", C.c_int), ("phi", C.c_double), ("pos", C.c_double * 3), ("normal", C.c_double * 3),
                 ("t1", C.c_double * 3), ("t2", C.c_double * 3), ("trace_a", C.c_double),
                 ("trace_b", C.c_double), ("r", C.c_double), ("mphi", C.c_double), ("lam_sum", C.c_double),
                 ("wrench", C.c_double * 6), ("nfacet", C.c_int), ("nactive", C.c_int)]
@@ -149,7 +149,7 @@ def step_record(desc, params, dt, q, v, tau=None, cap=20000):
     contacts = []
     for i in range(min(n.value, cap)):
         k = cs[i]
-        contacts.append(dict(geom_a=k.geom_a, geom_b=k.geom_b, body_a=k.body_a, body_b=k.body_b, phi=k.phi,
+        contacts.append(dict(geom_a=k.geom_a, geom_b=k.geom_b, body_a=k.body_a, body_b=k.body_b, sub=k.sub, phi=k.phi,
                              pos=np.array(k.pos[:]), normal=np.array(k.normal[:]), t1=np.array(k.t1[:]),
                              t2=np.array(k.t2[:]), trace_a=k.trace_a, trace_b=k.trace_b, r=k.r, mphi=k.mphi,
                              lam_sum=k.lam_sum, wrench=np.array(k.wrench[:]), nfacet=k.nfacet,

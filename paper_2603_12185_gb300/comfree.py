@@ -1,0 +1,287 @@
+"""Thin Python binding of libcomfree (include/comfree.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels; PyTorch provides the device
+memory (the batch workspace and state tensors) and the stream.  There is no CPU fallback:
+loading fails loudly when libcomfree.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcomfree.so")
+
+CF_OK = 0
+STATUS = {0: "CF_OK", 1: "CF_ERR_INVALID_ARGUMENT", 2: "CF_ERR_OUT_OF_MEMORY", 3: "CF_ERR_CUDA",
+          4: "CF_ERR_CONTACT_OVERFLOW", 5: "CF_ERR_NONFINITE", 6: "CF_ERR_TIMEOUT", 7: "CF_ERR_UNSUPPORTED"}
+
+
+class CfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("nbody", C.c_int32), ("ngeom", C.c_int32)] + [
+        (n, C.c_void_p) for n in ("body_parent", "body_jnt", "body_pos", "body_quat", "body_axis", "body_ipos",
+                                  "body_mass", "body_inertia", "body_damping", "geom_type", "geom_body", "geom_pos",
+                                  "geom_quat", "geom_size", "geom_mu")] + [("pile", C.c_int32)]
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("nscene", C.c_int32), ("scenes", C.POINTER(SceneDesc)), ("gravity", C.c_double * 3),
+                ("k_user", C.c_double), ("d_user", C.c_double), ("solimp", C.c_double * 5), ("margin", C.c_double),
+                ("n_t", C.c_int32), ("n_tor", C.c_int32), ("n_rol", C.c_int32), ("trace_mode", C.c_int32)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("max_ctrl_steps", C.c_int32), ("contact_capture", C.c_int32), ("grad_steps", C.c_int32),
+                ("grad_ckpt", C.c_int32)]
+
+
+class Contact(C.Structure):
+    _fields_ = [("geom_a", C.c_int32), ("geom_b", C.c_int32), ("sub", C.c_int32), ("pad", C.c_int32),
+                ("phi", C.c_float), ("pos", C.c_float * 3), ("normal", C.c_float * 3), ("lam_sum", C.c_float),
+                ("mphi", C.c_float), ("pad2", C.c_float * 3)]
+
+
+EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_workspace_bytes", "cf_batch_create",
+           "cf_batch_destroy", "cf_batch_sizes", "cf_set_state", "cf_get_state", "cf_set_ctrl", "cf_step",
+           "cf_get_contact_counts", "cf_get_contacts", "cf_batch_status", "cf_batch_autotune", "cf_batch_set_warps",
+           "cf_step_grad", "cf_status_string", "cf_last_error")
+
+_lib = None
+
+
+def lib():
+    """Load libcomfree.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2603_12185_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    P, V, I32, I64 = C.POINTER, C.c_void_p, C.c_int32, C.c_int64
+    L.cf_model_create.argtypes = [P(ModelDesc), P(V)]
+    L.cf_model_destroy.argtypes = [V]
+    L.cf_model_destroy.restype = None
+    L.cf_scene_sizes.argtypes = [V, I32, P(I32)]
+    L.cf_batch_workspace_bytes.argtypes = [V, I32, V, P(BatchOpts), P(C.c_size_t)]
+    L.cf_batch_create.argtypes = [V, I32, V, V, P(BatchOpts), V, C.c_size_t, V, P(V)]
+    L.cf_batch_destroy.argtypes = [V]
+    L.cf_batch_destroy.restype = None
+    L.cf_batch_sizes.argtypes = [V, P(I64), P(I64), P(I64)]
+    L.cf_set_state.argtypes = [V, V, V, I32, V]
+    L.cf_get_state.argtypes = [V, V, V, I32, V]
+    L.cf_set_ctrl.argtypes = [V, V, I32, I32, V]
+    L.cf_step.argtypes = [V, V, I32, C.c_float, I32, V]
+    L.cf_get_contact_counts.argtypes = [V, V, I32, V]
+    L.cf_get_contacts.argtypes = [V, V, V, V]
+    L.cf_batch_status.argtypes = [V, V, I32, V]
+    L.cf_batch_autotune.argtypes = [V, C.c_float, V, V]
+    L.cf_batch_set_warps.argtypes = [V, I32, I32]
+    L.cf_step_grad.argtypes = [V, I32, C.c_float, V, V, V, V, V, V]
+    L.cf_status_string.argtypes = [I32]
+    L.cf_status_string.restype = C.c_char_p
+    L.cf_last_error.argtypes = []
+    L.cf_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != CF_OK:
+        raise CfError(status, lib().cf_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(C.c_void_p)
+
+
+class Model:
+    """A validated model built from scene templates (scenes.Template) and parameters (scenes.Params)."""
+
+    _INT = ("body_parent", "body_jnt", "geom_type", "geom_body")
+
+    def __init__(self, templates, params):
+        keep = []
+        descs = (SceneDesc * len(templates))()
+        for i, t in enumerate(templates):
+            arrs = {}
+            for name, _ in SceneDesc._fields_[2:-1]:
+                a = np.ascontiguousarray(getattr(t, name), dtype=np.int32 if name in self._INT else np.float64)
+                arrs[name] = a
+                keep.append(a)
+            descs[i] = SceneDesc(len(t.body_parent), len(t.geom_type),
+                                 *[_ptr(arrs[n]) for n, _ in SceneDesc._fields_[2:-1]], int(bool(t.pile)))
+        d = ModelDesc()
+        d.nscene = len(templates)
+        d.scenes = descs
+        d.gravity[:] = list(params.gravity)
+        d.k_user, d.d_user = params.k_user, params.d_user
+        d.solimp[:] = list(params.solimp)
+        d.margin = params.margin
+        d.n_t, d.n_tor, d.n_rol, d.trace_mode = params.n_t, params.n_tor, params.n_rol, params.trace_mode
+        h = C.c_void_p()
+        check(lib().cf_model_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.templates = templates
+        self.params = params
+
+    def scene_sizes(self, scene):
+        s = (C.c_int32 * 5)()
+        check(lib().cf_scene_sizes(self.h, scene, s))
+        return dict(nq=s[0], nv=s[1], nu=s[2], nbody=s[3], ngeom=s[4])
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cf_model_destroy(self.h)
+            self.h = None
+
+
+class Batch:
+    """W worlds stepped on the GPU inside a caller-owned (torch) device workspace."""
+
+    def __init__(self, model, scene_of_world, world_params=None, max_ctrl_steps=1, contact_capture=0, grad_steps=0,
+                 grad_ckpt=10, device="cuda", stream=None):
+        self.model = model
+        self.scene_of_world = np.ascontiguousarray(scene_of_world, dtype=np.int32)
+        self.W = len(self.scene_of_world)
+        self.opts = BatchOpts(max_ctrl_steps, contact_capture, grad_steps, grad_ckpt)
+        nbytes = C.c_size_t()
+        check(lib().cf_batch_workspace_bytes(model.h, self.W, _ptr(self.scene_of_world), C.byref(self.opts),
+                                             C.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=device)
+        off = (-self.workspace.data_ptr()) % 256
+        self.ws_ptr = self.workspace.data_ptr() + off
+        wp = None if world_params is None else np.ascontiguousarray(world_params, dtype=np.float32)
+        h = C.c_void_p()
+        check(lib().cf_batch_create(model.h, self.W, _ptr(self.scene_of_world), _ptr(wp), C.byref(self.opts),
+                                    C.c_void_p(self.ws_ptr), nbytes.value, _stream(stream), C.byref(h)))
+        self.h = h
+        nq, nv, nu = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().cf_batch_sizes(h, C.byref(nq), C.byref(nv), C.byref(nu)))
+        self.total_nq, self.total_nv, self.total_nu = nq.value, nv.value, nu.value
+        self.device = device
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cf_batch_destroy(self.h)
+            self.h = None
+
+    # ---- state ----
+    def set_state(self, q, v, stream=None):
+        on_dev = isinstance(q, torch.Tensor) and q.is_cuda
+        if on_dev:
+            q = q.contiguous().float()
+            v = v.contiguous().float()
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float32)
+            v = np.ascontiguousarray(v, dtype=np.float32)
+        assert (q.numel() if on_dev else q.size) == self.total_nq
+        check(lib().cf_set_state(self.h, _ptr(q), _ptr(v), int(on_dev), _stream(stream)))
+
+    def get_state(self, out_q=None, out_v=None, stream=None):
+        """Device tensors by default; host numpy arrays when the outputs given are numpy/pinned CPU."""
+        if out_q is None:
+            out_q = torch.empty(self.total_nq, dtype=torch.float32, device=self.device)
+            out_v = torch.empty(self.total_nv, dtype=torch.float32, device=self.device)
+        on_dev = isinstance(out_q, torch.Tensor) and out_q.is_cuda
+        check(lib().cf_get_state(self.h, _ptr(out_q), _ptr(out_v), int(on_dev), _stream(stream)))
+        return out_q, out_v
+
+    def set_ctrl(self, tau, stream=None):
+        on_dev = isinstance(tau, torch.Tensor) and tau.is_cuda
+        if on_dev:
+            tau = tau.contiguous().float()
+            T = tau.numel() // max(self.total_nu, 1)
+        else:
+            tau = np.ascontiguousarray(tau, dtype=np.float32)
+            T = tau.size // max(self.total_nu, 1)
+        check(lib().cf_set_ctrl(self.h, _ptr(tau), T, int(on_dev), _stream(stream)))
+
+    def step(self, dt, nsteps=1, worlds=None, stream=None):
+        wl = None if worlds is None else np.ascontiguousarray(worlds, dtype=np.int32)
+        check(lib().cf_step(self.h, _ptr(wl), 0 if wl is None else len(wl), float(dt), int(nsteps), _stream(stream)))
+
+    def contact_counts(self, stream=None):
+        out = np.zeros(self.W, np.int32)
+        check(lib().cf_get_contact_counts(self.h, _ptr(out), 0, _stream(stream)))
+        return out
+
+    def contact_counts_device(self, out, stream=None):
+        check(lib().cf_get_contact_counts(self.h, _ptr(out), 1, _stream(stream)))
+        return out
+
+    def contacts(self, stream=None):
+        """List (per world) of captured contacts as dicts (needs contact_capture > 0)."""
+        cap = self.opts.contact_capture
+        buf = (Contact * (self.W * cap))()
+        counts = np.zeros(self.W, np.int32)
+        check(lib().cf_get_contacts(self.h, buf, _ptr(counts), _stream(stream)))
+        out = []
+        for w in range(self.W):
+            lst = []
+            for i in range(counts[w]):
+                c = buf[w * cap + i]
+                lst.append(dict(geom_a=c.geom_a, geom_b=c.geom_b, sub=c.sub, phi=c.phi, pos=np.array(c.pos[:]),
+                                normal=np.array(c.normal[:]), lam_sum=c.lam_sum, mphi=c.mphi))
+            out.append(lst)
+        return out
+
+    def status(self, clear=False, stream=None):
+        flags = np.zeros(self.W, np.int32)
+        st = lib().cf_batch_status(self.h, _ptr(flags), int(clear), _stream(stream))
+        return st, flags
+
+    def autotune(self, dt, stream=None):
+        chosen = np.zeros(len(self.model.templates), np.int32)
+        check(lib().cf_batch_autotune(self.h, float(dt), _stream(stream), _ptr(chosen)))
+        return chosen
+
+    def set_warps(self, scene, warps):
+        check(lib().cf_batch_set_warps(self.h, int(scene), int(warps)))
+
+    def step_grad(self, T, dt, dqT, dvT, stream=None):
+        dq0 = torch.empty(self.total_nq, dtype=torch.float32, device=self.device)
+        dv0 = torch.empty(self.total_nv, dtype=torch.float32, device=self.device)
+        dtau = torch.zeros(max(T * self.total_nu, 1), dtype=torch.float32, device=self.device)
+        check(lib().cf_step_grad(self.h, int(T), float(dt), _ptr(dqT.contiguous()), _ptr(dvT.contiguous()), _ptr(dq0),
+                                 _ptr(dv0), _ptr(dtau), _stream(stream)))
+        return dq0, dv0, dtau[:T * self.total_nu].view(T, self.total_nu) if self.total_nu else dtau[:0]
+
+
+def flatten_state(sb):
+    """Concatenated (q, v) of a scenes.Batch in world order (float32)."""
+    return (np.concatenate([np.asarray(q, np.float32) for q in sb.q0]),
+            np.concatenate([np.asarray(v, np.float32) for v in sb.v0]))
+
+
+def flatten_params(sb):
+    blocks = [p for p in sb.world_param if p is not None]
+    if not blocks:
+        return None
+    return np.concatenate([np.asarray(p, np.float32).reshape(-1) for p in blocks])
+
+
+def from_scenes(sb, **opts):
+    """(Model, Batch) for a scenes.Batch with its initial state uploaded."""
+    m = Model(sb.templates, sb.params)
+    b = Batch(m, sb.world_scene, flatten_params(sb), **opts)
+    q, v = flatten_state(sb)
+    b.set_state(torch.from_numpy(q).cuda(), torch.from_numpy(v).cuda())
+    return m, b

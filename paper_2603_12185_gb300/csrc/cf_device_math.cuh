@@ -1,0 +1,337 @@
+// Device math shared by the step and adjoint kernels: vectors, rotations, narrowphase,
+// contact frame, the solimp gap scaling and the closed-form facet impulses.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cf_internal.cuh"
+
+namespace cf {
+
+struct f3 {
+  float x, y, z;
+};
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float norm3(f3 a) { return sqrtf(dot(a, a)); }
+
+// 3x3 rotation, row major
+struct M33 {
+  float m[9];
+};
+__device__ __forceinline__ f3 mul(const M33& R, f3 v) {
+  return {R.m[0] * v.x + R.m[1] * v.y + R.m[2] * v.z, R.m[3] * v.x + R.m[4] * v.y + R.m[5] * v.z,
+          R.m[6] * v.x + R.m[7] * v.y + R.m[8] * v.z};
+}
+__device__ __forceinline__ f3 mulT(const M33& R, f3 v) {
+  return {R.m[0] * v.x + R.m[3] * v.y + R.m[6] * v.z, R.m[1] * v.x + R.m[4] * v.y + R.m[7] * v.z,
+          R.m[2] * v.x + R.m[5] * v.y + R.m[8] * v.z};
+}
+__device__ __forceinline__ f3 col(const M33& R, int j) { return {R.m[j], R.m[3 + j], R.m[6 + j]}; }
+__device__ __forceinline__ M33 mul33(const M33& a, const M33& b) {
+  M33 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r.m[3 * i + j] = a.m[3 * i] * b.m[j] + a.m[3 * i + 1] * b.m[3 + j] + a.m[3 * i + 2] * b.m[6 + j];
+  return r;
+}
+// rotation matrix of the (re-normalised) quaternion (w, x, y, z)
+__device__ __forceinline__ M33 quat_mat(float w, float x, float y, float z) {
+  float s = rsqrtf(w * w + x * x + y * y + z * z);
+  w *= s; x *= s; y *= s; z *= s;
+  M33 r;
+  r.m[0] = 1.f - 2.f * (y * y + z * z); r.m[1] = 2.f * (x * y - w * z); r.m[2] = 2.f * (x * z + w * y);
+  r.m[3] = 2.f * (x * y + w * z); r.m[4] = 1.f - 2.f * (x * x + z * z); r.m[5] = 2.f * (y * z - w * x);
+  r.m[6] = 2.f * (x * z - w * y); r.m[7] = 2.f * (y * z + w * x); r.m[8] = 1.f - 2.f * (x * x + y * y);
+  return r;
+}
+// rotation by angle th about the unit axis a (Rodrigues)
+__device__ __forceinline__ M33 axis_rot(f3 a, float th) {
+  float s, c;
+  sincosf(th, &s, &c);
+  float t = 1.f - c;
+  M33 r;
+  r.m[0] = t * a.x * a.x + c; r.m[1] = t * a.x * a.y - s * a.z; r.m[2] = t * a.x * a.z + s * a.y;
+  r.m[3] = t * a.x * a.y + s * a.z; r.m[4] = t * a.y * a.y + c; r.m[5] = t * a.y * a.z - s * a.x;
+  r.m[6] = t * a.x * a.z - s * a.y; r.m[7] = t * a.y * a.z + s * a.x; r.m[8] = t * a.z * a.z + c;
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// narrowphase: phi (signed gap), midpoint contact point p, normal n from geom B to geom A
+// ---------------------------------------------------------------------------------------
+struct Raw {
+  float phi;
+  f3 p, n;
+};
+
+__device__ __forceinline__ Raw nf_sphere_sphere(f3 ca, float ra, f3 cb, float rb) {
+  f3 d = ca - cb;
+  float dist = norm3(d);
+  f3 n = dist > 0.f ? (1.f / dist) * d : mk3(0.f, 0.f, 1.f);
+  Raw k;
+  k.phi = dist - ra - rb;
+  k.p = 0.5f * ((ca - ra * n) + (cb + rb * n));
+  k.n = n;
+  return k;
+}
+
+__device__ __forceinline__ Raw nf_sphere_plane(f3 c, float r, f3 o, f3 nz) {
+  float dist = dot(nz, c - o);
+  Raw k;
+  k.phi = dist - r;
+  k.p = 0.5f * ((c - r * nz) + (c - dist * nz));
+  k.n = nz;
+  return k;
+}
+
+// closest points of segments [p1,q1], [p2,q2] (parameters s, t in [0,1]); near-parallel
+// segments (1 - cos^2 <= 1e-3) take the midpoint of the overlap of 2's projection onto 1.
+__device__ __forceinline__ void nf_segments(f3 p1, f3 q1, f3 p2, f3 q2, float& s, float& t) {
+  f3 d1 = q1 - p1, d2 = q2 - p2, r = p1 - p2;
+  float a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r), c = dot(d1, r), b = dot(d1, d2);
+  float denom = a * e - b * b;
+  if (denom > 1e-3f * (a * e)) {
+    s = fminf(fmaxf((b * f - c * e) / denom, 0.f), 1.f);
+    t = (b * s + f) / e;
+    if (t < 0.f) {
+      t = 0.f;
+      s = fminf(fmaxf(-c / a, 0.f), 1.f);
+    } else if (t > 1.f) {
+      t = 1.f;
+      s = fminf(fmaxf((b - c) / a, 0.f), 1.f);
+    }
+  } else {
+    float sp = dot(p2 - p1, d1) / a, sq = dot(q2 - p1, d1) / a;
+    float lo = fmaxf(0.f, fminf(sp, sq)), hi = fminf(1.f, fmaxf(sp, sq));
+    if (lo <= hi) s = 0.5f * (lo + hi);
+    else s = fmaxf(sp, sq) < 0.f ? 0.f : 1.f;
+    t = fminf(fmaxf((b * s + f) / e, 0.f), 1.f);
+  }
+}
+
+// sphere (centre c, radius r) against a box (centre bc, rotation R, half extents hs)
+__device__ __forceinline__ Raw nf_sphere_box(f3 c, float r, f3 bc, const M33& R, f3 hs, bool sphere_is_a) {
+  f3 l = mulT(R, c - bc);
+  float lc[3] = {l.x, l.y, l.z}, h[3] = {hs.x, hs.y, hs.z}, cl[3];
+  bool inside = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cl[i] = fminf(fmaxf(lc[i], -h[i]), h[i]);
+    if (lc[i] < -h[i] || lc[i] > h[i]) inside = false;
+  }
+  f3 nb, sbox;
+  float dist;
+  if (!inside) {
+    f3 qb = bc + mul(R, mk3(cl[0], cl[1], cl[2]));
+    f3 d = c - qb;
+    dist = norm3(d);
+    nb = (1.f / dist) * d;
+    sbox = qb;
+  } else {
+    int k = 0;
+    float best = h[0] - fabsf(lc[0]);
+#pragma unroll
+    for (int i = 1; i < 3; ++i) {
+      float g = h[i] - fabsf(lc[i]);
+      if (g < best) { best = g; k = i; }
+    }
+    float sg = lc[k] >= 0.f ? 1.f : -1.f;
+    nb = sg * col(R, k);
+    dist = -best;
+    float sl[3] = {lc[0], lc[1], lc[2]};
+    sl[k] = sg * h[k];
+    sbox = bc + mul(R, mk3(sl[0], sl[1], sl[2]));
+  }
+  Raw o;
+  o.phi = dist - r;
+  o.p = 0.5f * ((c - r * nb) + sbox);
+  o.n = sphere_is_a ? nb : -nb;
+  return o;
+}
+
+// argmin over t in [-h, h] of the box SDF at x0 + t w (box coordinates).  Outside the box:
+// root of the nondecreasing piecewise-linear derivative of sum_k max(|x_k| - s_k, 0)^2,
+// walking the slab breakpoints (a flat stretch takes its midpoint).  Through the box: best of
+// the endpoints and the pairwise crossings of the six lines +-x_k(t) - s_k.
+__device__ __forceinline__ float box_sdf_along(const float* x0, const float* w, const float* s, float t) {
+  float out2 = 0.f, inmax = -3.0e38f;
+  bool outside = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float e = fabsf(fmaf(t, w[k], x0[k])) - s[k];
+    if (e > 0.f) { outside = true; out2 = fmaf(e, e, out2); }
+    inmax = fmaxf(inmax, e);
+  }
+  return outside ? sqrtf(out2) : inmax;
+}
+__device__ __forceinline__ float box_dG(const float* x0, const float* w, const float* s, float t) {
+  float g = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float xk = fmaf(t, w[k], x0[k]);
+    float e = fabsf(xk) - s[k];
+    if (e > 0.f) g = fmaf(e, xk >= 0.f ? w[k] : -w[k], g);
+  }
+  return g;
+}
+__device__ inline float nf_capsule_box_param(f3 x0v, f3 wv, float h, f3 sv) {
+  float x0[3] = {x0v.x, x0v.y, x0v.z}, w[3] = {wv.x, wv.y, wv.z}, s[3] = {sv.x, sv.y, sv.z};
+  float lo = -h, hi = h;
+  bool hits = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (!hits) break;
+    if (w[k] == 0.f) {
+      if (fabsf(x0[k]) > s[k]) hits = false;
+    } else {
+      float ta = (-s[k] - x0[k]) / w[k], tb = (s[k] - x0[k]) / w[k];
+      if (ta > tb) { float tt = ta; ta = tb; tb = tt; }
+      lo = fmaxf(lo, ta);
+      hi = fminf(hi, tb);
+      if (lo > hi) hits = false;
+    }
+  }
+  if (!hits) {
+    if (box_dG(x0, w, s, -h) >= 0.f) return -h;
+    if (box_dG(x0, w, s, h) <= 0.f) return h;
+    float bp[8];
+    int nb = 0;
+    bp[nb++] = -h;
+    bp[nb++] = h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (w[k] != 0.f)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+          float tb = ((float)sg * s[k] - x0[k]) / w[k];
+          if (tb > -h && tb < h) bp[nb++] = tb;
+        }
+    for (int i = 1; i < nb; ++i) {  // insertion sort (<= 8 values)
+      float v = bp[i];
+      int j = i - 1;
+      while (j >= 0 && bp[j] > v) { bp[j + 1] = bp[j]; --j; }
+      bp[j + 1] = v;
+    }
+    for (int i = 0; i + 1 < nb; ++i) {
+      float ta = bp[i], tb = bp[i + 1];
+      float ga = box_dG(x0, w, s, ta), gb = box_dG(x0, w, s, tb);
+      if (ga <= 0.f && gb >= 0.f) {
+        if (ga == 0.f && gb == 0.f) return 0.5f * (ta + tb);
+        if (ga == 0.f) return ta;
+        if (gb == 0.f) return tb;
+        float tm = 0.5f * (ta + tb), num = 0.f, den = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          float xk = fmaf(tm, w[k], x0[k]);
+          if (fabsf(xk) - s[k] > 0.f) {
+            float sg = xk >= 0.f ? 1.f : -1.f;
+            num = fmaf(w[k], sg * s[k] - x0[k], num);
+            den = fmaf(w[k], w[k], den);
+          }
+        }
+        return num / den;
+      }
+    }
+    return 0.f;
+  }
+  float la[6], lb[6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    la[2 * k] = w[k];
+    lb[2 * k] = x0[k] - s[k];
+    la[2 * k + 1] = -w[k];
+    lb[2 * k + 1] = -x0[k] - s[k];
+  }
+  float best = -h, fbest = box_sdf_along(x0, w, s, -h);
+  {
+    float fh = box_sdf_along(x0, w, s, h);
+    if (fh < fbest) { fbest = fh; best = h; }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = i + 1; j < 6; ++j) {
+      float da = la[i] - la[j];
+      if (fabsf(da) > 1e-12f) {
+        float tc = (lb[j] - lb[i]) / da;
+        if (tc > -h && tc < h) {
+          float fc = box_sdf_along(x0, w, s, tc);
+          if (fc < fbest || (fc == fbest && tc < best)) { fbest = fc; best = tc; }
+        }
+      }
+    }
+  return best;
+}
+
+// contact frame: plane contacts use the plane's local x axis as t1; otherwise
+// t1 = normalize(e_z x n) when |n_z| < 0.5, else normalize(e_x x n); t2 = n x t1.
+__device__ __forceinline__ void contact_frame(f3 n, bool plane, f3 px, f3& t1, f3& t2) {
+  if (plane) {
+    t1 = px;
+  } else {
+    f3 c = fabsf(n.z) < 0.5f ? mk3(-n.y, n.x, 0.f) : mk3(0.f, -n.z, n.y);
+    t1 = rsqrtf(dot(c, c)) * c;
+  }
+  t2 = cross(n, t1);
+}
+
+// r(|phi|) of Eq. r_scaling, x clamped to [0, 1]
+__device__ __forceinline__ float solimp_r(const StepParams& P, float aphi) {
+  float x = fminf(fmaxf(aphi / P.solimp[2], 0.f), 1.f);
+  float m = P.solimp[3];
+  float g = x < m ? m * powf(x / m, P.solimp[4]) : 1.f - (1.f - m) * powf((1.f - x) / (1.f - m), P.solimp[4]);
+  return P.solimp[0] + (P.solimp[1] - P.solimp[0]) * g;
+}
+
+// Closed-form facet impulses of one contact (Eqs. tilde_defs, cf_wrench with
+// K = k M(phi)/dt, D = d M(phi)/dt, impulse lambda dt = (-kM (s dt + phi) - dM s)_+).
+// In: the contact-space velocities of the smooth prediction (normal, tangential pair,
+// torsion, rolling pair).  Out: the resultant impulse on A in the contact frame
+// w = (normal, t1, t2, torsion, rolling t1, rolling t2).
+__device__ __forceinline__ void facet_impulses(const StepParams& P, float vn, float vt1, float vt2, float wn,
+                                               float wr1, float wr2, float phi, float kM, float dM, float mu_t,
+                                               float mu_tor, float mu_rol, float w[6]) {
+  const float A = -kM * phi;                 // lambda = max(0, A - B s)
+  const float B = fmaf(kM, P.dt, dM);
+  float N = 0.f, F1 = 0.f, F2 = 0.f, T = 0.f, R1 = 0.f, R2 = 0.f;
+  for (int j = 0; j < P.n_t; ++j) {
+    float c = P.tcos[j], s = P.tsin[j];
+    float sv = vn - mu_t * (c * vt1 + s * vt2);
+    float lam = fmaxf(A - B * sv, 0.f);
+    N += lam;
+    F1 = fmaf(-mu_t * c, lam, F1);
+    F2 = fmaf(-mu_t * s, lam, F2);
+  }
+  if (P.n_tor == 2) {
+    float lp = fmaxf(A - B * (vn - mu_tor * wn), 0.f);
+    float lm = fmaxf(A - B * (vn + mu_tor * wn), 0.f);
+    N += lp + lm;
+    T = -mu_tor * (lp - lm);
+  }
+  for (int j = 0; j < P.n_rol; ++j) {
+    float c = P.rcos[j], s = P.rsin[j];
+    float sv = vn - mu_rol * (c * wr1 + s * wr2);
+    float lam = fmaxf(A - B * sv, 0.f);
+    N += lam;
+    R1 = fmaf(-mu_rol * c, lam, R1);
+    R2 = fmaf(-mu_rol * s, lam, R2);
+  }
+  w[0] = N; w[1] = F1; w[2] = F2; w[3] = T; w[4] = R1; w[5] = R2;
+}
+
+__device__ __forceinline__ unsigned long long to_fix(float x) {
+  x = fminf(fmaxf(x, -kFixClamp), kFixClamp);
+  return (unsigned long long)__float2ll_rn(x * kFixScale);
+}
+__device__ __forceinline__ float from_fix(unsigned long long a) {
+  return __ll2float_rn((long long)a) * kFixInv;
+}
+
+}  // namespace cf

@@ -1,0 +1,97 @@
+// Internal device-side data layout of libcomfree (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "comfree.h"
+
+namespace cf {
+
+constexpr int kBlock = 256;           // threads per CTA of the step kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kQueue = 64;            // per-warp candidate queue (entries)
+constexpr int kMaxFacetDirs = 16;     // n_t, n_rol <= 16
+constexpr int kMaxTreeDof = 8;        // hinge DoFs per tree handled by the articulated path
+constexpr float kFixScale = 1099511627776.0f;          // 2^40: fixed-point impulse quantum
+constexpr float kFixInv = 9.094947017729282e-13f;      // 2^-40
+constexpr float kFixClamp = 8.0e6f;                    // |impulse| clamp before conversion
+
+// ---------------------------------------------------------------------------------------
+// scene templates (uploaded once per batch into the workspace)
+// ---------------------------------------------------------------------------------------
+struct alignas(16) DScene {
+  int nbody, ngeom, nq, nv;
+  int nu, ntree, pile, nplane;
+  int body0, geom0, tree0, pair0;
+  int npair, plane0, maxdepth, pad;
+};
+
+struct alignas(16) DBody {
+  int parent, jnt, qoff, voff;      // parent is scene-local, offsets world-local
+  int uoff, tree, pad0, pad1;       // uoff: actuator slot of a hinge, -1 otherwise
+  float pos[3], quat[4], axis[3], ipos[3], mass, inertia[3], damping, pad2[2];
+};
+
+struct alignas(16) DGeom {
+  int type, body, pad0, pad1;
+  float pos[3], quat[4], size[3], mu[3], pad2[3];
+};
+
+struct alignas(16) DTree {
+  int body0, nbody, voff, nv;
+  int free, pad0, pad1, pad2;
+};
+
+struct alignas(16) DWorld {
+  int scene, qadr, vadr, padr;
+  int uadr, pad0, pad1, pad2;
+};
+
+struct alignas(16) DUnit {
+  int first, count, warps, pad;     // worlds order[first .. first+count) processed by groups
+};
+
+// ---------------------------------------------------------------------------------------
+// launch parameters
+// ---------------------------------------------------------------------------------------
+struct StepParams {
+  const DScene* scenes;
+  const DBody* bodies;
+  const DGeom* geoms;
+  const DTree* trees;
+  const uint32_t* pairs;     // (ga << 16) | gb, scene-local geom indices
+  const DWorld* worlds;
+  const DUnit* units;
+  const int* order;
+  int nunits;
+  float* q;
+  float* v;
+  const float* wparam;
+  const float* ctrl;
+  int total_nu;
+  int nctrl;
+  int* ncontact;
+  int* flags;
+  int* errword;
+  int* queue;                // [0] next unit, [1] finished CTAs (self-resetting)
+  cf_contact* capture;
+  int capture_cap;
+  float dt;
+  int nsteps;
+  float gravity[3];
+  float k_user, d_user;
+  float solimp[5];
+  float margin;
+  int n_t, n_tor, n_rol, trace_mode;
+  float tcos[kMaxFacetDirs], tsin[kMaxFacetDirs];
+  float rcos[kMaxFacetDirs], rsin[kMaxFacetDirs];
+};
+
+// bytes of dynamic shared memory one world of a scene needs in the step kernel
+size_t world_smem_bytes(const DScene& s, int warps);
+
+cudaError_t launch_step(const StepParams& p, int grid, size_t smem, cudaStream_t stream);
+int step_max_blocks_per_sm(size_t smem);
+size_t step_max_dynamic_smem();
+
+}  // namespace cf

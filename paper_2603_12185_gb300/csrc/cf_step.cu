@@ -1,0 +1,1061 @@
+// The fused ComFree step: one group of warps per world, the world's state staged in shared
+// memory for the whole step (or nsteps steps), persistent CTAs pulling work units.
+//
+// Per world and step (ComFree-Sim, Sec. III and Algorithm 1):
+//   A. smooth prediction v_s = v + M~^-1 (tau - c - b v) dt            (Eq. smooth_vel; Kernel I)
+//   B. pair loop: bounding-sphere broadphase compacted into per-warp queues, narrowphase,
+//      contact frame, M(phi), per-facet closed-form impulses and the J~^T lambda scatter into
+//      fixed-point shared accumulators                (Eqs. tilde_defs, cf_wrench; Kernels II-III)
+//   C. v+ = v_s + M~^-1 p, semi-implicit Euler                      (Eq. vel_correction; Kernel IV)
+#include <cstdio>
+
+#include "cf_device_math.cuh"
+
+namespace cf {
+
+__device__ __forceinline__ void group_sync(int gid, int nthreads) {
+  if (nthreads == 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ float ctrl_at(const StepParams& P, int step, int uadr, int uoff) {
+  if (P.nctrl <= 0 || uoff < 0) return 0.f;
+  int slice = step < P.nctrl ? step : P.nctrl - 1;
+  return P.ctrl[(size_t)slice * P.total_nu + uadr + uoff];
+}
+
+struct PlaneDev {
+  f3 o, n, x;
+  float mu[3];
+};
+
+__device__ __forceinline__ PlaneDev load_plane(const DGeom& g) {
+  M33 R = quat_mat(g.quat[0], g.quat[1], g.quat[2], g.quat[3]);
+  PlaneDev p;
+  p.o = mk3(g.pos[0], g.pos[1], g.pos[2]);
+  p.n = col(R, 2);
+  p.x = col(R, 0);
+  p.mu[0] = g.mu[0]; p.mu[1] = g.mu[1]; p.mu[2] = g.mu[2];
+  return p;
+}
+
+__device__ __forceinline__ void capture_contact(const StepParams& P, int world, int* s_count, int ga, int gb, int sub,
+                                                float phi, f3 p, f3 n, float lam, float mphi) {
+  int slot = atomicAdd(s_count + 1, 1);
+  if (slot < P.capture_cap) {
+    cf_contact c;
+    c.geom_a = ga; c.geom_b = gb; c.sub = sub; c.pad = 0;
+    c.phi = phi;
+    c.pos[0] = p.x; c.pos[1] = p.y; c.pos[2] = p.z;
+    c.normal[0] = n.x; c.normal[1] = n.y; c.normal[2] = n.z;
+    c.lam_sum = lam; c.mphi = mphi;
+    c.pad2[0] = c.pad2[1] = c.pad2[2] = 0.f;
+    P.capture[(size_t)world * P.capture_cap + slot] = c;
+  }
+}
+
+// =======================================================================================
+// pile worlds: free bodies, geom i on body i at its origin, static planes
+// =======================================================================================
+struct PileView {
+  int N, NP;
+  unsigned long long* acc;  // [6][N]
+  float *x, *y, *z, *qw, *qx, *qy, *qz;
+  float* v;                 // [6][N]
+  float* vs;                // [6][N]
+  float* R;                 // [9][N]
+  float *invm, *I0, *I1, *I2, *rad, *hl, *bnd, *s2;
+  int* type;
+  float* planes;            // [NP][12]
+  int* queue;               // [warps][kQueue]
+  int* count;               // [0] contacts, [1] captured
+};
+
+__host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
+  // acc (12 words/body) + 37 words/body + planes + queues + counters, 16-byte granules
+  size_t words = (size_t)N * 12 + (size_t)N * 37 + (size_t)NP * 12 + (size_t)warps * kQueue + 4;
+  return (words + 3) & ~(size_t)3;
+}
+
+__device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
+  PileView s;
+  s.N = N; s.NP = NP;
+  s.acc = reinterpret_cast<unsigned long long*>(base);
+  float* f = base + (size_t)N * 12;
+  s.x = f; f += N; s.y = f; f += N; s.z = f; f += N;
+  s.qw = f; f += N; s.qx = f; f += N; s.qy = f; f += N; s.qz = f; f += N;
+  s.v = f; f += 6 * N;
+  s.vs = f; f += 6 * N;
+  s.R = f; f += 9 * N;
+  s.invm = f; f += N; s.I0 = f; f += N; s.I1 = f; f += N; s.I2 = f; f += N;
+  s.rad = f; f += N; s.hl = f; f += N; s.bnd = f; f += N; s.s2 = f; f += N;
+  s.type = reinterpret_cast<int*>(f); f += N;
+  s.planes = f; f += (size_t)NP * 12;
+  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
+  s.count = reinterpret_cast<int*>(f);
+  return s;
+}
+
+__device__ __forceinline__ M33 pile_R(const PileView& s, int i) {
+  M33 R;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R.m[k] = s.R[k * s.N + i];
+  return R;
+}
+
+// translational trace tr(J_i M^-1 J_i^T) of a free body at lever r (world) or 1/m
+__device__ __forceinline__ float pile_trace(const StepParams& P, const PileView& s, int i, const M33& R, f3 r) {
+  float im = s.invm[i];
+  if (P.trace_mode) return im;
+  f3 l = mulT(R, r);
+  float i0 = 1.f / s.I0[i], i1 = 1.f / s.I1[i], i2 = 1.f / s.I2[i];
+  return 3.f * im + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
+}
+
+__device__ __forceinline__ void pile_apply(PileView& s, int i, const M33& R, f3 r, f3 f, f3 m, float sign) {
+  f3 ang = mulT(R, cross(r, f) + m);
+  atomicAdd(&s.acc[0 * s.N + i], to_fix(sign * f.x));
+  atomicAdd(&s.acc[1 * s.N + i], to_fix(sign * f.y));
+  atomicAdd(&s.acc[2 * s.N + i], to_fix(sign * f.z));
+  atomicAdd(&s.acc[3 * s.N + i], to_fix(sign * ang.x));
+  atomicAdd(&s.acc[4 * s.N + i], to_fix(sign * ang.y));
+  atomicAdd(&s.acc[5 * s.N + i], to_fix(sign * ang.z));
+}
+
+// one contact between body a and body b (b < 0: static plane with x axis px)
+__device__ __noinline__ void pile_contact(const StepParams& P, PileView& s, int world, int a, int b, int ga, int gb,
+                                          int sub, const Raw& k, bool plane, f3 px, const float* mu_b) {
+  f3 t1, t2;
+  contact_frame(k.n, plane, px, t1, t2);
+  M33 Ra = pile_R(s, a);
+  f3 ra = k.p - mk3(s.x[a], s.y[a], s.z[a]);
+  f3 wa = mul(Ra, mk3(s.vs[3 * s.N + a], s.vs[4 * s.N + a], s.vs[5 * s.N + a]));
+  f3 vc = mk3(s.vs[a], s.vs[s.N + a], s.vs[2 * s.N + a]) + cross(wa, ra);
+  f3 wc = wa;
+  float tr = pile_trace(P, s, a, Ra, ra);
+  float mu_t, mu_tor, mu_rol;
+  M33 Rb;
+  f3 rb;
+  if (b >= 0) {
+    Rb = pile_R(s, b);
+    rb = k.p - mk3(s.x[b], s.y[b], s.z[b]);
+    f3 wb = mul(Rb, mk3(s.vs[3 * s.N + b], s.vs[4 * s.N + b], s.vs[5 * s.N + b]));
+    vc = vc - (mk3(s.vs[b], s.vs[s.N + b], s.vs[2 * s.N + b]) + cross(wb, rb));
+    wc = wc - wb;
+    tr += pile_trace(P, s, b, Rb, rb);
+  }
+  // pair friction: the larger of the two geoms' coefficients (per-world geoms share the
+  // template's coefficients)
+  const DGeom& gA = P.geoms[ga];
+  mu_t = fmaxf(gA.mu[0], mu_b[0]);
+  mu_tor = fmaxf(gA.mu[1], mu_b[1]);
+  mu_rol = fmaxf(gA.mu[2], mu_b[2]);
+  float r = solimp_r(P, fabsf(k.phi));
+  float mphi = r / (1.f - r) / tr;
+  float w[6];
+  facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                 P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
+  f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
+  f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
+  pile_apply(s, a, Ra, ra, f, m, 1.f);
+  if (b >= 0) pile_apply(s, b, Rb, rb, f, m, -1.f);
+  atomicAdd(s.count, 1);
+  if (P.capture_cap > 0) capture_contact(P, world, s.count, ga, gb, sub, k.phi, k.p, k.n, w[0], mphi);
+}
+
+// narrowphase + solve for one candidate code: (a << 16) | b, or (a << 16) | 0x8000 | plane
+__device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& sc, int world, int code) {
+  int a = code >> 16, bc = code & 0xffff;
+  int ta = s.type[a];
+  f3 ca = mk3(s.x[a], s.y[a], s.z[a]);
+  const int ga = sc.geom0 + a;
+  if (bc & 0x8000) {
+    int pi = bc & 0x7fff;
+    const float* pl = s.planes + 12 * pi;
+    f3 o = mk3(pl[0], pl[1], pl[2]), nz = mk3(pl[3], pl[4], pl[5]), px = mk3(pl[6], pl[7], pl[8]);
+    const int gb = sc.geom0 + sc.plane0 + pi;
+    if (ta == CF_GEOM_SPHERE) {
+      Raw k = nf_sphere_plane(ca, s.rad[a], o, nz);
+      if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, 0, k, true, px, pl + 9);
+    } else if (ta == CF_GEOM_CAPSULE) {
+      M33 R = pile_R(s, a);
+      f3 ax = col(R, 2);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        Raw k = nf_sphere_plane(ca + (e ? s.hl[a] : -s.hl[a]) * ax, s.rad[a], o, nz);
+        if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, e, k, true, px, pl + 9);
+      }
+    } else if (ta == CF_GEOM_BOX) {
+      M33 R = pile_R(s, a);
+      for (int cidx = 0; cidx < 8; ++cidx) {
+        f3 corner = ca + mul(R, mk3((cidx & 4) ? s.rad[a] : -s.rad[a], (cidx & 2) ? s.hl[a] : -s.hl[a],
+                                    (cidx & 1) ? s.s2[a] : -s.s2[a]));
+        Raw k = nf_sphere_plane(corner, 0.f, o, nz);
+        if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, cidx, k, true, px, pl + 9);
+      }
+    }
+    return;
+  }
+  int b = bc;
+  int tb = s.type[b];
+  f3 cb = mk3(s.x[b], s.y[b], s.z[b]);
+  const int gb = sc.geom0 + b;
+  const float* mub = P.geoms[gb].mu;
+  Raw k;
+  k.phi = 3.0e38f;
+  if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
+    k = nf_sphere_sphere(ca, s.rad[a], cb, s.rad[b]);
+  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
+    f3 ua = col(pile_R(s, a), 2), ub = col(pile_R(s, b), 2);
+    f3 p1 = ca - s.hl[a] * ua, q1 = ca + s.hl[a] * ua, p2 = cb - s.hl[b] * ub, q2 = cb + s.hl[b] * ub;
+    float ss, tt;
+    nf_segments(p1, q1, p2, q2, ss, tt);
+    k = nf_sphere_sphere(p1 + ss * (q1 - p1), s.rad[a], p2 + tt * (q2 - p2), s.rad[b]);
+  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_SPHERE) {
+    f3 u = col(pile_R(s, a), 2);
+    float t = fminf(fmaxf(dot(cb - ca, u), -s.hl[a]), s.hl[a]);
+    k = nf_sphere_sphere(ca + t * u, s.rad[a], cb, s.rad[b]);
+  } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CAPSULE) {
+    f3 u = col(pile_R(s, b), 2);
+    float t = fminf(fmaxf(dot(ca - cb, u), -s.hl[b]), s.hl[b]);
+    k = nf_sphere_sphere(ca, s.rad[a], cb + t * u, s.rad[b]);
+  } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
+    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) return;  // box-box: unsupported pair
+    bool boxA = ta == CF_GEOM_BOX;
+    int ib = boxA ? a : b, io = boxA ? b : a;
+    M33 Rbx = pile_R(s, ib);
+    f3 cbx = boxA ? ca : cb, co = boxA ? cb : ca;
+    f3 hs = mk3(s.rad[ib], s.hl[ib], s.s2[ib]);
+    if (s.type[io] == CF_GEOM_SPHERE) {
+      k = nf_sphere_box(co, s.rad[io], cbx, Rbx, hs, !boxA);
+    } else {
+      f3 u = col(pile_R(s, io), 2);
+      float t = nf_capsule_box_param(mulT(Rbx, co - cbx), mulT(Rbx, u), s.hl[io], hs);
+      k = nf_sphere_box(co + t * u, s.rad[io], cbx, Rbx, hs, !boxA);
+    }
+  }
+  if (k.phi < P.margin) pile_contact(P, s, world, a, b, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f), mub);
+}
+
+// decode body-body pair index k of N bodies: pairs (i, (i + o) mod N), o = 1..H, plus
+// (i, i + N/2) for i < N/2 when N is even; returns the ordered pair a < b
+__device__ __forceinline__ void pile_pair_decode(int k, int N, int& a, int& b) {
+  int H = (N - 1) >> 1;
+  int i, j;
+  if (k < N * H) {
+    i = k % N;
+    j = i + 1 + k / N;
+    if (j >= N) j -= N;
+  } else {
+    i = k - N * H;
+    j = i + (N >> 1);
+  }
+  a = min(i, j);
+  b = max(i, j);
+}
+
+__device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
+  const DWorld W = P.worlds[world];
+  const DScene sc = P.scenes[W.scene];
+  const int N = sc.nbody, NP = sc.nplane;
+  const int T = gwarps * 32;
+  const int tid = threadIdx.x - gid * T;
+  const int lane = threadIdx.x & 31, wig = tid >> 5;
+  PileView s = pile_view(smem, N, NP, gwarps);
+  const float* q = P.q + W.qadr;
+  const float* v = P.v + W.vadr;
+  const float dt = P.dt;
+
+  // load state and per-world parameters
+  for (int i = tid; i < N; i += T) {
+    const float* qi = q + 7 * i;
+    s.x[i] = qi[0]; s.y[i] = qi[1]; s.z[i] = qi[2];
+    s.qw[i] = qi[3]; s.qx[i] = qi[4]; s.qy[i] = qi[5]; s.qz[i] = qi[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s.v[k * N + i] = v[6 * i + k];
+    float m, i0, i1, i2, ty, r, h, s2;
+    if (W.padr >= 0) {
+      const float4* pp = reinterpret_cast<const float4*>(P.wparam + W.padr + 8 * i);
+      float4 p0 = pp[0], p1 = pp[1];
+      m = p0.x; i0 = p0.y; i1 = p0.z; i2 = p0.w; ty = p1.x; r = p1.y; h = p1.z; s2 = p1.w;
+    } else {
+      const DBody& bd = P.bodies[sc.body0 + i];
+      const DGeom& gd = P.geoms[sc.geom0 + i];
+      m = bd.mass; i0 = bd.inertia[0]; i1 = bd.inertia[1]; i2 = bd.inertia[2];
+      ty = (float)gd.type; r = gd.size[0]; h = gd.size[1]; s2 = gd.size[2];
+    }
+    int t = (int)ty;
+    s.invm[i] = 1.f / m; s.I0[i] = i0; s.I1[i] = i1; s.I2[i] = i2;
+    s.type[i] = t; s.rad[i] = r; s.hl[i] = h; s.s2[i] = s2;
+    s.bnd[i] = t == CF_GEOM_SPHERE ? r : (t == CF_GEOM_CAPSULE ? r + h : sqrtf(r * r + h * h + s2 * s2));
+  }
+  for (int pi = tid; pi < NP; pi += T) {
+    PlaneDev pl = load_plane(P.geoms[sc.geom0 + sc.plane0 + pi]);
+    float* o = s.planes + 12 * pi;
+    o[0] = pl.o.x; o[1] = pl.o.y; o[2] = pl.o.z; o[3] = pl.n.x; o[4] = pl.n.y; o[5] = pl.n.z;
+    o[6] = pl.x.x; o[7] = pl.x.y; o[8] = pl.x.z; o[9] = pl.mu[0]; o[10] = pl.mu[1]; o[11] = pl.mu[2];
+  }
+  const int H = (N - 1) >> 1;
+  const int nbb = N * H + ((N & 1) ? 0 : (N >> 1));
+  const int ncand = nbb + N * NP;
+  const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
+  int* queue = s.queue + wig * kQueue;
+
+  for (int step = 0; step < P.nsteps; ++step) {
+    group_sync(gid, T);
+    // ---- A. kinematics and smooth prediction (free body: c = (-m g, w x I w)) ----
+    for (int i = tid; i < N; i += T) {
+      M33 R = quat_mat(s.qw[i], s.qx[i], s.qy[i], s.qz[i]);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s.R[k * N + i] = R.m[k];
+      float w0 = s.v[3 * N + i], w1 = s.v[4 * N + i], w2 = s.v[5 * N + i];
+      float i0 = s.I0[i], i1 = s.I1[i], i2 = s.I2[i];
+      f3 gy = cross(mk3(w0, w1, w2), mk3(i0 * w0, i1 * w1, i2 * w2));
+      s.vs[i] = s.v[i] + g.x * dt;
+      s.vs[N + i] = s.v[N + i] + g.y * dt;
+      s.vs[2 * N + i] = s.v[2 * N + i] + g.z * dt;
+      s.vs[3 * N + i] = w0 - dt * gy.x / i0;
+      s.vs[4 * N + i] = w1 - dt * gy.y / i1;
+      s.vs[5 * N + i] = w2 - dt * gy.z / i2;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s.acc[k * N + i] = 0ull;
+    }
+    if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
+    group_sync(gid, T);
+
+    // ---- B. broadphase into per-warp queues, narrowphase + impulses on full warps ----
+    int qn = 0;
+    const float margin = P.margin;
+    for (int base = wig * 32; base < ncand; base += T) {
+      int k = base + lane;
+      int code = -1;
+      if (k < ncand) {
+        if (k < nbb) {
+          int a, b;
+          pile_pair_decode(k, N, a, b);
+          float dx = s.x[a] - s.x[b], dy = s.y[a] - s.y[b], dz = s.z[a] - s.z[b];
+          float rr = s.bnd[a] + s.bnd[b] + margin;
+          if (dx * dx + dy * dy + dz * dz < rr * rr) code = (a << 16) | b;
+        } else {
+          int kk = k - nbb;
+          int a = kk % N, pi = kk / N;
+          const float* pl = s.planes + 12 * pi;
+          float d = (s.x[a] - pl[0]) * pl[3] + (s.y[a] - pl[1]) * pl[4] + (s.z[a] - pl[2]) * pl[5];
+          if (d < s.bnd[a] + margin) code = (a << 16) | 0x8000 | pi;
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, code >= 0);
+      if (code >= 0) queue[qn + __popc(m & ((1u << lane) - 1u))] = code;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        pile_candidate(P, s, sc, world, queue[qn - 32 + lane]);
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    if (lane < qn) pile_candidate(P, s, sc, world, queue[lane]);
+    group_sync(gid, T);
+
+    // ---- C. velocity correction and semi-implicit Euler ----
+    for (int i = tid; i < N; i += T) {
+      float im = s.invm[i];
+      float v0 = s.vs[i] + from_fix(s.acc[i]) * im;
+      float v1 = s.vs[N + i] + from_fix(s.acc[N + i]) * im;
+      float v2 = s.vs[2 * N + i] + from_fix(s.acc[2 * N + i]) * im;
+      float w0 = s.vs[3 * N + i] + from_fix(s.acc[3 * N + i]) / s.I0[i];
+      float w1 = s.vs[4 * N + i] + from_fix(s.acc[4 * N + i]) / s.I1[i];
+      float w2 = s.vs[5 * N + i] + from_fix(s.acc[5 * N + i]) / s.I2[i];
+      s.v[i] = v0; s.v[N + i] = v1; s.v[2 * N + i] = v2;
+      s.v[3 * N + i] = w0; s.v[4 * N + i] = w1; s.v[5 * N + i] = w2;
+      s.x[i] += v0 * dt; s.y[i] += v1 * dt; s.z[i] += v2 * dt;
+      float wn = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+      float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
+      if (wn > 0.f) {
+        float sn, cs;
+        sincosf(0.5f * wn * dt, &sn, &cs);
+        float sc_ = sn / wn;
+        dq0 = cs; dq1 = sc_ * w0; dq2 = sc_ * w1; dq3 = sc_ * w2;
+      }
+      float a0 = s.qw[i], a1 = s.qx[i], a2 = s.qy[i], a3 = s.qz[i];
+      float n0 = a0 * dq0 - a1 * dq1 - a2 * dq2 - a3 * dq3;
+      float n1 = a0 * dq1 + a1 * dq0 + a2 * dq3 - a3 * dq2;
+      float n2 = a0 * dq2 - a1 * dq3 + a2 * dq0 + a3 * dq1;
+      float n3 = a0 * dq3 + a1 * dq2 - a2 * dq1 + a3 * dq0;
+      float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+      s.qw[i] = n0 * inv; s.qx[i] = n1 * inv; s.qy[i] = n2 * inv; s.qz[i] = n3 * inv;
+    }
+  }
+  group_sync(gid, T);
+  // ---- write back ----
+  float* qo = P.q + W.qadr;
+  float* vo = P.v + W.vadr;
+  bool bad = false;
+  for (int i = tid; i < N; i += T) {
+    float* qi = qo + 7 * i;
+    qi[0] = s.x[i]; qi[1] = s.y[i]; qi[2] = s.z[i];
+    qi[3] = s.qw[i]; qi[4] = s.qx[i]; qi[5] = s.qy[i]; qi[6] = s.qz[i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) vo[6 * i + k] = s.v[k * N + i];
+    float chk = s.x[i] + s.y[i] + s.z[i] + s.qw[i] + s.v[i] + s.v[N + i] + s.v[2 * N + i] + s.v[3 * N + i] +
+                s.v[4 * N + i] + s.v[5 * N + i];
+    if (!isfinite(chk)) bad = true;
+  }
+  if (bad) {
+    atomicOr(P.flags + world, CF_FLAG_NONFINITE);
+    atomicOr(P.errword, CF_FLAG_NONFINITE);
+  }
+  if (tid == 0) {
+    P.ncontact[world] = s.count[0];
+    if (P.capture_cap > 0 && s.count[1] > P.capture_cap) {
+      atomicOr(P.flags + world, CF_FLAG_CONTACT_OVERFLOW);
+      atomicOr(P.errword, CF_FLAG_CONTACT_OVERFLOW);
+    }
+  }
+}
+
+// =======================================================================================
+// articulated worlds: free bodies and fixed-base hinge trees, explicit geom pair lists
+// =======================================================================================
+struct ArticView {
+  int nb, ng, nv, nq, ntree;
+  unsigned long long* acc;   // [nv]
+  float* q;                  // [nq]
+  float* v;                  // [nv]
+  float* vs;                 // [nv]
+  float* tau;                // [nv]
+  float* bx;                 // [nb][3]  body origin
+  float* bR;                 // [nb][9]
+  float* bom;                // [nb][3]  world angular velocity (smooth)
+  float* bvo;                // [nb][3]  world velocity of the origin (smooth)
+  float* bax;                // [nb][3]  world hinge axis
+  float* gc;                 // [ng][3]
+  float* gR;                 // [ng][9]
+  float* gb;                 // [ng]     bounding radius
+  float* minv;               // [ntree][kMaxTreeDof^2]
+  int* queue;
+  int* count;
+};
+
+__host__ __device__ inline size_t artic_floats(int nb, int ng, int nq, int nv, int ntree, int warps) {
+  size_t words = (size_t)nv * 2 + nq + 3 * (size_t)nv + (size_t)nb * 21 + (size_t)ng * 13 +
+                 (size_t)ntree * kMaxTreeDof * kMaxTreeDof + (size_t)warps * kQueue + 4;
+  return (words + 3) & ~(size_t)3;
+}
+
+__device__ inline ArticView artic_view(float* base, const DScene& sc, int warps) {
+  ArticView s;
+  s.nb = sc.nbody; s.ng = sc.ngeom; s.nv = sc.nv; s.nq = sc.nq; s.ntree = sc.ntree;
+  s.acc = reinterpret_cast<unsigned long long*>(base);
+  float* f = base + 2 * (size_t)sc.nv;
+  s.q = f; f += sc.nq;
+  s.v = f; f += sc.nv;
+  s.vs = f; f += sc.nv;
+  s.tau = f; f += sc.nv;
+  s.bx = f; f += 3 * sc.nbody;
+  s.bR = f; f += 9 * sc.nbody;
+  s.bom = f; f += 3 * sc.nbody;
+  s.bvo = f; f += 3 * sc.nbody;
+  s.bax = f; f += 3 * sc.nbody;
+  s.gc = f; f += 3 * sc.ngeom;
+  s.gR = f; f += 9 * sc.ngeom;
+  s.gb = f; f += sc.ngeom;
+  s.minv = f; f += (size_t)sc.ntree * kMaxTreeDof * kMaxTreeDof;
+  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
+  s.count = reinterpret_cast<int*>(f);
+  return s;
+}
+
+__device__ __forceinline__ f3 ld3(const float* p) { return mk3(p[0], p[1], p[2]); }
+__device__ __forceinline__ void st3(float* p, f3 a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+__device__ __forceinline__ M33 ld33(const float* p) {
+  M33 r;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) r.m[k] = p[k];
+  return r;
+}
+
+// world inertia product R diag(I) R^T u
+__device__ __forceinline__ f3 iw_mul(const M33& R, const float* I, f3 u) {
+  f3 l = mulT(R, u);
+  return mul(R, mk3(I[0] * l.x, I[1] * l.y, I[2] * l.z));
+}
+
+// One hinge tree (thread per tree): kinematics, composite-rigid-body inertia, Newton-Euler
+// bias, implicit damping, Cholesky inverse, smooth velocity and body twists.
+__device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr, int uadr,
+                                   int step) {
+  const DBody* B = P.bodies + sc.body0;
+  const float dt = P.dt;
+  if (tr.free) {
+    const int b = tr.body0;
+    const DBody& bd = B[b];
+    const float* qb = s.q + bd.qoff;
+    M33 R = quat_mat(qb[3], qb[4], qb[5], qb[6]);
+    st3(s.bx + 3 * b, mk3(qb[0], qb[1], qb[2]));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.bR[9 * b + k] = R.m[k];
+    const float* vb = s.v + bd.voff;
+    f3 w = mk3(vb[3], vb[4], vb[5]);
+    f3 gy = cross(w, mk3(bd.inertia[0] * w.x, bd.inertia[1] * w.y, bd.inertia[2] * w.z));
+    float* vsb = s.vs + bd.voff;
+    vsb[0] = vb[0] + P.gravity[0] * dt;
+    vsb[1] = vb[1] + P.gravity[1] * dt;
+    vsb[2] = vb[2] + P.gravity[2] * dt;
+    vsb[3] = w.x - dt * gy.x / bd.inertia[0];
+    vsb[4] = w.y - dt * gy.y / bd.inertia[1];
+    vsb[5] = w.z - dt * gy.z / bd.inertia[2];
+    st3(s.bom + 3 * b, mul(R, mk3(vsb[3], vsb[4], vsb[5])));
+    st3(s.bvo + 3 * b, mk3(vsb[0], vsb[1], vsb[2]));
+    st3(s.bax + 3 * b, mk3(0.f, 0.f, 0.f));
+    return;
+  }
+  const int n = tr.nv, b0 = tr.body0, v0 = tr.voff;
+  // -- forward kinematics (bodies of the tree are contiguous, parents first) --
+  f3 com[kMaxTreeDof];
+  for (int j = 0; j < n; ++j) {
+    const int b = b0 + j;
+    const DBody& bd = B[b];
+    M33 Rp;
+    f3 xp = mk3(0.f, 0.f, 0.f);
+    if (bd.parent >= 0) {
+      Rp = ld33(s.bR + 9 * bd.parent);
+      xp = ld3(s.bx + 3 * bd.parent);
+    } else {
+      for (int k = 0; k < 9; ++k) Rp.m[k] = (k % 4 == 0) ? 1.f : 0.f;
+    }
+    M33 Rfix = mul33(Rp, quat_mat(bd.quat[0], bd.quat[1], bd.quat[2], bd.quat[3]));
+    f3 ax = mk3(bd.axis[0], bd.axis[1], bd.axis[2]);
+    ax = rsqrtf(dot(ax, ax)) * ax;
+    M33 R = mul33(Rfix, axis_rot(ax, s.q[bd.qoff]));
+    f3 x = xp + mul(Rp, mk3(bd.pos[0], bd.pos[1], bd.pos[2]));
+    st3(s.bx + 3 * b, x);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.bR[9 * b + k] = R.m[k];
+    st3(s.bax + 3 * b, mul(Rfix, ax));
+    com[j] = x + mul(R, mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]));
+  }
+  // -- composite rigid bodies: mass, first moment, inertia about the world origin --
+  float mc[kMaxTreeDof];
+  f3 hc[kMaxTreeDof];
+  float Io[kMaxTreeDof][6];  // xx yy zz xy xz yz
+  for (int j = 0; j < n; ++j) {
+    const DBody& bd = B[b0 + j];
+    M33 R = ld33(s.bR + 9 * (b0 + j));
+    float m = bd.mass;
+    f3 c = com[j];
+    // R diag(I) R^T + m (|c|^2 1 - c c^T)
+    float Iw[6];
+    {
+      float I0 = bd.inertia[0], I1 = bd.inertia[1], I2 = bd.inertia[2];
+      const float* r = R.m;
+      Iw[0] = r[0] * r[0] * I0 + r[1] * r[1] * I1 + r[2] * r[2] * I2;
+      Iw[1] = r[3] * r[3] * I0 + r[4] * r[4] * I1 + r[5] * r[5] * I2;
+      Iw[2] = r[6] * r[6] * I0 + r[7] * r[7] * I1 + r[8] * r[8] * I2;
+      Iw[3] = r[0] * r[3] * I0 + r[1] * r[4] * I1 + r[2] * r[5] * I2;
+      Iw[4] = r[0] * r[6] * I0 + r[1] * r[7] * I1 + r[2] * r[8] * I2;
+      Iw[5] = r[3] * r[6] * I0 + r[4] * r[7] * I1 + r[5] * r[8] * I2;
+    }
+    float cc = dot(c, c);
+    Io[j][0] = Iw[0] + m * (cc - c.x * c.x);
+    Io[j][1] = Iw[1] + m * (cc - c.y * c.y);
+    Io[j][2] = Iw[2] + m * (cc - c.z * c.z);
+    Io[j][3] = Iw[3] - m * c.x * c.y;
+    Io[j][4] = Iw[4] - m * c.x * c.z;
+    Io[j][5] = Iw[5] - m * c.y * c.z;
+    mc[j] = m;
+    hc[j] = m * c;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    int p = B[b0 + j].parent;
+    if (p >= 0) {
+      int jp = p - b0;
+      mc[jp] += mc[j];
+      hc[jp] = hc[jp] + hc[j];
+      for (int k = 0; k < 6; ++k) Io[jp][k] += Io[j][k];
+    }
+  }
+  // -- M_ij = a_i . L_{o_i}(composite of subtree j moving with unit rate of joint j) --
+  float M[kMaxTreeDof][kMaxTreeDof];
+  for (int j = 0; j < n; ++j) {
+    f3 aj = ld3(s.bax + 3 * (b0 + j)), oj = ld3(s.bx + 3 * (b0 + j));
+    f3 cC = (1.f / mc[j]) * hc[j];
+    float cc = dot(cC, cC);
+    // inertia about the composite COM: I_O - m (|c|^2 1 - c c^T)
+    float I6[6] = {Io[j][0] - mc[j] * (cc - cC.x * cC.x), Io[j][1] - mc[j] * (cc - cC.y * cC.y),
+                   Io[j][2] - mc[j] * (cc - cC.z * cC.z), Io[j][3] + mc[j] * cC.x * cC.y,
+                   Io[j][4] + mc[j] * cC.x * cC.z, Io[j][5] + mc[j] * cC.y * cC.z};
+    f3 Ia = mk3(I6[0] * aj.x + I6[3] * aj.y + I6[4] * aj.z, I6[3] * aj.x + I6[1] * aj.y + I6[5] * aj.z,
+                I6[4] * aj.x + I6[5] * aj.y + I6[2] * aj.z);
+    f3 lin = mc[j] * cross(aj, cC - oj);
+    for (int i = j; i >= 0; i = (B[b0 + i].parent >= 0 ? B[b0 + i].parent - b0 : -1)) {
+      f3 ai = ld3(s.bax + 3 * (b0 + i)), oi = ld3(s.bx + 3 * (b0 + i));
+      float mij = dot(ai, Ia + cross(cC - oi, lin));
+      M[i][j] = mij;
+      M[j][i] = mij;
+    }
+  }
+  // zero entries of non-ancestor pairs
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      bool rel = false;
+      for (int a = j; a >= 0; a = (B[b0 + a].parent >= 0 ? B[b0 + a].parent - b0 : -1))
+        if (a == i) rel = true;
+      for (int a = i; a >= 0; a = (B[b0 + a].parent >= 0 ? B[b0 + a].parent - b0 : -1))
+        if (a == j) rel = true;
+      if (!rel) M[i][j] = 0.f;
+    }
+  // -- Newton-Euler bias with zero joint acceleration, world accelerating at -g --
+  f3 om[kMaxTreeDof], omd[kMaxTreeDof], ac[kMaxTreeDof], F[kMaxTreeDof], Nn[kMaxTreeDof];
+  const f3 gv = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
+  for (int j = 0; j < n; ++j) {
+    const DBody& bd = B[b0 + j];
+    int p = bd.parent >= 0 ? bd.parent - b0 : -1;
+    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
+    float qd = s.v[v0 + j];
+    f3 omp = p >= 0 ? om[p] : mk3(0.f, 0.f, 0.f), omdp = p >= 0 ? omd[p] : mk3(0.f, 0.f, 0.f);
+    om[j] = omp + qd * a;
+    omd[j] = omdp + cross(omp, qd * a);
+    f3 aanc;
+    if (p >= 0) {
+      f3 ro = x - com[p];
+      aanc = ac[p] + cross(omdp, ro) + cross(omp, cross(omp, ro));
+    } else {
+      aanc = -gv;
+    }
+    f3 rc = com[j] - x;
+    ac[j] = aanc + cross(omd[j], rc) + cross(om[j], cross(om[j], rc));
+    M33 R = ld33(s.bR + 9 * (b0 + j));
+    F[j] = bd.mass * ac[j];
+    Nn[j] = iw_mul(R, bd.inertia, omd[j]) + cross(om[j], iw_mul(R, bd.inertia, om[j]));
+  }
+  f3 ft[kMaxTreeDof], nt[kMaxTreeDof];
+  for (int j = 0; j < n; ++j) { ft[j] = mk3(0.f, 0.f, 0.f); nt[j] = mk3(0.f, 0.f, 0.f); }
+  float rhs[kMaxTreeDof];
+  for (int j = n - 1; j >= 0; --j) {
+    const DBody& bd = B[b0 + j];
+    ft[j] = ft[j] + F[j];
+    nt[j] = nt[j] + Nn[j] + cross(com[j], F[j]);
+    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
+    float c = dot(a, nt[j] - cross(x, ft[j]));
+    float tau = ctrl_at(P, step, uadr, bd.uoff);
+    rhs[j] = tau - c - bd.damping * s.v[v0 + j];
+    int p = bd.parent >= 0 ? bd.parent - b0 : -1;
+    if (p >= 0) { ft[p] = ft[p] + ft[j]; nt[p] = nt[p] + nt[j]; }
+    M[j][j] += dt * bd.damping;
+  }
+  // -- Cholesky M~ = L L^T, then the explicit inverse L^-T L^-1 --
+  float L[kMaxTreeDof][kMaxTreeDof];
+  for (int j = 0; j < n; ++j) {
+    float d = M[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    d = sqrtf(fmaxf(d, 1e-30f));
+    L[j][j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      float t = M[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / d;
+    }
+  }
+  float Li[kMaxTreeDof][kMaxTreeDof];  // L^-1 (lower)
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) Li[i][j] = 0.f;
+    Li[j][j] = 1.f / L[j][j];
+    for (int i = j + 1; i < n; ++i) {
+      float t = 0.f;
+      for (int k = j; k < i; ++k) t += L[i][k] * Li[k][j];
+      Li[i][j] = -t / L[i][i];
+    }
+  }
+  float* mi = s.minv + (size_t)(&tr - (P.trees + sc.tree0)) * kMaxTreeDof * kMaxTreeDof;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      float t = 0.f;
+      for (int k = max(i, j); k < n; ++k) t += Li[k][i] * Li[k][j];
+      mi[i * kMaxTreeDof + j] = t;
+    }
+  // -- smooth velocity and body twists --
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    for (int j = 0; j < n; ++j) t += mi[i * kMaxTreeDof + j] * rhs[j];
+    s.vs[v0 + i] = s.v[v0 + i] + dt * t;
+  }
+  for (int j = 0; j < n; ++j) {
+    const DBody& bd = B[b0 + j];
+    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
+    f3 omp = mk3(0.f, 0.f, 0.f), vop = mk3(0.f, 0.f, 0.f), xp = mk3(0.f, 0.f, 0.f);
+    if (bd.parent >= 0) {
+      omp = ld3(s.bom + 3 * bd.parent);
+      vop = ld3(s.bvo + 3 * bd.parent);
+      xp = ld3(s.bx + 3 * bd.parent);
+    }
+    st3(s.bom + 3 * (b0 + j), omp + s.vs[v0 + j] * a);
+    st3(s.bvo + 3 * (b0 + j), vop + cross(omp, x - xp));
+  }
+}
+
+// trace of the translational point Jacobian of body b at world point p through M~^-1
+__device__ float artic_trace(const StepParams& P, const ArticView& s, const DScene& sc, int b, f3 p) {
+  const DBody* B = P.bodies + sc.body0;
+  const DBody& bd = B[b];
+  if (P.trace_mode) return 1.f / bd.mass;
+  const DTree& tr = P.trees[sc.tree0 + bd.tree];
+  if (tr.free) {
+    M33 R = ld33(s.bR + 9 * b);
+    f3 r = p - ld3(s.bx + 3 * b);
+    f3 l = mulT(R, r);
+    float i0 = 1.f / bd.inertia[0], i1 = 1.f / bd.inertia[1], i2 = 1.f / bd.inertia[2];
+    return 3.f / bd.mass + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
+  }
+  const float* mi = s.minv + (size_t)bd.tree * kMaxTreeDof * kMaxTreeDof;
+  int idx[kMaxTreeDof];
+  f3 cc[kMaxTreeDof];
+  int n = 0;
+  for (int a = b; a >= 0; a = B[a].parent) {
+    idx[n] = B[a].voff - tr.voff;
+    cc[n] = cross(ld3(s.bax + 3 * a), p - ld3(s.bx + 3 * a));
+    ++n;
+  }
+  float t = 0.f;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) t += mi[idx[i] * kMaxTreeDof + idx[j]] * dot(cc[i], cc[j]);
+  return t;
+}
+
+__device__ void artic_apply(const StepParams& P, ArticView& s, const DScene& sc, int b, f3 p, f3 f, f3 m) {
+  const DBody* B = P.bodies + sc.body0;
+  const DBody& bd = B[b];
+  const DTree& tr = P.trees[sc.tree0 + bd.tree];
+  if (tr.free) {
+    M33 R = ld33(s.bR + 9 * b);
+    f3 ang = mulT(R, cross(p - ld3(s.bx + 3 * b), f) + m);
+    unsigned long long* a = s.acc + bd.voff;
+    atomicAdd(a + 0, to_fix(f.x)); atomicAdd(a + 1, to_fix(f.y)); atomicAdd(a + 2, to_fix(f.z));
+    atomicAdd(a + 3, to_fix(ang.x)); atomicAdd(a + 4, to_fix(ang.y)); atomicAdd(a + 5, to_fix(ang.z));
+    return;
+  }
+  for (int a = b; a >= 0; a = B[a].parent) {
+    f3 ax = ld3(s.bax + 3 * a);
+    float gen = dot(ax, cross(p - ld3(s.bx + 3 * a), f) + m);
+    atomicAdd(s.acc + B[a].voff, to_fix(gen));
+  }
+}
+
+__device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world, int ga,
+                                           int gb, int sub, const Raw& k, bool plane, f3 px) {
+  const DGeom& GA = P.geoms[sc.geom0 + ga];
+  const DGeom& GB = P.geoms[sc.geom0 + gb];
+  const int ba = GA.body, bb = GB.body;
+  f3 t1, t2;
+  contact_frame(k.n, plane, px, t1, t2);
+  f3 oma = ld3(s.bom + 3 * ba);
+  f3 vc = ld3(s.bvo + 3 * ba) + cross(oma, k.p - ld3(s.bx + 3 * ba));
+  f3 wc = oma;
+  float tr = artic_trace(P, s, sc, ba, k.p);
+  if (bb >= 0) {
+    f3 omb = ld3(s.bom + 3 * bb);
+    vc = vc - (ld3(s.bvo + 3 * bb) + cross(omb, k.p - ld3(s.bx + 3 * bb)));
+    wc = wc - omb;
+    tr += artic_trace(P, s, sc, bb, k.p);
+  }
+  float r = solimp_r(P, fabsf(k.phi));
+  float mphi = r / (1.f - r) / tr;
+  float w[6];
+  facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                 P.k_user * mphi, P.d_user * mphi, fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]),
+                 fmaxf(GA.mu[2], GB.mu[2]), w);
+  f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
+  f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
+  artic_apply(P, s, sc, ba, k.p, f, m);
+  if (bb >= 0) artic_apply(P, s, sc, bb, k.p, -f, -m);
+  atomicAdd(s.count, 1);
+  if (P.capture_cap > 0)
+    capture_contact(P, world, s.count, sc.geom0 + ga, sc.geom0 + gb, sub, k.phi, k.p, k.n, w[0], mphi);
+}
+
+// narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
+__device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
+  int ga = code >> 16, gb = code & 0xffff;
+  const DGeom* G = P.geoms + sc.geom0;
+  int ta = G[ga].type, tb = G[gb].type;
+  if (ta == CF_GEOM_PLANE) { int t = ga; ga = gb; gb = t; t = ta; ta = tb; tb = t; }
+  f3 ca = ld3(s.gc + 3 * ga), cb = ld3(s.gc + 3 * gb);
+  M33 Ra = ld33(s.gR + 9 * ga), Rb = ld33(s.gR + 9 * gb);
+  const float* sa = G[ga].size;
+  const float* sb = G[gb].size;
+  if (tb == CF_GEOM_PLANE) {
+    f3 nz = col(Rb, 2), px = col(Rb, 0);
+    if (ta == CF_GEOM_SPHERE) {
+      Raw k = nf_sphere_plane(ca, sa[0], cb, nz);
+      if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, 0, k, true, px);
+    } else if (ta == CF_GEOM_CAPSULE) {
+      f3 ax = col(Ra, 2);
+      for (int e = 0; e < 2; ++e) {
+        Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
+        if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, e, k, true, px);
+      }
+    } else if (ta == CF_GEOM_BOX) {
+      for (int ci = 0; ci < 8; ++ci) {
+        f3 corner = ca + mul(Ra, mk3((ci & 4) ? sa[0] : -sa[0], (ci & 2) ? sa[1] : -sa[1], (ci & 1) ? sa[2] : -sa[2]));
+        Raw k = nf_sphere_plane(corner, 0.f, cb, nz);
+        if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, ci, k, true, px);
+      }
+    }
+    return;
+  }
+  Raw k;
+  k.phi = 3.0e38f;
+  if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
+    k = nf_sphere_sphere(ca, sa[0], cb, sb[0]);
+  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
+    f3 ua = col(Ra, 2), ub = col(Rb, 2);
+    f3 p1 = ca - sa[1] * ua, q1 = ca + sa[1] * ua, p2 = cb - sb[1] * ub, q2 = cb + sb[1] * ub;
+    float ss, tt;
+    nf_segments(p1, q1, p2, q2, ss, tt);
+    k = nf_sphere_sphere(p1 + ss * (q1 - p1), sa[0], p2 + tt * (q2 - p2), sb[0]);
+  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_SPHERE) {
+    f3 u = col(Ra, 2);
+    float t = fminf(fmaxf(dot(cb - ca, u), -sa[1]), sa[1]);
+    k = nf_sphere_sphere(ca + t * u, sa[0], cb, sb[0]);
+  } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CAPSULE) {
+    f3 u = col(Rb, 2);
+    float t = fminf(fmaxf(dot(ca - cb, u), -sb[1]), sb[1]);
+    k = nf_sphere_sphere(ca, sa[0], cb + t * u, sb[0]);
+  } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
+    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) return;
+    bool boxA = ta == CF_GEOM_BOX;
+    const M33& Rbx = boxA ? Ra : Rb;
+    f3 cbx = boxA ? ca : cb, co = boxA ? cb : ca;
+    const float* bs = boxA ? sa : sb;
+    const float* os = boxA ? sb : sa;
+    int to = boxA ? tb : ta;
+    f3 hs = mk3(bs[0], bs[1], bs[2]);
+    if (to == CF_GEOM_SPHERE) {
+      k = nf_sphere_box(co, os[0], cbx, Rbx, hs, !boxA);
+    } else {
+      f3 u = col(boxA ? Rb : Ra, 2);
+      float t = nf_capsule_box_param(mulT(Rbx, co - cbx), mulT(Rbx, u), os[1], hs);
+      k = nf_sphere_box(co + t * u, os[0], cbx, Rbx, hs, !boxA);
+    }
+  }
+  if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
+}
+
+__device__ void artic_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
+  const DWorld W = P.worlds[world];
+  const DScene sc = P.scenes[W.scene];
+  const int T = gwarps * 32;
+  const int tid = threadIdx.x - gid * T;
+  const int lane = threadIdx.x & 31, wig = tid >> 5;
+  ArticView s = artic_view(smem, sc, gwarps);
+  const DBody* B = P.bodies + sc.body0;
+  const DGeom* G = P.geoms + sc.geom0;
+  for (int i = tid; i < sc.nq; i += T) s.q[i] = P.q[W.qadr + i];
+  for (int i = tid; i < sc.nv; i += T) s.v[i] = P.v[W.vadr + i];
+  int* queue = s.queue + wig * kQueue;
+  const float dt = P.dt;
+
+  for (int step = 0; step < P.nsteps; ++step) {
+    group_sync(gid, T);
+    for (int t = tid; t < sc.ntree; t += T) artic_tree_prepare(P, s, sc, P.trees[sc.tree0 + t], W.uadr, step);
+    for (int i = tid; i < sc.nv; i += T) s.acc[i] = 0ull;
+    if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
+    group_sync(gid, T);
+    for (int g = tid; g < sc.ngeom; g += T) {
+      const DGeom& gd = G[g];
+      M33 Rl = quat_mat(gd.quat[0], gd.quat[1], gd.quat[2], gd.quat[3]);
+      f3 c;
+      M33 R;
+      if (gd.body >= 0) {
+        M33 Rb = ld33(s.bR + 9 * gd.body);
+        c = ld3(s.bx + 3 * gd.body) + mul(Rb, mk3(gd.pos[0], gd.pos[1], gd.pos[2]));
+        R = mul33(Rb, Rl);
+      } else {
+        c = mk3(gd.pos[0], gd.pos[1], gd.pos[2]);
+        R = Rl;
+      }
+      st3(s.gc + 3 * g, c);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s.gR[9 * g + k] = R.m[k];
+      s.gb[g] = gd.type == CF_GEOM_SPHERE ? gd.size[0]
+                : gd.type == CF_GEOM_CAPSULE ? gd.size[0] + gd.size[1]
+                : sqrtf(gd.size[0] * gd.size[0] + gd.size[1] * gd.size[1] + gd.size[2] * gd.size[2]);
+    }
+    group_sync(gid, T);
+    // ---- B. pair loop with per-warp compaction ----
+    int qn = 0;
+    for (int base = wig * 32; base < sc.npair; base += T) {
+      int k = base + lane;
+      int code = -1;
+      if (k < sc.npair) {
+        uint32_t pr = P.pairs[sc.pair0 + k];
+        int ga = pr >> 16, gb = pr & 0xffff;
+        bool pa = G[ga].type == CF_GEOM_PLANE, pb = G[gb].type == CF_GEOM_PLANE;
+        if (pa || pb) {
+          int gp = pa ? ga : gb, go = pa ? gb : ga;
+          f3 nz = mk3(s.gR[9 * gp + 2], s.gR[9 * gp + 5], s.gR[9 * gp + 8]);
+          float d = dot(nz, ld3(s.gc + 3 * go) - ld3(s.gc + 3 * gp));
+          if (d < s.gb[go] + P.margin) code = (int)pr;
+        } else {
+          f3 d = ld3(s.gc + 3 * ga) - ld3(s.gc + 3 * gb);
+          float rr = s.gb[ga] + s.gb[gb] + P.margin;
+          if (dot(d, d) < rr * rr) code = (int)pr;
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, code >= 0);
+      if (code >= 0) queue[qn + __popc(m & ((1u << lane) - 1u))] = code;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        artic_candidate(P, s, sc, world, queue[qn - 32 + lane]);
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    if (lane < qn) artic_candidate(P, s, sc, world, queue[lane]);
+    group_sync(gid, T);
+    // ---- C. correction and integration, per tree ----
+    for (int t = tid; t < sc.ntree; t += T) {
+      const DTree& tr = P.trees[sc.tree0 + t];
+      if (tr.free) {
+        const DBody& bd = B[tr.body0];
+        float* vb = s.v + bd.voff;
+        const float* vsb = s.vs + bd.voff;
+        float im = 1.f / bd.mass;
+        for (int k = 0; k < 3; ++k) vb[k] = vsb[k] + from_fix(s.acc[bd.voff + k]) * im;
+        for (int k = 0; k < 3; ++k) vb[3 + k] = vsb[3 + k] + from_fix(s.acc[bd.voff + 3 + k]) / bd.inertia[k];
+        float* qb = s.q + bd.qoff;
+        for (int k = 0; k < 3; ++k) qb[k] += vb[k] * dt;
+        float w0 = vb[3], w1 = vb[4], w2 = vb[5];
+        float wn = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+        float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
+        if (wn > 0.f) {
+          float sn, cs;
+          sincosf(0.5f * wn * dt, &sn, &cs);
+          float sc_ = sn / wn;
+          dq0 = cs; dq1 = sc_ * w0; dq2 = sc_ * w1; dq3 = sc_ * w2;
+        }
+        float a0 = qb[3], a1 = qb[4], a2 = qb[5], a3 = qb[6];
+        float n0 = a0 * dq0 - a1 * dq1 - a2 * dq2 - a3 * dq3;
+        float n1 = a0 * dq1 + a1 * dq0 + a2 * dq3 - a3 * dq2;
+        float n2 = a0 * dq2 - a1 * dq3 + a2 * dq0 + a3 * dq1;
+        float n3 = a0 * dq3 + a1 * dq2 - a2 * dq1 + a3 * dq0;
+        float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+        qb[3] = n0 * inv; qb[4] = n1 * inv; qb[5] = n2 * inv; qb[6] = n3 * inv;
+      } else {
+        const float* mi = s.minv + (size_t)t * kMaxTreeDof * kMaxTreeDof;
+        float pv[kMaxTreeDof];
+        for (int j = 0; j < tr.nv; ++j) pv[j] = from_fix(s.acc[tr.voff + j]);
+        for (int i = 0; i < tr.nv; ++i) {
+          float acc = 0.f;
+          for (int j = 0; j < tr.nv; ++j) acc += mi[i * kMaxTreeDof + j] * pv[j];
+          s.v[tr.voff + i] = s.vs[tr.voff + i] + acc;
+        }
+        for (int j = 0; j < tr.nbody; ++j) {
+          const DBody& bd = B[tr.body0 + j];
+          s.q[bd.qoff] += s.v[bd.voff] * dt;
+        }
+      }
+    }
+  }
+  group_sync(gid, T);
+  bool bad = false;
+  for (int i = tid; i < sc.nq; i += T) {
+    P.q[W.qadr + i] = s.q[i];
+    if (!isfinite(s.q[i])) bad = true;
+  }
+  for (int i = tid; i < sc.nv; i += T) {
+    P.v[W.vadr + i] = s.v[i];
+    if (!isfinite(s.v[i])) bad = true;
+  }
+  if (bad) {
+    atomicOr(P.flags + world, CF_FLAG_NONFINITE);
+    atomicOr(P.errword, CF_FLAG_NONFINITE);
+  }
+  if (tid == 0) {
+    P.ncontact[world] = s.count[0];
+    if (P.capture_cap > 0 && s.count[1] > P.capture_cap) {
+      atomicOr(P.flags + world, CF_FLAG_CONTACT_OVERFLOW);
+      atomicOr(P.errword, CF_FLAG_CONTACT_OVERFLOW);
+    }
+  }
+}
+
+// =======================================================================================
+// persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
+// kWarps / warps worlds, one per group of `warps` warps
+// =======================================================================================
+__global__ void __launch_bounds__(kBlock) step_kernel(StepParams P) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_unit;
+  const int warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(P.queue, 1);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= P.nunits) break;
+    const DUnit U = P.units[u];
+    const int gid = warp / U.warps;
+    if (gid < U.count) {
+      const int world = P.order[U.first + gid];
+      const DScene& sc = P.scenes[P.worlds[world].scene];
+      size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, U.warps)
+                           : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, U.warps);
+      float* base = smem + per * gid;
+      if (sc.pile) pile_world(P, base, world, gid, U.warps);
+      else artic_world(P, base, world, gid, U.warps);
+    }
+    __syncthreads();
+  }
+  // the last CTA to finish resets the work counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    int done = atomicAdd(P.queue + 1, 1);
+    if (done == (int)gridDim.x - 1) {
+      P.queue[0] = 0;
+      P.queue[1] = 0;
+      __threadfence();
+    }
+  }
+}
+
+size_t world_smem_bytes(const DScene& s, int warps) {
+  size_t f = s.pile ? pile_floats(s.nbody, s.nplane, warps) : artic_floats(s.nbody, s.ngeom, s.nq, s.nv, s.ntree, warps);
+  return f * sizeof(float);
+}
+
+static size_t g_max_dyn = 0;
+
+// opt in to the largest dynamic shared memory the device allows next to the static part
+static cudaError_t ensure_attr() {
+  if (g_max_dyn) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, step_kernel);
+  if (e != cudaSuccess) return e;
+  size_t dyn = (size_t)optin - fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) g_max_dyn = dyn;
+  return e;
+}
+
+size_t step_max_dynamic_smem() { return ensure_attr() == cudaSuccess ? g_max_dyn : 0; }
+
+cudaError_t launch_step(const StepParams& p, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e = ensure_attr();
+  if (e != cudaSuccess) return e;
+  if (smem > g_max_dyn) return cudaErrorInvalidValue;
+  step_kernel<<<grid, kBlock, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+int step_max_blocks_per_sm(size_t smem) {
+  if (ensure_attr() != cudaSuccess) return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel, kBlock, smem) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace cf

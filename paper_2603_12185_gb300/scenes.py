@@ -248,7 +248,7 @@ def make_spheres_on_plane(nworld=64, nbody=8, seed=0, radius=0.05, mass=1.0, mu=
                  {"workload": f"spheres_on_plane_{nworld}x{nbody}"})
 
 
-def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6):
+def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False):
     """Per-world sphere/capsule mixes placed without overlap of their bounding spheres.
 
     Random sequential deposition, vectorised across worlds: body k draws x, y uniformly inside
@@ -266,7 +266,7 @@ def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6):
         pos[:, k, 0] = -half + bk + 2 * (half - bk) * rng.random(nworld)
         pos[:, k, 1] = -half + bk + 2 * (half - bk) * rng.random(nworld)
         z = bk + np.maximum(box_h - 2 * bk, 0.0) * rng.random(nworld)
-        if k:
+        if k and not jammed:
             dxy2 = ((pos[:, :k, :2] - pos[:, k:k + 1, :2]) ** 2).sum(-1)
             lim = bound[:, :k] + bk[:, None]
             dz = np.sqrt(np.maximum(lim * lim - dxy2, 0.0))
@@ -300,18 +300,22 @@ PILE_PARAMS = dict(k_user=0.1, d_user=0.001, n_t=8, n_tor=2, n_rol=8)
 PILE_MU = (0.8, 0.005, 0.005)
 
 
-def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000):
+def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False):
     """Walled bins (floor + 4 walls at +-0.3 m) with a seeded 50/50 sphere/capsule mix.
 
     Spheres r ~ U[0.03, 0.06] m; capsules r = 0.03 m, half length ~ U[0.03, 0.08] m; density
     1000 kg/m^3; uniform random orientations; zero velocity; 6D cone with 8 tangential,
-    2 torsional and 8 rolling facets, mu = 0.8, torsional/rolling coefficients 0.005 m."""
+    2 torsional and 8 rolling facets, mu = 0.8, torsional/rolling coefficients 0.005 m.
+
+    jammed=True skips the overlap rejection: bodies start interpenetrating anywhere in the
+    0.6 m cube, so the very first step already resolves thousands of contacts per world (a
+    contact-rich input for single-step checks at full size)."""
     rng = np.random.default_rng(seed)
     pp, pq = _planes(True)
     t = _pile_template(f"pile{nbody}", nbody, pp, pq, PILE_MU)
-    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody)
+    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody, jammed=jammed)
     return Batch([t], Params(**PILE_PARAMS), np.zeros(nworld, np.int32), blocks, q0, v0, dt, nsteps,
-                 {"workload": f"pile_{nworld}x{nbody}"})
+                 {"workload": f"pile_{nworld}x{nbody}" + ("_jammed" if jammed else "")})
 
 
 # ----------------------------------------------------------------------------------------
