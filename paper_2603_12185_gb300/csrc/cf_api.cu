@@ -282,6 +282,8 @@ struct cf_batch {
   std::vector<DUnit> units;    // all worlds
   int nunits = 0;
   size_t smem_all = 0;
+  bool artic_all = false;
+  int variant = 0;             // pile kernel occupancy variant (autotuned)
   int nctrl = 0;
   int num_sms = 0;
   template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -366,15 +368,17 @@ extern "C" cf_status cf_batch_workspace_bytes(const cf_model* m, int32_t n_world
 
 // worlds of `list` grouped by scene into units of kWarps / warps worlds, units sorted by cost
 static void build_units(const cf_batch* b, const std::vector<int>& list, std::vector<int>& order,
-                        std::vector<DUnit>& units, size_t& smem) {
+                        std::vector<DUnit>& units, size_t& smem, bool& artic) {
   std::map<int, std::vector<int>> by_scene;
   for (int w : list) by_scene[b->worlds[w].scene].push_back(w);
   std::vector<std::pair<float, DUnit>> tmp;
   order.clear();
   smem = 0;
+  artic = false;
   for (auto& kv : by_scene) {
     int sidx = kv.first;
     const DScene& sc = b->model.scenes[sidx];
+    if (!sc.pile) artic = true;
     int wp = b->warps[sidx];
     int per = kWarps / wp;
     float cost = b->model.cost[sidx] / (float)wp;
@@ -398,7 +402,7 @@ static void build_units(const cf_batch* b, const std::vector<int>& list, std::ve
 static cf_status upload_units(cf_batch* b, cudaStream_t st) {
   std::vector<int> all(b->W), order;
   for (int w = 0; w < b->W; ++w) all[w] = w;
-  build_units(b, all, order, b->units, b->smem_all);
+  build_units(b, all, order, b->units, b->smem_all, b->artic_all);
   b->nunits = (int)b->units.size();
   if (b->smem_all > step_max_dynamic_smem())
     return fail(CF_ERR_UNSUPPORTED, "a work unit needs %zu bytes of shared memory", b->smem_all);
@@ -629,11 +633,11 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
   return p;
 }
 
-static cf_status launch(const cf_batch* b, StepParams& p, size_t smem, cudaStream_t s) {
+static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t smem, cudaStream_t s) {
   if (p.nunits <= 0) return CF_OK;
-  int per_sm = step_max_blocks_per_sm(smem);
+  int per_sm = step_max_blocks_per_sm(artic, b->variant, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
-  cudaError_t e = launch_step(p, grid, smem, s);
+  cudaError_t e = launch_step(p, artic, b->variant, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "step launch");
   return CF_OK;
 }
@@ -644,7 +648,7 @@ extern "C" cf_status cf_step(cf_batch* b, const int32_t* worlds, int32_t n, floa
   if (nsteps < 1) return fail(CF_ERR_INVALID_ARGUMENT, "nsteps must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
   StepParams p = make_params(b, dt, nsteps);
-  if (!worlds) return launch(b, p, b->smem_all, s);
+  if (!worlds) return launch(b, p, b->artic_all, b->smem_all, s);
   if (n < 0 || n > b->W) return fail(CF_ERR_INVALID_ARGUMENT, "bad world count %d", n);
   std::vector<int> list(worlds, worlds + n), seen(b->W, 0);
   for (int w : list) {
@@ -654,7 +658,8 @@ extern "C" cf_status cf_step(cf_batch* b, const int32_t* worlds, int32_t n, floa
   std::vector<int> order;
   std::vector<DUnit> units;
   size_t smem = 0;
-  build_units(b, list, order, units, smem);
+  bool artic = false;
+  build_units(b, list, order, units, smem, artic);
   if (units.empty()) return CF_OK;
   CF_CUDA(cudaMemcpyAsync(b->ws + b->L.sub_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s),
           "upload subset");
@@ -663,7 +668,7 @@ extern "C" cf_status cf_step(cf_batch* b, const int32_t* worlds, int32_t n, floa
   p.order = b->at<int>(b->L.sub_order);
   p.units = b->at<DUnit>(b->L.sub_units);
   p.nunits = (int)units.size();
-  cf_status st = launch(b, p, smem, s);
+  cf_status st = launch(b, p, artic, smem, s);
   // the host lists above are pageable: the copies completed before cudaMemcpyAsync returned
   return st;
 }
@@ -749,7 +754,8 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
       std::vector<int> order;
       std::vector<DUnit> units;
       size_t smem = 0;
-      build_units(b, list, order, units, smem);
+      bool artic = false;
+      build_units(b, list, order, units, smem, artic);
       if (smem > step_max_dynamic_smem()) continue;
       cudaMemcpyAsync(b->ws + b->L.sub_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(b->ws + b->L.sub_units, units.data(), sizeof(DUnit) * units.size(), cudaMemcpyHostToDevice, s);
@@ -757,10 +763,10 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
       p.order = b->at<int>(b->L.sub_order);
       p.units = b->at<DUnit>(b->L.sub_units);
       p.nunits = (int)units.size();
-      cf_status st = launch(b, p, smem, s);  // warm-up
+      cf_status st = launch(b, p, artic, smem, s);  // warm-up
       if (st != CF_OK) return st;
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) launch(b, p, smem, s);
+      for (int r = 0; r < 3; ++r) launch(b, p, artic, smem, s);
       cudaEventRecord(e1, s);
       CF_CUDA(cudaEventSynchronize(e1), "autotune timing");
       float ms = 0.f;
@@ -772,6 +778,29 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
     }
     b->warps[sc] = best_w;
     if (chosen) chosen[sc] = best_w;
+  }
+  // occupancy variant of the pile kernel, timed on the whole batch with the chosen warps
+  {
+    cf_status st = upload_units(b, s);
+    if (st != CF_OK) return st;
+    if (!b->artic_all) {
+      float best = 3e38f;
+      int best_v = 0;
+      for (int var = 0; var < kPileVariants; ++var) {
+        b->variant = var;
+        StepParams p = make_params(b, dt, 1);
+        st = launch(b, p, false, b->smem_all, s);
+        if (st != CF_OK) return st;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch(b, p, false, b->smem_all, s);
+        cudaEventRecord(e1, s);
+        CF_CUDA(cudaEventSynchronize(e1), "autotune timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_v = var; }
+      }
+      b->variant = best_v;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -792,8 +821,11 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
     return fail(CF_ERR_INVALID_ARGUMENT, "T = %d outside [1, min(grad_steps, max_ctrl_steps)]", T);
   if (!(dt > 0.f)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
   if (!dL_dqT || !dL_dvT || !dL_dq0 || !dL_dv0) return fail(CF_ERR_INVALID_ARGUMENT, "null gradient buffer");
-  for (const DScene& sc : b->model.scenes)
-    if (sc.pile) return fail(CF_ERR_UNSUPPORTED, "the adjoint covers articulated (non-pile) scenes only");
+  for (int w = 0; w < b->W; ++w) {
+    const char* why = nullptr;
+    if (!grad_scene_supported(b->model.scenes[b->worlds[w].scene], &why))
+      return fail(CF_ERR_UNSUPPORTED, "world %d: %s", w, why);
+  }
   StepParams p = make_params(b, dt, 1);
   GradArgs g{};
   g.T = T;
@@ -801,13 +833,15 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
   g.W = b->W;
   g.total_nq = b->total_nq;
   g.total_nv = b->total_nv;
+  g.total_nu = b->total_nu;
   g.tape = b->ws + b->L.grad;
   g.dqT = dL_dqT;
   g.dvT = dL_dvT;
   g.dq0 = dL_dq0;
   g.dv0 = dL_dv0;
-  g.dtau = dL_dtau;
+  g.dtau = b->total_nu > 0 ? dL_dtau : nullptr;
   g.num_sms = b->num_sms;
+  g.smem = b->smem_all;
   cudaError_t e = run_grad(p, g, b->nctrl, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return CF_OK;

@@ -70,6 +70,7 @@ struct StepParams {
   const float* ctrl;
   int total_nu;
   int nctrl;
+  int ctrl_offset;           // control slice of the launch's first step
   int* ncontact;
   int* flags;
   int* errword;
@@ -90,8 +91,12 @@ struct StepParams {
 // bytes of dynamic shared memory one world of a scene needs in the step kernel
 size_t world_smem_bytes(const DScene& s, int warps);
 
-cudaError_t launch_step(const StepParams& p, int grid, size_t smem, cudaStream_t stream);
-int step_max_blocks_per_sm(size_t smem);
+// artic = the launch contains worlds of non-pile scenes (selects the kernel instantiation);
+// variant 0..2 = pile-only kernel compiled for 2, 3 or 4 resident CTAs per SM
+constexpr int kStepVariants = 4;
+constexpr int kPileVariants = 3;
+cudaError_t launch_step(const StepParams& p, bool artic, int variant, int grid, size_t smem, cudaStream_t stream);
+int step_max_blocks_per_sm(bool artic, int variant, size_t smem);
 size_t step_max_dynamic_smem();
 
 }  // namespace cf

@@ -1,0 +1,623 @@
+// The learned MPPI proposal: a 3-layer MLP (in -> hidden -> hidden -> out, GELU) trained and
+// evaluated with BF16 operands and FP32 accumulation on the 5th-generation tensor cores.
+//
+// GEMM D[M x N] = A[M x K] . B[N x K]^T (both K-major BF16): per CTA a 128 x BN tile, TMA loads
+// of 128B-swizzled 64-wide K slices into a 4-stage shared-memory ring (mbarrier handshakes),
+// one thread issues tcgen05.mma (kind::f16, M=128, N=BN, K=16 per instruction) into a TMEM
+// accumulator, and four warps run the fused epilogue from tcgen05.ld (bias, GELU or its
+// derivative, BF16/FP32 stores).  Every mbarrier wait is bounded: a wait that gives up sets the
+// error word, the CTA skips its remaining work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "comfree.h"
+#include "cf_internal.cuh"
+
+namespace cf {
+namespace mlp {
+
+constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+enum Epi { EPI_BIAS_GELU = 0, EPI_BIAS_F32 = 1, EPI_F32 = 2, EPI_GELU_BWD = 3 };
+
+struct EpiArgs {
+  const float* bias;        // [N] (EPI_BIAS_*)
+  __nv_bfloat16* out_bf16;  // [M x ldo] activations (GELU) or gradients (GELU_BWD)
+  __nv_bfloat16* out_z;     // [M x ldo] pre-activation (EPI_BIAS_GELU)
+  const __nv_bfloat16* z;   // [M x ldo] pre-activation read by EPI_GELU_BWD
+  float* out_f32;           // [M x ldo] (EPI_BIAS_F32, EPI_F32)
+  int ldo;
+  int m_valid;              // rows >= m_valid are not stored
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// bounded wait on the phase with the given parity; false = gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t addr = smem_u32(bar);
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused by swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // 128B swizzle
+  return d;
+}
+
+// instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                   const __grid_constant__ CUtensorMap tmB, EpiArgs ep, int K) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = K / BK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(&done, 1);
+    s_ok = 1;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_bf16(BM, BN);
+
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    const int pre = nk < STAGES ? nk : STAGES;
+    for (int s = 0; s < pre; ++s) {
+      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      tma_load_2d(sA + s * A_BYTES, &tmA, s * BK, m0, &full[s]);
+      tma_load_2d(sB + s * B_BYTES, &tmB, s * BK, n0, &full[s]);
+    }
+    for (int k = 0; k < nk && ok; ++k) {
+      const int s = k % STAGES;
+      const uint32_t par = (k / STAGES) & 1;
+      if (!mbar_wait(&full[s], par)) { ok = false; break; }
+      tc_fence_after();
+      const uint64_t da = smem_desc(smem_u32(sA + s * A_BYTES));
+      const uint64_t db = smem_desc(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (k | kk) ? 1u : 0u);
+      umma_commit(&empty[s]);
+      if (k + STAGES < nk) {
+        if (!mbar_wait(&empty[s], par)) { ok = false; break; }
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        tma_load_2d(sA + s * A_BYTES, &tmA, (k + STAGES) * BK, m0, &full[s]);
+        tma_load_2d(sB + s * B_BYTES, &tmB, (k + STAGES) * BK, n0, &full[s]);
+      }
+    }
+    if (ok) {
+      umma_commit(&done);
+    } else {
+      s_ok = 0;
+      atomicOr(ep.err, CF_FLAG_TIMEOUT);
+      mbar_arrive(&done);
+    }
+  }
+  __syncwarp();
+  bool ok = mbar_wait(&done, 0);
+  tc_fence_after();
+  if (!ok && lane == 0) atomicOr(ep.err, CF_FLAG_TIMEOUT);
+  if (ok && s_ok) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(tbase + c, v);
+      if (row < ep.m_valid) {
+        const int n = n0 + c;
+        const size_t o = (size_t)row * ep.ldo + n;
+        if (EPI == EPI_BIAS_GELU) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            float z0 = v[i] + ep.bias[n + i], z1 = v[i + 1] + ep.bias[n + i + 1];
+            *reinterpret_cast<__nv_bfloat162*>(ep.out_z + o + i) = __floats2bfloat162_rn(z0, z1);
+            *reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o + i) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+          }
+        } else if (EPI == EPI_BIAS_F32) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) ep.out_f32[o + i] = v[i] + ep.bias[n + i];
+        } else if (EPI == EPI_F32) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) ep.out_f32[o + i] = v[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            float g0 = v[i] * gelu_grad(__bfloat162float(ep.z[o + i]));
+            float g1 = v[i + 1] * gelu_grad(__bfloat162float(ep.z[o + i + 1]));
+            *reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o + i) = __floats2bfloat162_rn(g0, g1);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------------------
+// features [B x fin] fp32 -> [Bp x kin] bf16, zero padded in both directions
+__global__ void pack_input(const float* x, int B, int fin, int Bp, int kin, __nv_bfloat16* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp * kin) return;
+  int r = i / kin, c = i % kin;
+  out[i] = __float2bfloat16_rn(r < B && c < fin ? x[(size_t)r * fin + c] : 0.f);
+}
+
+// out[c][r] = in[r][c] for a [R x C] bf16 matrix (32 x 32 tiles through shared memory)
+__global__ void transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int r = r0 + k, c = c0 + threadIdx.x;
+    t[k][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < C && r < R) out[(size_t)c * R + r] = t[threadIdx.x][k];
+  }
+}
+
+// Gaussian negative log-likelihood of targets a under mean mu = y[:, :D] and log-std
+// s = clamp(y[:, D:], lo, hi):  l = sum_d ((a - mu)^2 / (2 e^{2s}) + s) / (B D).
+// Writes dL/dy as bf16 into dy [Bp x 2D] (zero rows past B) and accumulates the loss.
+__global__ void nll_grad(const float* y, const float* a, int B, int Bp, int D, float lo, float hi, __nv_bfloat16* dy,
+                         float* loss) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < Bp * D) {
+    int r = i / D, d = i % D;
+    float gmu = 0.f, gs = 0.f;
+    if (r < B) {
+      float mu = y[(size_t)r * 2 * D + d], sr = y[(size_t)r * 2 * D + D + d];
+      float s = fminf(fmaxf(sr, lo), hi);
+      float e = a[(size_t)r * D + d] - mu;
+      float iv = expf(-2.f * s);
+      float inv_n = 1.f / ((float)B * (float)D);
+      l = (0.5f * e * e * iv + s) * inv_n;
+      gmu = -e * iv * inv_n;
+      gs = (sr > lo && sr < hi) ? (1.f - e * e * iv) * inv_n : 0.f;
+    }
+    dy[(size_t)r * 2 * D + d] = __float2bfloat16_rn(gmu);
+    dy[(size_t)r * 2 * D + D + d] = __float2bfloat16_rn(gs);
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l);
+}
+
+// db[n] = sum_r g[r][n] (fp32 accumulation of bf16 gradients), one thread per column
+__global__ void bias_grad(const __nv_bfloat16* g, int R, int N, float* db) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int r = 0; r < R; ++r) s += __bfloat162float(g[(size_t)r * N + n]);
+  db[n] = s;
+}
+
+// Adam on the fp32 master weights; refreshes the bf16 copy (and its transpose when given)
+__global__ void adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, float c1,
+                     float c2, __nv_bfloat16* wb, __nv_bfloat16* wt, int rows, int cols) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  if (wb) wb[i] = __float2bfloat16_rn(wi);
+  if (wt) {
+    int r = i / cols, c = i % cols;
+    wt[(size_t)c * rows + r] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void to_bf16(const float* w, int n, __nv_bfloat16* wb, __nv_bfloat16* wt, int rows, int cols) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  wb[i] = __float2bfloat16_rn(w[i]);
+  if (wt) {
+    int r = i / cols, c = i % cols;
+    wt[(size_t)c * rows + r] = __float2bfloat16_rn(w[i]);
+  }
+}
+
+}  // namespace mlp
+}  // namespace cf
+
+// =======================================================================================
+// host side
+// =======================================================================================
+using namespace cf::mlp;
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+thread_local char g_mlp_err[256];
+
+cf_status mfail(cf_status s, const char* msg) {
+  snprintf(g_mlp_err, sizeof(g_mlp_err), "%s", msg);
+  return s;
+}
+
+bool get_encoder() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  return true;
+}
+
+// 2D bf16 tensor map of a row-major [rows x cols] matrix, box = 64 columns x box_rows rows
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t gemm_smem(int BN) { return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024; }
+
+template <int BN, int EPI>
+cudaError_t gemm_launch(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem(BN));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(N / BN, M / BM);
+  gemm_kernel<BN, EPI><<<grid, 128, gemm_smem(BN), s>>>(ta, tb, ep, K);
+  return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s) {
+  if (M % BM || K % BK || N % 64) return cudaErrorInvalidValue;
+  if (N % 128 == 0) return gemm_launch<128, EPI>(A, M, B, N, K, ep, s);
+  return gemm_launch<64, EPI>(A, M, B, N, K, ep, s);
+}
+
+inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+struct cf_mlp {
+  int fin, kin, H, O, maxB, Bp_max;
+  char* ws;
+  // fp32 master parameters and Adam moments, contiguous: W1 b1 W2 b2 W3 b3
+  float *w, *g, *m, *v;
+  size_t nparam;
+  size_t oW1, ob1, oW2, ob2, oW3, ob3;
+  __nv_bfloat16 *W1b, *W2b, *W3b, *W2t, *W3t;
+  __nv_bfloat16 *X0, *Z1, *H1, *Z2, *H2, *dY, *dA2, *dA1, *dYt, *H2t, *dA2t, *H1t, *dA1t, *X0t;
+  float *Y, *loss;
+  int* err;
+  long step;
+};
+
+static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
+  int kin = (fin + 63) / 64 * 64;
+  int Bp = (maxB + 127) / 128 * 128;
+  size_t np = (size_t)H * kin + H + (size_t)H * H + H + (size_t)O * H + O;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = al(off + bytes); return r; };
+  size_t o_w = take(np * 4), o_g = take(np * 4), o_m = take(np * 4), o_v = take(np * 4);
+  size_t o_W1b = take((size_t)H * kin * 2), o_W2b = take((size_t)H * H * 2), o_W3b = take((size_t)O * H * 2);
+  size_t o_W2t = take((size_t)H * H * 2), o_W3t = take((size_t)O * H * 2);
+  size_t o_X0 = take((size_t)Bp * kin * 2), o_Z1 = take((size_t)Bp * H * 2), o_H1 = take((size_t)Bp * H * 2);
+  size_t o_Z2 = take((size_t)Bp * H * 2), o_H2 = take((size_t)Bp * H * 2), o_dY = take((size_t)Bp * O * 2);
+  size_t o_dA2 = take((size_t)Bp * H * 2), o_dA1 = take((size_t)Bp * H * 2), o_dYt = take((size_t)Bp * O * 2);
+  size_t o_H2t = take((size_t)Bp * H * 2), o_dA2t = take((size_t)Bp * H * 2), o_H1t = take((size_t)Bp * H * 2);
+  size_t o_dA1t = take((size_t)Bp * H * 2), o_X0t = take((size_t)Bp * kin * 2);
+  size_t o_Y = take((size_t)Bp * O * 4), o_loss = take(16), o_err = take(16);
+  if (m) {
+    char* b = m->ws;
+    m->fin = fin; m->kin = kin; m->H = H; m->O = O; m->maxB = maxB; m->Bp_max = Bp;
+    m->nparam = np;
+    m->w = (float*)(b + o_w); m->g = (float*)(b + o_g); m->m = (float*)(b + o_m); m->v = (float*)(b + o_v);
+    m->oW1 = 0; m->ob1 = m->oW1 + (size_t)H * kin; m->oW2 = m->ob1 + H; m->ob2 = m->oW2 + (size_t)H * H;
+    m->oW3 = m->ob2 + H; m->ob3 = m->oW3 + (size_t)O * H;
+    m->W1b = (__nv_bfloat16*)(b + o_W1b); m->W2b = (__nv_bfloat16*)(b + o_W2b); m->W3b = (__nv_bfloat16*)(b + o_W3b);
+    m->W2t = (__nv_bfloat16*)(b + o_W2t); m->W3t = (__nv_bfloat16*)(b + o_W3t);
+    m->X0 = (__nv_bfloat16*)(b + o_X0); m->Z1 = (__nv_bfloat16*)(b + o_Z1); m->H1 = (__nv_bfloat16*)(b + o_H1);
+    m->Z2 = (__nv_bfloat16*)(b + o_Z2); m->H2 = (__nv_bfloat16*)(b + o_H2); m->dY = (__nv_bfloat16*)(b + o_dY);
+    m->dA2 = (__nv_bfloat16*)(b + o_dA2); m->dA1 = (__nv_bfloat16*)(b + o_dA1); m->dYt = (__nv_bfloat16*)(b + o_dYt);
+    m->H2t = (__nv_bfloat16*)(b + o_H2t); m->dA2t = (__nv_bfloat16*)(b + o_dA2t); m->H1t = (__nv_bfloat16*)(b + o_H1t);
+    m->dA1t = (__nv_bfloat16*)(b + o_dA1t); m->X0t = (__nv_bfloat16*)(b + o_X0t);
+    m->Y = (float*)(b + o_Y); m->loss = (float*)(b + o_loss); m->err = (int*)(b + o_err);
+  }
+  return off;
+}
+
+static bool mlp_dims_ok(int fin, int H, int O) {
+  return fin >= 1 && fin <= 256 && H >= 64 && H <= 1024 && H % 128 == 0 && O >= 128 && O <= 4096 && O % 256 == 0;
+}
+
+extern "C" cf_status cf_mlp_workspace_bytes(int32_t fin, int32_t hidden, int32_t fout, int32_t max_batch, size_t* bytes) {
+  if (!bytes || !mlp_dims_ok(fin, hidden, fout) || max_batch < 1 || max_batch > (1 << 20))
+    return mfail(CF_ERR_INVALID_ARGUMENT, "mlp dims: 1 <= in <= 256, hidden % 128 == 0, out % 256 == 0");
+  *bytes = mlp_layout(fin, hidden, fout, max_batch, nullptr);
+  return CF_OK;
+}
+
+static void upd_bf16(cf_mlp* m, cudaStream_t s) {
+  auto go = [&](size_t off, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wt) {
+    int n = rows * cols;
+    to_bf16<<<(n + 255) / 256, 256, 0, s>>>(m->w + off, n, wb, wt, rows, cols);
+  };
+  go(m->oW1, m->H, m->kin, m->W1b, nullptr);
+  go(m->oW2, m->H, m->H, m->W2b, m->W2t);
+  go(m->oW3, m->O, m->H, m->W3b, m->W3t);
+}
+
+extern "C" cf_status cf_mlp_create(int32_t fin, int32_t hidden, int32_t fout, int32_t max_batch, const float* params,
+                                   void* device_workspace, size_t bytes, void* stream, cf_mlp** out) {
+  size_t need = 0;
+  cf_status st = cf_mlp_workspace_bytes(fin, hidden, fout, max_batch, &need);
+  if (st != CF_OK) return st;
+  if (!out || !device_workspace || bytes < need || (reinterpret_cast<uintptr_t>(device_workspace) & 255))
+    return mfail(CF_ERR_INVALID_ARGUMENT, "mlp workspace missing, too small or not 256-byte aligned");
+  if (!params) return mfail(CF_ERR_INVALID_ARGUMENT, "initial parameters required");
+  if (!get_encoder()) return mfail(CF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cf_mlp* m = new (std::nothrow) cf_mlp();
+  if (!m) return mfail(CF_ERR_OUT_OF_MEMORY, "mlp allocation");
+  m->ws = static_cast<char*>(device_workspace);
+  mlp_layout(fin, hidden, fout, max_batch, m);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(m->ws, 0, need, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->w, params, m->nparam * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    upd_bf16(m, s);
+    e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) {
+    delete m;
+    return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  m->step = 0;
+  *out = m;
+  return CF_OK;
+}
+
+extern "C" void cf_mlp_destroy(cf_mlp* m) { delete m; }
+
+extern "C" cf_status cf_mlp_param_count(const cf_mlp* m, int64_t* n) {
+  if (!m || !n) return mfail(CF_ERR_INVALID_ARGUMENT, "null argument");
+  *n = (int64_t)m->nparam;
+  return CF_OK;
+}
+
+static cf_status forward(cf_mlp* m, const float* x, int B, cudaStream_t s) {
+  const int Bp = (B + 127) / 128 * 128;
+  int n = Bp * m->kin;
+  pack_input<<<(n + 255) / 256, 256, 0, s>>>(x, B, m->fin, Bp, m->kin, m->X0);
+  EpiArgs e1{};
+  e1.bias = m->w + m->ob1; e1.out_bf16 = m->H1; e1.out_z = m->Z1; e1.ldo = m->H; e1.m_valid = Bp; e1.err = m->err;
+  cudaError_t e = gemm<EPI_BIAS_GELU>(m->X0, Bp, m->W1b, m->H, m->kin, e1, s);
+  EpiArgs e2 = e1;
+  e2.bias = m->w + m->ob2; e2.out_bf16 = m->H2; e2.out_z = m->Z2;
+  if (e == cudaSuccess) e = gemm<EPI_BIAS_GELU>(m->H1, Bp, m->W2b, m->H, m->H, e2, s);
+  EpiArgs e3{};
+  e3.bias = m->w + m->ob3; e3.out_f32 = m->Y; e3.ldo = m->O; e3.m_valid = Bp; e3.err = m->err;
+  if (e == cudaSuccess) e = gemm<EPI_BIAS_F32>(m->H2, Bp, m->W3b, m->O, m->H, e3, s);
+  if (e != cudaSuccess) return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
+  return CF_OK;
+}
+
+extern "C" cf_status cf_mlp_forward(cf_mlp* m, const float* x, int32_t B, float* y, void* stream) {
+  if (!m || !x || !y || B < 1 || B > m->maxB) return mfail(CF_ERR_INVALID_ARGUMENT, "bad mlp forward arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cf_status st = forward(m, x, B, s);
+  if (st != CF_OK) return st;
+  if (cudaMemcpyAsync(y, m->Y, (size_t)B * m->O * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return mfail(CF_ERR_CUDA, "copy out");
+  return CF_OK;
+}
+
+// gradients of the Gaussian NLL into m->g (fp32, parameter layout); loss into m->loss
+static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float hi, cudaStream_t s) {
+  const int Bp = (B + 127) / 128 * 128, H = m->H, O = m->O, D = O / 2;
+  cudaMemsetAsync(m->loss, 0, 4, s);
+  int n = Bp * D;
+  nll_grad<<<(n + 255) / 256, 256, 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->loss);
+  dim3 tb(32, 8);
+  auto T = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
+    transpose_bf16<<<dim3((C + 31) / 32, (R + 31) / 32), tb, 0, s>>>(in, R, C, out);
+  };
+  cudaError_t e = cudaSuccess;
+  // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 (times gelu'(Z2))
+  T(m->dY, Bp, O, m->dYt);
+  T(m->H2, Bp, H, m->H2t);
+  EpiArgs ew{};
+  ew.out_f32 = m->g + m->oW3; ew.ldo = H; ew.m_valid = O; ew.err = m->err;
+  e = gemm<EPI_F32>(m->dYt, O, m->H2t, H, Bp, ew, s);
+  bias_grad<<<(O + 127) / 128, 128, 0, s>>>(m->dY, Bp, O, m->g + m->ob3);
+  EpiArgs eb{};
+  eb.out_bf16 = m->dA2; eb.z = m->Z2; eb.ldo = H; eb.m_valid = Bp; eb.err = m->err;
+  if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dY, Bp, m->W3t, H, O, eb, s);
+  // layer 2
+  T(m->dA2, Bp, H, m->dA2t);
+  T(m->H1, Bp, H, m->H1t);
+  ew.out_f32 = m->g + m->oW2; ew.ldo = H; ew.m_valid = H;
+  if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA2t, H, m->H1t, H, Bp, ew, s);
+  bias_grad<<<(H + 127) / 128, 128, 0, s>>>(m->dA2, Bp, H, m->g + m->ob2);
+  eb.out_bf16 = m->dA1; eb.z = m->Z1;
+  if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dA2, Bp, m->W2t, H, H, eb, s);
+  // layer 1
+  T(m->dA1, Bp, H, m->dA1t);
+  T(m->X0, Bp, m->kin, m->X0t);
+  ew.out_f32 = m->g + m->oW1; ew.ldo = m->kin; ew.m_valid = H;
+  if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA1t, H, m->X0t, m->kin, Bp, ew, s);
+  bias_grad<<<(H + 127) / 128, 128, 0, s>>>(m->dA1, Bp, H, m->g + m->ob1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
+  return CF_OK;
+}
+
+extern "C" cf_status cf_mlp_gradients(cf_mlp* m, const float* x, const float* target, int32_t B, float logstd_lo,
+                                      float logstd_hi, float* grads, float* loss, void* stream) {
+  if (!m || !x || !target || B < 1 || B > m->maxB) return mfail(CF_ERR_INVALID_ARGUMENT, "bad mlp arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cf_status st = forward(m, x, B, s);
+  if (st == CF_OK) st = backward(m, target, B, logstd_lo, logstd_hi, s);
+  if (st != CF_OK) return st;
+  if (grads) cudaMemcpyAsync(grads, m->g, m->nparam * 4, cudaMemcpyDeviceToDevice, s);
+  if (loss) cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToDevice, s);
+  return CF_OK;
+}
+
+extern "C" cf_status cf_mlp_train_step(cf_mlp* m, const float* x, const float* target, int32_t B, float lr,
+                                       float logstd_lo, float logstd_hi, float* loss, void* stream) {
+  cf_status st = cf_mlp_gradients(m, x, target, B, logstd_lo, logstd_hi, nullptr, loss, stream);
+  if (st != CF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+  auto go = [&](size_t off, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wt) {
+    int n = rows * cols;
+    adam<<<(n + 255) / 256, 256, 0, s>>>(m->w + off, m->g + off, m->m + off, m->v + off, n, lr, b1, b2, eps, c1, c2, wb,
+                                         wt, rows, cols);
+  };
+  go(m->oW1, m->H, m->kin, m->W1b, nullptr);
+  go(m->ob1, 1, m->H, nullptr, nullptr);
+  go(m->oW2, m->H, m->H, m->W2b, m->W2t);
+  go(m->ob2, 1, m->H, nullptr, nullptr);
+  go(m->oW3, m->O, m->H, m->W3b, m->W3t);
+  go(m->ob3, 1, m->O, nullptr, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return mfail(CF_ERR_CUDA, "adam launch");
+  return CF_OK;
+}
+
+extern "C" cf_status cf_mlp_get_params(const cf_mlp* m, float* params, void* stream) {
+  if (!m || !params) return mfail(CF_ERR_INVALID_ARGUMENT, "null argument");
+  if (cudaMemcpyAsync(params, m->w, m->nparam * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+    return mfail(CF_ERR_CUDA, "copy params");
+  return CF_OK;
+}
+
+extern "C" cf_status cf_mlp_status(cf_mlp* m, void* stream) {
+  if (!m) return mfail(CF_ERR_INVALID_ARGUMENT, "null argument");
+  int w = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&w, m->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return mfail(CF_ERR_CUDA, "read mlp status");
+  if (w & CF_FLAG_TIMEOUT) return mfail(CF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
+  return CF_OK;
+}
+
+extern "C" const char* cf_mlp_last_error(void) { return g_mlp_err; }

@@ -20,7 +20,8 @@ __device__ __forceinline__ void group_sync(int gid, int nthreads) {
 
 __device__ __forceinline__ float ctrl_at(const StepParams& P, int step, int uadr, int uoff) {
   if (P.nctrl <= 0 || uoff < 0) return 0.f;
-  int slice = step < P.nctrl ? step : P.nctrl - 1;
+  int slice = P.ctrl_offset + step;
+  slice = slice < P.nctrl ? slice : P.nctrl - 1;
   return P.ctrl[(size_t)slice * P.total_nu + uadr + uoff];
 }
 
@@ -60,11 +61,13 @@ __device__ __forceinline__ void capture_contact(const StepParams& P, int world, 
 struct PileView {
   int N, NP;
   unsigned long long* acc;  // [6][N]
-  float *x, *y, *z, *qw, *qx, *qy, *qz;
+  float4* pb;               // [N] position (x, y, z) and bounding radius
+  float *qw, *qx, *qy, *qz;
   float* v;                 // [6][N]
   float* vs;                // [6][N]
   float* R;                 // [9][N]
-  float *invm, *I0, *I1, *I2, *rad, *hl, *bnd, *s2;
+  float *invm, *I0, *I1, *I2, *rad, *hl, *s2;  // I0..I2: inverse principal inertia
+  float *mu0, *mu1, *mu2;   // friction coefficients of the body's geom
   int* type;
   float* planes;            // [NP][12]
   int* queue;               // [warps][kQueue]
@@ -72,8 +75,8 @@ struct PileView {
 };
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
-  // acc (12 words/body) + 37 words/body + planes + queues + counters, 16-byte granules
-  size_t words = (size_t)N * 12 + (size_t)N * 37 + (size_t)NP * 12 + (size_t)warps * kQueue + 4;
+  // acc (12 words/body) + 40 words/body + planes + queues + counters, 16-byte granules
+  size_t words = (size_t)N * 12 + (size_t)N * 40 + (size_t)NP * 12 + (size_t)warps * kQueue + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -82,13 +85,14 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   s.N = N; s.NP = NP;
   s.acc = reinterpret_cast<unsigned long long*>(base);
   float* f = base + (size_t)N * 12;
-  s.x = f; f += N; s.y = f; f += N; s.z = f; f += N;
+  s.pb = reinterpret_cast<float4*>(f); f += 4 * (size_t)N;
   s.qw = f; f += N; s.qx = f; f += N; s.qy = f; f += N; s.qz = f; f += N;
   s.v = f; f += 6 * N;
   s.vs = f; f += 6 * N;
   s.R = f; f += 9 * N;
   s.invm = f; f += N; s.I0 = f; f += N; s.I1 = f; f += N; s.I2 = f; f += N;
-  s.rad = f; f += N; s.hl = f; f += N; s.bnd = f; f += N; s.s2 = f; f += N;
+  s.rad = f; f += N; s.hl = f; f += N; s.s2 = f; f += N;
+  s.mu0 = f; f += N; s.mu1 = f; f += N; s.mu2 = f; f += N;
   s.type = reinterpret_cast<int*>(f); f += N;
   s.planes = f; f += (size_t)NP * 12;
   s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
@@ -108,7 +112,7 @@ __device__ __forceinline__ float pile_trace(const StepParams& P, const PileView&
   float im = s.invm[i];
   if (P.trace_mode) return im;
   f3 l = mulT(R, r);
-  float i0 = 1.f / s.I0[i], i1 = 1.f / s.I1[i], i2 = 1.f / s.I2[i];
+  float i0 = s.I0[i], i1 = s.I1[i], i2 = s.I2[i];  // inverse principal inertia
   return 3.f * im + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
 }
 
@@ -123,12 +127,13 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, const M33& R, f3 
 }
 
 // one contact between body a and body b (b < 0: static plane with x axis px)
-__device__ __noinline__ void pile_contact(const StepParams& P, PileView& s, int world, int a, int b, int ga, int gb,
+__device__ __forceinline__ void pile_contact(const StepParams& P, PileView& s, int world, int a, int b, int ga, int gb,
                                           int sub, const Raw& k, bool plane, f3 px, const float* mu_b) {
   f3 t1, t2;
   contact_frame(k.n, plane, px, t1, t2);
   M33 Ra = pile_R(s, a);
-  f3 ra = k.p - mk3(s.x[a], s.y[a], s.z[a]);
+  float4 pa = s.pb[a];
+  f3 ra = k.p - mk3(pa.x, pa.y, pa.z);
   f3 wa = mul(Ra, mk3(s.vs[3 * s.N + a], s.vs[4 * s.N + a], s.vs[5 * s.N + a]));
   f3 vc = mk3(s.vs[a], s.vs[s.N + a], s.vs[2 * s.N + a]) + cross(wa, ra);
   f3 wc = wa;
@@ -138,18 +143,17 @@ __device__ __noinline__ void pile_contact(const StepParams& P, PileView& s, int 
   f3 rb;
   if (b >= 0) {
     Rb = pile_R(s, b);
-    rb = k.p - mk3(s.x[b], s.y[b], s.z[b]);
+    float4 pbb = s.pb[b];
+    rb = k.p - mk3(pbb.x, pbb.y, pbb.z);
     f3 wb = mul(Rb, mk3(s.vs[3 * s.N + b], s.vs[4 * s.N + b], s.vs[5 * s.N + b]));
     vc = vc - (mk3(s.vs[b], s.vs[s.N + b], s.vs[2 * s.N + b]) + cross(wb, rb));
     wc = wc - wb;
     tr += pile_trace(P, s, b, Rb, rb);
   }
-  // pair friction: the larger of the two geoms' coefficients (per-world geoms share the
-  // template's coefficients)
-  const DGeom& gA = P.geoms[ga];
-  mu_t = fmaxf(gA.mu[0], mu_b[0]);
-  mu_tor = fmaxf(gA.mu[1], mu_b[1]);
-  mu_rol = fmaxf(gA.mu[2], mu_b[2]);
+  // pair friction: the larger of the two geoms' coefficients
+  mu_t = fmaxf(s.mu0[a], mu_b[0]);
+  mu_tor = fmaxf(s.mu1[a], mu_b[1]);
+  mu_rol = fmaxf(s.mu2[a], mu_b[2]);
   float r = solimp_r(P, fabsf(k.phi));
   float mphi = r / (1.f - r) / tr;
   float w[6];
@@ -167,7 +171,8 @@ __device__ __noinline__ void pile_contact(const StepParams& P, PileView& s, int 
 __device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& sc, int world, int code) {
   int a = code >> 16, bc = code & 0xffff;
   int ta = s.type[a];
-  f3 ca = mk3(s.x[a], s.y[a], s.z[a]);
+  float4 pa4 = s.pb[a];
+  f3 ca = mk3(pa4.x, pa4.y, pa4.z);
   const int ga = sc.geom0 + a;
   if (bc & 0x8000) {
     int pi = bc & 0x7fff;
@@ -198,9 +203,10 @@ __device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& s
   }
   int b = bc;
   int tb = s.type[b];
-  f3 cb = mk3(s.x[b], s.y[b], s.z[b]);
+  float4 pb4 = s.pb[b];
+  f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   const int gb = sc.geom0 + b;
-  const float* mub = P.geoms[gb].mu;
+  const float mub[3] = {s.mu0[b], s.mu1[b], s.mu2[b]};
   Raw k;
   k.phi = 3.0e38f;
   if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
@@ -237,23 +243,6 @@ __device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& s
   if (k.phi < P.margin) pile_contact(P, s, world, a, b, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f), mub);
 }
 
-// decode body-body pair index k of N bodies: pairs (i, (i + o) mod N), o = 1..H, plus
-// (i, i + N/2) for i < N/2 when N is even; returns the ordered pair a < b
-__device__ __forceinline__ void pile_pair_decode(int k, int N, int& a, int& b) {
-  int H = (N - 1) >> 1;
-  int i, j;
-  if (k < N * H) {
-    i = k % N;
-    j = i + 1 + k / N;
-    if (j >= N) j -= N;
-  } else {
-    i = k - N * H;
-    j = i + (N >> 1);
-  }
-  a = min(i, j);
-  b = max(i, j);
-}
-
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -269,7 +258,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   // load state and per-world parameters
   for (int i = tid; i < N; i += T) {
     const float* qi = q + 7 * i;
-    s.x[i] = qi[0]; s.y[i] = qi[1]; s.z[i] = qi[2];
+    float px = qi[0], py = qi[1], pz = qi[2];
     s.qw[i] = qi[3]; s.qx[i] = qi[4]; s.qy[i] = qi[5]; s.qz[i] = qi[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) s.v[k * N + i] = v[6 * i + k];
@@ -285,9 +274,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       ty = (float)gd.type; r = gd.size[0]; h = gd.size[1]; s2 = gd.size[2];
     }
     int t = (int)ty;
-    s.invm[i] = 1.f / m; s.I0[i] = i0; s.I1[i] = i1; s.I2[i] = i2;
+    s.invm[i] = 1.f / m; s.I0[i] = 1.f / i0; s.I1[i] = 1.f / i1; s.I2[i] = 1.f / i2;
     s.type[i] = t; s.rad[i] = r; s.hl[i] = h; s.s2[i] = s2;
-    s.bnd[i] = t == CF_GEOM_SPHERE ? r : (t == CF_GEOM_CAPSULE ? r + h : sqrtf(r * r + h * h + s2 * s2));
+    s.pb[i] = make_float4(px, py, pz,
+                          t == CF_GEOM_SPHERE ? r : (t == CF_GEOM_CAPSULE ? r + h : sqrtf(r * r + h * h + s2 * s2)));
+    const DGeom& gd = P.geoms[sc.geom0 + i];
+    s.mu0[i] = gd.mu[0]; s.mu1[i] = gd.mu[1]; s.mu2[i] = gd.mu[2];
   }
   for (int pi = tid; pi < NP; pi += T) {
     PlaneDev pl = load_plane(P.geoms[sc.geom0 + sc.plane0 + pi]);
@@ -296,8 +288,6 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     o[6] = pl.x.x; o[7] = pl.x.y; o[8] = pl.x.z; o[9] = pl.mu[0]; o[10] = pl.mu[1]; o[11] = pl.mu[2];
   }
   const int H = (N - 1) >> 1;
-  const int nbb = N * H + ((N & 1) ? 0 : (N >> 1));
-  const int ncand = nbb + N * NP;
   const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
   int* queue = s.queue + wig * kQueue;
 
@@ -309,14 +299,14 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
 #pragma unroll
       for (int k = 0; k < 9; ++k) s.R[k * N + i] = R.m[k];
       float w0 = s.v[3 * N + i], w1 = s.v[4 * N + i], w2 = s.v[5 * N + i];
-      float i0 = s.I0[i], i1 = s.I1[i], i2 = s.I2[i];
-      f3 gy = cross(mk3(w0, w1, w2), mk3(i0 * w0, i1 * w1, i2 * w2));
+      float ii0 = s.I0[i], ii1 = s.I1[i], ii2 = s.I2[i];  // inverse principal inertia
+      f3 gy = cross(mk3(w0, w1, w2), mk3(w0 / ii0, w1 / ii1, w2 / ii2));
       s.vs[i] = s.v[i] + g.x * dt;
       s.vs[N + i] = s.v[N + i] + g.y * dt;
       s.vs[2 * N + i] = s.v[2 * N + i] + g.z * dt;
-      s.vs[3 * N + i] = w0 - dt * gy.x / i0;
-      s.vs[4 * N + i] = w1 - dt * gy.y / i1;
-      s.vs[5 * N + i] = w2 - dt * gy.z / i2;
+      s.vs[3 * N + i] = w0 - dt * gy.x * ii0;
+      s.vs[4 * N + i] = w1 - dt * gy.y * ii1;
+      s.vs[5 * N + i] = w2 - dt * gy.z * ii2;
 #pragma unroll
       for (int k = 0; k < 6; ++k) s.acc[k * N + i] = 0ull;
     }
@@ -326,34 +316,80 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     // ---- B. broadphase into per-warp queues, narrowphase + impulses on full warps ----
     int qn = 0;
     const float margin = P.margin;
-    for (int base = wig * 32; base < ncand; base += T) {
-      int k = base + lane;
-      int code = -1;
-      if (k < ncand) {
-        if (k < nbb) {
-          int a, b;
-          pile_pair_decode(k, N, a, b);
-          float dx = s.x[a] - s.x[b], dy = s.y[a] - s.y[b], dz = s.z[a] - s.z[b];
-          float rr = s.bnd[a] + s.bnd[b] + margin;
-          if (dx * dx + dy * dy + dz * dz < rr * rr) code = (a << 16) | b;
-        } else {
-          int kk = k - nbb;
-          int a = kk % N, pi = kk / N;
-          const float* pl = s.planes + 12 * pi;
-          float d = (s.x[a] - pl[0]) * pl[3] + (s.y[a] - pl[1]) * pl[4] + (s.z[a] - pl[2]) * pl[5];
-          if (d < s.bnd[a] + margin) code = (a << 16) | 0x8000 | pi;
-        }
-      }
+    auto push = [&](int code) {
       unsigned m = __ballot_sync(0xffffffffu, code >= 0);
       if (code >= 0) queue[qn + __popc(m & ((1u << lane) - 1u))] = code;
       qn += __popc(m);
-      __syncwarp();
       if (qn >= 32) {
+        __syncwarp();
         pile_candidate(P, s, sc, world, queue[qn - 32 + lane]);
         qn -= 32;
         __syncwarp();
       }
+    };
+    // body-body pairs (i, i + o mod N), o = 1..H: the work items (32-body chunk, offset) are
+    // split into one contiguous run per warp; each lane keeps its body i in registers
+    {
+      const int nchunk = (N + 31) >> 5;
+      const int items = nchunk * H;
+      const int per = (items + gwarps - 1) / gwarps;
+      int it = wig * per;
+      const int end = min(it + per, items);
+      if (it < end) {
+        int c = it / H;
+        int o = it - c * H + 1;
+        int i = (c << 5) + lane;
+        float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
+        for (; it < end; ++it) {
+          int code = -1;
+          if (i < N) {
+            int j = i + o;
+            if (j >= N) j -= N;
+            float4 pj = s.pb[j];
+            float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
+            float rr = pi4.w + pj.w;
+            if (dx * dx + dy * dy + dz * dz < rr * rr) code = (min(i, j) << 16) | max(i, j);
+          }
+          push(code);
+          if (++o > H) {
+            o = 1;
+            ++c;
+            i = (c << 5) + lane;
+            if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
+          }
+        }
+      }
     }
+    // the half-way pairs (i, i + N/2), i < N/2, of an even N
+    if (!(N & 1)) {
+      for (int base = wig * 32; base < (N >> 1); base += T) {
+        int i = base + lane, code = -1;
+        if (i < (N >> 1)) {
+          int j = i + (N >> 1);
+          float4 a4 = s.pb[i], b4 = s.pb[j];
+          float dx = a4.x - b4.x, dy = a4.y - b4.y, dz = a4.z - b4.z;
+          float rr = a4.w + b4.w + margin;
+          if (dx * dx + dy * dy + dz * dz < rr * rr) code = (i << 16) | j;
+        }
+        push(code);
+      }
+    }
+    // body-plane pairs
+    for (int pi = 0; pi < NP; ++pi) {
+      const float* pl = s.planes + 12 * pi;
+      const float ox = pl[0], oy = pl[1], oz = pl[2], nx = pl[3], ny = pl[4], nz = pl[5];
+      for (int base = wig * 32; base < N; base += T) {
+        int a = base + lane, code = -1;
+        if (a < N) {
+          float4 a4 = s.pb[a];
+          float d = (a4.x - ox) * nx + (a4.y - oy) * ny + (a4.z - oz) * nz;
+          if (d < a4.w + margin) code = (a << 16) | 0x8000 | pi;
+        }
+        push(code);
+      }
+    }
+    __syncwarp();
     if (lane < qn) pile_candidate(P, s, sc, world, queue[lane]);
     group_sync(gid, T);
 
@@ -363,12 +399,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       float v0 = s.vs[i] + from_fix(s.acc[i]) * im;
       float v1 = s.vs[N + i] + from_fix(s.acc[N + i]) * im;
       float v2 = s.vs[2 * N + i] + from_fix(s.acc[2 * N + i]) * im;
-      float w0 = s.vs[3 * N + i] + from_fix(s.acc[3 * N + i]) / s.I0[i];
-      float w1 = s.vs[4 * N + i] + from_fix(s.acc[4 * N + i]) / s.I1[i];
-      float w2 = s.vs[5 * N + i] + from_fix(s.acc[5 * N + i]) / s.I2[i];
+      float w0 = s.vs[3 * N + i] + from_fix(s.acc[3 * N + i]) * s.I0[i];
+      float w1 = s.vs[4 * N + i] + from_fix(s.acc[4 * N + i]) * s.I1[i];
+      float w2 = s.vs[5 * N + i] + from_fix(s.acc[5 * N + i]) * s.I2[i];
       s.v[i] = v0; s.v[N + i] = v1; s.v[2 * N + i] = v2;
       s.v[3 * N + i] = w0; s.v[4 * N + i] = w1; s.v[5 * N + i] = w2;
-      s.x[i] += v0 * dt; s.y[i] += v1 * dt; s.z[i] += v2 * dt;
+      s.pb[i].x += v0 * dt; s.pb[i].y += v1 * dt; s.pb[i].z += v2 * dt;
       float wn = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
       float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
       if (wn > 0.f) {
@@ -393,11 +429,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   bool bad = false;
   for (int i = tid; i < N; i += T) {
     float* qi = qo + 7 * i;
-    qi[0] = s.x[i]; qi[1] = s.y[i]; qi[2] = s.z[i];
+    float4 p4 = s.pb[i];
+    qi[0] = p4.x; qi[1] = p4.y; qi[2] = p4.z;
     qi[3] = s.qw[i]; qi[4] = s.qx[i]; qi[5] = s.qy[i]; qi[6] = s.qz[i];
 #pragma unroll
     for (int k = 0; k < 6; ++k) vo[6 * i + k] = s.v[k * N + i];
-    float chk = s.x[i] + s.y[i] + s.z[i] + s.qw[i] + s.v[i] + s.v[N + i] + s.v[2 * N + i] + s.v[3 * N + i] +
+    float chk = p4.x + p4.y + p4.z + s.qw[i] + s.v[i] + s.v[N + i] + s.v[2 * N + i] + s.v[3 * N + i] +
                 s.v[4 * N + i] + s.v[5 * N + i];
     if (!isfinite(chk)) bad = true;
   }
@@ -985,7 +1022,8 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
-__global__ void __launch_bounds__(kBlock) step_kernel(StepParams P) {
+template <bool kArtic, int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_unit;
   const int warp = threadIdx.x >> 5;
@@ -1002,7 +1040,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(StepParams P) {
       size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, U.warps)
                            : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, U.warps);
       float* base = smem + per * gid;
-      if (sc.pile) pile_world(P, base, world, gid, U.warps);
+      if (!kArtic || sc.pile) pile_world(P, base, world, gid, U.warps);
       else artic_world(P, base, world, gid, U.warps);
     }
     __syncthreads();
@@ -1024,37 +1062,54 @@ size_t world_smem_bytes(const DScene& s, int warps) {
   return f * sizeof(float);
 }
 
-static size_t g_max_dyn = 0;
+// kernel variants: pile-only with 2, 3 or 4 resident CTAs per SM (register budget), and the
+// mixed (articulated) instantiation
+using StepFn = void (*)(StepParams);
+static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2>, step_kernel<false, 3>, step_kernel<false, 4>,
+                                                step_kernel<true, 2>};
+static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0};
 
-// opt in to the largest dynamic shared memory the device allows next to the static part
-static cudaError_t ensure_attr() {
-  if (g_max_dyn) return cudaSuccess;
+static int variant_index(bool artic, int variant) { return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant)); }
+
+static cudaError_t ensure_attr(int vi) {
+  if (g_max_dyn[vi]) return cudaSuccess;
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, step_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kVariants[vi]);
   if (e != cudaSuccess) return e;
   size_t dyn = (size_t)optin - fa.sharedSizeBytes;
-  e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  if (e == cudaSuccess) g_max_dyn = dyn;
+  e = cudaFuncSetAttribute(kVariants[vi], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  // prefer the largest shared-memory carveout so several CTAs fit per SM
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kVariants[vi], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) g_max_dyn[vi] = dyn;
   return e;
 }
 
-size_t step_max_dynamic_smem() { return ensure_attr() == cudaSuccess ? g_max_dyn : 0; }
+size_t step_max_dynamic_smem() {
+  size_t m = 0;
+  for (int i = 0; i < kStepVariants; ++i) {
+    if (ensure_attr(i) != cudaSuccess) return 0;
+    m = (m == 0 || g_max_dyn[i] < m) ? g_max_dyn[i] : m;
+  }
+  return m;
+}
 
-cudaError_t launch_step(const StepParams& p, int grid, size_t smem, cudaStream_t stream) {
-  cudaError_t e = ensure_attr();
+cudaError_t launch_step(const StepParams& p, bool artic, int variant, int grid, size_t smem, cudaStream_t stream) {
+  int vi = variant_index(artic, variant);
+  cudaError_t e = ensure_attr(vi);
   if (e != cudaSuccess) return e;
-  if (smem > g_max_dyn) return cudaErrorInvalidValue;
-  step_kernel<<<grid, kBlock, smem, stream>>>(p);
+  if (smem > g_max_dyn[vi]) return cudaErrorInvalidValue;
+  kVariants[vi]<<<grid, kBlock, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
-int step_max_blocks_per_sm(size_t smem) {
-  if (ensure_attr() != cudaSuccess) return 1;
+int step_max_blocks_per_sm(bool artic, int variant, size_t smem) {
+  int vi = variant_index(artic, variant);
+  if (ensure_attr(vi) != cudaSuccess) return 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel, kBlock, smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kVariants[vi], kBlock, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 
