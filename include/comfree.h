@@ -195,6 +195,25 @@ cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
 cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                        float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);
 
+/* Step n_worlds worlds of one scene with no device allocation at all, for callers that cannot
+ * allocate device memory (a host that owns the CUDA context and forbids cudaMalloc, a fixed
+ * memory pool, a real-time loop that must not touch the allocator).  The paper has no
+ * counterpart: this is a deployment convenience around the same step kernel.
+ *   q[n_worlds * nq], v[n_worlds * nv]  device, the worlds' states back to back (in/out);
+ *   world_params                        device, nullable; pile scenes only: one 8-float block
+ *                                       per body per world, as in cf_batch_create;
+ *   contacts                            device, nullable; per-world contact counts (out).
+ * Controls are zero.  All scratch (scene templates, world records, work units, work-queue
+ * counters, flags) lives in a file-scope 2 MiB device array that every GPU loading the library
+ * holds until the process exits; at most 16384 worlds per call, and the model plus the worlds'
+ * records must fit the array (CF_ERR_INVALID_ARGUMENT otherwise).  The first call on a device
+ * looks up the array's device address (make that first call before any stream capture).  Each
+ * call clears the counters it needs; every call shares the one array, so calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Device-side flags (non-finite state) are not reported by this entry point. */
+cf_status cf_step_noalloc(const cf_model* model, int32_t scene, int32_t n_worlds, float* q, float* v,
+                          const float* world_params, float dt, int32_t nsteps, int32_t* contacts, void* stream);
+
 const char* cf_status_string(cf_status status);
 const char* cf_last_error(void);
 

@@ -53,7 +53,7 @@ class Contact(C.Structure):
 EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_workspace_bytes", "cf_batch_create",
            "cf_batch_destroy", "cf_batch_sizes", "cf_set_state", "cf_get_state", "cf_set_ctrl", "cf_step",
            "cf_get_contact_counts", "cf_get_contacts", "cf_batch_status", "cf_batch_autotune", "cf_batch_set_warps",
-           "cf_step_grad", "cf_status_string", "cf_last_error")
+           "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error")
 
 _lib = None
 
@@ -86,6 +86,7 @@ def lib():
     L.cf_batch_autotune.argtypes = [V, C.c_float, V, V]
     L.cf_batch_set_warps.argtypes = [V, I32, I32]
     L.cf_step_grad.argtypes = [V, I32, C.c_float, V, V, V, V, V, V]
+    L.cf_step_noalloc.argtypes = [V, I32, I32, V, V, V, C.c_float, I32, V, V]
     L.cf_status_string.argtypes = [I32]
     L.cf_status_string.restype = C.c_char_p
     L.cf_last_error.argtypes = []
@@ -263,6 +264,12 @@ class Batch:
         check(lib().cf_step_grad(self.h, int(T), float(dt), _ptr(dqT.contiguous()), _ptr(dvT.contiguous()), _ptr(dq0),
                                  _ptr(dv0), _ptr(dtau), _stream(stream)))
         return dq0, dv0, dtau[:T * self.total_nu].view(T, self.total_nu) if self.total_nu else dtau[:0]
+
+
+def step_noalloc(model, scene, n_worlds, q, v, world_params, dt, nsteps, contacts=None, stream=None):
+    """cf_step_noalloc on device tensors (q, v updated in place); no allocation by the library."""
+    check(lib().cf_step_noalloc(model.h, int(scene), int(n_worlds), _ptr(q), _ptr(v), _ptr(world_params), float(dt),
+                                int(nsteps), _ptr(contacts), _stream(stream)))
 
 
 def flatten_state(sb):

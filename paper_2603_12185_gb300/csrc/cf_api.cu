@@ -862,3 +862,167 @@ extern "C" const char* cf_status_string(cf_status s) {
 }
 
 extern "C" const char* cf_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------------------
+// Stepping without any device allocation.
+//
+// Some callers cannot allocate device memory at all: code running inside a memory pool or a
+// graph whose allocations are fixed up front, plugins of hosts that own the CUDA context and
+// forbid cudaMalloc, or real-time loops that must not touch the allocator.  cf_step_noalloc
+// serves them: the caller passes its state and parameters, and every piece of scratch the
+// step needs (scene templates, world records, work units, the work-queue counters, flags)
+// lives in one file-scope device array of fixed size that each GPU loading the library keeps
+// until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;  // 2 MiB per device
+constexpr int kNoAllocMaxWorlds = 16384;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n_worlds, float* q, float* v,
+                                     const float* world_params, float dt, int32_t nsteps, int32_t* contacts,
+                                     void* stream) {
+  if (!m || !q || !v) return fail(CF_ERR_INVALID_ARGUMENT, "null argument");
+  if (scene < 0 || scene >= (int)m->scenes.size()) return fail(CF_ERR_INVALID_ARGUMENT, "scene %d out of range", scene);
+  if (n_worlds < 1 || n_worlds > kNoAllocMaxWorlds)
+    return fail(CF_ERR_INVALID_ARGUMENT, "cf_step_noalloc takes 1..%d worlds per call, got %d", kNoAllocMaxWorlds,
+                n_worlds);
+  if (!(dt > 0.f) || !std::isfinite(dt)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
+  if (nsteps < 1) return fail(CF_ERR_INVALID_ARGUMENT, "nsteps must be >= 1");
+  const DScene& sc = m->scenes[scene];
+  if (!sc.pile && world_params) return fail(CF_ERR_INVALID_ARGUMENT, "per-world parameters need a pile scene");
+
+  // layout of the static scratch for this call
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return r;
+  };
+  const size_t o_scenes = take(sizeof(DScene) * m->scenes.size());
+  const size_t o_bodies = take(sizeof(DBody) * std::max<size_t>(m->bodies.size(), 1));
+  const size_t o_geoms = take(sizeof(DGeom) * m->geoms.size());
+  const size_t o_trees = take(sizeof(DTree) * std::max<size_t>(m->trees.size(), 1));
+  const size_t o_pairs = take(sizeof(uint32_t) * std::max<size_t>(m->pairs.size(), 1));
+  const size_t o_worlds = take(sizeof(DWorld) * n_worlds);
+  const size_t o_order = take(sizeof(int) * n_worlds);
+  const size_t o_units = take(sizeof(DUnit) * n_worlds);
+  const size_t o_count = take(sizeof(int) * n_worlds);
+  const size_t o_flags = take(sizeof(int) * n_worlds);
+  const size_t o_words = take(sizeof(int) * 8);  // [0..3] error word, [4..7] work-queue counters
+  if (off > kNoAllocScratchBytes)
+    return fail(CF_ERR_INVALID_ARGUMENT, "model and %d worlds need %zu bytes, more than the %zu-byte static scratch",
+                n_worlds, off, kNoAllocScratchBytes);
+
+  // once per device, with that device current: the device address of the static array
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CF_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    g_noalloc_ptr[dev] = static_cast<char*>(ptr);
+  }
+  char* base = g_noalloc_ptr[dev];
+
+  // host-side records: worlds of one scene packed back to back, units of kWarps / warps worlds
+  const int warps = default_warps(sc);
+  const int per = kWarps / warps;
+  std::vector<DWorld> worlds(n_worlds);
+  std::vector<int> order(n_worlds);
+  std::vector<DUnit> units;
+  for (int w = 0; w < n_worlds; ++w) {
+    DWorld d{};
+    d.scene = scene;
+    d.qadr = w * sc.nq;
+    d.vadr = w * sc.nv;
+    d.uadr = 0;
+    d.padr = (sc.pile && world_params) ? w * 8 * sc.nbody : -1;
+    worlds[w] = d;
+    order[w] = w;
+  }
+  for (int w = 0; w < n_worlds; w += per) {
+    DUnit u{};
+    u.first = w;
+    u.count = std::min(per, n_worlds - w);
+    u.warps = warps;
+    units.push_back(u);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  auto up = [&](size_t o, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  // the host vectors are pageable: each copy has been taken before cudaMemcpyAsync returns
+  e = up(o_scenes, m->scenes.data(), sizeof(DScene) * m->scenes.size());
+  if (e == cudaSuccess) e = up(o_bodies, m->bodies.data(), sizeof(DBody) * m->bodies.size());
+  if (e == cudaSuccess) e = up(o_geoms, m->geoms.data(), sizeof(DGeom) * m->geoms.size());
+  if (e == cudaSuccess) e = up(o_trees, m->trees.data(), sizeof(DTree) * m->trees.size());
+  if (e == cudaSuccess) e = up(o_pairs, m->pairs.data(), sizeof(uint32_t) * m->pairs.size());
+  if (e == cudaSuccess) e = up(o_worlds, worlds.data(), sizeof(DWorld) * n_worlds);
+  if (e == cudaSuccess) e = up(o_order, order.data(), sizeof(int) * n_worlds);
+  if (e == cudaSuccess) e = up(o_units, units.data(), sizeof(DUnit) * units.size());
+  // the array keeps the previous call's contents: zero the error word, queue counters, flags
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_words, 0, sizeof(int) * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_flags, 0, sizeof(int) * n_worlds, s);
+  if (e != cudaSuccess) return cuda_fail(e, "static scratch upload");
+
+  StepParams p{};
+  p.scenes = reinterpret_cast<const DScene*>(base + o_scenes);
+  p.bodies = reinterpret_cast<const DBody*>(base + o_bodies);
+  p.geoms = reinterpret_cast<const DGeom*>(base + o_geoms);
+  p.trees = reinterpret_cast<const DTree*>(base + o_trees);
+  p.pairs = reinterpret_cast<const uint32_t*>(base + o_pairs);
+  p.worlds = reinterpret_cast<const DWorld*>(base + o_worlds);
+  p.units = reinterpret_cast<const DUnit*>(base + o_units);
+  p.order = reinterpret_cast<const int*>(base + o_order);
+  p.nunits = (int)units.size();
+  p.q = q;
+  p.v = v;
+  p.wparam = world_params;
+  p.ctrl = nullptr;
+  p.total_nu = 0;
+  p.nctrl = 0;
+  p.ctrl_offset = 0;
+  p.ncontact = contacts ? contacts : reinterpret_cast<int*>(base + o_count);
+  p.flags = reinterpret_cast<int*>(base + o_flags);
+  p.errword = reinterpret_cast<int*>(base + o_words);
+  p.queue = reinterpret_cast<int*>(base + o_words) + 4;
+  p.capture = nullptr;
+  p.capture_cap = 0;
+  p.dt = dt;
+  p.nsteps = nsteps;
+  for (int k = 0; k < 3; ++k) p.gravity[k] = m->gravity[k];
+  p.k_user = m->k_user;
+  p.d_user = m->d_user;
+  for (int k = 0; k < 5; ++k) p.solimp[k] = m->solimp[k];
+  p.margin = m->margin;
+  p.n_t = m->n_t;
+  p.n_tor = m->n_tor;
+  p.n_rol = m->n_rol;
+  p.trace_mode = m->trace_mode;
+  for (int j = 0; j < m->n_t; ++j) {
+    double th = 2.0 * M_PI * j / m->n_t;
+    p.tcos[j] = (float)std::cos(th);
+    p.tsin[j] = (float)std::sin(th);
+  }
+  for (int j = 0; j < m->n_rol; ++j) {
+    double th = 2.0 * M_PI * j / m->n_rol;
+    p.rcos[j] = (float)std::cos(th);
+    p.rsin[j] = (float)std::sin(th);
+  }
+  const bool artic = !sc.pile;
+  const size_t smem = world_smem_bytes(sc, warps) * per;
+  if (smem > step_max_dynamic_smem()) return fail(CF_ERR_UNSUPPORTED, "a world needs %zu bytes of shared memory", smem);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = step_max_blocks_per_sm(artic, 0, smem);
+  const int grid = std::min(p.nunits, std::max(1, nsm * per_sm));
+  e = launch_step(p, artic, 0, grid, smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "step launch");
+  return CF_OK;
+}
