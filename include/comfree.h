@@ -195,6 +195,75 @@ cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
 cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                        float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Sampling MPC (MPPI) around the step, for the in-hand reorientation task of Sec. V.
+ * ------------------------------------------------------------------------------------- */
+/* Weights of the fused MPC cost (Sec. V, Eq. mpc and the running/terminal costs after it;
+ * the paper tunes its weights per object and does not print them).  With the cost set,
+ * every cf_step of an articulated world adds, per step, the running cost of the state at the
+ * start of the step:
+ *   w_quat (1 - (q*^T q)^2) + w_pos (|dx| + |dy| + |dz|) + w_contact sum_tips |p - p_tip|^2
+ *   + w_joint |q_hinge - q_ref|^2 + w_fallen [|p_xy - p*_xy| > fall_radius]
+ * and, after the last step, the terminal cost term_pos |p - p*|^2 + term_quat (1 - (q*^T q)^2).
+ * p, q: position and quaternion of free body `body`; tips: the +z ends of the capsules of leaf
+ * hinge bodies. */
+typedef struct {
+  int32_t body;
+  float w_quat, w_pos, w_contact, w_joint, w_fallen, fall_radius, term_pos, term_quat;
+} cf_cost_desc;
+/* goals[W][7] (target position, quaternion), qref[total_nq] (home pose) and costs[W] are device
+ * pointers borrowed until the cost is switched off (desc = NULL).  costs accumulate (+=). */
+cf_status cf_set_cost(cf_batch* batch, const cf_cost_desc* desc, const float* goals, const float* qref,
+                      float* costs);
+/* controls of N rollouts over H steps: sample k < n_prop ~ N(prop_mean, exp(prop_logstd)^2),
+ * the others ~ N(mean, sigma^2), clipped to [-limit, limit].  noise[N][H][nu] standard normals
+ * (caller-drawn); ctrl[H][N * nu] (the cf_set_ctrl layout for N worlds of nu actuators);
+ * samples[N][H][nu].  All device pointers. */
+cf_status cf_mppi_sample(int32_t N, int32_t H, int32_t nu, const float* mean, const float* noise, float sigma,
+                         float limit, const float* prop_mean, const float* prop_logstd, int32_t n_prop, float* ctrl,
+                         float* samples, void* stream);
+/* MPPI update: w_k = exp(-(J_k - min J) / lambda), mean = sum w_k U_k / sum w_k (N <= 16384);
+ * stats[3] (nullable) = min cost, mean cost, effective sample size. */
+cf_status cf_mppi_update(int32_t N, int32_t H, int32_t nu, const float* costs, const float* samples, float lambda,
+                         float* mean, float* stats, void* stream);
+/* receding horizon: mean[h] <- mean[h + 1] for h < H - 1 */
+cf_status cf_mppi_shift(int32_t H, int32_t nu, float* mean, void* stream);
+/* copy one world's state into W back-to-back worlds */
+cf_status cf_broadcast_state(const float* q0, const float* v0, int32_t nq, int32_t nv, int32_t W, float* q, float* v,
+                             void* stream);
+/* out = concat(q[nq], v[nv], goal[ngoal]): the proposal's input features */
+cf_status cf_mppi_features(const float* q, int32_t nq, const float* v, int32_t nv, const float* goal, int32_t ngoal,
+                           float* out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned proposal for sampling MPC: a 3-layer perceptron in -> hidden -> hidden -> out with
+ * GELU, BF16 operands and FP32 accumulation on the tensor cores (the paper's MPPI controller,
+ * Sec. V, samples around a warm start only; the learned proposal is this library's addition).
+ * Output = Gaussian over an action sequence: out/2 means followed by out/2 log-stds.
+ * Parameters are FP32, flat: W1[hidden][kin] b1[hidden] W2[hidden][hidden] b2[hidden]
+ * W3[out][hidden] b3[out], kin = in rounded up to a multiple of 64 (padding columns unused).
+ * Limits: 1 <= in <= 256, hidden % 128 == 0 (<= 1024), out % 256 == 0 (<= 4096).
+ * ------------------------------------------------------------------------------------- */
+typedef struct cf_mlp cf_mlp;
+cf_status cf_mlp_workspace_bytes(int32_t fin, int32_t hidden, int32_t fout, int32_t max_batch, size_t* bytes);
+/* params: device FP32 initial parameters (copied); workspace: caller-owned, 256-byte aligned */
+cf_status cf_mlp_create(int32_t fin, int32_t hidden, int32_t fout, int32_t max_batch, const float* params,
+                        void* device_workspace, size_t bytes, void* stream, cf_mlp** out);
+void cf_mlp_destroy(cf_mlp* mlp);
+cf_status cf_mlp_param_count(const cf_mlp* mlp, int64_t* n);
+/* y[B][out] = MLP(x[B][in]) (device pointers, FP32 in and out) */
+cf_status cf_mlp_forward(cf_mlp* mlp, const float* x, int32_t B, float* y, void* stream);
+/* Gradient of the mean Gaussian negative log-likelihood of target[B][out/2] under the output
+ * (log-stds clamped to [lo, hi]); grads[n_params] and loss[1] are device pointers (nullable). */
+cf_status cf_mlp_gradients(cf_mlp* mlp, const float* x, const float* target, int32_t B, float logstd_lo,
+                           float logstd_hi, float* grads, float* loss, void* stream);
+/* one Adam step (beta 0.9/0.999, eps 1e-8) on that loss */
+cf_status cf_mlp_train_step(cf_mlp* mlp, const float* x, const float* target, int32_t B, float lr, float logstd_lo,
+                            float logstd_hi, float* loss, void* stream);
+cf_status cf_mlp_get_params(const cf_mlp* mlp, float* params, void* stream);
+/* synchronise; CF_ERR_TIMEOUT if a tensor-core pipeline wait gave up */
+cf_status cf_mlp_status(cf_mlp* mlp, void* stream);
+
 /* Step n_worlds worlds of one scene with no device allocation at all, for callers that cannot
  * allocate device memory (a host that owns the CUDA context and forbids cudaMalloc, a fixed
  * memory pool, a real-time loop that must not touch the allocator).  The paper has no

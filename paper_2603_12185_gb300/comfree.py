@@ -50,10 +50,19 @@ class Contact(C.Structure):
                 ("mphi", C.c_float), ("pad2", C.c_float * 3)]
 
 
+class CostDesc(C.Structure):
+    _fields_ = [("body", C.c_int32), ("w_quat", C.c_float), ("w_pos", C.c_float), ("w_contact", C.c_float),
+                ("w_joint", C.c_float), ("w_fallen", C.c_float), ("fall_radius", C.c_float), ("term_pos", C.c_float),
+                ("term_quat", C.c_float)]
+
+
 EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_workspace_bytes", "cf_batch_create",
            "cf_batch_destroy", "cf_batch_sizes", "cf_set_state", "cf_get_state", "cf_set_ctrl", "cf_step",
            "cf_get_contact_counts", "cf_get_contacts", "cf_batch_status", "cf_batch_autotune", "cf_batch_set_warps",
-           "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error")
+           "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error", "cf_mlp_workspace_bytes",
+           "cf_mlp_create", "cf_mlp_destroy", "cf_mlp_param_count", "cf_mlp_forward", "cf_mlp_gradients",
+           "cf_mlp_train_step", "cf_mlp_get_params", "cf_mlp_status", "cf_set_cost", "cf_mppi_sample",
+           "cf_mppi_update", "cf_mppi_shift", "cf_broadcast_state", "cf_mppi_features")
 
 _lib = None
 
@@ -87,6 +96,22 @@ def lib():
     L.cf_batch_set_warps.argtypes = [V, I32, I32]
     L.cf_step_grad.argtypes = [V, I32, C.c_float, V, V, V, V, V, V]
     L.cf_step_noalloc.argtypes = [V, I32, I32, V, V, V, C.c_float, I32, V, V]
+    L.cf_mlp_workspace_bytes.argtypes = [I32, I32, I32, I32, P(C.c_size_t)]
+    L.cf_mlp_create.argtypes = [I32, I32, I32, I32, V, V, C.c_size_t, V, P(V)]
+    L.cf_mlp_destroy.argtypes = [V]
+    L.cf_mlp_destroy.restype = None
+    L.cf_mlp_param_count.argtypes = [V, P(I64)]
+    L.cf_mlp_forward.argtypes = [V, V, I32, V, V]
+    L.cf_mlp_gradients.argtypes = [V, V, V, I32, C.c_float, C.c_float, V, V, V]
+    L.cf_mlp_train_step.argtypes = [V, V, V, I32, C.c_float, C.c_float, C.c_float, V, V]
+    L.cf_mlp_get_params.argtypes = [V, V, V]
+    L.cf_mlp_status.argtypes = [V, V]
+    L.cf_set_cost.argtypes = [V, P(CostDesc), V, V, V]
+    L.cf_mppi_sample.argtypes = [I32, I32, I32, V, V, C.c_float, C.c_float, V, V, I32, V, V, V]
+    L.cf_mppi_update.argtypes = [I32, I32, I32, V, V, C.c_float, V, V, V]
+    L.cf_mppi_shift.argtypes = [I32, I32, V, V]
+    L.cf_broadcast_state.argtypes = [V, V, I32, I32, I32, V, V, V]
+    L.cf_mppi_features.argtypes = [V, I32, V, I32, V, I32, V, V]
     L.cf_status_string.argtypes = [I32]
     L.cf_status_string.restype = C.c_char_p
     L.cf_last_error.argtypes = []
@@ -257,6 +282,14 @@ class Batch:
     def set_warps(self, scene, warps):
         check(lib().cf_batch_set_warps(self.h, int(scene), int(warps)))
 
+    def set_cost(self, desc, goals, qref, costs):
+        """Fused MPC cost (CostDesc or None to switch off); goals [W, 7], qref [total_nq], costs [W] on device."""
+        self._cost_refs = (goals, qref, costs)
+        if desc is None:
+            check(lib().cf_set_cost(self.h, None, None, None, None))
+        else:
+            check(lib().cf_set_cost(self.h, C.byref(desc), _ptr(goals), _ptr(qref), _ptr(costs)))
+
     def step_grad(self, T, dt, dqT, dvT, stream=None):
         dq0 = torch.empty(self.total_nq, dtype=torch.float32, device=self.device)
         dv0 = torch.empty(self.total_nv, dtype=torch.float32, device=self.device)
@@ -292,3 +325,84 @@ def from_scenes(sb, **opts):
     q, v = flatten_state(sb)
     b.set_state(torch.from_numpy(q).cuda(), torch.from_numpy(v).cuda())
     return m, b
+
+
+def mlp_param_shapes(fin, hidden, fout):
+    kin = (fin + 63) // 64 * 64
+    return [("W1", (hidden, kin)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+            ("W3", (fout, hidden)), ("b3", (fout,))]
+
+
+def mlp_init(fin, hidden, fout, seed=0, out_scale=0.1):
+    """Seeded uniform fan-in initialisation (flat FP32, the library's parameter layout); the padding
+    columns of W1 are zero and the output layer starts small."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    fans = {"W1": fin, "W2": hidden, "W3": hidden}
+    for name, shape in mlp_param_shapes(fin, hidden, fout):
+        if name.startswith("W"):
+            lim = np.sqrt(6.0 / fans[name]) * (out_scale if name == "W3" else 1.0)
+            w = rng.uniform(-lim, lim, shape)
+            if name == "W1":
+                w[:, fin:] = 0.0
+            parts.append(w.reshape(-1))
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class Mlp:
+    """The BF16 tensor-core MLP of the learned proposal (cf_mlp_*)."""
+
+    def __init__(self, fin=49, hidden=256, fout=1024, max_batch=4096, params=None, seed=0, device="cuda", stream=None):
+        self.fin, self.hidden, self.fout, self.max_batch = fin, hidden, fout, max_batch
+        n = C.c_size_t()
+        check(lib().cf_mlp_workspace_bytes(fin, hidden, fout, max_batch, C.byref(n)))
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        off = (-self.workspace.data_ptr()) % 256
+        p = mlp_init(fin, hidden, fout, seed) if params is None else np.asarray(params, np.float32)
+        pt = torch.from_numpy(np.ascontiguousarray(p)).to(device)
+        h = C.c_void_p()
+        check(lib().cf_mlp_create(fin, hidden, fout, max_batch, _ptr(pt), C.c_void_p(self.workspace.data_ptr() + off),
+                                  n.value, _stream(stream), C.byref(h)))
+        self.h = h
+        k = C.c_int64()
+        check(lib().cf_mlp_param_count(h, C.byref(k)))
+        self.nparam = k.value
+        self.device = device
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cf_mlp_destroy(self.h)
+            self.h = None
+
+    def forward(self, x, out=None, stream=None):
+        x = x.contiguous().float()
+        B = x.shape[0]
+        out = torch.empty(B, self.fout, dtype=torch.float32, device=self.device) if out is None else out
+        check(lib().cf_mlp_forward(self.h, _ptr(x), B, _ptr(out), _stream(stream)))
+        return out
+
+    def gradients(self, x, target, lo=-5.0, hi=2.0, stream=None):
+        x = x.contiguous().float()
+        target = target.contiguous().float()
+        g = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        check(lib().cf_mlp_gradients(self.h, _ptr(x), _ptr(target), x.shape[0], lo, hi, _ptr(g), _ptr(self.loss),
+                                     _stream(stream)))
+        return g, self.loss
+
+    def train_step(self, x, target, lr=1e-3, lo=-5.0, hi=2.0, stream=None):
+        x = x.contiguous().float()
+        target = target.contiguous().float()
+        check(lib().cf_mlp_train_step(self.h, _ptr(x), _ptr(target), x.shape[0], lr, lo, hi, _ptr(self.loss),
+                                      _stream(stream)))
+        return self.loss
+
+    def params(self, stream=None):
+        p = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        check(lib().cf_mlp_get_params(self.h, _ptr(p), _stream(stream)))
+        return p
+
+    def status(self, stream=None):
+        check(lib().cf_mlp_status(self.h, _stream(stream)))

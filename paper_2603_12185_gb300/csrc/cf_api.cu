@@ -44,6 +44,8 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+void cf::set_last_error(const char* msg) { g_err = msg; }
+
 // ---------------------------------------------------------------------------------------
 // model
 // ---------------------------------------------------------------------------------------
@@ -284,6 +286,12 @@ struct cf_batch {
   size_t smem_all = 0;
   bool artic_all = false;
   int variant = 0;             // pile kernel occupancy variant (autotuned)
+  // fused MPC cost (cf_set_cost)
+  float* cost = nullptr;
+  const float* goal = nullptr;
+  const float* qref = nullptr;
+  int cost_body = 0;
+  float cw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int nctrl = 0;
   int num_sms = 0;
   template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -630,6 +638,11 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
     p.rcos[j] = (float)std::cos(th);
     p.rsin[j] = (float)std::sin(th);
   }
+  p.cost = b->cost;
+  p.goal = b->goal;
+  p.qref = b->qref;
+  p.cost_body = b->cost_body;
+  for (int k = 0; k < 8; ++k) p.cw[k] = b->cw[k];
   return p;
 }
 
@@ -813,6 +826,29 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
   return upload_units(b, s);
 }
 
+extern "C" cf_status cf_set_cost(cf_batch* b, const cf_cost_desc* desc, const float* goals, const float* qref,
+                                 float* costs) {
+  if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
+  if (!desc) {
+    b->cost = nullptr;
+    return CF_OK;
+  }
+  if (!goals || !qref || !costs) return fail(CF_ERR_INVALID_ARGUMENT, "goals, qref and costs are required");
+  for (int w = 0; w < b->W; ++w) {
+    const DScene& sc = b->model.scenes[b->worlds[w].scene];
+    if (sc.pile) return fail(CF_ERR_UNSUPPORTED, "the fused MPC cost covers articulated scenes only");
+    if (desc->body < 0 || desc->body >= sc.nbody || b->model.bodies[sc.body0 + desc->body].jnt != CF_JOINT_FREE)
+      return fail(CF_ERR_INVALID_ARGUMENT, "cost body %d is not a free body of world %d", desc->body, w);
+  }
+  b->cost = costs;
+  b->goal = goals;
+  b->qref = qref;
+  b->cost_body = desc->body;
+  b->cw[0] = desc->w_quat; b->cw[1] = desc->w_pos; b->cw[2] = desc->w_contact; b->cw[3] = desc->w_joint;
+  b->cw[4] = desc->w_fallen; b->cw[5] = desc->fall_radius; b->cw[6] = desc->term_pos; b->cw[7] = desc->term_quat;
+  return CF_OK;
+}
+
 extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                                   float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream) {
   if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
@@ -827,6 +863,7 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
       return fail(CF_ERR_UNSUPPORTED, "world %d: %s", w, why);
   }
   StepParams p = make_params(b, dt, 1);
+  p.cost = nullptr;
   GradArgs g{};
   g.T = T;
   g.ckpt = b->opts.grad_ckpt;

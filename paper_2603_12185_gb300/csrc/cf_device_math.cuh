@@ -282,11 +282,12 @@ __device__ __forceinline__ void contact_frame(f3 n, bool plane, f3 px, f3& t1, f
   t2 = cross(n, t1);
 }
 
-// r(|phi|) of Eq. r_scaling, x clamped to [0, 1]
+// r(|phi|) of Eq. r_scaling, x clamped to [0, 1]; the default power p = 2 is a square
+__device__ __forceinline__ float solimp_pow(float y, float p) { return p == 2.f ? y * y : powf(y, p); }
 __device__ __forceinline__ float solimp_r(const StepParams& P, float aphi) {
   float x = fminf(fmaxf(aphi / P.solimp[2], 0.f), 1.f);
   float m = P.solimp[3];
-  float g = x < m ? m * powf(x / m, P.solimp[4]) : 1.f - (1.f - m) * powf((1.f - x) / (1.f - m), P.solimp[4]);
+  float g = x < m ? m * solimp_pow(x / m, P.solimp[4]) : 1.f - (1.f - m) * solimp_pow((1.f - x) / (1.f - m), P.solimp[4]);
   return P.solimp[0] + (P.solimp[1] - P.solimp[0]) * g;
 }
 
@@ -295,33 +296,43 @@ __device__ __forceinline__ float solimp_r(const StepParams& P, float aphi) {
 // In: the contact-space velocities of the smooth prediction (normal, tangential pair,
 // torsion, rolling pair).  Out: the resultant impulse on A in the contact frame
 // w = (normal, t1, t2, torsion, rolling t1, rolling t2).
+// With a = A - B v_n and the facet velocity s_j = v_n - mu (c_j v_1 + s_j v_2), each facet is
+// lambda_j = max(0, a + c_j (B mu v_1) + s_j (B mu v_2)).
 __device__ __forceinline__ void facet_impulses(const StepParams& P, float vn, float vt1, float vt2, float wn,
                                                float wr1, float wr2, float phi, float kM, float dM, float mu_t,
                                                float mu_tor, float mu_rol, float w[6]) {
-  const float A = -kM * phi;                 // lambda = max(0, A - B s)
   const float B = fmaf(kM, P.dt, dM);
+  const float a = -kM * phi - B * vn;
   float N = 0.f, F1 = 0.f, F2 = 0.f, T = 0.f, R1 = 0.f, R2 = 0.f;
-  for (int j = 0; j < P.n_t; ++j) {
-    float c = P.tcos[j], s = P.tsin[j];
-    float sv = vn - mu_t * (c * vt1 + s * vt2);
-    float lam = fmaxf(A - B * sv, 0.f);
-    N += lam;
-    F1 = fmaf(-mu_t * c, lam, F1);
-    F2 = fmaf(-mu_t * s, lam, F2);
+  {
+    const float b1 = B * mu_t * vt1, b2 = B * mu_t * vt2;
+    for (int j = 0; j < P.n_t; ++j) {
+      const float c = P.tcos[j], s = P.tsin[j];
+      const float lam = fmaxf(fmaf(c, b1, fmaf(s, b2, a)), 0.f);
+      N += lam;
+      F1 = fmaf(c, lam, F1);
+      F2 = fmaf(s, lam, F2);
+    }
+    F1 *= -mu_t;
+    F2 *= -mu_t;
   }
   if (P.n_tor == 2) {
-    float lp = fmaxf(A - B * (vn - mu_tor * wn), 0.f);
-    float lm = fmaxf(A - B * (vn + mu_tor * wn), 0.f);
+    const float bt = B * mu_tor * wn;
+    const float lp = fmaxf(a + bt, 0.f), lm = fmaxf(a - bt, 0.f);
     N += lp + lm;
     T = -mu_tor * (lp - lm);
   }
-  for (int j = 0; j < P.n_rol; ++j) {
-    float c = P.rcos[j], s = P.rsin[j];
-    float sv = vn - mu_rol * (c * wr1 + s * wr2);
-    float lam = fmaxf(A - B * sv, 0.f);
-    N += lam;
-    R1 = fmaf(-mu_rol * c, lam, R1);
-    R2 = fmaf(-mu_rol * s, lam, R2);
+  {
+    const float b1 = B * mu_rol * wr1, b2 = B * mu_rol * wr2;
+    for (int j = 0; j < P.n_rol; ++j) {
+      const float c = P.rcos[j], s = P.rsin[j];
+      const float lam = fmaxf(fmaf(c, b1, fmaf(s, b2, a)), 0.f);
+      N += lam;
+      R1 = fmaf(c, lam, R1);
+      R2 = fmaf(s, lam, R2);
+    }
+    R1 *= -mu_rol;
+    R2 *= -mu_rol;
   }
   w[0] = N; w[1] = F1; w[2] = F2; w[3] = T; w[4] = R1; w[5] = R2;
 }

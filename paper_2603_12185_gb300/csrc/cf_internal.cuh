@@ -86,7 +86,16 @@ struct StepParams {
   int n_t, n_tor, n_rol, trace_mode;
   float tcos[kMaxFacetDirs], tsin[kMaxFacetDirs];
   float rcos[kMaxFacetDirs], rsin[kMaxFacetDirs];
+  // fused MPC cost of articulated worlds (cost == nullptr: off)
+  float* cost;               // [W] += running cost of every step + terminal cost
+  const float* goal;         // [W][7] target position and quaternion
+  const float* qref;         // [total_nq] home pose (hinge coordinates used)
+  int cost_body;             // the free body whose pose is scored
+  float cw[8];               // quat, pos, contact, joint, fallen penalty, fall radius, terminal pos, terminal quat
 };
+
+// thread-local message returned by cf_last_error (set by every failing entry point)
+void set_last_error(const char* msg);
 
 // bytes of dynamic shared memory one world of a scene needs in the step kernel
 size_t world_smem_bytes(const DScene& s, int warps);

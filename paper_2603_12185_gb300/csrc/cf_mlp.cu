@@ -338,10 +338,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
-thread_local char g_mlp_err[256];
-
 cf_status mfail(cf_status s, const char* msg) {
-  snprintf(g_mlp_err, sizeof(g_mlp_err), "%s", msg);
+  cf::set_last_error(msg);
   return s;
 }
 
@@ -619,5 +617,3 @@ extern "C" cf_status cf_mlp_status(cf_mlp* m, void* stream) {
   if (w & CF_FLAG_TIMEOUT) return mfail(CF_ERR_TIMEOUT, "a tensor-core pipeline wait gave up");
   return CF_OK;
 }
-
-extern "C" const char* cf_mlp_last_error(void) { return g_mlp_err; }

@@ -878,6 +878,44 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
   if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
 }
 
+// MPC running cost of the state at the start of a step (Sec. V, Eq. mpc cost terms): object
+// orientation error 1 - (q*^T q)^2, absolute position errors, squared distances from the object
+// to the fingertips (the +z ends of the capsules of leaf bodies), squared deviation of the
+// hinges from the home pose, and a penalty once the object leaves the fall radius.
+__device__ float artic_running_cost(const StepParams& P, const ArticView& s, const DScene& sc, const DWorld& W,
+                                    int world) {
+  const DBody* B = P.bodies + sc.body0;
+  const DGeom* G = P.geoms + sc.geom0;
+  const float* gl = P.goal + 7 * world;
+  const float* qo = s.q + B[P.cost_body].qoff;
+  float dq = gl[3] * qo[3] + gl[4] * qo[4] + gl[5] * qo[5] + gl[6] * qo[6];
+  float c = P.cw[0] * (1.f - dq * dq);
+  c += P.cw[1] * (fabsf(qo[0] - gl[0]) + fabsf(qo[1] - gl[1]) + fabsf(qo[2] - gl[2]));
+  float tips = 0.f;
+  for (int g = 0; g < sc.ngeom; ++g) {
+    int b = G[g].body;
+    if (b < 0 || G[g].type != CF_GEOM_CAPSULE || B[b].jnt != CF_JOINT_HINGE) continue;
+    bool leaf = true;
+    for (int k = 0; k < sc.nbody; ++k)
+      if (B[k].parent == b) leaf = false;
+    if (!leaf) continue;
+    f3 tip = ld3(s.gc + 3 * g) + G[g].size[1] * mk3(s.gR[9 * g + 2], s.gR[9 * g + 5], s.gR[9 * g + 8]);
+    f3 d = mk3(qo[0], qo[1], qo[2]) - tip;
+    tips += dot(d, d);
+  }
+  c += P.cw[2] * tips;
+  float dj = 0.f;
+  for (int b = 0; b < sc.nbody; ++b)
+    if (B[b].jnt == CF_JOINT_HINGE) {
+      float e = s.q[B[b].qoff] - P.qref[W.qadr + B[b].qoff];
+      dj += e * e;
+    }
+  c += P.cw[3] * dj;
+  float rx = qo[0] - gl[0], ry = qo[1] - gl[1];
+  if (rx * rx + ry * ry > P.cw[5] * P.cw[5]) c += P.cw[4];
+  return c;
+}
+
 __device__ void artic_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -891,6 +929,7 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
   for (int i = tid; i < sc.nv; i += T) s.v[i] = P.v[W.vadr + i];
   int* queue = s.queue + wig * kQueue;
   const float dt = P.dt;
+  float cost_acc = 0.f;
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
@@ -919,6 +958,7 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
                 : sqrtf(gd.size[0] * gd.size[0] + gd.size[1] * gd.size[1] + gd.size[2] * gd.size[2]);
     }
     group_sync(gid, T);
+    if (P.cost && tid == 0) cost_acc += artic_running_cost(P, s, sc, W, world);
     // ---- B. pair loop with per-warp compaction ----
     int qn = 0;
     for (int base = wig * 32; base < sc.npair; base += T) {
@@ -1014,6 +1054,14 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
     if (P.capture_cap > 0 && s.count[1] > P.capture_cap) {
       atomicOr(P.flags + world, CF_FLAG_CONTACT_OVERFLOW);
       atomicOr(P.errword, CF_FLAG_CONTACT_OVERFLOW);
+    }
+    if (P.cost) {
+      // terminal cost of the final state: phi1 |p - p*|^2 + phi2 (1 - (q*^T q)^2)
+      const float* gl = P.goal + 7 * world;
+      const float* qo = s.q + P.bodies[sc.body0 + P.cost_body].qoff;
+      float dx = qo[0] - gl[0], dy = qo[1] - gl[1], dz = qo[2] - gl[2];
+      float dq = gl[3] * qo[3] + gl[4] * qo[4] + gl[5] * qo[5] + gl[6] * qo[6];
+      P.cost[world] += cost_acc + P.cw[6] * (dx * dx + dy * dy + dz * dz) + P.cw[7] * (1.f - dq * dq);
     }
   }
 }
