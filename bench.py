@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true")
     return ap.parse_args()
 
 
@@ -197,6 +198,67 @@ def run_e2e(res, steps):
     return dict(value=res["worlds"] * steps / sec, h2d=nbytes, d2h=nbytes)
 
 
+def run_extras(rank):
+    """The other workloads, each timed with CUDA events after warm-up (reported beside the headline):
+    mixed batches of uneven worlds in one persistent launch, the hand adjoint, an MPPI tick."""
+    import torch
+    from paper_2603_12185_gb300 import autograd as AG
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    out = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step
+    sb = S.make_mixed(8192, seed=2000 + rank)
+    _, b = CF.from_scenes(sb)
+    chosen = b.autotune(sb.dt)
+    for _ in range(300):
+        b.step(sb.dt, 1)
+    ms = timed(lambda: b.step(sb.dt, 1), 20)
+    c = b.contact_counts()
+    out["mixed_8192"] = {"world_steps_per_s": 8192 / (ms / 1e3), "ms_per_step": ms,
+                         "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
+    del b
+    # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
+    T = 100
+    sb = S.make_hand(1024, seed=2100 + rank)
+    _, b = CF.from_scenes(sb, max_ctrl_steps=T, grad_steps=T, grad_ckpt=10)
+    q0, v0 = CF.flatten_state(sb)
+    q0, v0 = torch.from_numpy(q0).cuda(), torch.from_numpy(v0).cuda()
+    tau = torch.randn(T, b.total_nu, device="cuda") * 0.05
+    gq = torch.randn(b.total_nq, device="cuda")
+    gv = torch.zeros(b.total_nv, device="cuda")
+
+    def grad_once():
+        b.set_state(q0, v0)
+        b.set_ctrl(tau.reshape(-1))
+        b.step_grad(T, sb.dt, gq, gv)
+
+    ms = timed(grad_once, 3)
+    out["adjoint_hand_1024x100"] = {"ms": ms, "world_steps_per_s": 1024 * T / (ms / 1e3)}
+    del b
+    # one MPPI control tick: 1024 rollouts x 32 steps of 5 ms with the fused cost
+    t = S.hand_template(0)
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    ctl = MP.HandMPPI(t, params, N=1024)
+    sbh = S.make_hand(1, seed=2200 + rank)
+    ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
+    ms = timed(ctl.tick, 10)
+    out["mppi_tick_1024x32"] = {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
+    return out
+
+
 def cpu_baseline(nbody, rank, budget_s=20.0, reference=False):
     """The FP64 oracle as it stands, OpenMP over the host cores, on a bounded sample: the first
     worlds of the same seeded workload, from their initial state."""
@@ -303,6 +365,8 @@ def main():
                     "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["steps"],
             "clocks": clk}
+    if not args.no_extras:
+        line["other_workloads"] = run_extras(rank)
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(args.bodies, rank)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

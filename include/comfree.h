@@ -231,9 +231,10 @@ cf_status cf_mppi_shift(int32_t H, int32_t nu, float* mean, void* stream);
 /* copy one world's state into W back-to-back worlds */
 cf_status cf_broadcast_state(const float* q0, const float* v0, int32_t nq, int32_t nv, int32_t W, float* q, float* v,
                              void* stream);
-/* out = concat(q[nq], v[nv], goal[ngoal]): the proposal's input features */
-cf_status cf_mppi_features(const float* q, int32_t nq, const float* v, int32_t nv, const float* goal, int32_t ngoal,
-                           float* out, void* stream);
+/* out = clamp(concat(q[nq], v_scale * v[nv], goal[ngoal]), -clamp, clamp): the proposal's
+ * input features (velocities scaled to the range of the pose coordinates) */
+cf_status cf_mppi_features(const float* q, int32_t nq, const float* v, int32_t nv, float v_scale, const float* goal,
+                           int32_t ngoal, float clamp, float* out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Learned proposal for sampling MPC: a 3-layer perceptron in -> hidden -> hidden -> out with

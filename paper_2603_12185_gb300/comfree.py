@@ -111,7 +111,7 @@ def lib():
     L.cf_mppi_update.argtypes = [I32, I32, I32, V, V, C.c_float, V, V, V]
     L.cf_mppi_shift.argtypes = [I32, I32, V, V]
     L.cf_broadcast_state.argtypes = [V, V, I32, I32, I32, V, V, V]
-    L.cf_mppi_features.argtypes = [V, I32, V, I32, V, I32, V, V]
+    L.cf_mppi_features.argtypes = [V, I32, V, I32, C.c_float, V, I32, C.c_float, V, V]
     L.cf_status_string.argtypes = [I32]
     L.cf_status_string.restype = C.c_char_p
     L.cf_last_error.argtypes = []

@@ -28,7 +28,8 @@ __global__ void mppi_sample_kernel(int N, int H, int nu, const float* mean, cons
 }
 
 // weights w_k = exp(-(J_k - min J) / lambda); mean <- sum_k w_k U_k / sum_k w_k.
-// One CTA; stats = (min cost, mean cost, effective sample size).
+// A rollout whose cost is not finite (its state blew up) gets weight 0; if no rollout is finite
+// the mean is left unchanged.  One CTA; stats = (min cost, mean finite cost, effective sample size).
 __global__ void mppi_update_kernel(int N, int H, int nu, const float* cost, const float* samples, float lambda,
                                    float* mean, float* stats) {
   extern __shared__ float w[];
@@ -38,8 +39,10 @@ __global__ void mppi_update_kernel(int N, int H, int nu, const float* cost, cons
   float mn = 3.0e38f, sm = 0.f;
   for (int k = tid; k < N; k += nt) {
     float c = cost[k];
-    mn = fminf(mn, c);
-    sm += c;
+    if (isfinite(c)) {
+      mn = fminf(mn, c);
+      sm += c;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
@@ -56,7 +59,8 @@ __global__ void mppi_update_kernel(int N, int H, int nu, const float* cost, cons
   __syncthreads();
   float ws = 0.f, wq = 0.f;
   for (int k = tid; k < N; k += nt) {
-    float e = expf(-(cost[k] - s_min) / lambda);
+    float c = cost[k];
+    float e = isfinite(c) ? expf(-(c - s_min) / lambda) : 0.f;
     w[k] = e;
     ws += e;
     wq += e * e;
@@ -76,10 +80,12 @@ __global__ void mppi_update_kernel(int N, int H, int nu, const float* cost, cons
   }
   __syncthreads();
   const int M = H * nu;
-  for (int r = tid; r < M; r += nt) {
-    float acc = 0.f;
-    for (int k = 0; k < N; ++k) acc = fmaf(w[k], samples[(size_t)k * M + r], acc);
-    mean[r] = acc / s_sum;
+  if (s_sum > 0.f && isfinite(s_sum)) {
+    for (int r = tid; r < M; r += nt) {
+      float acc = 0.f;
+      for (int k = 0; k < N; ++k) acc = fmaf(w[k], samples[(size_t)k * M + r], acc);
+      mean[r] = acc / s_sum;
+    }
   }
   if (tid == 0 && stats) {
     stats[0] = s_min;
@@ -148,19 +154,23 @@ extern "C" cf_status cf_broadcast_state(const float* q0, const float* v0, int32_
 }
 
 namespace cf {
-__global__ void concat_kernel(const float* a, int na, const float* b, int nb, const float* c, int nc, float* out) {
+__global__ void concat_kernel(const float* a, int na, const float* b, int nb, float bscale, const float* c, int nc,
+                              float clamp, float* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < na) out[i] = a[i];
-  else if (i < na + nb) out[i] = b[i - na];
-  else if (i < na + nb + nc) out[i] = c[i - na - nb];
+  float x;
+  if (i < na) x = a[i];
+  else if (i < na + nb) x = bscale * b[i - na];
+  else if (i < na + nb + nc) x = c[i - na - nb];
+  else return;
+  out[i] = fminf(fmaxf(x, -clamp), clamp);
 }
 }  // namespace cf
 
-extern "C" cf_status cf_mppi_features(const float* q, int32_t nq, const float* v, int32_t nv, const float* goal,
-                                      int32_t ngoal, float* out, void* stream) {
-  if (!q || !v || !out || nq < 0 || nv < 0 || ngoal < 0 || (ngoal && !goal))
+extern "C" cf_status cf_mppi_features(const float* q, int32_t nq, const float* v, int32_t nv, float v_scale,
+                                      const float* goal, int32_t ngoal, float clamp, float* out, void* stream) {
+  if (!q || !v || !out || nq < 0 || nv < 0 || ngoal < 0 || (ngoal && !goal) || !(clamp > 0.f))
     return mp_fail(CF_ERR_INVALID_ARGUMENT, "bad feature arguments");
   int n = nq + nv + ngoal;
-  concat_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(q, nq, v, nv, goal, ngoal, out);
+  concat_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(q, nq, v, nv, v_scale, goal, ngoal, clamp, out);
   return cudaGetLastError() == cudaSuccess ? CF_OK : mp_fail(CF_ERR_CUDA, "features launch");
 }

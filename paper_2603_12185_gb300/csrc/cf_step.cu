@@ -167,46 +167,11 @@ __device__ __forceinline__ void pile_contact(const StepParams& P, PileView& s, i
   if (P.capture_cap > 0) capture_contact(P, world, s.count, ga, gb, sub, k.phi, k.p, k.n, w[0], mphi);
 }
 
-// narrowphase + solve for one candidate code: (a << 16) | b, or (a << 16) | 0x8000 | plane
-__device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& sc, int world, int code) {
-  int a = code >> 16, bc = code & 0xffff;
-  int ta = s.type[a];
-  float4 pa4 = s.pb[a];
-  f3 ca = mk3(pa4.x, pa4.y, pa4.z);
-  const int ga = sc.geom0 + a;
-  if (bc & 0x8000) {
-    int pi = bc & 0x7fff;
-    const float* pl = s.planes + 12 * pi;
-    f3 o = mk3(pl[0], pl[1], pl[2]), nz = mk3(pl[3], pl[4], pl[5]), px = mk3(pl[6], pl[7], pl[8]);
-    const int gb = sc.geom0 + sc.plane0 + pi;
-    if (ta == CF_GEOM_SPHERE) {
-      Raw k = nf_sphere_plane(ca, s.rad[a], o, nz);
-      if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, 0, k, true, px, pl + 9);
-    } else if (ta == CF_GEOM_CAPSULE) {
-      M33 R = pile_R(s, a);
-      f3 ax = col(R, 2);
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        Raw k = nf_sphere_plane(ca + (e ? s.hl[a] : -s.hl[a]) * ax, s.rad[a], o, nz);
-        if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, e, k, true, px, pl + 9);
-      }
-    } else if (ta == CF_GEOM_BOX) {
-      M33 R = pile_R(s, a);
-      for (int cidx = 0; cidx < 8; ++cidx) {
-        f3 corner = ca + mul(R, mk3((cidx & 4) ? s.rad[a] : -s.rad[a], (cidx & 2) ? s.hl[a] : -s.hl[a],
-                                    (cidx & 1) ? s.s2[a] : -s.s2[a]));
-        Raw k = nf_sphere_plane(corner, 0.f, o, nz);
-        if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, cidx, k, true, px, pl + 9);
-      }
-    }
-    return;
-  }
-  int b = bc;
-  int tb = s.type[b];
-  float4 pb4 = s.pb[b];
-  f3 cb = mk3(pb4.x, pb4.y, pb4.z);
-  const int gb = sc.geom0 + b;
-  const float mub[3] = {s.mu0[b], s.mu1[b], s.mu2[b]};
+// narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none
+__device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca) {
+  const int ta = s.type[a], tb = s.type[b];
+  const float4 pb4 = s.pb[b];
+  const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
   if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
@@ -225,8 +190,7 @@ __device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& s
     f3 u = col(pile_R(s, b), 2);
     float t = fminf(fmaxf(dot(ca - cb, u), -s.hl[b]), s.hl[b]);
     k = nf_sphere_sphere(ca, s.rad[a], cb + t * u, s.rad[b]);
-  } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
-    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) return;  // box-box: unsupported pair
+  } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {  // box-box: unsupported pair
     bool boxA = ta == CF_GEOM_BOX;
     int ib = boxA ? a : b, io = boxA ? b : a;
     M33 Rbx = pile_R(s, ib);
@@ -240,7 +204,49 @@ __device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& s
       k = nf_sphere_box(co + t * u, s.rad[io], cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < P.margin) pile_contact(P, s, world, a, b, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f), mub);
+  return k;
+}
+
+// narrowphase of body a against a plane: sphere (sub 0), capsule end sphere sub, box corner sub
+__device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int sub, f3 ca, f3 o, f3 nz) {
+  const int ta = s.type[a];
+  f3 c = ca;
+  float r = s.rad[a];
+  if (ta == CF_GEOM_CAPSULE) {
+    c = ca + (sub ? s.hl[a] : -s.hl[a]) * col(pile_R(s, a), 2);
+  } else if (ta == CF_GEOM_BOX) {
+    c = ca + mul(pile_R(s, a), mk3((sub & 4) ? s.rad[a] : -s.rad[a], (sub & 2) ? s.hl[a] : -s.hl[a],
+                                   (sub & 1) ? s.s2[a] : -s.s2[a]));
+    r = 0.f;
+  }
+  return nf_sphere_plane(c, r, o, nz);
+}
+
+// narrowphase + solve for one candidate code: (a << 16) | b, or (a << 16) | 0x8000 | plane.
+// Plane candidates and body pairs reach the (inlined) solve through one site each, and the
+// queues are flushed between the two candidate loops, so a 32-lane batch is homogeneous.
+__device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& sc, int world, int code) {
+  const int a = code >> 16, bc = code & 0xffff;
+  const int ta = s.type[a];
+  const float4 pa4 = s.pb[a];
+  const f3 ca = mk3(pa4.x, pa4.y, pa4.z);
+  const int ga = sc.geom0 + a;
+  if (bc & 0x8000) {
+    const int pi = bc & 0x7fff;
+    const float* pl = s.planes + 12 * pi;
+    const f3 o = mk3(pl[0], pl[1], pl[2]), nz = mk3(pl[3], pl[4], pl[5]), px = mk3(pl[6], pl[7], pl[8]);
+    const int gb = sc.geom0 + sc.plane0 + pi;
+    const int nsub = ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
+    for (int sub = 0; sub < nsub; ++sub) {
+      const Raw k = pile_narrow_plane(s, a, sub, ca, o, nz);
+      if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, sub, k, true, px, pl + 9);
+    }
+    return;
+  }
+  const int b = bc;
+  const float mub[3] = {s.mu0[b], s.mu1[b], s.mu2[b]};
+  const Raw k = pile_narrow_pair(s, a, b, ca);
+  if (k.phi < P.margin) pile_contact(P, s, world, a, b, ga, sc.geom0 + b, 0, k, false, mk3(0.f, 0.f, 0.f), mub);
 }
 
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
@@ -375,6 +381,11 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
         push(code);
       }
     }
+    // flush the body-pair queue so that plane candidates form batches of their own
+    __syncwarp();
+    if (lane < qn) pile_candidate(P, s, sc, world, queue[lane]);
+    qn = 0;
+    __syncwarp();
     // body-plane pairs
     for (int pi = 0; pi < NP; ++pi) {
       const float* pl = s.planes + 12 * pi;

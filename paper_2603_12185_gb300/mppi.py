@@ -22,10 +22,11 @@ from . import comfree as CF
 from . import scenes as S
 
 NU, NQ, NV = 16, 23, 22
+V_SCALE, F_CLAMP = 0.1, 10.0   # proposal inputs: velocities x 0.1, every feature clamped to +-10
 
 
 def default_cost():
-    return CF.CostDesc(body=0, w_quat=2.0, w_pos=2.0, w_contact=0.5, w_joint=0.05, w_fallen=5.0, fall_radius=0.08,
+    return CF.CostDesc(body=0, w_quat=2.0, w_pos=2.0, w_contact=10.0, w_joint=0.05, w_fallen=5.0, fall_radius=0.08,
                        term_pos=50.0, term_quat=20.0)
 
 
@@ -43,7 +44,7 @@ def task_cost(q, goal):
 
 
 class HandMPPI:
-    def __init__(self, template, params, N=1024, H=32, dt=0.005, sigma=0.08, lam=0.5, limit=0.15, mlp=None,
+    def __init__(self, template, params, N=1024, H=32, dt=0.005, sigma=1.0, lam=0.1, limit=2.0, mlp=None,
                  n_prop=0, seed=0, cost=None, device="cuda"):
         self.N, self.H, self.dt, self.sigma, self.lam, self.limit = N, H, dt, sigma, lam, limit
         self.mlp, self.n_prop = mlp, (n_prop if mlp is not None else 0)
@@ -82,8 +83,8 @@ class HandMPPI:
 
     def features(self, qp, vp):
         g = self.goals[0, 3:7].contiguous()
-        CF.check(CF.lib().cf_mppi_features(CF._ptr(qp), NQ, CF._ptr(vp), NV, CF._ptr(g), 4, CF._ptr(self.feat),
-                                           CF._stream()))
+        CF.check(CF.lib().cf_mppi_features(CF._ptr(qp), NQ, CF._ptr(vp), NV, V_SCALE, CF._ptr(g), 4, F_CLAMP,
+                                           CF._ptr(self.feat), CF._stream()))
         return self.feat
 
     def tick(self):
@@ -127,8 +128,9 @@ def random_goal(q0, rng):
 def run_episode(ctl, q0, v0, goal, ticks, record=None):
     ctl.reset(q0, v0, goal)
     for _ in range(ticks):
-        qp, vp = ctl.plant.get_state()
-        feat = torch.cat([qp, vp, torch.as_tensor(goal[3:7].astype(np.float32), device=qp.device)])
+        if record is not None:
+            qp, vp = ctl.plant.get_state()
+            feat = ctl.features(qp, vp)[0].clone()
         plan = ctl.tick()
         if record is not None:
             record.append((feat, plan))
@@ -150,6 +152,8 @@ def collect_and_train(template, params, episodes=32, ticks=60, N=1024, seed=0, e
         finals.append(run_episode(ctl, sb.q0[e], sb.v0[e], goal, ticks, rec))
     X = torch.stack([r[0] for r in rec])
     Y = torch.stack([r[1] for r in rec])
+    keep = torch.isfinite(X).all(1) & torch.isfinite(Y).all(1)
+    X, Y = X[keep].contiguous(), Y[keep].contiguous()
     mlp = mlp or CF.Mlp(NQ + NV + 4, 256, 2 * 32 * NU, max_batch=max(len(rec), 128), seed=seed)
     losses = []
     for ep in range(epochs):
