@@ -27,6 +27,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2603_12185_gb300 import replicas as R  # noqa: E402
+
 EPISODE = 1000
 WORLDS = 4096
 BODIES = 256
@@ -117,24 +119,20 @@ def dist_setup():
 
 
 def barrier_max(x, world):
+    """Max over the replicas (after a barrier): the whole job is as slow as its slowest rank."""
     if world == 1:
         return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    from paper_2603_12185_gb300 import replicas as R
     dist.barrier()
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return R.reduce_scalar(x, "max")
 
 
 def barrier_sum(x, world):
     if world == 1:
         return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_2603_12185_gb300 import replicas as R
+    return R.reduce_scalar(x, "sum")
 
 
 def run_pile(nbody, nworld, steps, warmup, rank, timed_events=True, flush=None):
@@ -143,7 +141,7 @@ def run_pile(nbody, nworld, steps, warmup, rank, timed_events=True, flush=None):
     import torch
     from paper_2603_12185_gb300 import comfree as CF
     from paper_2603_12185_gb300 import scenes as S
-    sb = S.make_pile(nworld, nbody, seed=1000 + rank)
+    sb = S.make_pile(nworld, nbody, seed=R.rank_seed(1000, rank))
     model, b = CF.from_scenes(sb)
     b.autotune(sb.dt)
     stream = torch.cuda.current_stream()
@@ -220,7 +218,7 @@ def run_extras(rank):
         return e0.elapsed_time(e1) / reps
 
     # uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step
-    sb = S.make_mixed(8192, seed=2000 + rank)
+    sb = S.make_mixed(8192, seed=R.rank_seed(2000, rank))
     _, b = CF.from_scenes(sb)
     chosen = b.autotune(sb.dt)
     for _ in range(300):
@@ -232,7 +230,7 @@ def run_extras(rank):
     del b
     # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
     T = 100
-    sb = S.make_hand(1024, seed=2100 + rank)
+    sb = S.make_hand(1024, seed=R.rank_seed(2100, rank))
     _, b = CF.from_scenes(sb, max_ctrl_steps=T, grad_steps=T, grad_ckpt=10)
     q0, v0 = CF.flatten_state(sb)
     q0, v0 = torch.from_numpy(q0).cuda(), torch.from_numpy(v0).cuda()
@@ -252,7 +250,7 @@ def run_extras(rank):
     t = S.hand_template(0)
     params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
     ctl = MP.HandMPPI(t, params, N=1024)
-    sbh = S.make_hand(1, seed=2200 + rank)
+    sbh = S.make_hand(1, seed=R.rank_seed(2200, rank))
     ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
     ms = timed(ctl.tick, 10)
     out["mppi_tick_1024x32"] = {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
@@ -265,7 +263,7 @@ def cpu_baseline(nbody, rank, budget_s=20.0, reference=False):
     from oracle import oracle as O
     from paper_2603_12185_gb300 import scenes as S
     nw = 16
-    sb = S.make_pile(nw, nbody, seed=1000 + rank)
+    sb = S.make_pile(nw, nbody, seed=R.rank_seed(1000, rank))
     runner = O.BatchRunner([sb.world(w) for w in range(nw)], sb.params)
     q = np.concatenate([np.asarray(x, np.float64) for x in sb.q0])
     v = np.concatenate([np.asarray(x, np.float64) for x in sb.v0])

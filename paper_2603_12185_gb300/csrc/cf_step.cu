@@ -333,52 +333,29 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
         __syncwarp();
       }
     };
-    // body-body pairs (i, i + o mod N), o = 1..H: the work items (32-body chunk, offset) are
-    // split into one contiguous run per warp; each lane keeps its body i in registers
+    // body-body pairs in 32 x 32 tiles (i-chunk <= j-chunk), dealt round-robin to the warps:
+    // each lane keeps body i in registers, the j loop is warp-uniform (broadcast loads)
     {
       const int nchunk = (N + 31) >> 5;
-      const int items = nchunk * H;
-      const int per = (items + gwarps - 1) / gwarps;
-      int it = wig * per;
-      const int end = min(it + per, items);
-      if (it < end) {
-        int c = it / H;
-        int o = it - c * H + 1;
-        int i = (c << 5) + lane;
-        float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int ntile = nchunk * (nchunk + 1) / 2;
+      for (int t = wig; t < ntile; t += gwarps) {
+        int ci = 0, rem = t;
+        while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
+        const int cj = ci + rem;
+        const int i = (ci << 5) + lane;
+        float4 pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
         if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
-        for (; it < end; ++it) {
-          int code = -1;
-          if (i < N) {
-            int j = i + o;
-            if (j >= N) j -= N;
-            float4 pj = s.pb[j];
-            float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
-            float rr = pi4.w + pj.w;
-            if (dx * dx + dy * dy + dz * dz < rr * rr) code = (min(i, j) << 16) | max(i, j);
-          }
+        const int j0 = cj << 5;
+        const int kmax = min(32, N - j0);
+        for (int k = 0; k < kmax; ++k) {
+          const int j = j0 + k;
+          const float4 pj = s.pb[j];
+          const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
+          const float rr = pi4.w + pj.w;
+          const bool up = ci != cj || lane < k;   // i < j
+          const int code = (up && dx * dx + dy * dy + dz * dz < rr * rr) ? ((i << 16) | j) : -1;
           push(code);
-          if (++o > H) {
-            o = 1;
-            ++c;
-            i = (c << 5) + lane;
-            if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
-          }
         }
-      }
-    }
-    // the half-way pairs (i, i + N/2), i < N/2, of an even N
-    if (!(N & 1)) {
-      for (int base = wig * 32; base < (N >> 1); base += T) {
-        int i = base + lane, code = -1;
-        if (i < (N >> 1)) {
-          int j = i + (N >> 1);
-          float4 a4 = s.pb[i], b4 = s.pb[j];
-          float dx = a4.x - b4.x, dy = a4.y - b4.y, dz = a4.z - b4.z;
-          float rr = a4.w + b4.w + margin;
-          if (dx * dx + dy * dy + dz * dz < rr * rr) code = (i << 16) | j;
-        }
-        push(code);
       }
     }
     // flush the body-pair queue so that plane candidates form batches of their own
