@@ -69,7 +69,8 @@ typedef struct cf_batch cf_batch;
  * free body with no children (its body frame at its centre of mass), or a fixed-base tree of
  * hinges whose bodies are contiguous.  Arrays are host pointers, FP64, read during
  * cf_model_create only.  `pile` != 0 declares the layout "body i is free and carries geom i at
- * its origin; geoms nbody.. are static planes"; only such scenes accept per-world overrides. */
+ * its origin; geoms nbody.. are static planes" (at most 32767 bodies and 4096 planes, else
+ * CF_ERR_UNSUPPORTED); only such scenes accept per-world overrides. */
 typedef struct {
   int32_t nbody, ngeom;
   const int32_t* body_parent;   /* [nbody] parent body or -1                              */

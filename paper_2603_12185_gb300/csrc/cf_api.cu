@@ -187,7 +187,8 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
     }
     for (int g = d.nbody; g < d.ngeom; ++g)
       if (G[g].type != CF_GEOM_PLANE) return fail(CF_ERR_INVALID_ARGUMENT, "scene %d: pile extra geoms must be planes", si);
-    if (d.nbody >= 32768 || nplane >= 32768) return fail(CF_ERR_UNSUPPORTED, "scene %d: pile too large", si);
+    if (d.nbody >= 32768 || d.ngeom - d.nbody > 4096)
+      return fail(CF_ERR_UNSUPPORTED, "scene %d: pile too large (at most 32767 bodies and 4096 planes)", si);
     sc.plane0 = d.nbody;
     sc.nplane = d.ngeom - d.nbody;
   } else {

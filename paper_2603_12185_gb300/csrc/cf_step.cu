@@ -63,20 +63,25 @@ struct PileView {
   unsigned long long* acc;  // [6][N]
   float4* pb;               // [N] position (x, y, z) and bounding radius
   float *qw, *qx, *qy, *qz;
-  float* v;                 // [6][N]
-  float* vs;                // [6][N]
+  float* v;                 // [6][N] v, overwritten in place by v_s in phase A and by v+ in phase C
   float* R;                 // [9][N]
   float *invm, *I0, *I1, *I2, *rad, *hl, *s2;  // I0..I2: inverse principal inertia
   float *mu0, *mu1, *mu2;   // friction coefficients of the body's geom
   int* type;
   float* planes;            // [NP][12]
-  int* queue;               // [warps][kQueue]
+  int* queue;               // [warps][kQueue] broadphase candidates
+  float* cq;                // [warps][8][kQueue] contacts: p.xyz, n.xyz, phi, code
   int* count;               // [0] contacts, [1] captured
 };
 
+// contact codes: body pair (a << 16) | b; plane (a << 16) | 0x8000 | (sub << 12) | plane
+constexpr int kPlaneBit = 0x8000;
+constexpr int kPlaneMask = 0xfff;
+constexpr int kCqWords = 8;
+
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
-  // acc (12 words/body) + 40 words/body + planes + queues + counters, 16-byte granules
-  size_t words = (size_t)N * 12 + (size_t)N * 40 + (size_t)NP * 12 + (size_t)warps * kQueue + 4;
+  // acc (12 words/body) + 34 words/body + planes + both queues + counters, 16-byte granules
+  size_t words = (size_t)N * 12 + (size_t)N * 34 + (size_t)NP * 12 + (size_t)warps * kQueue * (1 + kCqWords) + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -88,13 +93,13 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   s.pb = reinterpret_cast<float4*>(f); f += 4 * (size_t)N;
   s.qw = f; f += N; s.qx = f; f += N; s.qy = f; f += N; s.qz = f; f += N;
   s.v = f; f += 6 * N;
-  s.vs = f; f += 6 * N;
   s.R = f; f += 9 * N;
   s.invm = f; f += N; s.I0 = f; f += N; s.I1 = f; f += N; s.I2 = f; f += N;
   s.rad = f; f += N; s.hl = f; f += N; s.s2 = f; f += N;
   s.mu0 = f; f += N; s.mu1 = f; f += N; s.mu2 = f; f += N;
   s.type = reinterpret_cast<int*>(f); f += N;
   s.planes = f; f += (size_t)NP * 12;
+  s.cq = f; f += (size_t)warps * kQueue * kCqWords;
   s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
   s.count = reinterpret_cast<int*>(f);
   return s;
@@ -126,34 +131,54 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, const M33& R, f3 
   atomicAdd(&s.acc[5 * s.N + i], to_fix(sign * ang.z));
 }
 
-// one contact between body a and body b (b < 0: static plane with x axis px)
-__device__ __forceinline__ void pile_contact(const StepParams& P, PileView& s, int world, int a, int b, int ga, int gb,
-                                          int sub, const Raw& k, bool plane, f3 px, const float* mu_b) {
+// Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
+// (a plane contributes nothing).
+__device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
+                                           const float* cq, int slot) {
+  Raw k;
+  k.p = mk3(cq[slot], cq[kQueue + slot], cq[2 * kQueue + slot]);
+  k.n = mk3(cq[3 * kQueue + slot], cq[4 * kQueue + slot], cq[5 * kQueue + slot]);
+  k.phi = cq[6 * kQueue + slot];
+  const int code = __float_as_int(cq[7 * kQueue + slot]);
+  const int a = code >> 16, bc = code & 0xffff;
+  const bool plane = (bc & kPlaneBit) != 0;
+  const int b = plane ? -1 : bc;
+  f3 px = mk3(0.f, 0.f, 0.f);
+  float mub0, mub1, mub2;
+  int gb, sub = 0;
+  if (plane) {
+    const float* pl = s.planes + 12 * (bc & kPlaneMask);
+    px = mk3(pl[6], pl[7], pl[8]);
+    mub0 = pl[9]; mub1 = pl[10]; mub2 = pl[11];
+    gb = sc.geom0 + sc.plane0 + (bc & kPlaneMask);
+    sub = (bc >> 12) & 7;
+  } else {
+    mub0 = s.mu0[b]; mub1 = s.mu1[b]; mub2 = s.mu2[b];
+    gb = sc.geom0 + b;
+  }
+  const int N = s.N;
   f3 t1, t2;
   contact_frame(k.n, plane, px, t1, t2);
   M33 Ra = pile_R(s, a);
   float4 pa = s.pb[a];
   f3 ra = k.p - mk3(pa.x, pa.y, pa.z);
-  f3 wa = mul(Ra, mk3(s.vs[3 * s.N + a], s.vs[4 * s.N + a], s.vs[5 * s.N + a]));
-  f3 vc = mk3(s.vs[a], s.vs[s.N + a], s.vs[2 * s.N + a]) + cross(wa, ra);
+  f3 wa = mul(Ra, mk3(s.v[3 * N + a], s.v[4 * N + a], s.v[5 * N + a]));
+  f3 vc = mk3(s.v[a], s.v[N + a], s.v[2 * N + a]) + cross(wa, ra);
   f3 wc = wa;
   float tr = pile_trace(P, s, a, Ra, ra);
-  float mu_t, mu_tor, mu_rol;
   M33 Rb;
   f3 rb;
   if (b >= 0) {
     Rb = pile_R(s, b);
     float4 pbb = s.pb[b];
     rb = k.p - mk3(pbb.x, pbb.y, pbb.z);
-    f3 wb = mul(Rb, mk3(s.vs[3 * s.N + b], s.vs[4 * s.N + b], s.vs[5 * s.N + b]));
-    vc = vc - (mk3(s.vs[b], s.vs[s.N + b], s.vs[2 * s.N + b]) + cross(wb, rb));
+    f3 wb = mul(Rb, mk3(s.v[3 * N + b], s.v[4 * N + b], s.v[5 * N + b]));
+    vc = vc - (mk3(s.v[b], s.v[N + b], s.v[2 * N + b]) + cross(wb, rb));
     wc = wc - wb;
     tr += pile_trace(P, s, b, Rb, rb);
   }
   // pair friction: the larger of the two geoms' coefficients
-  mu_t = fmaxf(s.mu0[a], mu_b[0]);
-  mu_tor = fmaxf(s.mu1[a], mu_b[1]);
-  mu_rol = fmaxf(s.mu2[a], mu_b[2]);
+  const float mu_t = fmaxf(s.mu0[a], mub0), mu_tor = fmaxf(s.mu1[a], mub1), mu_rol = fmaxf(s.mu2[a], mub2);
   float r = solimp_r(P, fabsf(k.phi));
   float mphi = r / (1.f - r) / tr;
   float w[6];
@@ -164,32 +189,33 @@ __device__ __forceinline__ void pile_contact(const StepParams& P, PileView& s, i
   pile_apply(s, a, Ra, ra, f, m, 1.f);
   if (b >= 0) pile_apply(s, b, Rb, rb, f, m, -1.f);
   atomicAdd(s.count, 1);
-  if (P.capture_cap > 0) capture_contact(P, world, s.count, ga, gb, sub, k.phi, k.p, k.n, w[0], mphi);
+  if (P.capture_cap > 0) capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi);
 }
 
-// narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none
+// narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none.
+// Spheres are handled as capsules of zero half length, so sphere-sphere and sphere-capsule
+// in either order share one branch.
 __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca) {
   const int ta = s.type[a], tb = s.type[b];
   const float4 pb4 = s.pb[b];
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
-  if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
-    k = nf_sphere_sphere(ca, s.rad[a], cb, s.rad[b]);
-  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
+  if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
     f3 ua = col(pile_R(s, a), 2), ub = col(pile_R(s, b), 2);
     f3 p1 = ca - s.hl[a] * ua, q1 = ca + s.hl[a] * ua, p2 = cb - s.hl[b] * ub, q2 = cb + s.hl[b] * ub;
     float ss, tt;
     nf_segments(p1, q1, p2, q2, ss, tt);
     k = nf_sphere_sphere(p1 + ss * (q1 - p1), s.rad[a], p2 + tt * (q2 - p2), s.rad[b]);
-  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_SPHERE) {
-    f3 u = col(pile_R(s, a), 2);
-    float t = fminf(fmaxf(dot(cb - ca, u), -s.hl[a]), s.hl[a]);
-    k = nf_sphere_sphere(ca + t * u, s.rad[a], cb, s.rad[b]);
-  } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CAPSULE) {
-    f3 u = col(pile_R(s, b), 2);
-    float t = fminf(fmaxf(dot(ca - cb, u), -s.hl[b]), s.hl[b]);
-    k = nf_sphere_sphere(ca, s.rad[a], cb + t * u, s.rad[b]);
+  } else if (ta != CF_GEOM_BOX && tb != CF_GEOM_BOX) {  // sphere-sphere, capsule-sphere, sphere-capsule
+    const bool capA = ta == CF_GEOM_CAPSULE;
+    const int ic = capA ? a : b;
+    const f3 cc = capA ? ca : cb, cs = capA ? cb : ca;
+    const float h = ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE ? 0.f : s.hl[ic];
+    const f3 u = col(pile_R(s, ic), 2);
+    const float t = fminf(fmaxf(dot(cs - cc, u), -h), h);
+    const f3 pc = cc + t * u;
+    k = nf_sphere_sphere(capA ? pc : ca, s.rad[a], capA ? cb : pc, s.rad[b]);
   } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {  // box-box: unsupported pair
     bool boxA = ta == CF_GEOM_BOX;
     int ib = boxA ? a : b, io = boxA ? b : a;
@@ -222,31 +248,26 @@ __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int s
   return nf_sphere_plane(c, r, o, nz);
 }
 
-// narrowphase + solve for one candidate code: (a << 16) | b, or (a << 16) | 0x8000 | plane.
-// Plane candidates and body pairs reach the (inlined) solve through one site each, and the
-// queues are flushed between the two candidate loops, so a 32-lane batch is homogeneous.
-__device__ void pile_candidate(const StepParams& P, PileView& s, const DScene& sc, int world, int code) {
+// number of sub-contacts a candidate can produce (a plane: per end sphere or box corner)
+__device__ __forceinline__ int pile_nsub(const PileView& s, int code) {
+  if (code < 0 || !((code & 0xffff) & kPlaneBit)) return code < 0 ? 0 : 1;
+  const int ta = s.type[code >> 16];
+  return ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
+}
+
+// narrowphase of candidate `code` (-1: none), sub-contact `sub`; true when it is a contact
+__device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView& s, int code, int sub, Raw& k) {
+  if (code < 0) return false;
   const int a = code >> 16, bc = code & 0xffff;
-  const int ta = s.type[a];
   const float4 pa4 = s.pb[a];
   const f3 ca = mk3(pa4.x, pa4.y, pa4.z);
-  const int ga = sc.geom0 + a;
-  if (bc & 0x8000) {
-    const int pi = bc & 0x7fff;
-    const float* pl = s.planes + 12 * pi;
-    const f3 o = mk3(pl[0], pl[1], pl[2]), nz = mk3(pl[3], pl[4], pl[5]), px = mk3(pl[6], pl[7], pl[8]);
-    const int gb = sc.geom0 + sc.plane0 + pi;
-    const int nsub = ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
-    for (int sub = 0; sub < nsub; ++sub) {
-      const Raw k = pile_narrow_plane(s, a, sub, ca, o, nz);
-      if (k.phi < P.margin) pile_contact(P, s, world, a, -1, ga, gb, sub, k, true, px, pl + 9);
-    }
-    return;
+  if (bc & kPlaneBit) {
+    const float* pl = s.planes + 12 * (bc & kPlaneMask);
+    k = pile_narrow_plane(s, a, sub, ca, mk3(pl[0], pl[1], pl[2]), mk3(pl[3], pl[4], pl[5]));
+  } else {
+    k = pile_narrow_pair(s, a, bc, ca);
   }
-  const int b = bc;
-  const float mub[3] = {s.mu0[b], s.mu1[b], s.mu2[b]};
-  const Raw k = pile_narrow_pair(s, a, b, ca);
-  if (k.phi < P.margin) pile_contact(P, s, world, a, b, ga, sc.geom0 + b, 0, k, false, mk3(0.f, 0.f, 0.f), mub);
+  return k.phi < P.margin;
 }
 
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
@@ -293,13 +314,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     o[0] = pl.o.x; o[1] = pl.o.y; o[2] = pl.o.z; o[3] = pl.n.x; o[4] = pl.n.y; o[5] = pl.n.z;
     o[6] = pl.x.x; o[7] = pl.x.y; o[8] = pl.x.z; o[9] = pl.mu[0]; o[10] = pl.mu[1]; o[11] = pl.mu[2];
   }
-  const int H = (N - 1) >> 1;
   const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
   int* queue = s.queue + wig * kQueue;
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
-    // ---- A. kinematics and smooth prediction (free body: c = (-m g, w x I w)) ----
+    // ---- A. kinematics and smooth prediction (free body: c = (-m g, w x I w)), v -> v_s ----
     for (int i = tid; i < N; i += T) {
       M33 R = quat_mat(s.qw[i], s.qx[i], s.qy[i], s.qz[i]);
 #pragma unroll
@@ -307,89 +327,125 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       float w0 = s.v[3 * N + i], w1 = s.v[4 * N + i], w2 = s.v[5 * N + i];
       float ii0 = s.I0[i], ii1 = s.I1[i], ii2 = s.I2[i];  // inverse principal inertia
       f3 gy = cross(mk3(w0, w1, w2), mk3(w0 / ii0, w1 / ii1, w2 / ii2));
-      s.vs[i] = s.v[i] + g.x * dt;
-      s.vs[N + i] = s.v[N + i] + g.y * dt;
-      s.vs[2 * N + i] = s.v[2 * N + i] + g.z * dt;
-      s.vs[3 * N + i] = w0 - dt * gy.x * ii0;
-      s.vs[4 * N + i] = w1 - dt * gy.y * ii1;
-      s.vs[5 * N + i] = w2 - dt * gy.z * ii2;
+      s.v[i] += g.x * dt;
+      s.v[N + i] += g.y * dt;
+      s.v[2 * N + i] += g.z * dt;
+      s.v[3 * N + i] = w0 - dt * gy.x * ii0;
+      s.v[4 * N + i] = w1 - dt * gy.y * ii1;
+      s.v[5 * N + i] = w2 - dt * gy.z * ii2;
 #pragma unroll
       for (int k = 0; k < 6; ++k) s.acc[k * N + i] = 0ull;
     }
     if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
     group_sync(gid, T);
 
-    // ---- B. broadphase into per-warp queues, narrowphase + impulses on full warps ----
-    int qn = 0;
-    const float margin = P.margin;
-    auto push = [&](int code) {
-      unsigned m = __ballot_sync(0xffffffffu, code >= 0);
-      if (code >= 0) queue[qn + __popc(m & ((1u << lane) - 1u))] = code;
-      qn += __popc(m);
-      if (qn >= 32) {
-        __syncwarp();
-        pile_candidate(P, s, sc, world, queue[qn - 32 + lane]);
-        qn -= 32;
-        __syncwarp();
-      }
-    };
-    // body-body pairs in 32 x 32 tiles (i-chunk <= j-chunk), dealt round-robin to the warps:
-    // each lane keeps body i in registers, the j loop is warp-uniform (broadcast loads)
+    // ---- B. broadphase -> candidate queue -> narrowphase -> contact queue -> solve ----
+    // Each warp walks its share of the candidate pairs one 32-lane row at a time: body pairs
+    // in 32 x 32 tiles (i-chunk <= j-chunk) dealt round-robin to the warps, each lane holding
+    // body i in registers while the j loop is warp-uniform (broadcast loads); then every body
+    // against each plane.  Bounding-sphere hits are compacted into the candidate queue; every
+    // 32 candidates run the narrowphase one per lane, whose hits are compacted into the
+    // contact queue; every 32 contacts are solved one per lane.  So the solve, the costly
+    // part, runs on full warps although only a fraction of the candidates touch.
     {
+      const float margin = P.margin;
+      const unsigned lt = (1u << lane) - 1u;
+      float* cq = s.cq + wig * kQueue * kCqWords;
       const int nchunk = (N + 31) >> 5;
       const int ntile = nchunk * (nchunk + 1) / 2;
-      for (int t = wig; t < ntile; t += gwarps) {
-        int ci = 0, rem = t;
+      int qn = 0, cn = 0;
+      int phase = 0;  // 0: body-pair tiles, 1: planes, 2: done
+      int t = wig, k = 0, kmax = 0, j0 = 0, ci = 0, cj = 0;
+      float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      int pl_i = 0, base = wig * 32;
+      auto load_tile = [&]() {
+        int rem = t;
+        ci = 0;
         while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
-        const int cj = ci + rem;
+        cj = ci + rem;
         const int i = (ci << 5) + lane;
-        float4 pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
+        pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
         if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
-        const int j0 = cj << 5;
-        const int kmax = min(32, N - j0);
-        for (int k = 0; k < kmax; ++k) {
-          const int j = j0 + k;
-          const float4 pj = s.pb[j];
+        j0 = cj << 5;
+        kmax = min(32, N - j0);
+        k = 0;
+      };
+      if (t < ntile) load_tile();
+      else phase = NP > 0 ? 1 : 2;
+      while (true) {
+        int code = -1;
+        if (phase == 0) {
+          const float4 pj = s.pb[j0 + k];
           const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
           const float rr = pi4.w + pj.w;
-          const bool up = ci != cj || lane < k;   // i < j
-          const int code = (up && dx * dx + dy * dy + dz * dz < rr * rr) ? ((i << 16) | j) : -1;
-          push(code);
+          const bool up = ci != cj || lane < k;  // i < j
+          if (up && dx * dx + dy * dy + dz * dz < rr * rr) code = ((((ci << 5) + lane)) << 16) | (j0 + k);
+          if (++k == kmax) {
+            t += gwarps;
+            if (t < ntile) load_tile();
+            else phase = NP > 0 ? 1 : 2;
+          }
+        } else if (phase == 1) {
+          const int a = base + lane;
+          if (a < N) {
+            const float* pl = s.planes + 12 * pl_i;
+            const float4 a4 = s.pb[a];
+            const float d = (a4.x - pl[0]) * pl[3] + (a4.y - pl[1]) * pl[4] + (a4.z - pl[2]) * pl[5];
+            if (d < a4.w + margin) code = (a << 16) | kPlaneBit | pl_i;
+          }
+          base += T;
+          if (base >= N) {
+            base = wig * 32;
+            if (++pl_i == NP) phase = 2;
+          }
         }
+        const bool flush = phase == 2;
+        const unsigned m = __ballot_sync(0xffffffffu, code >= 0);
+        if (code >= 0) queue[qn + __popc(m & lt)] = code;
+        qn += __popc(m);
+        while (qn >= 32 || (flush && (qn > 0 || cn > 0))) {
+          __syncwarp();
+          const int nb = min(qn, 32);
+          const int mine = lane < nb ? queue[qn - nb + lane] : -1;
+          qn -= nb;
+          const int my_nsub = pile_nsub(s, mine);
+          const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
+          for (int sub = 0; sub < nsub; ++sub) {
+            Raw kc;
+            const bool hit = sub < my_nsub && pile_narrow(P, s, mine, sub, kc);
+            const unsigned hm = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+              const int slot = cn + __popc(hm & lt);
+              cq[slot] = kc.p.x; cq[kQueue + slot] = kc.p.y; cq[2 * kQueue + slot] = kc.p.z;
+              cq[3 * kQueue + slot] = kc.n.x; cq[4 * kQueue + slot] = kc.n.y; cq[5 * kQueue + slot] = kc.n.z;
+              cq[6 * kQueue + slot] = kc.phi;
+              cq[7 * kQueue + slot] = __int_as_float(sub == 0 ? mine : (mine | (sub << 12)));
+            }
+            cn += __popc(hm);
+            const bool last = flush && qn == 0 && sub + 1 == nsub;
+            while (cn >= 32 || (last && cn > 0)) {
+              __syncwarp();
+              const int ns = min(cn, 32);
+              if (lane < ns) pile_solve(P, s, sc, world, cq, cn - ns + lane);
+              cn -= ns;
+              __syncwarp();
+            }
+          }
+        }
+        if (flush) break;
       }
     }
-    // flush the body-pair queue so that plane candidates form batches of their own
-    __syncwarp();
-    if (lane < qn) pile_candidate(P, s, sc, world, queue[lane]);
-    qn = 0;
-    __syncwarp();
-    // body-plane pairs
-    for (int pi = 0; pi < NP; ++pi) {
-      const float* pl = s.planes + 12 * pi;
-      const float ox = pl[0], oy = pl[1], oz = pl[2], nx = pl[3], ny = pl[4], nz = pl[5];
-      for (int base = wig * 32; base < N; base += T) {
-        int a = base + lane, code = -1;
-        if (a < N) {
-          float4 a4 = s.pb[a];
-          float d = (a4.x - ox) * nx + (a4.y - oy) * ny + (a4.z - oz) * nz;
-          if (d < a4.w + margin) code = (a << 16) | 0x8000 | pi;
-        }
-        push(code);
-      }
-    }
-    __syncwarp();
-    if (lane < qn) pile_candidate(P, s, sc, world, queue[lane]);
     group_sync(gid, T);
 
     // ---- C. velocity correction and semi-implicit Euler ----
     for (int i = tid; i < N; i += T) {
       float im = s.invm[i];
-      float v0 = s.vs[i] + from_fix(s.acc[i]) * im;
-      float v1 = s.vs[N + i] + from_fix(s.acc[N + i]) * im;
-      float v2 = s.vs[2 * N + i] + from_fix(s.acc[2 * N + i]) * im;
-      float w0 = s.vs[3 * N + i] + from_fix(s.acc[3 * N + i]) * s.I0[i];
-      float w1 = s.vs[4 * N + i] + from_fix(s.acc[4 * N + i]) * s.I1[i];
-      float w2 = s.vs[5 * N + i] + from_fix(s.acc[5 * N + i]) * s.I2[i];
+      float v0 = s.v[i] + from_fix(s.acc[i]) * im;
+      float v1 = s.v[N + i] + from_fix(s.acc[N + i]) * im;
+      float v2 = s.v[2 * N + i] + from_fix(s.acc[2 * N + i]) * im;
+      float w0 = s.v[3 * N + i] + from_fix(s.acc[3 * N + i]) * s.I0[i];
+      float w1 = s.v[4 * N + i] + from_fix(s.acc[4 * N + i]) * s.I1[i];
+      float w2 = s.v[5 * N + i] + from_fix(s.acc[5 * N + i]) * s.I2[i];
       s.v[i] = v0; s.v[N + i] = v1; s.v[2 * N + i] = v2;
       s.v[3 * N + i] = w0; s.v[4 * N + i] = w1; s.v[5 * N + i] = w2;
       s.pb[i].x += v0 * dt; s.pb[i].y += v1 * dt; s.pb[i].z += v2 * dt;
