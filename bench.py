@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--episode", type=int, default=EPISODE, help="episode length (the timed steps are its last)")
+    ap.add_argument("--jammed", action="store_true",
+                    help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
     return ap.parse_args()
 
 
@@ -135,18 +138,20 @@ def barrier_sum(x, world):
     return R.reduce_scalar(x, "sum")
 
 
-def run_pile(nbody, nworld, steps, warmup, rank, timed_events=True, flush=None):
+def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, jammed=False):
     """Simulate the episode; time the last `steps` steps with CUDA events on the launch stream,
-    flushing L2 (256 MB write) between timed steps outside the timed intervals."""
+    flushing L2 (256 MB write) between timed steps outside the timed intervals.  The autotuner
+    runs half way through the untimed part, on a state like the timed one (it restores it)."""
     import torch
     from paper_2603_12185_gb300 import comfree as CF
     from paper_2603_12185_gb300 import scenes as S
-    sb = S.make_pile(nworld, nbody, seed=R.rank_seed(1000, rank))
+    sb = S.make_pile(nworld, nbody, seed=R.rank_seed(1000, rank), jammed=jammed)
     model, b = CF.from_scenes(sb)
-    b.autotune(sb.dt)
     stream = torch.cuda.current_stream()
-    preroll = max(warmup, EPISODE - steps)
-    for _ in range(preroll):
+    preroll = max(warmup, episode - steps)
+    for i in range(preroll):
+        if i == preroll // 2:
+            b.autotune(sb.dt)
         b.step(sb.dt, 1)
     torch.cuda.synchronize()
     counts = torch.zeros(nworld, dtype=torch.int32, device="cuda")
@@ -318,7 +323,8 @@ def main():
     sweep = {}
     if not args.no_sweep:
         for n in SWEEP:
-            r = run_pile(n, args.worlds, min(args.steps, 100), args.warmup, rank, flush=flush)
+            r = run_pile(n, args.worlds, min(args.steps, 100), args.warmup, rank, flush=flush, episode=args.episode,
+                         jammed=args.jammed)
             sec = barrier_max(r["ms"] / 1e3, world)
             sweep[str(n)] = {"world_steps_per_s": world * r["worlds"] * r["steps"] / sec,
                              "contacts_per_s": barrier_sum(r["contacts"], world) / sec,
@@ -331,7 +337,8 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    res = run_pile(args.bodies, args.worlds, args.steps, args.warmup, rank, flush=flush)
+    res = run_pile(args.bodies, args.worlds, args.steps, args.warmup, rank, flush=flush, episode=args.episode,
+                   jammed=args.jammed)
     torch.cuda.synchronize()
     clk = clocks.stop()
     sec = barrier_max(res["ms"] / 1e3, world)
@@ -350,9 +357,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "world-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / res["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"pile_{res['worlds']}x{res['bodies']}", "worlds_per_gpu": res["worlds"],
+            "config": {"workload": f"pile_{res['worlds']}x{res['bodies']}" + ("_jammed" if args.jammed else ""),
+                       "worlds_per_gpu": res["worlds"],
                        "bodies_per_world": res["bodies"], "facets_per_contact": 18, "dt": 0.002,
-                       "episode_steps": EPISODE, "timed_steps": f"last {res['steps']} of the episode",
+                       "episode_steps": args.episode, "timed_steps": f"last {res['steps']} of the episode",
                        "preroll_untimed": res["preroll"], "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "contacts_per_s": total_contacts / sec,

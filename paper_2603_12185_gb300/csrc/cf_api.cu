@@ -799,8 +799,13 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
     if (st != CF_OK) return st;
     if (!b->artic_all) {
       float best = 3e38f;
-      int best_v = 0;
+      int best_v = 0, prev_blocks = 0;
       for (int var = 0; var < kPileVariants; ++var) {
+        // a variant built for more resident blocks only pays when the shared memory lets
+        // those blocks in; otherwise it just spills
+        const int blocks = step_max_blocks_per_sm(false, var, b->smem_all);
+        if (blocks <= prev_blocks) continue;
+        prev_blocks = blocks;
         b->variant = var;
         StepParams p = make_params(b, dt, 1);
         st = launch(b, p, false, b->smem_all, s);

@@ -75,8 +75,10 @@ struct Raw {
 
 __device__ __forceinline__ Raw nf_sphere_sphere(f3 ca, float ra, f3 cb, float rb) {
   f3 d = ca - cb;
-  float dist = norm3(d);
-  f3 n = dist > 0.f ? (1.f / dist) * d : mk3(0.f, 0.f, 1.f);
+  const float d2 = dot(d, d);
+  const float inv = rsqrtf(d2);
+  const float dist = d2 > 0.f ? d2 * inv : 0.f;
+  f3 n = d2 > 0.f ? inv * d : mk3(0.f, 0.f, 1.f);
   Raw k;
   k.phi = dist - ra - rb;
   k.p = 0.5f * ((ca - ra * n) + (cb + rb * n));
@@ -100,14 +102,14 @@ __device__ __forceinline__ void nf_segments(f3 p1, f3 q1, f3 p2, f3 q2, float& s
   float a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r), c = dot(d1, r), b = dot(d1, d2);
   float denom = a * e - b * b;
   if (denom > 1e-3f * (a * e)) {
-    s = fminf(fmaxf((b * f - c * e) / denom, 0.f), 1.f);
-    t = (b * s + f) / e;
+    s = fminf(fmaxf(__fdividef(b * f - c * e, denom), 0.f), 1.f);
+    t = __fdividef(b * s + f, e);
     if (t < 0.f) {
       t = 0.f;
-      s = fminf(fmaxf(-c / a, 0.f), 1.f);
+      s = fminf(fmaxf(__fdividef(-c, a), 0.f), 1.f);
     } else if (t > 1.f) {
       t = 1.f;
-      s = fminf(fmaxf((b - c) / a, 0.f), 1.f);
+      s = fminf(fmaxf(__fdividef(b - c, a), 0.f), 1.f);
     }
   } else {
     float sp = dot(p2 - p1, d1) / a, sq = dot(q2 - p1, d1) / a;
@@ -285,10 +287,23 @@ __device__ __forceinline__ void contact_frame(f3 n, bool plane, f3 px, f3& t1, f
 // r(|phi|) of Eq. r_scaling, x clamped to [0, 1]; the default power p = 2 is a square
 __device__ __forceinline__ float solimp_pow(float y, float p) { return p == 2.f ? y * y : powf(y, p); }
 __device__ __forceinline__ float solimp_r(const StepParams& P, float aphi) {
-  float x = fminf(fmaxf(aphi / P.solimp[2], 0.f), 1.f);
+  float x = fminf(fmaxf(__fdividef(aphi, P.solimp[2]), 0.f), 1.f);
   float m = P.solimp[3];
-  float g = x < m ? m * solimp_pow(x / m, P.solimp[4]) : 1.f - (1.f - m) * solimp_pow((1.f - x) / (1.f - m), P.solimp[4]);
+  float g = x < m ? m * solimp_pow(__fdividef(x, m), P.solimp[4])
+                  : 1.f - (1.f - m) * solimp_pow(__fdividef(1.f - x, 1.f - m), P.solimp[4]);
   return P.solimp[0] + (P.solimp[1] - P.solimp[0]) * g;
+}
+
+// Eight facets at angles j * 45 degrees: lambda_j = max(0, a + c_j b1 + s_j b2); returns
+// sum lambda_j, sum c_j lambda_j and sum s_j lambda_j.
+__device__ __forceinline__ void octa_facets(float a, float b1, float b2, float h, float& sn, float& s1, float& s2) {
+  const float u = h * b1, v = h * b2;
+  const float l0 = fmaxf(a + b1, 0.f), l2 = fmaxf(a + b2, 0.f), l4 = fmaxf(a - b1, 0.f), l6 = fmaxf(a - b2, 0.f);
+  const float l1 = fmaxf(a + u + v, 0.f), l3 = fmaxf(a - u + v, 0.f), l5 = fmaxf(a - u - v, 0.f),
+              l7 = fmaxf(a + u - v, 0.f);
+  sn = ((l0 + l4) + (l2 + l6)) + ((l1 + l5) + (l3 + l7));
+  s1 = (l0 - l4) + h * ((l1 - l5) + (l7 - l3));
+  s2 = (l2 - l6) + h * ((l1 - l5) + (l3 - l7));
 }
 
 // Closed-form facet impulses of one contact (Eqs. tilde_defs, cf_wrench with
@@ -304,6 +319,29 @@ __device__ __forceinline__ void facet_impulses(const StepParams& P, float vn, fl
   const float B = fmaf(kM, P.dt, dM);
   const float a = -kM * phi - B * vn;
   float N = 0.f, F1 = 0.f, F2 = 0.f, T = 0.f, R1 = 0.f, R2 = 0.f;
+  if (P.n_t == 8 && P.n_tor == 2 && P.n_rol == 8) {
+    // the 6D cone with 8 + 2 + 8 facets: directions at multiples of 45 degrees, so the facet
+    // sums reduce to signed combinations (h = cos 45 = sin 45)
+    const float h = 0.70710678f;
+    float sn, s1, s2;
+    octa_facets(a, B * mu_t * vt1, B * mu_t * vt2, h, sn, s1, s2);
+    N = sn; F1 = -mu_t * s1; F2 = -mu_t * s2;
+    const float bt = B * mu_tor * wn;
+    const float lp = fmaxf(a + bt, 0.f), lm = fmaxf(a - bt, 0.f);
+    N += lp + lm;
+    T = -mu_tor * (lp - lm);
+    octa_facets(a, B * mu_rol * wr1, B * mu_rol * wr2, h, sn, s1, s2);
+    N += sn; R1 = -mu_rol * s1; R2 = -mu_rol * s2;
+    w[0] = N; w[1] = F1; w[2] = F2; w[3] = T; w[4] = R1; w[5] = R2;
+    return;
+  }
+  if (P.n_t == 4 && P.n_tor == 0 && P.n_rol == 0) {  // the 4-facet pyramid: directions +-t1, +-t2
+    const float b1 = B * mu_t * vt1, b2 = B * mu_t * vt2;
+    const float l0 = fmaxf(a + b1, 0.f), l1 = fmaxf(a + b2, 0.f), l2 = fmaxf(a - b1, 0.f), l3 = fmaxf(a - b2, 0.f);
+    w[0] = (l0 + l2) + (l1 + l3); w[1] = -mu_t * (l0 - l2); w[2] = -mu_t * (l1 - l3);
+    w[3] = 0.f; w[4] = 0.f; w[5] = 0.f;
+    return;
+  }
   {
     const float b1 = B * mu_t * vt1, b2 = B * mu_t * vt2;
     for (int j = 0; j < P.n_t; ++j) {

@@ -180,7 +180,7 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   // pair friction: the larger of the two geoms' coefficients
   const float mu_t = fmaxf(s.mu0[a], mub0), mu_tor = fmaxf(s.mu1[a], mub1), mu_rol = fmaxf(s.mu2[a], mub2);
   float r = solimp_r(P, fabsf(k.phi));
-  float mphi = r / (1.f - r) / tr;
+  float mphi = __fdividef(r, (1.f - r) * tr);
   float w[6];
   facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                  P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
@@ -340,13 +340,14 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     group_sync(gid, T);
 
     // ---- B. broadphase -> candidate queue -> narrowphase -> contact queue -> solve ----
-    // Each warp walks its share of the candidate pairs one 32-lane row at a time: body pairs
-    // in 32 x 32 tiles (i-chunk <= j-chunk) dealt round-robin to the warps, each lane holding
-    // body i in registers while the j loop is warp-uniform (broadcast loads); then every body
-    // against each plane.  Bounding-sphere hits are compacted into the candidate queue; every
-    // 32 candidates run the narrowphase one per lane, whose hits are compacted into the
-    // contact queue; every 32 contacts are solved one per lane.  So the solve, the costly
-    // part, runs on full warps although only a fraction of the candidates touch.
+    // Body pairs are tested in 32 x 32 tiles (i-chunk <= j-chunk) dealt round-robin to the
+    // warps: each lane holds body i in registers, the j loop is warp-uniform (broadcast loads)
+    // and the bounding-sphere hits of a tile are kept as a 32-bit mask per lane, then drained
+    // one candidate per lane per pass; after the tiles, every body is tested against each
+    // plane.  Candidates are compacted into the candidate queue; every 32 of them run the
+    // narrowphase one per lane, whose hits are compacted into the contact queue; every 32
+    // contacts are solved one per lane.  So the solve, the costly part, runs on full warps
+    // although only a fraction of the candidates touch.
     {
       const float margin = P.margin;
       const unsigned lt = (1u << lane) - 1u;
@@ -355,35 +356,46 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       const int ntile = nchunk * (nchunk + 1) / 2;
       int qn = 0, cn = 0;
       int phase = 0;  // 0: body-pair tiles, 1: planes, 2: done
-      int t = wig, k = 0, kmax = 0, j0 = 0, ci = 0, cj = 0;
-      float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      int t = wig - gwarps, j0 = 0, i0 = 0;  // the first pass of the loop advances to tile wig
+      unsigned hits = 0;  // this lane's remaining bounding-sphere hits in the current tile (bit k: body j0 + k)
       int pl_i = 0, base = wig * 32;
-      auto load_tile = [&]() {
-        int rem = t;
-        ci = 0;
-        while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
-        cj = ci + rem;
-        const int i = (ci << 5) + lane;
-        pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
-        if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
-        j0 = cj << 5;
-        kmax = min(32, N - j0);
-        k = 0;
+      // advance to this warp's next tile (from t) with any hit; test it one j per step (broadcast
+      // loads), keeping the hits as a bit mask per lane
+      auto next_tile = [&]() {
+        while (true) {
+          if (t >= ntile) { phase = NP > 0 ? 1 : 2; return; }
+          int rem = t, ci = 0;
+          while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
+          const int cj = ci + rem;
+          i0 = ci << 5;
+          const int i = i0 + lane;
+          float4 pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
+          if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
+          j0 = cj << 5;
+          const int kmax = min(32, N - j0);
+          unsigned m = 0;
+#pragma unroll 8
+          for (int k = 0; k < kmax; ++k) {
+            const float4 pj = s.pb[j0 + k];
+            const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
+            const float rr = pi4.w + pj.w;
+            if (dx * dx + dy * dy + dz * dz < rr * rr) m |= 1u << k;
+          }
+          hits = ci != cj ? m : (m & (0xfffffffeu << lane));  // diagonal tile: j > i only
+          if (__any_sync(0xffffffffu, hits != 0)) return;
+          t += gwarps;
+        }
       };
-      if (t < ntile) load_tile();
-      else phase = NP > 0 ? 1 : 2;
       while (true) {
         int code = -1;
         if (phase == 0) {
-          const float4 pj = s.pb[j0 + k];
-          const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
-          const float rr = pi4.w + pj.w;
-          const bool up = ci != cj || lane < k;  // i < j
-          if (up && dx * dx + dy * dy + dz * dz < rr * rr) code = ((((ci << 5) + lane)) << 16) | (j0 + k);
-          if (++k == kmax) {
+          if (hits) {
+            code = ((i0 + lane) << 16) | (j0 + __ffs(hits) - 1);
+            hits &= hits - 1;
+          }
+          if (!__any_sync(0xffffffffu, hits != 0)) {
             t += gwarps;
-            if (t < ntile) load_tile();
-            else phase = NP > 0 ? 1 : 2;
+            next_tile();
           }
         } else if (phase == 1) {
           const int a = base + lane;
@@ -840,7 +852,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
     tr += artic_trace(P, s, sc, bb, k.p);
   }
   float r = solimp_r(P, fabsf(k.phi));
-  float mphi = r / (1.f - r) / tr;
+  float mphi = __fdividef(r, (1.f - r) * tr);
   float w[6];
   facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                  P.k_user * mphi, P.d_user * mphi, fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]),
