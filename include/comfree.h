@@ -44,7 +44,7 @@ typedef enum {
   CF_ERR_OUT_OF_MEMORY = 2,    /* host allocation failed / workspace too small        */
   CF_ERR_CUDA = 3,             /* a CUDA runtime call failed (message in cf_last_error) */
   CF_ERR_CONTACT_OVERFLOW = 4, /* contact capture buffer full for some world          */
-  CF_ERR_NONFINITE = 5,        /* a world produced a NaN/Inf state                    */
+  CF_ERR_NONFINITE = 5,        /* a world produced a NaN/Inf state or left the range   */
   CF_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                       */
   CF_ERR_UNSUPPORTED = 7       /* a valid but unsupported request                     */
 } cf_status;
@@ -53,6 +53,7 @@ typedef enum {
 #define CF_FLAG_NONFINITE 1
 #define CF_FLAG_CONTACT_OVERFLOW 2
 #define CF_FLAG_TIMEOUT 4
+#define CF_FLAG_RANGE 8  /* a contact's velocity change left the pile scatter's range (|dv| > 4096 per step) */
 
 /* geom and joint kinds */
 #define CF_GEOM_PLANE 0   /* static only; the plane through pos with normal = local +z   */

@@ -561,6 +561,7 @@ static cf_status read_errword(const cf_batch* b, cudaStream_t s, int* word) {
 
 static cf_status status_of_word(int w) {
   if (w & CF_FLAG_NONFINITE) return fail(CF_ERR_NONFINITE, "a world produced a non-finite state");
+  if (w & CF_FLAG_RANGE) return fail(CF_ERR_NONFINITE, "a contact velocity change left the scatter range");
   if (w & CF_FLAG_TIMEOUT) return fail(CF_ERR_TIMEOUT, "a bounded device wait gave up");
   if (w & CF_FLAG_CONTACT_OVERFLOW) return fail(CF_ERR_CONTACT_OVERFLOW, "contact capture overflow");
   return CF_OK;

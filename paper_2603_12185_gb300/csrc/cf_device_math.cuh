@@ -383,4 +383,20 @@ __device__ __forceinline__ float from_fix(unsigned long long a) {
   return __ll2float_rn((long long)a) * kFixInv;
 }
 
+// Two-word fixed point for the pile scatter: x 2^16 = h + f with h = floor(x 2^16) and the
+// fraction f in [0, 1) (both exact in FP32); h goes to a signed 32-bit word and round(f 2^20)
+// to an unsigned one, by native 32-bit shared atomics.  Integer sums do not depend on the
+// order, so the result is deterministic; the quantum is 2^-36 and the sum is exact while
+// |sum| < 2^15 and a word receives fewer than 4096 contributions.
+__device__ __forceinline__ void fix2_add(int* hi, unsigned* lo, float x, bool& range) {
+  range |= !(fabsf(x) <= kFix2Range);
+  x = fminf(fmaxf(x, -kFix2Range), kFix2Range) * kFix2Hi;
+  const float h = floorf(x);
+  atomicAdd(hi, (int)h);
+  atomicAdd(lo, __float2uint_rn((x - h) * kFix2Lo));
+}
+__device__ __forceinline__ float fix2_get(int hi, unsigned lo) {
+  return fmaf((float)hi, kFix2HiInv, (float)lo * kFix2LoInv);
+}
+
 }  // namespace cf

@@ -15,6 +15,12 @@ constexpr int kMaxTreeDof = 8;        // hinge DoFs per tree handled by the arti
 constexpr float kFixScale = 1099511627776.0f;          // 2^40: fixed-point impulse quantum
 constexpr float kFixInv = 9.094947017729282e-13f;      // 2^-40
 constexpr float kFixClamp = 8.0e6f;                    // |impulse| clamp before conversion
+// two-word velocity-change accumulators of pile worlds: x = hi 2^-16 + lo 2^-36
+constexpr float kFix2Hi = 65536.0f;                    // 2^16
+constexpr float kFix2Lo = 1048576.0f;                  // 2^20 (fraction bits of the low word)
+constexpr float kFix2HiInv = 1.52587890625e-05f;       // 2^-16
+constexpr float kFix2LoInv = 1.4551915228366852e-11f;  // 2^-36
+constexpr float kFix2Range = 4096.0f;                  // |dv| per contribution; larger raises CF_FLAG_RANGE
 
 // ---------------------------------------------------------------------------------------
 // scene templates (uploaded once per batch into the workspace)

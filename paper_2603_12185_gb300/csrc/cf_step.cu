@@ -4,8 +4,9 @@
 // Per world and step (ComFree-Sim, Sec. III and Algorithm 1):
 //   A. smooth prediction v_s = v + M~^-1 (tau - c - b v) dt            (Eq. smooth_vel; Kernel I)
 //   B. pair loop: bounding-sphere broadphase compacted into per-warp queues, narrowphase,
-//      contact frame, M(phi), per-facet closed-form impulses and the J~^T lambda scatter into
-//      fixed-point shared accumulators                (Eqs. tilde_defs, cf_wrench; Kernels II-III)
+//      contact frame, M(phi), per-facet closed-form impulses and the scatter of J~^T lambda
+//      (articulated worlds) or of M^-1 J~^T lambda (free bodies) into fixed-point shared
+//      accumulators                                    (Eqs. tilde_defs, cf_wrench; Kernels II-III)
 //   C. v+ = v_s + M~^-1 p, semi-implicit Euler                      (Eq. vel_correction; Kernel IV)
 #include <cstdio>
 
@@ -60,7 +61,8 @@ __device__ __forceinline__ void capture_contact(const StepParams& P, int world, 
 // =======================================================================================
 struct PileView {
   int N, NP;
-  unsigned long long* acc;  // [6][N]
+  int* acch;                // [6][N] velocity change (v; body-frame w), high words
+  unsigned* accl;           // [6][N] low words
   float4* pb;               // [N] position (x, y, z) and bounding radius
   float *qw, *qx, *qy, *qz;
   float* v;                 // [6][N] v, overwritten in place by v_s in phase A and by v+ in phase C
@@ -80,7 +82,7 @@ constexpr int kPlaneMask = 0xfff;
 constexpr int kCqWords = 8;
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
-  // acc (12 words/body) + 34 words/body + planes + both queues + counters, 16-byte granules
+  // accumulators (12 words/body) + 34 words/body + planes + both queues + counters, 16-byte granules
   size_t words = (size_t)N * 12 + (size_t)N * 34 + (size_t)NP * 12 + (size_t)warps * kQueue * (1 + kCqWords) + 4;
   return (words + 3) & ~(size_t)3;
 }
@@ -88,7 +90,8 @@ __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
 __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   PileView s;
   s.N = N; s.NP = NP;
-  s.acc = reinterpret_cast<unsigned long long*>(base);
+  s.acch = reinterpret_cast<int*>(base);
+  s.accl = reinterpret_cast<unsigned*>(base + (size_t)N * 6);
   float* f = base + (size_t)N * 12;
   s.pb = reinterpret_cast<float4*>(f); f += 4 * (size_t)N;
   s.qw = f; f += N; s.qx = f; f += N; s.qy = f; f += N; s.qz = f; f += N;
@@ -112,29 +115,33 @@ __device__ __forceinline__ M33 pile_R(const PileView& s, int i) {
   return R;
 }
 
-// translational trace tr(J_i M^-1 J_i^T) of a free body at lever r (world) or 1/m
-__device__ __forceinline__ float pile_trace(const StepParams& P, const PileView& s, int i, const M33& R, f3 r) {
-  float im = s.invm[i];
+// translational trace tr(J_i M^-1 J_i^T) of a free body at lever r (world) or 1/m;
+// im = 1/m, ii = inverse principal inertia
+__device__ __forceinline__ float pile_trace(const StepParams& P, float im, f3 ii, const M33& R, f3 r) {
   if (P.trace_mode) return im;
   f3 l = mulT(R, r);
-  float i0 = s.I0[i], i1 = s.I1[i], i2 = s.I2[i];  // inverse principal inertia
-  return 3.f * im + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
+  return 3.f * im + dot(r, r) * (ii.x + ii.y + ii.z) - (l.x * l.x * ii.x + l.y * l.y * ii.y + l.z * l.z * ii.z);
 }
 
-__device__ __forceinline__ void pile_apply(PileView& s, int i, const M33& R, f3 r, f3 f, f3 m, float sign) {
-  f3 ang = mulT(R, cross(r, f) + m);
-  atomicAdd(&s.acc[0 * s.N + i], to_fix(sign * f.x));
-  atomicAdd(&s.acc[1 * s.N + i], to_fix(sign * f.y));
-  atomicAdd(&s.acc[2 * s.N + i], to_fix(sign * f.z));
-  atomicAdd(&s.acc[3 * s.N + i], to_fix(sign * ang.x));
-  atomicAdd(&s.acc[4 * s.N + i], to_fix(sign * ang.y));
-  atomicAdd(&s.acc[5 * s.N + i], to_fix(sign * ang.z));
+// scatter the velocity change M^-1 J~^T lambda of one body: linear (world) and angular (body
+// frame), the contact wrench (f, m) acting at lever r with the given sign
+__device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, const M33& R, f3 r, f3 f, f3 m,
+                                           float sign, bool& range) {
+  const f3 ang = mulT(R, cross(r, f) + m);
+  const float sm = sign * im;
+  const int N = s.N;
+  fix2_add(s.acch + i, s.accl + i, sm * f.x, range);
+  fix2_add(s.acch + N + i, s.accl + N + i, sm * f.y, range);
+  fix2_add(s.acch + 2 * N + i, s.accl + 2 * N + i, sm * f.z, range);
+  fix2_add(s.acch + 3 * N + i, s.accl + 3 * N + i, sign * ii.x * ang.x, range);
+  fix2_add(s.acch + 4 * N + i, s.accl + 4 * N + i, sign * ii.y * ang.y, range);
+  fix2_add(s.acch + 5 * N + i, s.accl + 5 * N + i, sign * ii.z * ang.z, range);
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
 // (a plane contributes nothing).
 __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
-                                           const float* cq, int slot) {
+                                           const float* cq, int slot, bool& range) {
   Raw k;
   k.p = mk3(cq[slot], cq[kQueue + slot], cq[2 * kQueue + slot]);
   k.n = mk3(cq[3 * kQueue + slot], cq[4 * kQueue + slot], cq[5 * kQueue + slot]);
@@ -165,9 +172,12 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   f3 wa = mul(Ra, mk3(s.v[3 * N + a], s.v[4 * N + a], s.v[5 * N + a]));
   f3 vc = mk3(s.v[a], s.v[N + a], s.v[2 * N + a]) + cross(wa, ra);
   f3 wc = wa;
-  float tr = pile_trace(P, s, a, Ra, ra);
+  const float ima = s.invm[a];
+  const f3 iia = mk3(s.I0[a], s.I1[a], s.I2[a]);
+  float tr = pile_trace(P, ima, iia, Ra, ra);
   M33 Rb;
-  f3 rb;
+  f3 rb, iib;
+  float imb = 0.f;
   if (b >= 0) {
     Rb = pile_R(s, b);
     float4 pbb = s.pb[b];
@@ -175,7 +185,9 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
     f3 wb = mul(Rb, mk3(s.v[3 * N + b], s.v[4 * N + b], s.v[5 * N + b]));
     vc = vc - (mk3(s.v[b], s.v[N + b], s.v[2 * N + b]) + cross(wb, rb));
     wc = wc - wb;
-    tr += pile_trace(P, s, b, Rb, rb);
+    imb = s.invm[b];
+    iib = mk3(s.I0[b], s.I1[b], s.I2[b]);
+    tr += pile_trace(P, imb, iib, Rb, rb);
   }
   // pair friction: the larger of the two geoms' coefficients
   const float mu_t = fmaxf(s.mu0[a], mub0), mu_tor = fmaxf(s.mu1[a], mub1), mu_rol = fmaxf(s.mu2[a], mub2);
@@ -186,8 +198,8 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
                  P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
   f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
   f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
-  pile_apply(s, a, Ra, ra, f, m, 1.f);
-  if (b >= 0) pile_apply(s, b, Rb, rb, f, m, -1.f);
+  pile_apply(s, a, ima, iia, Ra, ra, f, m, 1.f, range);
+  if (b >= 0) pile_apply(s, b, imb, iib, Rb, rb, f, m, -1.f, range);
   atomicAdd(s.count, 1);
   if (P.capture_cap > 0) capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi);
 }
@@ -316,6 +328,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   }
   const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
   int* queue = s.queue + wig * kQueue;
+  bool range = false;  // some velocity change left the scatter's range
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
@@ -334,7 +347,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       s.v[4 * N + i] = w1 - dt * gy.y * ii1;
       s.v[5 * N + i] = w2 - dt * gy.z * ii2;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) s.acc[k * N + i] = 0ull;
+      for (int k = 0; k < 6; ++k) { s.acch[k * N + i] = 0; s.accl[k * N + i] = 0u; }
     }
     if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
     group_sync(gid, T);
@@ -438,7 +451,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
             while (cn >= 32 || (last && cn > 0)) {
               __syncwarp();
               const int ns = min(cn, 32);
-              if (lane < ns) pile_solve(P, s, sc, world, cq, cn - ns + lane);
+              if (lane < ns) pile_solve(P, s, sc, world, cq, cn - ns + lane, range);
               cn -= ns;
               __syncwarp();
             }
@@ -451,13 +464,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
 
     // ---- C. velocity correction and semi-implicit Euler ----
     for (int i = tid; i < N; i += T) {
-      float im = s.invm[i];
-      float v0 = s.v[i] + from_fix(s.acc[i]) * im;
-      float v1 = s.v[N + i] + from_fix(s.acc[N + i]) * im;
-      float v2 = s.v[2 * N + i] + from_fix(s.acc[2 * N + i]) * im;
-      float w0 = s.v[3 * N + i] + from_fix(s.acc[3 * N + i]) * s.I0[i];
-      float w1 = s.v[4 * N + i] + from_fix(s.acc[4 * N + i]) * s.I1[i];
-      float w2 = s.v[5 * N + i] + from_fix(s.acc[5 * N + i]) * s.I2[i];
+      float v0 = s.v[i] + fix2_get(s.acch[i], s.accl[i]);
+      float v1 = s.v[N + i] + fix2_get(s.acch[N + i], s.accl[N + i]);
+      float v2 = s.v[2 * N + i] + fix2_get(s.acch[2 * N + i], s.accl[2 * N + i]);
+      float w0 = s.v[3 * N + i] + fix2_get(s.acch[3 * N + i], s.accl[3 * N + i]);
+      float w1 = s.v[4 * N + i] + fix2_get(s.acch[4 * N + i], s.accl[4 * N + i]);
+      float w2 = s.v[5 * N + i] + fix2_get(s.acch[5 * N + i], s.accl[5 * N + i]);
       s.v[i] = v0; s.v[N + i] = v1; s.v[2 * N + i] = v2;
       s.v[3 * N + i] = w0; s.v[4 * N + i] = w1; s.v[5 * N + i] = w2;
       s.pb[i].x += v0 * dt; s.pb[i].y += v1 * dt; s.pb[i].z += v2 * dt;
@@ -497,6 +509,10 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   if (bad) {
     atomicOr(P.flags + world, CF_FLAG_NONFINITE);
     atomicOr(P.errword, CF_FLAG_NONFINITE);
+  }
+  if (range) {
+    atomicOr(P.flags + world, CF_FLAG_RANGE);
+    atomicOr(P.errword, CF_FLAG_RANGE);
   }
   if (tid == 0) {
     P.ncontact[world] = s.count[0];

@@ -97,6 +97,25 @@ def test_nonfinite_state_is_reported():
     assert st == 0 and not flags.any()
 
 
+def test_velocity_change_out_of_range_is_reported():
+    """Two overlapping spheres closing at 1e6 m/s: the contact's velocity change exceeds the
+    pile scatter's range, which raises CF_FLAG_RANGE (8) and CF_ERR_NONFINITE (5) instead of
+    wrapping the fixed-point words."""
+    sb = S.make_pile(2, 16, seed=7)
+    _, b = CF.from_scenes(sb)
+    q, v = _state(b)
+    nq, nv = 7 * 16, 6 * 16
+    q[nq:nq + 3] = [0.0, 0.0, 0.2]                  # world 1: body 0 and body 1 overlap
+    q[nq + 7:nq + 10] = [0.0, 0.0, 0.2 + 0.01]
+    v[nv + 2] = 1e6
+    v[nv + 6 + 2] = -1e6
+    b.set_state(torch.from_numpy(q).cuda(), torch.from_numpy(v).cuda())
+    b.step(sb.dt, 1)
+    st, flags = b.status()
+    assert st == 5 and flags[1] & 8 and not flags[0] & 8
+    b.status(clear=True)
+
+
 def test_invalid_arguments_are_rejected():
     sb = S.make_pile(2, 16, seed=8)
     _, b = CF.from_scenes(sb)
