@@ -35,6 +35,20 @@ BODIES = 256
 SWEEP = (16, 64)
 BYTES_PER_BODY = (7 + 6) * 4 * 2 + 8 * 4   # q, v read + written, 8-float parameter block read
 METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of HBM roofline"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel launch of the
+# 4096 x 256 pile workload late in the episode, from one ncu capture of the kernel sources
+# whose digest is given; reported as null once the sources differ from the ones measured.
+STEP_SOURCES = ("cf_step.cu", "cf_device_math.cuh", "cf_internal.cuh")
+TRAFFIC = {"digest": "3cbda01874997844", "bytes": 92.96e6}
+
+
+def step_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_12185_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -50,6 +64,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--episode", type=int, default=EPISODE, help="episode length (the timed steps are its last)")
+    ap.add_argument("--warps", type=int, default=0,
+                    help="warps per world (0: autotune); a fixed shape makes profiles comparable")
     ap.add_argument("--jammed", action="store_true",
                     help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
     return ap.parse_args()
@@ -138,7 +154,7 @@ def barrier_sum(x, world):
     return R.reduce_scalar(x, "sum")
 
 
-def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, jammed=False):
+def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, jammed=False, warps=0):
     """Simulate the episode; time the last `steps` steps with CUDA events on the launch stream,
     flushing L2 (256 MB write) between timed steps outside the timed intervals.  The autotuner
     runs half way through the untimed part, on a state like the timed one (it restores it)."""
@@ -149,8 +165,10 @@ def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, ja
     model, b = CF.from_scenes(sb)
     stream = torch.cuda.current_stream()
     preroll = max(warmup, episode - steps)
+    if warps > 0:
+        b.set_warps(0, warps)
     for i in range(preroll):
-        if i == preroll // 2:
+        if i == preroll // 2 and warps <= 0:
             b.autotune(sb.dt)
         b.step(sb.dt, 1)
     torch.cuda.synchronize()
@@ -338,7 +356,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     res = run_pile(args.bodies, args.worlds, args.steps, args.warmup, rank, flush=flush, episode=args.episode,
-                   jammed=args.jammed)
+                   jammed=args.jammed, warps=args.warps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     sec = barrier_max(res["ms"] / 1e3, world)
@@ -352,7 +370,9 @@ def main():
     alg_bytes = res["worlds"] * res["bodies"] * BYTES_PER_BODY
     achieved = alg_bytes / launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk and src,
+                "frac": achieved / pk["hbm_gbs"],
+                "traffic": TRAFFIC["bytes"] if TRAFFIC["digest"] == step_digest() else None,
+                "kernel_digest": step_digest(), "peak_source": src,
                 "kernel": "cf::step_kernel", "algorithmic_bytes_per_launch": alg_bytes}
     line = {"metric": METRIC, "value": value, "unit": "world-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / res["steps"], "higher_is_better": True,
