@@ -240,6 +240,15 @@ def run_extras(rank):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    # small case: 64 worlds x 8 spheres on a plane, 500 steps, one launch per step and one
+    # launch for all 500 steps (the kernel keeps the worlds in shared memory across steps)
+    sb = S.make_spheres_on_plane(64, seed=R.rank_seed(1900, rank))
+    _, b = CF.from_scenes(sb)
+    ms1 = timed(lambda: b.step(sb.dt, 1), 500)
+    ms500 = timed(lambda: b.step(sb.dt, 500), 3)
+    out["spheres_64x8"] = {"world_steps_per_s": 64 / (ms1 / 1e3), "ms_per_step": ms1,
+                           "world_steps_per_s_500_steps_per_launch": 64 * 500 / (ms500 / 1e3)}
+    del b
     # uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step
     sb = S.make_mixed(8192, seed=R.rank_seed(2000, rank))
     _, b = CF.from_scenes(sb)

@@ -164,6 +164,22 @@ def collect_and_train(template, params, episodes=32, ticks=60, N=1024, seed=0, e
     return mlp, float(np.mean(finals))
 
 
+def cold_start_costs(template, params, N, mlp=None, n_prop=0, goals_seed=77, episodes=16, seed=5):
+    """Best rollout cost of the first control tick from a cold start (zero warm-start mean) on
+    seeded held-out starts and goals: how good a plan N rollouts find with and without the
+    proposal before any warm start helps.  Returns the per-goal costs."""
+    rng = np.random.default_rng(goals_seed)
+    sb = S.make_hand(episodes, seed=goals_seed + 1)
+    goals = [random_goal(sb.q0[e], rng) for e in range(episodes)]
+    ctl = HandMPPI(template, params, N=N, seed=seed, mlp=mlp, n_prop=n_prop)
+    out = []
+    for e in range(episodes):
+        ctl.reset(sb.q0[e], sb.v0[e], goals[e])
+        ctl.tick()
+        out.append(float(ctl.stats[0].item()))
+    return np.array(out)
+
+
 def compare(template, params, mlp, goals_seed=123, episodes=8, ticks=60, plain_N=1024, learned_N=(128, 256, 512),
             n_prop_frac=0.5):
     """Final task cost of plain MPPI (plain_N rollouts) against MPPI with the proposal at fewer rollouts,
