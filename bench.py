@@ -246,8 +246,12 @@ def run_extras(rank):
     _, b = CF.from_scenes(sb)
     ms1 = timed(lambda: b.step(sb.dt, 1), 500)
     ms500 = timed(lambda: b.step(sb.dt, 500), 3)
+    g = b.graph(sb.dt, 1, repeat=100)         # 100 one-step launches in one CUDA graph
+    ms_graph = timed(g.replay, 5) / 100
     out["spheres_64x8"] = {"world_steps_per_s": 64 / (ms1 / 1e3), "ms_per_step": ms1,
+                           "world_steps_per_s_graph": 64 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
                            "world_steps_per_s_500_steps_per_launch": 64 * 500 / (ms500 / 1e3)}
+    del g
     del b
     # uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step
     sb = S.make_mixed(8192, seed=R.rank_seed(2000, rank))
@@ -257,8 +261,12 @@ def run_extras(rank):
         b.step(sb.dt, 1)
     ms = timed(lambda: b.step(sb.dt, 1), 20)
     c = b.contact_counts()
+    g = b.graph(sb.dt, 1, repeat=10)          # ten one-step launches captured in one CUDA graph
+    ms_graph = timed(g.replay, 5) / 10
     out["mixed_8192"] = {"world_steps_per_s": 8192 / (ms / 1e3), "ms_per_step": ms,
+                         "world_steps_per_s_graph": 8192 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
                          "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
+    del g
     del b
     # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
     T = 100

@@ -156,7 +156,11 @@ cf_status cf_set_ctrl(cf_batch* batch, const float* tau, int32_t T, int32_t on_d
 
 /* Advance worlds nsteps steps of length dt (one launch; the state stays on chip across the
  * nsteps).  worlds: NULL = all, else a host list of n distinct world indices.  Errors:
- * CF_ERR_INVALID_ARGUMENT (dt <= 0, nsteps < 1, bad index), CF_ERR_CUDA (launch failure). */
+ * CF_ERR_INVALID_ARGUMENT (dt <= 0, nsteps < 1, bad index), CF_ERR_CUDA (launch failure).
+ * With worlds == NULL the call enqueues exactly one kernel launch and nothing else, so it may
+ * be captured into a CUDA graph (replays then re-run the same dt, nsteps and launch shape);
+ * make one uncaptured call first, which sets the kernel's attributes.  The subset form copies
+ * its world list from pageable host memory and cannot be captured. */
 cf_status cf_step(cf_batch* batch, const int32_t* worlds, int32_t n, float dt, int32_t nsteps, void* stream);
 
 /* Per-world number of contacts (phi < margin) detected in the last step of the last cf_step,

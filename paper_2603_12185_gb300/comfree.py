@@ -244,6 +244,18 @@ class Batch:
         wl = None if worlds is None else np.ascontiguousarray(worlds, dtype=np.int32)
         check(lib().cf_step(self.h, _ptr(wl), 0 if wl is None else len(wl), float(dt), int(nsteps), _stream(stream)))
 
+    def graph(self, dt, nsteps=1, repeat=1):
+        """A CUDA graph of `repeat` all-world cf_step launches (dt, nsteps each); replay() runs
+        them again on the current stream.  One eager step first sets the kernel attributes, so
+        the batch advances by nsteps here."""
+        self.step(dt, nsteps)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(repeat):
+                self.step(dt, nsteps)
+        return g
+
     def contact_counts(self, stream=None):
         out = np.zeros(self.W, np.int32)
         check(lib().cf_get_contact_counts(self.h, _ptr(out), 0, _stream(stream)))
