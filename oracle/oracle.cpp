@@ -17,6 +17,7 @@
  *   4. all-pairs narrowphase -> contacts (phi, point, normal)
  *   5. per contact: frame, relative Jacobian blocks J_n, J_t, J_tor, J_rol      (Sec. III-A)
  *      and the constraint-space impedance M(phi)                    (Eqs. k_d_setting, r_scaling)
+ *      (or, trace_mode 2, the exact diagonal impedance of each facet, Sec. III-B)
  *   6. per facet: J~ = J_n - mu_s d_j^T J_s, s = J~ v_s,
  *      lambda dt = ( -k M(phi) (s dt + phi) - d M(phi) s )_+        (Eqs. tilde_defs, cf_wrench)
  *   7. p = sum J~^T lambda dt                                         (Algorithm 1, Kernel III)
@@ -100,7 +101,8 @@ typedef struct {
   double solimp[5]; /* r_min, r_max, width, midpoint, power */
   double margin;
   int n_t, n_tor, n_rol;
-  int trace_mode; /* 0: tr(J_i M~^-1 J_i^T) of the translational point Jacobian, 1: 1/m_i */
+  int trace_mode; /* 0: tr(J_i M~^-1 J_i^T) of the translational point Jacobian, 1: 1/m_i,
+                     2: the exact diagonal impedance of Sec. III-B, one value per facet */
 } ow_params;
 
 /* one detected contact, for tests */
@@ -855,7 +857,20 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           }
           S sv(0.0);
           for (int i = 0; i < st.nv; ++i) sv += Jf[i] * vs[i];
-          S lam = -kM * (sv * DT + k.phi) - dM * sv;
+          S lam;
+          if (prm->trace_mode == 2) {
+            /* Sec. III-B, the diagonal form K dt + D = 1/(dt w_j), w_j = J~_j M~^-1 J~_j^T; the
+               user's (k, d) keep splitting it between the gap and the velocity term:
+               M_j = 1 / ((k dt + d) w_j) in place of M(phi) */
+            tmp = Jf;
+            solve_all(st, L, tmp);
+            S wj(0.0);
+            for (int i = 0; i < st.nv; ++i) wj += Jf[i] * tmp[i];
+            S Mj = S(1.0) / ((S(prm->k_user) * DT + S(prm->d_user)) * wj);
+            lam = -S(prm->k_user) * Mj * (sv * DT + k.phi) - S(prm->d_user) * Mj * sv;
+          } else {
+            lam = -kM * (sv * DT + k.phi) - dM * sv;
+          }
           if (lam < S(0.0)) lam = S(0.0);
           else ++nact;
           ++nf;
@@ -882,7 +897,7 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           rc.t1[0] = val(t1.x); rc.t1[1] = val(t1.y); rc.t1[2] = val(t1.z);
           rc.t2[0] = val(t2.x); rc.t2[1] = val(t2.y); rc.t2[2] = val(t2.z);
           rc.trace_a = val(trace[0]); rc.trace_b = val(trace[1]);
-          rc.r = val(r); rc.mphi = val(mphi); rc.lam_sum = val(wrench[0]);
+          rc.r = val(r); rc.mphi = prm->trace_mode == 2 ? 0.0 : val(mphi); rc.lam_sum = val(wrench[0]);
           for (int i = 0; i < 6; ++i) rc.wrench[i] = val(wrench[i]);
           rc.nfacet = nf; rc.nactive = nact;
           rec->contacts.push_back(rc);

@@ -100,7 +100,8 @@ class Params:
     n_t: int = 4
     n_tor: int = 0
     n_rol: int = 0
-    trace_mode: int = 0  # 0: translational point-Jacobian trace, 1: sum of 1/m of the bodies
+    trace_mode: int = 0  # 0: translational point-Jacobian trace, 1: sum of 1/m of the bodies,
+    #                      2: exact diagonal impedance per facet (Sec. III-B)
 
 
 @dataclass

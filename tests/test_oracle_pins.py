@@ -132,6 +132,40 @@ def test_worked_single_contact_step(oracle, v0x):
         assert sum(lam) == pytest.approx(4 * Mphi * 0.000223544, rel=1e-9)  # printed digits of the hand sum
 
 
+def test_exact_impedance_worked_step(oracle):
+    """The exact diagonal impedance of Sec. III-B (trace_mode 2), by hand: a 1 kg sphere
+    (r = 0.05, I = 1e-3) at rest 2 mm into the plane, 4 facets, mu = 0.5.  Facet j's row is
+    (u_j, l x u_j) with u_j = n - mu d_j and lever l = (0, 0, -(r - 0.001)); its diagonal
+    w_j = |u_j|^2 / m + |l x u_j|^2 / I = 1.25 + (0.5 * 0.049)^2 / 1e-3 = 1.85025, and
+    M_j = 1 / ((k dt + d) w_j) takes the place of M(phi)."""
+    k, dd, mu, phi = 0.1, 0.001, 0.5, -0.002
+    w = 1.25 + (0.5 * 0.049) ** 2 / 1e-3
+    Mj = 1.0 / ((k * DT + dd) * w)
+    s = -G * DT
+    lam = -k * Mj * (s * DT + phi) - dd * Mj * s
+    assert lam == pytest.approx(450.389 * 0.000223544, rel=1e-5)   # printed digits of the hand values
+    d = Wd.sphere_on_plane()
+    q, v = Wd.free_state((0, 0, 0.048))
+    rec = oracle.step_record(d, Wd.params(n_t=4, trace_mode=2), DT, q, v)
+    c = rec["contacts"][0]
+    assert c["lam_sum"] == pytest.approx(4 * lam, rel=1e-12)
+    np.testing.assert_allclose(rec["v"][:3], [0, 0, s + 4 * lam], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][3:], 0.0, atol=1e-15)
+
+
+def test_exact_impedance_cancels_each_facet_velocity(oracle):
+    """With k = 0 the diagonal form gives every active facet the impulse -s_j / w_j that alone
+    brings its own velocity to zero.  Frictionless 4-facet contact of a sphere falling at 1 m/s:
+    four equal facets J_n with w = 1/m, so v+_n = s - 4 s = -3 s, s = v_n - g dt."""
+    d = Wd.sphere_on_plane(mu=(0.0, 0.0, 0.0))
+    q, v = Wd.free_state((0, 0, 0.05 - 1e-6), lin=(0, 0, -1.0))
+    p = Wd.params(n_t=4, trace_mode=2, k_user=0.0, d_user=0.001)
+    rec = oracle.step_record(d, p, DT, q, v)
+    s = -1.0 - G * DT
+    np.testing.assert_allclose(rec["v"][:3], [0, 0, -3 * s], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(rec["v"][3:], 0.0, atol=1e-14)
+
+
 def test_rest_penetration_fixed_point(oracle):
     """A sphere at rest settles where the F facet impulses carry its weight:
     F M(phi) (k (g dt^2 + |phi|) + d g dt) = m g dt (all facets see s = -g dt), with M(phi) at
