@@ -268,6 +268,31 @@ def run_extras(rank):
                          "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
     del g
     del b
+    # exact diagonal impedance (trace_mode 2) against the heuristic: one step of the jammed
+    # 4096 x 256 pile from the same state (events around the step only)
+    import dataclasses
+    sbj = S.make_pile(4096, 256, seed=R.rank_seed(1950, rank), jammed=True)
+    res = {}
+    for mode in (0, 2):
+        sbj.params = dataclasses.replace(sbj.params, trace_mode=mode)
+        _, bj = CF.from_scenes(sbj)
+        bj.set_warps(0, 4)
+        q0, v0 = bj.get_state()
+        q0, v0 = q0.clone(), v0.clone()
+        ts = []
+        for i in range(6):
+            bj.set_state(q0, v0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bj.step(sbj.dt, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            if i:
+                ts.append(e0.elapsed_time(e1))
+        res["heuristic" if mode == 0 else "exact"] = {"ms_per_step": float(np.mean(ts)),
+                                                      "contacts_per_world": float(bj.contact_counts().mean())}
+        del bj
+    out["exact_impedance_jammed_pile_4096x256"] = res
     # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
     T = 100
     sb = S.make_hand(1024, seed=R.rank_seed(2100, rank))

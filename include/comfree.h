@@ -103,7 +103,10 @@ typedef struct {
   int32_t n_t, n_tor, n_rol; /* facets per subspace (Eq. tilde_defs); n_tor in {0, 2},
                                 n_t and n_rol in {0, 2..16} (symmetric unit directions)  */
   int32_t trace_mode;      /* 0: M(phi) with tr(J_i M~^-1 J_i^T) of body i's translational
-                              point Jacobian; 1: 1/m_i per body                         */
+                              point Jacobian; 1: 1/m_i per body; 2: the exact diagonal
+                              impedance of Sec. III-B instead of M(phi): per facet j,
+                              M_j = 1 / ((k_user dt + d_user) J~_j M~^-1 J~_j^T) (solimp
+                              unused; cf_step_grad answers CF_ERR_UNSUPPORTED)           */
 } cf_model_desc;
 
 /* Validate a description and build the host model.  Errors: CF_ERR_INVALID_ARGUMENT for a

@@ -232,7 +232,7 @@ extern "C" cf_status cf_model_create(const cf_model_desc* desc, cf_model** out) 
   const double* si = desc->solimp;
   if (!(si[0] > 0.0 && si[0] <= si[1] && si[1] < 1.0 && si[2] > 0.0 && si[3] > 0.0 && si[3] < 1.0 && si[4] >= 1.0))
     return fail(CF_ERR_INVALID_ARGUMENT, "solimp must satisfy 0 < r_min <= r_max < 1, width > 0, 0 < mid < 1, power >= 1");
-  if (desc->trace_mode != 0 && desc->trace_mode != 1) return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode must be 0 or 1");
+  if (desc->trace_mode < 0 || desc->trace_mode > 2) return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode must be 0, 1 or 2");
   cf_model* m = new (std::nothrow) cf_model();
   if (!m) return fail(CF_ERR_OUT_OF_MEMORY, "model allocation");
   for (int s = 0; s < desc->nscene; ++s) {
@@ -650,9 +650,10 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
 
 static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t smem, cudaStream_t s) {
   if (p.nunits <= 0) return CF_OK;
-  int per_sm = step_max_blocks_per_sm(artic, b->variant, smem);
+  const int var = b->model.trace_mode == 2 ? kExactVariant : b->variant;
+  int per_sm = step_max_blocks_per_sm(artic, var, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
-  cudaError_t e = launch_step(p, artic, b->variant, grid, smem, s);
+  cudaError_t e = launch_step(p, artic, var, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "step launch");
   return CF_OK;
 }
@@ -798,7 +799,7 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
   {
     cf_status st = upload_units(b, s);
     if (st != CF_OK) return st;
-    if (!b->artic_all) {
+    if (!b->artic_all && b->model.trace_mode != 2) {
       float best = 3e38f;
       int best_v = 0, prev_blocks = 0;
       for (int var = 0; var < kPileVariants; ++var) {
@@ -860,6 +861,7 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
                                   float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream) {
   if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
   if (b->opts.grad_steps <= 0) return fail(CF_ERR_UNSUPPORTED, "batch created without an adjoint tape (grad_steps = 0)");
+  if (b->model.trace_mode == 2) return fail(CF_ERR_UNSUPPORTED, "the adjoint covers the heuristic impedance only");
   if (T < 1 || T > b->opts.grad_steps || T > b->opts.max_ctrl_steps)
     return fail(CF_ERR_INVALID_ARGUMENT, "T = %d outside [1, min(grad_steps, max_ctrl_steps)]", T);
   if (!(dt > 0.f)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
@@ -1060,13 +1062,14 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
     p.rsin[j] = (float)std::sin(th);
   }
   const bool artic = !sc.pile;
+  const int var = m->trace_mode == 2 ? kExactVariant : 0;
   const size_t smem = world_smem_bytes(sc, warps) * per;
   if (smem > step_max_dynamic_smem()) return fail(CF_ERR_UNSUPPORTED, "a world needs %zu bytes of shared memory", smem);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = step_max_blocks_per_sm(artic, 0, smem);
+  const int per_sm = step_max_blocks_per_sm(artic, var, smem);
   const int grid = std::min(p.nunits, std::max(1, nsm * per_sm));
-  e = launch_step(p, artic, 0, grid, smem, s);
+  e = launch_step(p, artic, var, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "step launch");
   return CF_OK;
 }

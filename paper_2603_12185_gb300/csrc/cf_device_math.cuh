@@ -306,6 +306,73 @@ __device__ __forceinline__ void octa_facets(float a, float b1, float b2, float h
   s2 = (l2 - l6) + h * ((l1 - l5) + (l3 - l7));
 }
 
+// Gram matrix, through M~^-1, of a contact's six basis rows: point velocity along n, t1, t2
+// (0..2) and relative angular velocity about n, t1, t2 (3..5) -- the entries the facet rows
+// J~_j = J_n - mu d_j^T J_s need for their diagonals w_j = J~_j M~^-1 J~_j^T.
+struct Gram {
+  float nn, n1, n2, t11, t12, t22;  // translational block
+  float n3, r33;                    // torsional
+  float n4, n5, r44, r45, r55;      // rolling
+};
+
+__device__ __forceinline__ void gram_zero(Gram& g) {
+  g.nn = g.n1 = g.n2 = g.t11 = g.t12 = g.t22 = g.n3 = g.r33 = g.n4 = g.n5 = g.r44 = g.r45 = g.r55 = 0.f;
+}
+
+// add a free body: inverse mass im, inverse principal inertia ii, rotation R, lever r
+__device__ __forceinline__ void gram_add_free(Gram& g, float im, f3 ii, const M33& R, f3 r, f3 n, f3 t1, f3 t2) {
+  const f3 a0 = mulT(R, cross(r, n)), a1 = mulT(R, cross(r, t1)), a2 = mulT(R, cross(r, t2));
+  const f3 e0 = mulT(R, n), e1 = mulT(R, t1), e2 = mulT(R, t2);
+  auto q = [&](f3 x, f3 y) { return x.x * y.x * ii.x + x.y * y.y * ii.y + x.z * y.z * ii.z; };
+  g.nn += im + q(a0, a0); g.n1 += q(a0, a1); g.n2 += q(a0, a2);
+  g.t11 += im + q(a1, a1); g.t12 += q(a1, a2); g.t22 += im + q(a2, a2);
+  g.n3 += q(a0, e0); g.r33 += q(e0, e0);
+  g.n4 += q(a0, e1); g.n5 += q(a0, e2); g.r44 += q(e1, e1); g.r45 += q(e1, e2); g.r55 += q(e2, e2);
+}
+
+// the diagonal of a facet row n_row - mu (c x + s y) for the Gram entries of its rows:
+// nn, (n.x, n.y), (x.x, x.y, y.y)
+__device__ __forceinline__ float gram_facet(float nn, float nx, float ny, float xx, float xy, float yy, float mu,
+                                            float c, float s) {
+  return nn - 2.f * mu * (c * nx + s * ny) + mu * mu * (c * c * xx + 2.f * c * s * xy + s * s * yy);
+}
+
+// Facet impulses with the exact diagonal impedance of Sec. III-B: K_j dt + D_j = 1/(dt w_j),
+// split between the gap and the velocity term as k : d, i.e. M(phi) replaced per facet by
+// M_j = 1 / ((k dt + d) w_j).  Same inputs and output as facet_impulses.
+__device__ __forceinline__ void facet_impulses_exact(const StepParams& P, float vn, float vt1, float vt2, float wn,
+                                                     float wr1, float wr2, float phi, float mu_t, float mu_tor,
+                                                     float mu_rol, const Gram& g, float w[6]) {
+  const float kd = fmaf(P.k_user, P.dt, P.d_user);
+  const float a = -P.k_user * phi - kd * vn;
+  float N = 0.f, F1 = 0.f, F2 = 0.f, T = 0.f, R1 = 0.f, R2 = 0.f;
+  for (int j = 0; j < P.n_t; ++j) {
+    const float c = P.tcos[j], s = P.tsin[j];
+    const float gj = a + kd * mu_t * (c * vt1 + s * vt2);
+    if (gj > 0.f) {
+      const float lam = gj / (kd * gram_facet(g.nn, g.n1, g.n2, g.t11, g.t12, g.t22, mu_t, c, s));
+      N += lam; F1 = fmaf(c, lam, F1); F2 = fmaf(s, lam, F2);
+    }
+  }
+  for (int j = 0; j < P.n_tor; ++j) {
+    const float sg = (j & 1) ? -1.f : 1.f;
+    const float gj = a + kd * mu_tor * sg * wn;
+    if (gj > 0.f) {
+      const float lam = gj / (kd * (g.nn - 2.f * mu_tor * sg * g.n3 + mu_tor * mu_tor * g.r33));
+      N += lam; T = fmaf(sg, lam, T);
+    }
+  }
+  for (int j = 0; j < P.n_rol; ++j) {
+    const float c = P.rcos[j], s = P.rsin[j];
+    const float gj = a + kd * mu_rol * (c * wr1 + s * wr2);
+    if (gj > 0.f) {
+      const float lam = gj / (kd * gram_facet(g.nn, g.n4, g.n5, g.r44, g.r45, g.r55, mu_rol, c, s));
+      N += lam; R1 = fmaf(c, lam, R1); R2 = fmaf(s, lam, R2);
+    }
+  }
+  w[0] = N; w[1] = -mu_t * F1; w[2] = -mu_t * F2; w[3] = -mu_tor * T; w[4] = -mu_rol * R1; w[5] = -mu_rol * R2;
+}
+
 // Closed-form facet impulses of one contact (Eqs. tilde_defs, cf_wrench with
 // K = k M(phi)/dt, D = d M(phi)/dt, impulse lambda dt = (-kM (s dt + phi) - dM s)_+).
 // In: the contact-space velocities of the smooth prediction (normal, tangential pair,

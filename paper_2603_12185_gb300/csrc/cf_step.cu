@@ -139,7 +139,9 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, 
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
-// (a plane contributes nothing).
+// (a plane contributes nothing).  kGeneral: the instantiation that also offers the exact
+// diagonal impedance (trace_mode 2).
+template <bool kGeneral>
 __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
                                            const float* cq, int slot, bool& range) {
   Raw k;
@@ -191,11 +193,21 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   }
   // pair friction: the larger of the two geoms' coefficients
   const float mu_t = fmaxf(s.mu0[a], mub0), mu_tor = fmaxf(s.mu1[a], mub1), mu_rol = fmaxf(s.mu2[a], mub2);
-  float r = solimp_r(P, fabsf(k.phi));
-  float mphi = __fdividef(r, (1.f - r) * tr);
+  float mphi = 0.f;
   float w[6];
-  facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
-                 P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
+  if (kGeneral && P.trace_mode == 2) {
+    Gram g;
+    gram_zero(g);
+    gram_add_free(g, ima, iia, Ra, ra, k.n, t1, t2);
+    if (b >= 0) gram_add_free(g, imb, iib, Rb, rb, k.n, t1, t2);
+    facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                         mu_t, mu_tor, mu_rol, g, w);
+  } else {
+    float r = solimp_r(P, fabsf(k.phi));
+    mphi = __fdividef(r, (1.f - r) * tr);
+    facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                   P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
+  }
   f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
   f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
   pile_apply(s, a, ima, iia, Ra, ra, f, m, 1.f, range);
@@ -282,6 +294,7 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
   return k.phi < P.margin;
 }
 
+template <bool kGeneral>
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -451,7 +464,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
             while (cn >= 32 || (last && cn > 0)) {
               __syncwarp();
               const int ns = min(cn, 32);
-              if (lane < ns) pile_solve(P, s, sc, world, cq, cn - ns + lane, range);
+              if (lane < ns) pile_solve<kGeneral>(P, s, sc, world, cq, cn - ns + lane, range);
               cn -= ns;
               __syncwarp();
             }
@@ -850,6 +863,64 @@ __device__ void artic_apply(const StepParams& P, ArticView& s, const DScene& sc,
   }
 }
 
+// Gram matrix of a contact's six basis rows through M~^-1 (exact diagonal impedance): free
+// bodies in closed form; hinge chains through their joint-space rows and the tree's explicit
+// M~^-1, with the rows of two bodies of one tree combined first (J = J_A - J_B).
+__device__ __noinline__ void artic_gram(const StepParams& P, const ArticView& s, const DScene& sc, int ba, int bb,
+                                        f3 p, f3 n, f3 t1, f3 t2, Gram& g) {
+  const DBody* B = P.bodies + sc.body0;
+  float G[2][6][kMaxTreeDof];
+  int gtree[2] = {-1, -1}, gnv[2] = {0, 0};
+  int ng = 0;
+  gram_zero(g);
+  for (int side = 0; side < 2; ++side) {
+    const int b = side ? bb : ba;
+    if (b < 0) continue;
+    const float sg = side ? -1.f : 1.f;
+    const DBody& bd = B[b];
+    const DTree& tr = P.trees[sc.tree0 + bd.tree];
+    if (tr.free) {
+      gram_add_free(g, 1.f / bd.mass, mk3(1.f / bd.inertia[0], 1.f / bd.inertia[1], 1.f / bd.inertia[2]),
+                    ld33(s.bR + 9 * b), p - ld3(s.bx + 3 * b), n, t1, t2);
+      continue;
+    }
+    int slot = (ng > 0 && gtree[0] == bd.tree) ? 0 : ng;
+    if (slot == ng) {
+      gtree[slot] = bd.tree; gnv[slot] = tr.nv;
+      for (int x = 0; x < 6; ++x)
+        for (int i = 0; i < kMaxTreeDof; ++i) G[slot][x][i] = 0.f;
+      ++ng;
+    }
+    for (int a = b; a >= 0; a = B[a].parent) {
+      const int k = B[a].voff - tr.voff;
+      const f3 ax = ld3(s.bax + 3 * a);
+      const f3 lin = cross(ax, p - ld3(s.bx + 3 * a));  // point velocity per unit joint rate
+      G[slot][0][k] += sg * dot(n, lin); G[slot][1][k] += sg * dot(t1, lin); G[slot][2][k] += sg * dot(t2, lin);
+      G[slot][3][k] += sg * dot(n, ax); G[slot][4][k] += sg * dot(t1, ax); G[slot][5][k] += sg * dot(t2, ax);
+    }
+  }
+  for (int slot = 0; slot < ng; ++slot) {
+    const float* mi = s.minv + (size_t)gtree[slot] * kMaxTreeDof * kMaxTreeDof;
+    const int nv = gnv[slot];
+    float H[6][kMaxTreeDof];  // M~^-1 G_y
+    for (int y = 0; y < 6; ++y)
+      for (int i = 0; i < nv; ++i) {
+        float acc = 0.f;
+        for (int j = 0; j < nv; ++j) acc += mi[i * kMaxTreeDof + j] * G[slot][y][j];
+        H[y][i] = acc;
+      }
+    auto q = [&](int x, int y) {
+      float acc = 0.f;
+      for (int i = 0; i < nv; ++i) acc += G[slot][x][i] * H[y][i];
+      return acc;
+    };
+    g.nn += q(0, 0); g.n1 += q(0, 1); g.n2 += q(0, 2); g.t11 += q(1, 1); g.t12 += q(1, 2); g.t22 += q(2, 2);
+    g.n3 += q(0, 3); g.r33 += q(3, 3);
+    g.n4 += q(0, 4); g.n5 += q(0, 5); g.r44 += q(4, 4); g.r45 += q(4, 5); g.r55 += q(5, 5);
+  }
+}
+
+template <bool kExact>
 __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world, int ga,
                                            int gb, int sub, const Raw& k, bool plane, f3 px) {
   const DGeom& GA = P.geoms[sc.geom0 + ga];
@@ -867,12 +938,20 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
     wc = wc - omb;
     tr += artic_trace(P, s, sc, bb, k.p);
   }
-  float r = solimp_r(P, fabsf(k.phi));
-  float mphi = __fdividef(r, (1.f - r) * tr);
+  float mphi = 0.f;
   float w[6];
-  facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
-                 P.k_user * mphi, P.d_user * mphi, fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]),
-                 fmaxf(GA.mu[2], GB.mu[2]), w);
+  if (kExact && P.trace_mode == 2) {
+    Gram g;
+    artic_gram(P, s, sc, ba, bb, k.p, k.n, t1, t2, g);
+    facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                         fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]), fmaxf(GA.mu[2], GB.mu[2]), g, w);
+  } else {
+    float r = solimp_r(P, fabsf(k.phi));
+    mphi = __fdividef(r, (1.f - r) * tr);
+    facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
+                   P.k_user * mphi, P.d_user * mphi, fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]),
+                   fmaxf(GA.mu[2], GB.mu[2]), w);
+  }
   f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
   f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
   artic_apply(P, s, sc, ba, k.p, f, m);
@@ -883,6 +962,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
 }
 
 // narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
+template <bool kExact>
 __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
   int ga = code >> 16, gb = code & 0xffff;
   const DGeom* G = P.geoms + sc.geom0;
@@ -896,18 +976,18 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     f3 nz = col(Rb, 2), px = col(Rb, 0);
     if (ta == CF_GEOM_SPHERE) {
       Raw k = nf_sphere_plane(ca, sa[0], cb, nz);
-      if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, 0, k, true, px);
+      if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, true, px);
     } else if (ta == CF_GEOM_CAPSULE) {
       f3 ax = col(Ra, 2);
       for (int e = 0; e < 2; ++e) {
         Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
-        if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, e, k, true, px);
+        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, e, k, true, px);
       }
     } else if (ta == CF_GEOM_BOX) {
       for (int ci = 0; ci < 8; ++ci) {
         f3 corner = ca + mul(Ra, mk3((ci & 4) ? sa[0] : -sa[0], (ci & 2) ? sa[1] : -sa[1], (ci & 1) ? sa[2] : -sa[2]));
         Raw k = nf_sphere_plane(corner, 0.f, cb, nz);
-        if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, ci, k, true, px);
+        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, ci, k, true, px);
       }
     }
     return;
@@ -947,7 +1027,7 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
       k = nf_sphere_box(co + t * u, os[0], cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < P.margin) artic_contact(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
+  if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
 }
 
 // MPC running cost of the state at the start of a step (Sec. V, Eq. mpc cost terms): object
@@ -988,6 +1068,7 @@ __device__ float artic_running_cost(const StepParams& P, const ArticView& s, con
   return c;
 }
 
+template <bool kExact>
 __device__ void artic_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -1056,12 +1137,12 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
       qn += __popc(m);
       __syncwarp();
       if (qn >= 32) {
-        artic_candidate(P, s, sc, world, queue[qn - 32 + lane]);
+        artic_candidate<kExact>(P, s, sc, world, queue[qn - 32 + lane]);
         qn -= 32;
         __syncwarp();
       }
     }
-    if (lane < qn) artic_candidate(P, s, sc, world, queue[lane]);
+    if (lane < qn) artic_candidate<kExact>(P, s, sc, world, queue[lane]);
     group_sync(gid, T);
     // ---- C. correction and integration, per tree ----
     for (int t = tid; t < sc.ntree; t += T) {
@@ -1142,7 +1223,9 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
-template <bool kArtic, int kMinBlocks>
+// kArtic: articulated worlds compiled in; kExact: the exact diagonal impedance (trace_mode 2)
+// compiled into the pile path, so that the other instantiations keep their register budget.
+template <bool kArtic, int kMinBlocks, bool kExact>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_unit;
@@ -1160,8 +1243,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) 
       size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, U.warps)
                            : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, U.warps);
       float* base = smem + per * gid;
-      if (!kArtic || sc.pile) pile_world(P, base, world, gid, U.warps);
-      else artic_world(P, base, world, gid, U.warps);
+      if (!kArtic || sc.pile) pile_world<kExact>(P, base, world, gid, U.warps);
+      else artic_world<kExact>(P, base, world, gid, U.warps);
     }
     __syncthreads();
   }
@@ -1185,11 +1268,15 @@ size_t world_smem_bytes(const DScene& s, int warps) {
 // kernel variants: pile-only with 2, 3 or 4 resident CTAs per SM (register budget), and the
 // mixed (articulated) instantiation
 using StepFn = void (*)(StepParams);
-static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2>, step_kernel<false, 3>, step_kernel<false, 4>,
-                                                step_kernel<true, 2>};
-static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0};
+static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2, false>, step_kernel<false, 3, false>,
+                                                step_kernel<false, 4, false>, step_kernel<true, 2, false>,
+                                                step_kernel<true, 2, true>};
+static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0, 0};
 
-static int variant_index(bool artic, int variant) { return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant)); }
+static int variant_index(bool artic, int variant) {
+  if (variant == kExactVariant) return 4;
+  return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant));
+}
 
 static cudaError_t ensure_attr(int vi) {
   if (g_max_dyn[vi]) return cudaSuccess;
