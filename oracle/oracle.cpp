@@ -93,6 +93,8 @@ typedef struct {
   const double* geom_quat;     /* [ngeom*4]                                            */
   const double* geom_size;     /* [ngeom*3]                                            */
   const double* geom_mu;       /* [ngeom*3] tangential, torsional, rolling             */
+  const double* body_range;    /* [nbody*2] hinge limits (lower, upper); lower < upper limits */
+  const double* body_frictionloss; /* [nbody] hinge dry friction (N m)                  */
 } ow_world;
 
 typedef struct {
@@ -904,6 +906,50 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         }
       }
     }
+  /* joint limits and dry joint friction (Sec. III-A names them in the system model; the paper
+     gives no formula, so these are readings):
+     - a limit is a one-row frictionless constraint J = +e_k (lower, gap q - lo) or -e_k (upper,
+       gap hi - q) under the same impulse law as a contact facet, its "trace" (M~^-1)_kk;
+     - dry friction applies the impulse that alone would stop the predicted joint velocity,
+       clamped to +-frictionloss dt.
+     Both act on the smooth prediction and add to p like the contacts. */
+  for (int b = 0; b < w->nbody; ++b) {
+    if (w->body_jnt[b] != HINGE) continue;
+    const double lo = w->body_range ? w->body_range[2 * b] : 0.0;
+    const double hi = w->body_range ? w->body_range[2 * b + 1] : 0.0;
+    const double fl = w->body_frictionloss ? w->body_frictionloss[b] : 0.0;
+    if (!(lo < hi) && !(fl > 0.0)) continue;
+    const int kd = st.vadr[b];
+    tmp.assign(st.nv, S(0.0));
+    tmp[kd] = S(1.0);
+    solve_all(st, L, tmp);
+    const S wkk = tmp[kd];
+    if (lo < hi) {
+      for (int side = 0; side < 2; ++side) {
+        const S gap = side == 0 ? q[st.qadr[b]] - S(lo) : S(hi) - q[st.qadr[b]];
+        if (!(val(gap) < margin)) continue;
+        const S sgn(side == 0 ? 1.0 : -1.0);
+        const S sv = sgn * vs[kd];
+        S Mk;
+        if (prm->trace_mode == 2) {
+          Mk = S(1.0) / ((S(prm->k_user) * DT + S(prm->d_user)) * wkk);
+        } else {
+          const S r = solimp_r(fabs(gap), prm->solimp);
+          Mk = r / (S(1.0) - r) / wkk;
+        }
+        S lam = -S(prm->k_user) * Mk * (sv * DT + gap) - S(prm->d_user) * Mk * sv;
+        if (lam > S(0.0)) pgen[kd] += sgn * lam;
+      }
+    }
+    if (fl > 0.0) {
+      S lam = -vs[kd] / wkk;
+      const S cap = S(fl) * DT;
+      if (lam > cap) lam = cap;
+      if (lam < -cap) lam = -cap;
+      pgen[kd] += lam;
+    }
+  }
+
   /* 8. velocity correction, Eq. vel_correction */
   std::vector<S> dv = pgen;
   solve_all(st, L, dv);

@@ -39,7 +39,8 @@ class OWorld(C.Structure):
     _fields_ = [("nbody", C.c_int), ("ngeom", C.c_int)] + [
         (n, C.c_void_p) for n in ("body_parent", "body_jnt", "body_pos", "body_quat", "body_axis", "body_ipos",
                                   "body_mass", "body_inertia", "body_damping", "geom_type", "geom_body",
-                                  "geom_pos", "geom_quat", "geom_size", "geom_mu")]
+                                  "geom_pos", "geom_quat", "geom_size", "geom_mu", "body_range",
+                                  "body_frictionloss")]
 
 
 class OParams(C.Structure):
@@ -93,12 +94,19 @@ class World:
 
     _INT = ("body_parent", "body_jnt", "geom_type", "geom_body")
 
+    # optional per-body arrays: absent means no joint limits and no joint friction
+    _OPTIONAL = {"body_range": 2, "body_frictionloss": 1}
+
     def __init__(self, desc):
         self.arrays = {}
+        nb = len(desc["body_parent"])
         for k in OWorld._fields_[2:]:
             name = k[0]
             dt = np.int32 if name in self._INT else np.float64
-            self.arrays[name] = np.ascontiguousarray(np.asarray(desc[name], dtype=dt).reshape(-1))
+            val = desc.get(name)
+            if val is None:
+                val = np.zeros(nb * self._OPTIONAL[name])
+            self.arrays[name] = np.ascontiguousarray(np.asarray(val, dtype=dt).reshape(-1))
         self.s = OWorld(len(self.arrays["body_parent"]), len(self.arrays["geom_type"]),
                         *[_p(self.arrays[k[0]]) for k in OWorld._fields_[2:]])
         nq, nv = C.c_int(), C.c_int()

@@ -123,6 +123,8 @@ class Template:
     geom_size: np.ndarray
     geom_mu: np.ndarray
     pile: bool = False
+    body_range: np.ndarray = None         # [nbody, 2] hinge limits (lower < upper limits), or None
+    body_frictionloss: np.ndarray = None  # [nbody] hinge dry friction (N m), or None
 
     @property
     def nbody(self):
@@ -172,6 +174,9 @@ class Batch:
             "body_parent", "body_jnt", "body_pos", "body_quat", "body_axis", "body_ipos", "body_mass",
             "body_inertia", "body_damping", "geom_type", "geom_body", "geom_pos", "geom_quat", "geom_size",
             "geom_mu")}
+        for k in ("body_range", "body_frictionloss"):
+            if getattr(t, k) is not None:
+                d[k] = np.array(getattr(t, k), dtype=np.float64)
         p = self.world_param[w]
         if p is not None:
             nb = t.nbody

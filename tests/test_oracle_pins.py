@@ -166,6 +166,37 @@ def test_exact_impedance_cancels_each_facet_velocity(oracle):
     np.testing.assert_allclose(rec["v"][3:], 0.0, atol=1e-14)
 
 
+def _hinge(axis, ipos, rng=(0.0, 0.0), fl=0.0, inertia=(1e-3, 1e-3, 2e-3)):
+    return Wd.world([dict(parent=-1, jnt=S.HINGE, pos=(0, 0, 1.0), axis=axis, ipos=ipos, mass=1.0, inertia=inertia,
+                          range=rng, frictionloss=fl)],
+                    [dict(type=S.PLANE, body=-1)])
+
+
+@pytest.mark.parametrize("q0,v_exp", [(-0.51, 0.019), (0.51, -0.019), (0.2, 0.0)])
+def test_joint_limit_closed_form(oracle, q0, v_exp):
+    """A limit is a one-row constraint with the contact impulse law (reading 15).  A vertical
+    hinge (no gravity torque) at rest, 1 cm past its limit [-0.5, 0.5]: r(|gap|) = r_max = 0.95,
+    M = r/(1-r) / (M~^-1)_kk, lambda dt = k M |gap|, so v+ = (M~^-1)_kk lambda dt =
+    k r/(1-r) |gap| = 0.1 * 19 * 0.01 = 0.019 rad/s whatever the inertia; inside the range
+    nothing happens."""
+    d = _hinge((0, 0, 1), (0, 0, 0), rng=(-0.5, 0.5))
+    q, v, _ = oracle.step(d, Wd.params(), DT, 1, [q0], [0.0])
+    assert v[0] == pytest.approx(v_exp, rel=1e-12, abs=1e-15)
+    assert q[0] == pytest.approx(q0 + DT * v_exp, rel=1e-12)
+
+
+@pytest.mark.parametrize("fl", [2.0, 0.5])
+def test_dry_joint_friction_closed_form(oracle, fl):
+    """Dry joint friction (reading 15): a horizontal hinge (axis y) with its 1 kg centre of mass
+    10 cm out along x carries the gravity torque 0.981 N m about M = 1e-3 + 1 * 0.1^2 = 0.011.
+    The stopping impulse -v_s M = -0.981 dt fits inside +-fl dt for fl = 2 (the joint holds:
+    v+ = 0); for fl = 0.5 it saturates: v+ = (0.981 - 0.5) dt / 0.011."""
+    d = _hinge((0, 1, 0), (0.1, 0, 0), fl=fl)
+    q, v, _ = oracle.step(d, Wd.params(), DT, 1, [0.0], [0.0])
+    exp = 0.0 if fl == 2.0 else (0.981 - 0.5) * DT / 0.011
+    assert v[0] == pytest.approx(exp, rel=1e-9, abs=1e-15)
+
+
 def test_rest_penetration_fixed_point(oracle):
     """A sphere at rest settles where the F facet impulses carry its weight:
     F M(phi) (k (g dt^2 + |phi|) + d g dt) = m g dt (all facets see s = -g dt), with M(phi) at

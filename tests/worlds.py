@@ -24,6 +24,8 @@ def world(bodies, geoms):
         "geom_quat": np.array([g.get("quat", (1, 0, 0, 0)) for g in geoms], float).reshape(-1, 4),
         "geom_size": np.array([g.get("size", (0, 0, 0)) for g in geoms], float).reshape(-1, 3),
         "geom_mu": np.array([g.get("mu", (0.5, 0.0, 0.0)) for g in geoms], float).reshape(-1, 3),
+        "body_range": np.array([b.get("range", (0.0, 0.0)) for b in bodies], float).reshape(nb, 2),
+        "body_frictionloss": np.array([b.get("frictionloss", 0.0) for b in bodies], float).reshape(nb),
     }
     return d
 
