@@ -393,7 +393,7 @@ def test_mass_matrix_matches_kinetic_energy(oracle):
             d = {k: getattr(t, k) for k in t.__dataclass_fields__ if k not in ("name", "pile")}
             # fingers only: drop the free cube (its quasi-velocity is not a q-derivative)
             keep = np.arange(1, t.nbody)
-            d = {k: (v[keep] if k.startswith("body_") else v) for k, v in d.items()}
+            d = {k: (v[keep] if k.startswith("body_") and v is not None else v) for k, v in d.items()}
             d["body_parent"] = np.where(d["body_parent"] > 0, d["body_parent"] - 1, -1).astype(np.int32)
             d["geom_body"] = np.where(d["geom_body"] > 0, d["geom_body"] - 1, -1).astype(np.int32)
             d["geom_type"] = np.where(d["geom_body"] >= 0, d["geom_type"], S.PLANE).astype(np.int32)
