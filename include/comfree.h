@@ -90,6 +90,9 @@ typedef struct {
   const double* geom_size;      /* [ngeom][3]                                             */
   const double* geom_mu;        /* [ngeom][3] tangential, torsional, rolling coefficients */
   int32_t pile;
+  const double* body_range;     /* [nbody][2] hinge limits (lower, upper), nullable; a hinge
+                                   with lower < upper is limited (Sec. III-A)             */
+  const double* body_frictionloss; /* [nbody] hinge dry friction (N m, >= 0), nullable     */
 } cf_scene_desc;
 
 /* Global model parameters (one set per model). */

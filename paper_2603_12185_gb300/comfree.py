@@ -30,7 +30,8 @@ class SceneDesc(C.Structure):
     _fields_ = [("nbody", C.c_int32), ("ngeom", C.c_int32)] + [
         (n, C.c_void_p) for n in ("body_parent", "body_jnt", "body_pos", "body_quat", "body_axis", "body_ipos",
                                   "body_mass", "body_inertia", "body_damping", "geom_type", "geom_body", "geom_pos",
-                                  "geom_quat", "geom_size", "geom_mu")] + [("pile", C.c_int32)]
+                                  "geom_quat", "geom_size", "geom_mu")] + [("pile", C.c_int32)] + [
+        (n, C.c_void_p) for n in ("body_range", "body_frictionloss")]
 
 
 class ModelDesc(C.Structure):
@@ -146,14 +147,20 @@ class Model:
     def __init__(self, templates, params):
         keep = []
         descs = (SceneDesc * len(templates))()
+        required = [n for n, _ in SceneDesc._fields_[2:17]]
+        optional = ("body_range", "body_frictionloss")
         for i, t in enumerate(templates):
             arrs = {}
-            for name, _ in SceneDesc._fields_[2:-1]:
-                a = np.ascontiguousarray(getattr(t, name), dtype=np.int32 if name in self._INT else np.float64)
+            for name in required + list(optional):
+                val = getattr(t, name, None)
+                if val is None:
+                    arrs[name] = None
+                    continue
+                a = np.ascontiguousarray(val, dtype=np.int32 if name in self._INT else np.float64)
                 arrs[name] = a
                 keep.append(a)
-            descs[i] = SceneDesc(len(t.body_parent), len(t.geom_type),
-                                 *[_ptr(arrs[n]) for n, _ in SceneDesc._fields_[2:-1]], int(bool(t.pile)))
+            descs[i] = SceneDesc(len(t.body_parent), len(t.geom_type), *[_ptr(arrs[n]) for n in required],
+                                 int(bool(t.pile)), *[_ptr(arrs[n]) for n in optional])
         d = ModelDesc()
         d.nscene = len(templates)
         d.scenes = descs

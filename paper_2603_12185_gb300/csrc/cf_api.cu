@@ -113,6 +113,23 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
     for (int k = 0; k < 4; ++k) o.quat[k] = (float)d.body_quat[4 * b + k];
     o.mass = (float)mass;
     o.damping = (float)d.body_damping[b];
+    o.limited = 0;
+    o.range[0] = o.range[1] = 0.f;
+    o.frictionloss = 0.f;
+    if (j == CF_JOINT_HINGE && d.body_range && d.body_range[2 * b] < d.body_range[2 * b + 1]) {
+      if (!std::isfinite(d.body_range[2 * b]) || !std::isfinite(d.body_range[2 * b + 1]))
+        return fail(CF_ERR_INVALID_ARGUMENT, "scene %d body %d: joint range must be finite", si, b);
+      o.limited = 1;
+      o.range[0] = (float)d.body_range[2 * b];
+      o.range[1] = (float)d.body_range[2 * b + 1];
+    }
+    if (d.body_frictionloss) {
+      const double fl = d.body_frictionloss[b];
+      if (!(fl >= 0.0) || !std::isfinite(fl))
+        return fail(CF_ERR_INVALID_ARGUMENT, "scene %d body %d: frictionloss must be >= 0", si, b);
+      if (j == CF_JOINT_HINGE) o.frictionloss = (float)fl;
+    }
+    if (o.limited || o.frictionloss > 0.f) sc.joints = 1;
     if (j == CF_JOINT_FREE) {
       for (int k = 0; k < 3; ++k)
         if (d.body_ipos[3 * b + k] != 0.0)

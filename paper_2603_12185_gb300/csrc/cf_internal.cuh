@@ -29,13 +29,15 @@ struct alignas(16) DScene {
   int nbody, ngeom, nq, nv;
   int nu, ntree, pile, nplane;
   int body0, geom0, tree0, pair0;
-  int npair, plane0, maxdepth, pad;
+  int npair, plane0, maxdepth, joints;  // joints: some hinge is limited or has dry friction
 };
 
 struct alignas(16) DBody {
   int parent, jnt, qoff, voff;      // parent is scene-local, offsets world-local
   int uoff, tree, pad0, pad1;       // uoff: actuator slot of a hinge, -1 otherwise
-  float pos[3], quat[4], axis[3], ipos[3], mass, inertia[3], damping, pad2[2];
+  float pos[3], quat[4], axis[3], ipos[3], mass, inertia[3], damping, frictionloss;
+  float range[2];                   // hinge limits (used when limited != 0)
+  int limited, pad3[3];
 };
 
 struct alignas(16) DGeom {

@@ -961,6 +961,48 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
     capture_contact(P, world, s.count, sc.geom0 + ga, sc.geom0 + gb, sub, k.phi, k.p, k.n, w[0], mphi);
 }
 
+// Joint limits and dry joint friction of one hinge tree (Sec. III-A's system model), closed
+// form from the smooth prediction like the contacts: a limit is a one-row frictionless
+// constraint J = +-e_k with gap q - lower or upper - q under the facet impulse law, its trace
+// (M~^-1)_kk; dry friction applies the impulse that alone stops the predicted joint velocity,
+// clamped to +-frictionloss dt.
+__device__ void artic_joint_constraints(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr, int t) {
+  if (tr.free) return;
+  const DBody* B = P.bodies + sc.body0;
+  const float* mi = s.minv + (size_t)t * kMaxTreeDof * kMaxTreeDof;
+  for (int j = 0; j < tr.nbody; ++j) {
+    const DBody& bd = B[tr.body0 + j];
+    if (!bd.limited && !(bd.frictionloss > 0.f)) continue;
+    const int k = bd.voff - tr.voff;
+    const float wkk = mi[k * kMaxTreeDof + k];
+    const float vsk = s.vs[bd.voff];
+    float pk = 0.f;
+    if (bd.limited) {
+      const float q = s.q[bd.qoff];
+      for (int side = 0; side < 2; ++side) {
+        const float gap = side ? bd.range[1] - q : q - bd.range[0];
+        if (!(gap < P.margin)) continue;
+        const float sg = side ? -1.f : 1.f;
+        const float sv = sg * vsk;
+        float Mk;
+        if (P.trace_mode == 2) {
+          Mk = 1.f / (fmaf(P.k_user, P.dt, P.d_user) * wkk);
+        } else {
+          const float r = solimp_r(P, fabsf(gap));
+          Mk = r / ((1.f - r) * wkk);
+        }
+        const float lam = -P.k_user * Mk * fmaf(sv, P.dt, gap) - P.d_user * Mk * sv;
+        if (lam > 0.f) pk += sg * lam;
+      }
+    }
+    if (bd.frictionloss > 0.f) {
+      const float cap = bd.frictionloss * P.dt;
+      pk += fminf(fmaxf(-vsk / wkk, -cap), cap);
+    }
+    atomicAdd(s.acc + bd.voff, to_fix(pk));
+  }
+}
+
 // narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
 template <bool kExact>
 __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
@@ -1143,6 +1185,8 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
       }
     }
     if (lane < qn) artic_candidate<kExact>(P, s, sc, world, queue[lane]);
+    if (sc.joints)
+      for (int t = tid; t < sc.ntree; t += T) artic_joint_constraints(P, s, sc, P.trees[sc.tree0 + t], t);
     group_sync(gid, T);
     // ---- C. correction and integration, per tree ----
     for (int t = tid; t < sc.ntree; t += T) {

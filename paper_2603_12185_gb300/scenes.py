@@ -31,6 +31,7 @@ Generators:
 """
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass, field
 import numpy as np
 
@@ -422,9 +423,25 @@ def hand_states(rng, nworld):
 HAND_PARAMS = dict(k_user=0.1, d_user=0.002, n_t=8, n_tor=2, n_rol=8)
 
 
-def make_hand(nworld=1024, seed=0, dt=0.002, nsteps=100, d_user=0.002):
+def with_joint_limits(t, abduction=(-0.35, 0.35), flexion=(-0.2, 1.3), frictionloss=0.0):
+    """Copy of a hand template whose hinges are limited (the first joint of each finger to
+    `abduction`, the three flexion joints to `flexion`, radians) and carry dry friction."""
+    rng_ = np.zeros((t.nbody, 2))
+    fl = np.zeros(t.nbody)
+    for b in range(t.nbody):
+        if t.body_jnt[b] != HINGE:
+            continue
+        first = t.body_parent[b] < 0 or t.body_jnt[t.body_parent[b]] != HINGE
+        rng_[b] = abduction if first else flexion
+        fl[b] = frictionloss
+    return dataclasses.replace(t, name=t.name + "_limited", body_range=rng_, body_frictionloss=fl)
+
+
+def make_hand(nworld=1024, seed=0, dt=0.002, nsteps=100, d_user=0.002, joint_limits=False, frictionloss=0.0):
     rng = np.random.default_rng(seed)
     t = hand_template(seed)
+    if joint_limits or frictionloss > 0.0:
+        t = with_joint_limits(t, frictionloss=frictionloss)
     q0, v0 = hand_states(rng, nworld)
     p = dict(HAND_PARAMS)
     p["d_user"] = d_user
