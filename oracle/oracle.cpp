@@ -792,8 +792,24 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         V3<S> x0 = mulT(bg.R, cg.c - bg.c), wl = mulT(bg.R, cg.R.col(2));
         S t = capsule_box_param(x0, wl, S(cs[1]), vload<S>(bs));
         sphere_box(cg.c + t * cg.R.col(2), S(cs[0]), bg.c, bg.R, vload<S>(bs), capA, raw);
+      } else if (ta == BOX && tb == BOX) {
+        /* box-box: every corner of either box against the other box's signed distance (the
+           box-plane rule with the other box in place of the plane); A's corners are subs 0..7,
+           B's 8..15.  Edges crossing edges with no corner inside are not detected. */
+        for (int side = 0; side < 2; ++side) {
+          const GeomPose<S>& cg = side ? G[gb] : G[ga];   /* the box whose corners are tested */
+          const GeomPose<S>& bg = side ? G[ga] : G[gb];
+          const double* cs = side ? sb : sa;
+          const double* bs = side ? sa : sb;
+          for (int cx = -1; cx <= 1; cx += 2)
+            for (int cy = -1; cy <= 1; cy += 2)
+              for (int cz = -1; cz <= 1; cz += 2) {
+                V3<S> corner = cg.c + mul(cg.R, V3<S>(S(cx * cs[0]), S(cy * cs[1]), S(cz * cs[2])));
+                sphere_box(corner, S(0.0), bg.c, bg.R, vload<S>(bs), side == 0, raw);
+              }
+        }
       } else {
-        continue; /* box-box: not a supported pair */
+        continue;
       }
       for (size_t ri = 0; ri < raw.size(); ++ri) raw[ri].sub = (int)ri;
       for (RawContact<S>& k : raw) {

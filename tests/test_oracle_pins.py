@@ -549,6 +549,67 @@ def test_narrowphase_distance_brute_force(oracle, ta, tb):
     assert done >= 3
 
 
+def _quat_mat(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _box_sdf_point(p, c, R, hs):
+    """Signed distance of point p to a box (textbook: outside part plus inside part)."""
+    l = R.T @ (p - c)
+    d = np.abs(l) - hs
+    return np.linalg.norm(np.maximum(d, 0.0)) + min(max(d[0], d[1], d[2]), 0.0)
+
+
+def test_box_box_corner_contacts_match_signed_distance(oracle):
+    """Box-box (reading 16): every corner of either box within the margin of the other box is a
+    contact whose gap is that corner's signed distance to the other box (an independent numpy
+    box SDF here); A's corners are subs 0..7 (x, y, z sign bits 4, 2, 1), B's 8..15."""
+    rng = np.random.default_rng(21)
+    ha, hb = np.array([0.03, 0.04, 0.05]), np.array([0.045, 0.025, 0.035])
+    checked = 0
+    for trial in range(30):
+        qa = np.concatenate([rng.uniform(-0.01, 0.01, 3), S.random_quats(rng, 1)[0]])
+        qb = np.concatenate([rng.uniform(-0.01, 0.01, 3) + rng.standard_normal(3) * 0.05, S.random_quats(rng, 1)[0]])
+        ga, gb = dict(type=S.BOX, size=tuple(ha)), dict(type=S.BOX, size=tuple(hb))
+        d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(ga, body=0), dict(gb, body=1)])
+        margin = 0.01
+        rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=margin), DT, np.concatenate([qa, qb]),
+                                 np.zeros(12))
+        Ra, Rb = _quat_mat(qa[3:]), _quat_mat(qb[3:])
+        want = {}
+        for side, (c, R, h, oc, oR, oh) in enumerate([(qa[:3], Ra, ha, qb[:3], Rb, hb), (qb[:3], Rb, hb, qa[:3], Ra, ha)]):
+            for k in range(8):
+                sgn = np.array([1 if k & 4 else -1, 1 if k & 2 else -1, 1 if k & 1 else -1])
+                corner = c + R @ (sgn * h)
+                phi = _box_sdf_point(corner, oc, oR, oh)
+                if phi < margin:
+                    want[8 * side + k] = phi
+        got = {c["sub"]: c["phi"] for c in rec["contacts"]}
+        assert set(got) == set(want)
+        for k in want:
+            assert got[k] == pytest.approx(want[k], abs=1e-12)
+        checked += len(want)
+    assert checked > 20
+
+
+def test_box_box_stacked_cubes(oracle):
+    """A 10 cm cube resting on another, offset (1, 0.5) cm and 2 mm into it: exactly one
+    corner of each box lies inside the other (gap -2 mm through the nearest, horizontal, face),
+    normals point from the upper box (B) down to the lower (A)."""
+    h = (0.05, 0.05, 0.05)
+    d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(type=S.BOX, body=0, size=h), dict(type=S.BOX, body=1, size=h)])
+    q = np.array([0, 0, 0.05, 1, 0, 0, 0, 0.01, 0.005, 0.148, 1, 0, 0, 0], float)
+    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0)), DT, q, np.zeros(12))
+    cs = sorted(rec["contacts"], key=lambda c: c["sub"])
+    assert [c["sub"] for c in cs] == [7, 8]
+    for c in cs:
+        assert c["phi"] == pytest.approx(-0.002, abs=1e-12)
+        np.testing.assert_allclose(c["normal"], [0, 0, -1], atol=1e-12)
+
+
 def test_box_plane_corners_and_capsule_plane_endpoints(oracle):
     """Box-plane emits every corner below the margin; capsule-plane both end spheres."""
     d = Wd.world([dict(mass=1.0), dict(mass=1.0)],
