@@ -551,6 +551,77 @@ static void sphere_box(const V3<S>& c, S r, const V3<S>& bc, const M3<S>& R, con
   out.push_back(k);
 }
 
+/* Box-box contacts (reading 16): the separating-axis test over the six face axes (A's three,
+ * then B's) picks the axis of least overlap, whose box is the reference and whose face toward
+ * the other (incident) box is the reference face.  The incident box's face most anti-parallel
+ * to it is clipped by the reference face's four side planes (Sutherland-Hodgman: incident
+ * vertices in cyclic order from (+,+) of its two in-face axes, planes in the order +k1, -k1,
+ * +k2, -k2 with k1, k2 the reference face's in-plane axes after the normal axis); each clipped
+ * vertex (at most 8, subs in polygon order) gives a contact with gap = its signed distance to
+ * the reference plane, point = its midpoint with its projection, normal = the reference face
+ * normal oriented from B to A.  Edge-edge contacts of crossed edges are not generated. */
+template <class S>
+static void box_box(const V3<S>& ca, const M3<S>& Ra, const V3<S>& ha, const V3<S>& cb, const M3<S>& Rb,
+                    const V3<S>& hb, std::vector<RawContact<S>>& out) {
+  const V3<S> d = cb - ca;
+  const S hav[3] = {ha.x, ha.y, ha.z}, hbv[3] = {hb.x, hb.y, hb.z};
+  int best = 0;
+  S best_sep(0.0);
+  for (int k = 0; k < 6; ++k) {
+    const V3<S> u = k < 3 ? Ra.col(k) : Rb.col(k - 3);
+    S ra(0.0), rb(0.0);
+    for (int i = 0; i < 3; ++i) {
+      ra += hav[i] * fabs(dot(Ra.col(i), u));
+      rb += hbv[i] * fabs(dot(Rb.col(i), u));
+    }
+    const S sep = fabs(dot(d, u)) - ra - rb;
+    if (k == 0 || sep > best_sep) { best_sep = sep; best = k; }
+  }
+  const bool refA = best < 3;
+  const int jr = best % 3;
+  const V3<S> cR = refA ? ca : cb, cI = refA ? cb : ca;
+  const M3<S>& RR = refA ? Ra : Rb;
+  const M3<S>& RI = refA ? Rb : Ra;
+  const S* hR = refA ? hav : hbv;
+  const S* hI = refA ? hbv : hav;
+  const V3<S> nR = (dot(cI - cR, RR.col(jr)) >= S(0.0) ? S(1.0) : S(-1.0)) * RR.col(jr);
+  int ji = 0;
+  S most(0.0);
+  for (int i = 0; i < 3; ++i) {
+    const S c = fabs(dot(RI.col(i), nR));
+    if (i == 0 || c > most) { most = c; ji = i; }
+  }
+  const S si = dot(RI.col(ji), nR) > S(0.0) ? S(-1.0) : S(1.0);  /* incident face faces the reference */
+  const int i1 = (ji + 1) % 3, i2 = (ji + 2) % 3;
+  const V3<S> fc = cI + (si * hI[ji]) * RI.col(ji);
+  const V3<S> e1 = hI[i1] * RI.col(i1), e2 = hI[i2] * RI.col(i2);
+  std::vector<V3<S>> poly = {fc + e1 + e2, fc - e1 + e2, fc - e1 - e2, fc + e1 - e2};
+  const int k1 = (jr + 1) % 3, k2 = (jr + 2) % 3;
+  const int axes[4] = {k1, k1, k2, k2};
+  const S sg[4] = {S(1.0), S(-1.0), S(1.0), S(-1.0)};
+  for (int pl = 0; pl < 4 && !poly.empty(); ++pl) {
+    const V3<S> u = sg[pl] * RR.col(axes[pl]);
+    const S h = hR[axes[pl]];
+    std::vector<V3<S>> next;
+    for (size_t v = 0; v < poly.size(); ++v) {
+      const V3<S>& P = poly[v];
+      const V3<S>& Q = poly[(v + 1) % poly.size()];
+      const S dP = dot(P - cR, u) - h, dQ = dot(Q - cR, u) - h;
+      if (dP <= S(0.0)) next.push_back(P);
+      if ((dP <= S(0.0)) != (dQ <= S(0.0))) next.push_back(P + (dP / (dP - dQ)) * (Q - P));
+    }
+    poly.swap(next);
+  }
+  for (size_t v = 0; v < poly.size(); ++v) {
+    RawContact<S> k;
+    const S dist = dot(poly[v] - cR, nR) - hR[jr];
+    k.phi = dist;
+    k.p = poly[v] - (S(0.5) * dist) * nR;
+    k.n = refA ? -nR : nR;
+    out.push_back(k);
+  }
+}
+
 /* Box signed distance along the capsule axis: f(t) = sdf_box(x0 + t w), t in [-h, h], in box
  * coordinates.  f is convex; t* = argmin f.  If the axis stays outside the box, f^2 is the
  * C1 piecewise quadratic sum_k max(|x_k(t)| - s_k, 0)^2, and t* is the root of its
@@ -793,21 +864,7 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         S t = capsule_box_param(x0, wl, S(cs[1]), vload<S>(bs));
         sphere_box(cg.c + t * cg.R.col(2), S(cs[0]), bg.c, bg.R, vload<S>(bs), capA, raw);
       } else if (ta == BOX && tb == BOX) {
-        /* box-box: every corner of either box against the other box's signed distance (the
-           box-plane rule with the other box in place of the plane); A's corners are subs 0..7,
-           B's 8..15.  Edges crossing edges with no corner inside are not detected. */
-        for (int side = 0; side < 2; ++side) {
-          const GeomPose<S>& cg = side ? G[gb] : G[ga];   /* the box whose corners are tested */
-          const GeomPose<S>& bg = side ? G[ga] : G[gb];
-          const double* cs = side ? sb : sa;
-          const double* bs = side ? sa : sb;
-          for (int cx = -1; cx <= 1; cx += 2)
-            for (int cy = -1; cy <= 1; cy += 2)
-              for (int cz = -1; cz <= 1; cz += 2) {
-                V3<S> corner = cg.c + mul(cg.R, V3<S>(S(cx * cs[0]), S(cy * cs[1]), S(cz * cs[2])));
-                sphere_box(corner, S(0.0), bg.c, bg.R, vload<S>(bs), side == 0, raw);
-              }
-        }
+        box_box(G[ga].c, G[ga].R, vload<S>(sa), G[gb].c, G[gb].R, vload<S>(sb), raw);
       } else {
         continue;
       }

@@ -563,51 +563,86 @@ def _box_sdf_point(p, c, R, hs):
     return np.linalg.norm(np.maximum(d, 0.0)) + min(max(d[0], d[1], d[2]), 0.0)
 
 
-def test_box_box_corner_contacts_match_signed_distance(oracle):
-    """Box-box (reading 16): every corner of either box within the margin of the other box is a
-    contact whose gap is that corner's signed distance to the other box (an independent numpy
-    box SDF here); A's corners are subs 0..7 (x, y, z sign bits 4, 2, 1), B's 8..15."""
+def _box_pair_contacts(oracle, ha, hb, qa, qb, margin=0.0):
+    d = Wd.world([dict(mass=1.0), dict(mass=1.0)],
+                 [dict(type=S.BOX, body=0, size=tuple(ha)), dict(type=S.BOX, body=1, size=tuple(hb))])
+    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=margin), DT, np.concatenate([qa, qb]),
+                             np.zeros(12))
+    return {c["sub"]: c for c in rec["contacts"]}
+
+
+def test_box_box_is_symmetric_under_swapping_the_boxes(oracle):
+    """Reading 16 does not depend on which box is A (random overlapping pairs, no ties): the same
+    reference face and clipped polygon, so the same subs, gaps and points, normals negated."""
     rng = np.random.default_rng(21)
     ha, hb = np.array([0.03, 0.04, 0.05]), np.array([0.045, 0.025, 0.035])
-    checked = 0
-    for trial in range(30):
+    seen = 0
+    for trial in range(40):
         qa = np.concatenate([rng.uniform(-0.01, 0.01, 3), S.random_quats(rng, 1)[0]])
-        qb = np.concatenate([rng.uniform(-0.01, 0.01, 3) + rng.standard_normal(3) * 0.05, S.random_quats(rng, 1)[0]])
-        ga, gb = dict(type=S.BOX, size=tuple(ha)), dict(type=S.BOX, size=tuple(hb))
-        d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(ga, body=0), dict(gb, body=1)])
-        margin = 0.01
-        rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=margin), DT, np.concatenate([qa, qb]),
-                                 np.zeros(12))
-        Ra, Rb = _quat_mat(qa[3:]), _quat_mat(qb[3:])
-        want = {}
-        for side, (c, R, h, oc, oR, oh) in enumerate([(qa[:3], Ra, ha, qb[:3], Rb, hb), (qb[:3], Rb, hb, qa[:3], Ra, ha)]):
-            for k in range(8):
-                sgn = np.array([1 if k & 4 else -1, 1 if k & 2 else -1, 1 if k & 1 else -1])
-                corner = c + R @ (sgn * h)
-                phi = _box_sdf_point(corner, oc, oR, oh)
-                if phi < margin:
-                    want[8 * side + k] = phi
-        got = {c["sub"]: c["phi"] for c in rec["contacts"]}
-        assert set(got) == set(want)
-        for k in want:
-            assert got[k] == pytest.approx(want[k], abs=1e-12)
-        checked += len(want)
-    assert checked > 20
+        qb = np.concatenate([rng.uniform(-0.01, 0.01, 3) + rng.standard_normal(3) * 0.04, S.random_quats(rng, 1)[0]])
+        ab = _box_pair_contacts(oracle, ha, hb, qa, qb, margin=0.005)
+        ba = _box_pair_contacts(oracle, hb, ha, qb, qa, margin=0.005)
+        assert set(ab) == set(ba)
+        for k, c in ab.items():
+            o = ba[k]
+            assert o["phi"] == pytest.approx(c["phi"], abs=1e-12)
+            np.testing.assert_allclose(o["normal"], -np.asarray(c["normal"]), atol=1e-12)
+            np.testing.assert_allclose(o["pos"], c["pos"], atol=1e-12)
+            assert abs(np.linalg.norm(c["normal"]) - 1.0) < 1e-12
+        seen += len(ab)
+    assert seen > 30
 
 
-def test_box_box_stacked_cubes(oracle):
-    """A 10 cm cube resting on another, offset (1, 0.5) cm and 2 mm into it: exactly one
-    corner of each box lies inside the other (gap -2 mm through the nearest, horizontal, face),
-    normals point from the upper box (B) down to the lower (A)."""
-    h = (0.05, 0.05, 0.05)
-    d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(type=S.BOX, body=0, size=h), dict(type=S.BOX, body=1, size=h)])
+def test_box_box_rotated_cube_on_a_slab(oracle):
+    """A 10 cm cube turned 45 degrees about z rests 1 mm into a 40 x 40 x 10 cm slab: the slab's
+    top face is the reference, the cube's bottom face lies inside it unclipped, so its four
+    corners are the contacts: gap -1 mm, normal from the cube (B) down to the slab (A), points
+    halfway between the corners and the slab's top."""
+    c45 = np.cos(np.pi / 8)
+    qa = np.array([0, 0, 0.05, 1, 0, 0, 0], float)
+    qb = np.array([0.01, 0.02, 0.149, c45, 0, 0, np.sin(np.pi / 8)], float)
+    cs = _box_pair_contacts(oracle, (0.2, 0.2, 0.05), (0.05, 0.05, 0.05), qa, qb)
+    assert sorted(cs) == [0, 1, 2, 3]
+    r = 0.05 * np.sqrt(2)
+    got = sorted((round(c["pos"][0], 9), round(c["pos"][1], 9)) for c in cs.values())
+    want = sorted((round(0.01 + r * np.cos(a), 9), round(0.02 + r * np.sin(a), 9))
+                  for a in np.pi / 4 + np.pi / 4 + np.arange(4) * np.pi / 2)
+    np.testing.assert_allclose(got, want, atol=1e-9)
+    for c in cs.values():
+        assert c["phi"] == pytest.approx(-0.001, abs=1e-12)
+        np.testing.assert_allclose(c["normal"], [0, 0, -1], atol=1e-12)
+        assert c["pos"][2] == pytest.approx(0.0995, abs=1e-12)
+
+
+def test_box_box_offset_faces_clip_to_the_overlap_rectangle(oracle):
+    """Equal 10 cm cubes face to face, the upper offset (1, 0.5) cm and 2 mm deep: the clipped
+    polygon is the overlap rectangle x in [-0.04, 0.05], y in [-0.045, 0.05]."""
     q = np.array([0, 0, 0.05, 1, 0, 0, 0, 0.01, 0.005, 0.148, 1, 0, 0, 0], float)
-    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0)), DT, q, np.zeros(12))
-    cs = sorted(rec["contacts"], key=lambda c: c["sub"])
-    assert [c["sub"] for c in cs] == [7, 8]
-    for c in cs:
+    cs = _box_pair_contacts(oracle, (0.05,) * 3, (0.05,) * 3, q[:7], q[7:])
+    assert len(cs) == 4
+    got = sorted((round(c["pos"][0], 12), round(c["pos"][1], 12)) for c in cs.values())
+    np.testing.assert_allclose(got, sorted([(-0.04, -0.045), (-0.04, 0.05), (0.05, -0.045), (0.05, 0.05)]), atol=1e-12)
+    for c in cs.values():
         assert c["phi"] == pytest.approx(-0.002, abs=1e-12)
         np.testing.assert_allclose(c["normal"], [0, 0, -1], atol=1e-12)
+
+
+def test_box_box_stack_settles_in_place(oracle):
+    """Three aligned 10 cm cubes stacked on the floor hold for 0.4 s: each rests within 1.2 cm
+    of its stacking height (the contacts are soft and sink under the load above) and has moved
+    less than 5 mm sideways.  k = 1, d = 0.01, 4 facets.  (Over longer horizons this stack
+    creeps sideways slowly, and the softer k = 0.3 rocks it over: a property of the impedance
+    reading, recorded in the design notes.)"""
+    h = (0.05, 0.05, 0.05)
+    d = Wd.world([dict(mass=1.0, inertia=S.box_mass_inertia(h, 1.0)[1]) for _ in range(3)],
+                 [dict(type=S.PLANE, body=-1)] + [dict(type=S.BOX, body=i, size=h) for i in range(3)])
+    q = np.array([0, 0, 0.05, 1, 0, 0, 0, 0.005, 0, 0.151, 1, 0, 0, 0, -0.004, 0.003, 0.252, 1, 0, 0, 0], float)
+    q1, v1, _ = oracle.step(d, Wd.params(n_t=4, k_user=1.0, d_user=0.01), DT, 200, q, np.zeros(18))
+    q1 = q1.reshape(3, 7)
+    assert np.abs(v1).max() < 0.1
+    for i in range(3):
+        assert abs(q1[i, 2] - (0.05 + 0.1 * i)) < 0.012
+        assert np.hypot(*(q1[i, :2] - q.reshape(3, 7)[i, :2])) < 0.005
 
 
 def test_box_plane_corners_and_capsule_plane_endpoints(oracle):
