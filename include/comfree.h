@@ -70,7 +70,7 @@ typedef struct cf_batch cf_batch;
  * free body with no children (its body frame at its centre of mass), or a fixed-base tree of
  * hinges whose bodies are contiguous.  Arrays are host pointers, FP64, read during
  * cf_model_create only.  `pile` != 0 declares the layout "body i is free and carries geom i at
- * its origin; geoms nbody.. are static planes" (at most 32767 bodies and 4096 planes, else
+ * its origin; geoms nbody.. are static planes" (at most 4096 bodies and 4096 planes, else
  * CF_ERR_UNSUPPORTED); only such scenes accept per-world overrides. */
 typedef struct {
   int32_t nbody, ngeom;
@@ -137,8 +137,8 @@ cf_status cf_batch_workspace_bytes(const cf_model* model, int32_t n_worlds, cons
 
 /* Create a batch inside the caller's device workspace (at least cf_batch_workspace_bytes,
  * 256-byte aligned).  world_params (host, nullable) holds, in world order, one block of 8
- * floats per body for every world of a pile scene: mass, I1, I2, I3, geom type (sphere or
- * capsule), size0, size1, size2; worlds of other scenes contribute nothing.  NULL keeps the
+ * floats per body for every world of a pile scene: mass, I1, I2, I3, geom type (sphere,
+ * capsule or box), size0, size1, size2; worlds of other scenes contribute nothing.  NULL keeps the
  * scene defaults.  The initial state is the scene's zero state (identity poses) until
  * cf_set_state.  The workspace must outlive the batch.  Synchronises `stream`. */
 cf_status cf_batch_create(const cf_model* model, int32_t n_worlds, const int32_t* scene_of_world,

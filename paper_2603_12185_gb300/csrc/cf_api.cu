@@ -204,8 +204,8 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
     }
     for (int g = d.nbody; g < d.ngeom; ++g)
       if (G[g].type != CF_GEOM_PLANE) return fail(CF_ERR_INVALID_ARGUMENT, "scene %d: pile extra geoms must be planes", si);
-    if (d.nbody >= 32768 || d.ngeom - d.nbody > 4096)
-      return fail(CF_ERR_UNSUPPORTED, "scene %d: pile too large (at most 32767 bodies and 4096 planes)", si);
+    if (d.nbody > 4096 || d.ngeom - d.nbody > 4096)
+      return fail(CF_ERR_UNSUPPORTED, "scene %d: pile too large (at most 4096 bodies and 4096 planes)", si);
     sc.plane0 = d.nbody;
     sc.nplane = d.ngeom - d.nbody;
   } else {
@@ -218,10 +218,14 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
         if (ba < 0 && bb < 0) continue;
         if (ba == bb) continue;
         if (ba >= 0 && bb >= 0 && (B[ba].parent == bb || B[bb].parent == ba)) continue;
-        if (G[a].type == CF_GEOM_BOX && G[b].type == CF_GEOM_BOX) continue;
         m->pairs.push_back(((uint32_t)a << 16) | (uint32_t)b);
       }
     if (d.ngeom >= 32768) return fail(CF_ERR_UNSUPPORTED, "scene %d: too many geoms", si);
+  }
+  {
+    int nbox = 0;
+    for (int g = 0; g < d.ngeom; ++g) nbox += G[g].type == CF_GEOM_BOX && G[g].body >= 0;
+    sc.boxbox = nbox >= 2 ? 1 : 0;
   }
   sc.npair = (int)m->pairs.size() - sc.pair0;
   sc.nq = nq;
@@ -303,6 +307,7 @@ struct cf_batch {
   int nunits = 0;
   size_t smem_all = 0;
   bool artic_all = false;
+  bool ext = false;  // needs the extended kernel: exact impedance or possible box-box contacts
   int variant = 0;             // pile kernel occupancy variant (autotuned)
   // fused MPC cost (cf_set_cost)
   float* cost = nullptr;
@@ -485,8 +490,9 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
       for (int i = 0; i < sc.nbody; ++i) {
         const float* p = params.data() + d.padr + 8 * i;
         int ty = (int)p[4];
-        bool ok = p[0] > 0.f && p[1] > 0.f && p[2] > 0.f && p[3] > 0.f && (ty == CF_GEOM_SPHERE || ty == CF_GEOM_CAPSULE) &&
-                  p[5] > 0.f && (ty == CF_GEOM_SPHERE || p[6] > 0.f) && (float)ty == p[4];
+        bool ok = p[0] > 0.f && p[1] > 0.f && p[2] > 0.f && p[3] > 0.f &&
+                  (ty == CF_GEOM_SPHERE || ty == CF_GEOM_CAPSULE || ty == CF_GEOM_BOX) && p[5] > 0.f &&
+                  (ty == CF_GEOM_SPHERE || p[6] > 0.f) && (ty != CF_GEOM_BOX || p[7] > 0.f) && (float)ty == p[4];
         if (!ok) {
           delete b;
           return fail(CF_ERR_INVALID_ARGUMENT, "world %d body %d: bad override block", w, i);
@@ -507,6 +513,19 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
         p[4] = (float)gd.type; p[5] = gd.size[0]; p[6] = gd.size[1]; p[7] = gd.size[2];
       }
     }
+  }
+  // the extended kernel serves the exact impedance and worlds where two boxes may touch
+  b->ext = m->trace_mode == 2;
+  for (int w = 0; w < n_worlds && !b->ext; ++w) {
+    const DWorld& d = b->worlds[w];
+    const DScene& sc = m->scenes[d.scene];
+    if (d.padr < 0) {
+      if (sc.boxbox) b->ext = true;
+      continue;
+    }
+    int nbox = 0;
+    for (int i = 0; i < sc.nbody; ++i) nbox += (int)params[d.padr + 8 * i + 4] == CF_GEOM_BOX;
+    if (nbox >= 2) b->ext = true;
   }
   // zero state with identity orientations
   std::vector<float> q0(b->total_nq, 0.f);
@@ -667,7 +686,7 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
 
 static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t smem, cudaStream_t s) {
   if (p.nunits <= 0) return CF_OK;
-  const int var = b->model.trace_mode == 2 ? kExactVariant : b->variant;
+  const int var = b->ext ? kExactVariant : b->variant;
   int per_sm = step_max_blocks_per_sm(artic, var, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
   cudaError_t e = launch_step(p, artic, var, grid, smem, s);
@@ -816,7 +835,7 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
   {
     cf_status st = upload_units(b, s);
     if (st != CF_OK) return st;
-    if (!b->artic_all && b->model.trace_mode != 2) {
+    if (!b->artic_all && !b->ext) {
       float best = 3e38f;
       int best_v = 0, prev_blocks = 0;
       for (int var = 0; var < kPileVariants; ++var) {
@@ -1079,7 +1098,8 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
     p.rsin[j] = (float)std::sin(th);
   }
   const bool artic = !sc.pile;
-  const int var = m->trace_mode == 2 ? kExactVariant : 0;
+  // per-world override blocks live on the device here, so a pile with overrides may hold boxes
+  const int var = (m->trace_mode == 2 || sc.boxbox || (sc.pile && world_params)) ? kExactVariant : 0;
   const size_t smem = world_smem_bytes(sc, warps) * per;
   if (smem > step_max_dynamic_smem()) return fail(CF_ERR_UNSUPPORTED, "a world needs %zu bytes of shared memory", smem);
   int nsm = 0;

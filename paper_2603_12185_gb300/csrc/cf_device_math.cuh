@@ -306,6 +306,77 @@ __device__ __forceinline__ void octa_facets(float a, float b1, float b2, float h
   s2 = (l2 - l6) + h * ((l1 - l5) + (l3 - l7));
 }
 
+// Box-box contact `sub` (0..7) of two boxes (centres, rotations, half extents): the
+// separating-axis test over the six face axes (A's first; the least overlap wins) picks the
+// reference face; the incident box's face most anti-parallel to it is clipped by the reference
+// face's side planes (vertices from (+,+) of its in-face axes in cyclic order; planes +k1, -k1,
+// +k2, -k2); clipped vertex `sub` gives gap = its distance to the reference plane, point = the
+// midpoint with its projection, normal = the reference normal from B to A.  phi = +inf when the
+// polygon has fewer vertices.  Crossed edges give no contact.
+static __device__ __noinline__ Raw nf_box_box(f3 ca, M33 Ra, f3 ha, f3 cb, M33 Rb, f3 hb, int sub) {
+  Raw o;
+  o.phi = 3.0e38f;
+  o.p = ca;
+  o.n = mk3(0.f, 0.f, 1.f);
+  const f3 d = cb - ca;
+  const float hav[3] = {ha.x, ha.y, ha.z}, hbv[3] = {hb.x, hb.y, hb.z};
+  int best = 0;
+  float best_sep = 0.f;
+  for (int k = 0; k < 6; ++k) {
+    const f3 u = k < 3 ? col(Ra, k) : col(Rb, k - 3);
+    float ra = 0.f, rb = 0.f;
+    for (int i = 0; i < 3; ++i) {
+      ra += hav[i] * fabsf(dot(col(Ra, i), u));
+      rb += hbv[i] * fabsf(dot(col(Rb, i), u));
+    }
+    const float sep = fabsf(dot(d, u)) - ra - rb;
+    if (k == 0 || sep > best_sep) { best_sep = sep; best = k; }
+  }
+  const bool refA = best < 3;
+  const int jr = best % 3;
+  const f3 cR = refA ? ca : cb, cI = refA ? cb : ca;
+  const M33 RR = refA ? Ra : Rb, RI = refA ? Rb : Ra;
+  const float* hR = refA ? hav : hbv;
+  const float* hI = refA ? hbv : hav;
+  const f3 nR = (dot(cI - cR, col(RR, jr)) >= 0.f ? 1.f : -1.f) * col(RR, jr);
+  int ji = 0;
+  float most = 0.f;
+  for (int i = 0; i < 3; ++i) {
+    const float c = fabsf(dot(col(RI, i), nR));
+    if (i == 0 || c > most) { most = c; ji = i; }
+  }
+  const float si = dot(col(RI, ji), nR) > 0.f ? -1.f : 1.f;
+  const int i1 = (ji + 1) % 3, i2 = (ji + 2) % 3;
+  const f3 fc = cI + (si * hI[ji]) * col(RI, ji);
+  const f3 e1 = hI[i1] * col(RI, i1), e2 = hI[i2] * col(RI, i2);
+  f3 poly[8], tmp[8];
+  poly[0] = fc + e1 + e2; poly[1] = fc - e1 + e2; poly[2] = fc - e1 - e2; poly[3] = fc + e1 - e2;
+  int n = 4;
+  const int k1 = (jr + 1) % 3, k2 = (jr + 2) % 3;
+  for (int pl = 0; pl < 4 && n > 0; ++pl) {
+    const int ax = pl < 2 ? k1 : k2;
+    const f3 u = ((pl & 1) ? -1.f : 1.f) * col(RR, ax);
+    const float h = hR[ax];
+    int m = 0;
+    for (int v = 0; v < n; ++v) {
+      const f3 P = poly[v], Q = poly[v + 1 < n ? v + 1 : 0];
+      const float dP = dot(P - cR, u) - h, dQ = dot(Q - cR, u) - h;
+      if (dP <= 0.f && m < 8) tmp[m++] = P;
+      if ((dP <= 0.f) != (dQ <= 0.f) && m < 8) tmp[m++] = P + (dP / (dP - dQ)) * (Q - P);
+    }
+    for (int v = 0; v < m; ++v) poly[v] = tmp[v];
+    n = m;
+  }
+  if (sub < n) {
+    const f3 v = poly[sub];
+    const float dist = dot(v - cR, nR) - hR[jr];
+    o.phi = dist;
+    o.p = v - (0.5f * dist) * nR;
+    o.n = refA ? -1.f * nR : nR;
+  }
+  return o;
+}
+
 // Gram matrix, through M~^-1, of a contact's six basis rows: point velocity along n, t1, t2
 // (0..2) and relative angular velocity about n, t1, t2 (3..5) -- the entries the facet rows
 // J~_j = J_n - mu d_j^T J_s need for their diagonals w_j = J~_j M~^-1 J~_j^T.

@@ -76,9 +76,14 @@ struct PileView {
   int* count;               // [0] contacts, [1] captured
 };
 
-// contact codes: body pair (a << 16) | b; plane (a << 16) | 0x8000 | (sub << 12) | plane
+// Codes (pile bodies <= 4096, planes <= 4096): a candidate is (a << 16) | b for a body pair and
+// (a << 16) | 0x8000 | plane for a body-plane pair; a queued contact adds its sub-contact (box
+// corners and clipped box-box vertices: 0..7) as (sub & 7) << 12, and (sub >> 3) << 28.
 constexpr int kPlaneBit = 0x8000;
 constexpr int kPlaneMask = 0xfff;
+constexpr int kBodyMask = 0xfff;
+
+__device__ __forceinline__ int code_with_sub(int code, int sub) { return code | ((sub & 7) << 12) | ((sub >> 3) << 28); }
 constexpr int kCqWords = 8;
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
@@ -139,8 +144,8 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, 
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
-// (a plane contributes nothing).  kGeneral: the instantiation that also offers the exact
-// diagonal impedance (trace_mode 2).
+// (a plane contributes nothing).  kGeneral: the extended instantiation (exact diagonal
+// impedance, box-box contacts).
 template <bool kGeneral>
 __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
                                            const float* cq, int slot, bool& range) {
@@ -149,18 +154,18 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   k.n = mk3(cq[3 * kQueue + slot], cq[4 * kQueue + slot], cq[5 * kQueue + slot]);
   k.phi = cq[6 * kQueue + slot];
   const int code = __float_as_int(cq[7 * kQueue + slot]);
-  const int a = code >> 16, bc = code & 0xffff;
+  const int a = (code >> 16) & kBodyMask, bc = code & 0xffff;
   const bool plane = (bc & kPlaneBit) != 0;
-  const int b = plane ? -1 : bc;
+  const int b = plane ? -1 : (bc & kBodyMask);
+  const int sub = ((bc >> 12) & 7) | (((code >> 28) & 1) << 3);
   f3 px = mk3(0.f, 0.f, 0.f);
   float mub0, mub1, mub2;
-  int gb, sub = 0;
+  int gb;
   if (plane) {
     const float* pl = s.planes + 12 * (bc & kPlaneMask);
     px = mk3(pl[6], pl[7], pl[8]);
     mub0 = pl[9]; mub1 = pl[10]; mub2 = pl[11];
     gb = sc.geom0 + sc.plane0 + (bc & kPlaneMask);
-    sub = (bc >> 12) & 7;
   } else {
     mub0 = s.mu0[b]; mub1 = s.mu1[b]; mub2 = s.mu2[b];
     gb = sc.geom0 + b;
@@ -219,7 +224,8 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
 // narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none.
 // Spheres are handled as capsules of zero half length, so sphere-sphere and sphere-capsule
 // in either order share one branch.
-__device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca) {
+template <bool kExt>
+__device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca, int sub) {
   const int ta = s.type[a], tb = s.type[b];
   const float4 pb4 = s.pb[b];
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
@@ -240,7 +246,11 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
     const float t = fminf(fmaxf(dot(cs - cc, u), -h), h);
     const f3 pc = cc + t * u;
     k = nf_sphere_sphere(capA ? pc : ca, s.rad[a], capA ? cb : pc, s.rad[b]);
-  } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {  // box-box: unsupported pair
+  } else if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertex `sub`
+    if (kExt)
+      k = nf_box_box(ca, pile_R(s, a), mk3(s.rad[a], s.hl[a], s.s2[a]), cb, pile_R(s, b), mk3(s.rad[b], s.hl[b], s.s2[b]),
+                   sub);
+  } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {
     bool boxA = ta == CF_GEOM_BOX;
     int ib = boxA ? a : b, io = boxA ? b : a;
     M33 Rbx = pile_R(s, ib);
@@ -273,13 +283,16 @@ __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int s
 }
 
 // number of sub-contacts a candidate can produce (a plane: per end sphere or box corner)
+template <bool kExt>
 __device__ __forceinline__ int pile_nsub(const PileView& s, int code) {
-  if (code < 0 || !((code & 0xffff) & kPlaneBit)) return code < 0 ? 0 : 1;
+  if (code < 0) return 0;
   const int ta = s.type[code >> 16];
+  if (!(code & kPlaneBit)) return kExt && ta == CF_GEOM_BOX && s.type[code & kBodyMask] == CF_GEOM_BOX ? 8 : 1;
   return ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
 }
 
 // narrowphase of candidate `code` (-1: none), sub-contact `sub`; true when it is a contact
+template <bool kExt>
 __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView& s, int code, int sub, Raw& k) {
   if (code < 0) return false;
   const int a = code >> 16, bc = code & 0xffff;
@@ -289,7 +302,7 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
     const float* pl = s.planes + 12 * (bc & kPlaneMask);
     k = pile_narrow_plane(s, a, sub, ca, mk3(pl[0], pl[1], pl[2]), mk3(pl[3], pl[4], pl[5]));
   } else {
-    k = pile_narrow_pair(s, a, bc, ca);
+    k = pile_narrow_pair<kExt>(s, a, bc, ca, sub);
   }
   return k.phi < P.margin;
 }
@@ -446,18 +459,18 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
           const int nb = min(qn, 32);
           const int mine = lane < nb ? queue[qn - nb + lane] : -1;
           qn -= nb;
-          const int my_nsub = pile_nsub(s, mine);
+          const int my_nsub = pile_nsub<kGeneral>(s, mine);
           const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
           for (int sub = 0; sub < nsub; ++sub) {
             Raw kc;
-            const bool hit = sub < my_nsub && pile_narrow(P, s, mine, sub, kc);
+            const bool hit = sub < my_nsub && pile_narrow<kGeneral>(P, s, mine, sub, kc);
             const unsigned hm = __ballot_sync(0xffffffffu, hit);
             if (hit) {
               const int slot = cn + __popc(hm & lt);
               cq[slot] = kc.p.x; cq[kQueue + slot] = kc.p.y; cq[2 * kQueue + slot] = kc.p.z;
               cq[3 * kQueue + slot] = kc.n.x; cq[4 * kQueue + slot] = kc.n.y; cq[5 * kQueue + slot] = kc.n.z;
               cq[6 * kQueue + slot] = kc.phi;
-              cq[7 * kQueue + slot] = __int_as_float(sub == 0 ? mine : (mine | (sub << 12)));
+              cq[7 * kQueue + slot] = __int_as_float(code_with_sub(mine, sub));
             }
             cn += __popc(hm);
             const bool last = flush && qn == 0 && sub + 1 == nsub;
@@ -1053,7 +1066,13 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     float t = fminf(fmaxf(dot(ca - cb, u), -sb[1]), sb[1]);
     k = nf_sphere_sphere(ca, sa[0], cb + t * u, sb[0]);
   } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
-    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) return;
+    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertices, subs 0..7
+      for (int sub = 0; kExact && sub < 8; ++sub) {
+        const Raw kb = nf_box_box(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, Rb, mk3(sb[0], sb[1], sb[2]), sub);
+        if (kb.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, sub, kb, false, mk3(0.f, 0.f, 0.f));
+      }
+      return;
+    }
     bool boxA = ta == CF_GEOM_BOX;
     const M33& Rbx = boxA ? Ra : Rb;
     f3 cbx = boxA ? ca : cb, co = boxA ? cb : ca;
@@ -1267,8 +1286,9 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
-// kArtic: articulated worlds compiled in; kExact: the exact diagonal impedance (trace_mode 2)
-// compiled into the pile path, so that the other instantiations keep their register budget.
+// kArtic: articulated worlds compiled in; kExact: the extended instantiation, with the exact
+// diagonal impedance (trace_mode 2) and box-box contacts compiled in, so that the other
+// instantiations keep their register budget.
 template <bool kArtic, int kMinBlocks, bool kExact>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];

@@ -255,7 +255,7 @@ def make_spheres_on_plane(nworld=64, nbody=8, seed=0, radius=0.05, mass=1.0, mu=
                  {"workload": f"spheres_on_plane_{nworld}x{nbody}"})
 
 
-def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False):
+def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False, box_frac=0.0):
     """Per-world sphere/capsule mixes placed without overlap of their bounding spheres.
 
     Random sequential deposition, vectorised across worlds: body k draws x, y uniformly inside
@@ -267,6 +267,13 @@ def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False):
     r = np.where(is_caps, 0.03, rng.uniform(0.03, 0.06, size=(nworld, n)))
     h = np.where(is_caps, rng.uniform(0.03, 0.08, size=(nworld, n)), 0.0)
     bound = r + h
+    is_box = np.zeros((nworld, n), bool)
+    hs = np.zeros((nworld, n, 3))
+    if box_frac > 0.0:  # boxes with half extents U[0.02, 0.045] m replace a fraction of the bodies
+        is_box = rng.random((nworld, n)) < box_frac
+        hs = rng.uniform(0.02, 0.045, size=(nworld, n, 3))
+        is_caps = is_caps & ~is_box
+        bound = np.where(is_box, np.linalg.norm(hs, axis=2), bound)
     pos = np.zeros((nworld, n, 3))
     for k in range(n):
         bk = bound[:, k]
@@ -287,6 +294,13 @@ def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False):
     for w in range(nworld):
         blk = np.zeros((n, PARAM_STRIDE))
         for i in range(n):
+            if is_box[w, i]:
+                m, inertia = box_mass_inertia(hs[w, i], rho * 8.0 * float(np.prod(hs[w, i])))
+                blk[i, 0] = m
+                blk[i, 1:4] = inertia
+                blk[i, 4] = BOX
+                blk[i, 5:8] = hs[w, i]
+                continue
             if is_caps[w, i]:
                 m, inertia = capsule_mass_inertia(r[w, i], h[w, i], rho)
                 blk[i, 4] = CAPSULE
@@ -307,7 +321,7 @@ PILE_PARAMS = dict(k_user=0.1, d_user=0.001, n_t=8, n_tor=2, n_rol=8)
 PILE_MU = (0.8, 0.005, 0.005)
 
 
-def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False):
+def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False, box_frac=0.0):
     """Walled bins (floor + 4 walls at +-0.3 m) with a seeded 50/50 sphere/capsule mix.
 
     Spheres r ~ U[0.03, 0.06] m; capsules r = 0.03 m, half length ~ U[0.03, 0.08] m; density
@@ -320,9 +334,10 @@ def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False
     rng = np.random.default_rng(seed)
     pp, pq = _planes(True)
     t = _pile_template(f"pile{nbody}", nbody, pp, pq, PILE_MU)
-    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody, jammed=jammed)
+    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody, jammed=jammed, box_frac=box_frac)
     return Batch([t], Params(**PILE_PARAMS), np.zeros(nworld, np.int32), blocks, q0, v0, dt, nsteps,
-                 {"workload": f"pile_{nworld}x{nbody}" + ("_jammed" if jammed else "")})
+                 {"workload": f"pile_{nworld}x{nbody}" + ("_jammed" if jammed else "") +
+                  (f"_boxes{box_frac:g}" if box_frac > 0 else "")})
 
 
 # ----------------------------------------------------------------------------------------
