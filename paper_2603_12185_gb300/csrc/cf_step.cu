@@ -64,12 +64,8 @@ struct PileView {
   int* acch;                // [6][N] velocity change (v; body-frame w), high words
   unsigned* accl;           // [6][N] low words
   float4* pb;               // [N] position (x, y, z) and bounding radius
-  float *qw, *qx, *qy, *qz;
-  float* v;                 // [6][N] v, overwritten in place by v_s in phase A and by v+ in phase C
-  float* R;                 // [9][N]
-  float *invm, *I0, *I1, *I2, *rad, *hl, *s2;  // I0..I2: inverse principal inertia
-  float *mu0, *mu1, *mu2;   // friction coefficients of the body's geom
-  int* type;
+  float4* rec;              // [N][7] body records, see kRec*
+  const DGeom* geoms;       // the scene's geoms: body i carries geom i (friction coefficients)
   float* planes;            // [NP][12]
   int* queue;               // [warps][kQueue] broadphase candidates
   float* cq;                // [warps][8][kQueue] contacts: p.xyz, n.xyz, phi, code
@@ -86,9 +82,15 @@ constexpr int kBodyMask = 0xfff;
 __device__ __forceinline__ int code_with_sub(int code, int sub) { return code | ((sub & 7) << 12) | ((sub >> 3) << 28); }
 constexpr int kCqWords = 8;
 
+// Body record of a pile body, 7 float4 (one vector load each):
+//   0: linear velocity (v, then v_s, then v+), 1/m      1: body-frame angular velocity, 1/I_0
+//   2: R row 0, 1/I_1        3: R row 1, 1/I_2          4: R row 2, size 0 (radius)
+//   5: size 1, size 2, geom type (int bits), 0          6: orientation quaternion (w, x, y, z)
+constexpr int kRec = 7;
+
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
-  // accumulators (12 words/body) + 34 words/body + planes + both queues + counters, 16-byte granules
-  size_t words = (size_t)N * 12 + (size_t)N * 34 + (size_t)NP * 12 + (size_t)warps * kQueue * (1 + kCqWords) + 4;
+  // accumulators (12 words/body) + position (4) + record (28) + planes + both queues + counters
+  size_t words = (size_t)N * 12 + (size_t)N * 32 + (size_t)NP * 12 + (size_t)warps * kQueue * (1 + kCqWords) + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -99,13 +101,7 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   s.accl = reinterpret_cast<unsigned*>(base + (size_t)N * 6);
   float* f = base + (size_t)N * 12;
   s.pb = reinterpret_cast<float4*>(f); f += 4 * (size_t)N;
-  s.qw = f; f += N; s.qx = f; f += N; s.qy = f; f += N; s.qz = f; f += N;
-  s.v = f; f += 6 * N;
-  s.R = f; f += 9 * N;
-  s.invm = f; f += N; s.I0 = f; f += N; s.I1 = f; f += N; s.I2 = f; f += N;
-  s.rad = f; f += N; s.hl = f; f += N; s.s2 = f; f += N;
-  s.mu0 = f; f += N; s.mu1 = f; f += N; s.mu2 = f; f += N;
-  s.type = reinterpret_cast<int*>(f); f += N;
+  s.rec = reinterpret_cast<float4*>(f); f += 4 * (size_t)kRec * N;
   s.planes = f; f += (size_t)NP * 12;
   s.cq = f; f += (size_t)warps * kQueue * kCqWords;
   s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
@@ -114,11 +110,19 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
 }
 
 __device__ __forceinline__ M33 pile_R(const PileView& s, int i) {
+  const float4 a = s.rec[kRec * i + 2], b = s.rec[kRec * i + 3], c = s.rec[kRec * i + 4];
   M33 R;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) R.m[k] = s.R[k * s.N + i];
+  R.m[0] = a.x; R.m[1] = a.y; R.m[2] = a.z; R.m[3] = b.x; R.m[4] = b.y; R.m[5] = b.z;
+  R.m[6] = c.x; R.m[7] = c.y; R.m[8] = c.z;
   return R;
 }
+__device__ __forceinline__ f3 pile_axis(const PileView& s, int i) {  // body z axis (column 2 of R)
+  return mk3(s.rec[kRec * i + 2].z, s.rec[kRec * i + 3].z, s.rec[kRec * i + 4].z);
+}
+__device__ __forceinline__ int pile_type(const PileView& s, int i) { return __float_as_int(s.rec[kRec * i + 5].z); }
+__device__ __forceinline__ float pile_rad(const PileView& s, int i) { return s.rec[kRec * i + 4].w; }
+__device__ __forceinline__ float pile_hl(const PileView& s, int i) { return s.rec[kRec * i + 5].x; }
+__device__ __forceinline__ float pile_s2(const PileView& s, int i) { return s.rec[kRec * i + 5].y; }
 
 // translational trace tr(J_i M^-1 J_i^T) of a free body at lever r (world) or 1/m;
 // im = 1/m, ii = inverse principal inertia
@@ -167,20 +171,21 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
     mub0 = pl[9]; mub1 = pl[10]; mub2 = pl[11];
     gb = sc.geom0 + sc.plane0 + (bc & kPlaneMask);
   } else {
-    mub0 = s.mu0[b]; mub1 = s.mu1[b]; mub2 = s.mu2[b];
+    const float* mb = s.geoms[b].mu;
+    mub0 = mb[0]; mub1 = mb[1]; mub2 = mb[2];
     gb = sc.geom0 + b;
   }
-  const int N = s.N;
   f3 t1, t2;
   contact_frame(k.n, plane, px, t1, t2);
   M33 Ra = pile_R(s, a);
   float4 pa = s.pb[a];
   f3 ra = k.p - mk3(pa.x, pa.y, pa.z);
-  f3 wa = mul(Ra, mk3(s.v[3 * N + a], s.v[4 * N + a], s.v[5 * N + a]));
-  f3 vc = mk3(s.v[a], s.v[N + a], s.v[2 * N + a]) + cross(wa, ra);
+  const float4 va = s.rec[kRec * a], wa4 = s.rec[kRec * a + 1];
+  f3 wa = mul(Ra, mk3(wa4.x, wa4.y, wa4.z));
+  f3 vc = mk3(va.x, va.y, va.z) + cross(wa, ra);
   f3 wc = wa;
-  const float ima = s.invm[a];
-  const f3 iia = mk3(s.I0[a], s.I1[a], s.I2[a]);
+  const float ima = va.w;
+  const f3 iia = mk3(wa4.w, s.rec[kRec * a + 2].w, s.rec[kRec * a + 3].w);
   float tr = pile_trace(P, ima, iia, Ra, ra);
   M33 Rb;
   f3 rb, iib;
@@ -189,15 +194,17 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
     Rb = pile_R(s, b);
     float4 pbb = s.pb[b];
     rb = k.p - mk3(pbb.x, pbb.y, pbb.z);
-    f3 wb = mul(Rb, mk3(s.v[3 * N + b], s.v[4 * N + b], s.v[5 * N + b]));
-    vc = vc - (mk3(s.v[b], s.v[N + b], s.v[2 * N + b]) + cross(wb, rb));
+    const float4 vb = s.rec[kRec * b], wb4 = s.rec[kRec * b + 1];
+    f3 wb = mul(Rb, mk3(wb4.x, wb4.y, wb4.z));
+    vc = vc - (mk3(vb.x, vb.y, vb.z) + cross(wb, rb));
     wc = wc - wb;
-    imb = s.invm[b];
-    iib = mk3(s.I0[b], s.I1[b], s.I2[b]);
+    imb = vb.w;
+    iib = mk3(wb4.w, s.rec[kRec * b + 2].w, s.rec[kRec * b + 3].w);
     tr += pile_trace(P, imb, iib, Rb, rb);
   }
   // pair friction: the larger of the two geoms' coefficients
-  const float mu_t = fmaxf(s.mu0[a], mub0), mu_tor = fmaxf(s.mu1[a], mub1), mu_rol = fmaxf(s.mu2[a], mub2);
+  const float* ma = s.geoms[a].mu;
+  const float mu_t = fmaxf(ma[0], mub0), mu_tor = fmaxf(ma[1], mub1), mu_rol = fmaxf(ma[2], mub2);
   float mphi = 0.f;
   float w[6];
   if (kGeneral && P.trace_mode == 2) {
@@ -226,42 +233,42 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
 // in either order share one branch.
 template <bool kExt>
 __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca, int sub) {
-  const int ta = s.type[a], tb = s.type[b];
+  const int ta = pile_type(s, a), tb = pile_type(s, b);
   const float4 pb4 = s.pb[b];
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
   if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
-    f3 ua = col(pile_R(s, a), 2), ub = col(pile_R(s, b), 2);
-    f3 p1 = ca - s.hl[a] * ua, q1 = ca + s.hl[a] * ua, p2 = cb - s.hl[b] * ub, q2 = cb + s.hl[b] * ub;
+    f3 ua = pile_axis(s, a), ub = pile_axis(s, b);
+    f3 p1 = ca - pile_hl(s, a) * ua, q1 = ca + pile_hl(s, a) * ua, p2 = cb - pile_hl(s, b) * ub, q2 = cb + pile_hl(s, b) * ub;
     float ss, tt;
     nf_segments(p1, q1, p2, q2, ss, tt);
-    k = nf_sphere_sphere(p1 + ss * (q1 - p1), s.rad[a], p2 + tt * (q2 - p2), s.rad[b]);
+    k = nf_sphere_sphere(p1 + ss * (q1 - p1), pile_rad(s, a), p2 + tt * (q2 - p2), pile_rad(s, b));
   } else if (ta != CF_GEOM_BOX && tb != CF_GEOM_BOX) {  // sphere-sphere, capsule-sphere, sphere-capsule
     const bool capA = ta == CF_GEOM_CAPSULE;
     const int ic = capA ? a : b;
     const f3 cc = capA ? ca : cb, cs = capA ? cb : ca;
-    const float h = ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE ? 0.f : s.hl[ic];
-    const f3 u = col(pile_R(s, ic), 2);
+    const float h = ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE ? 0.f : pile_hl(s, ic);
+    const f3 u = pile_axis(s, ic);
     const float t = fminf(fmaxf(dot(cs - cc, u), -h), h);
     const f3 pc = cc + t * u;
-    k = nf_sphere_sphere(capA ? pc : ca, s.rad[a], capA ? cb : pc, s.rad[b]);
+    k = nf_sphere_sphere(capA ? pc : ca, pile_rad(s, a), capA ? cb : pc, pile_rad(s, b));
   } else if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertex `sub`
     if (kExt)
-      k = nf_box_box(ca, pile_R(s, a), mk3(s.rad[a], s.hl[a], s.s2[a]), cb, pile_R(s, b), mk3(s.rad[b], s.hl[b], s.s2[b]),
+      k = nf_box_box(ca, pile_R(s, a), mk3(pile_rad(s, a), pile_hl(s, a), pile_s2(s, a)), cb, pile_R(s, b), mk3(pile_rad(s, b), pile_hl(s, b), pile_s2(s, b)),
                    sub);
   } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {
     bool boxA = ta == CF_GEOM_BOX;
     int ib = boxA ? a : b, io = boxA ? b : a;
     M33 Rbx = pile_R(s, ib);
     f3 cbx = boxA ? ca : cb, co = boxA ? cb : ca;
-    f3 hs = mk3(s.rad[ib], s.hl[ib], s.s2[ib]);
-    if (s.type[io] == CF_GEOM_SPHERE) {
-      k = nf_sphere_box(co, s.rad[io], cbx, Rbx, hs, !boxA);
+    f3 hs = mk3(pile_rad(s, ib), pile_hl(s, ib), pile_s2(s, ib));
+    if (pile_type(s, io) == CF_GEOM_SPHERE) {
+      k = nf_sphere_box(co, pile_rad(s, io), cbx, Rbx, hs, !boxA);
     } else {
-      f3 u = col(pile_R(s, io), 2);
-      float t = nf_capsule_box_param(mulT(Rbx, co - cbx), mulT(Rbx, u), s.hl[io], hs);
-      k = nf_sphere_box(co + t * u, s.rad[io], cbx, Rbx, hs, !boxA);
+      f3 u = pile_axis(s, io);
+      float t = nf_capsule_box_param(mulT(Rbx, co - cbx), mulT(Rbx, u), pile_hl(s, io), hs);
+      k = nf_sphere_box(co + t * u, pile_rad(s, io), cbx, Rbx, hs, !boxA);
     }
   }
   return k;
@@ -269,14 +276,14 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
 
 // narrowphase of body a against a plane: sphere (sub 0), capsule end sphere sub, box corner sub
 __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int sub, f3 ca, f3 o, f3 nz) {
-  const int ta = s.type[a];
+  const int ta = pile_type(s, a);
   f3 c = ca;
-  float r = s.rad[a];
+  float r = pile_rad(s, a);
   if (ta == CF_GEOM_CAPSULE) {
-    c = ca + (sub ? s.hl[a] : -s.hl[a]) * col(pile_R(s, a), 2);
+    c = ca + (sub ? pile_hl(s, a) : -pile_hl(s, a)) * pile_axis(s, a);
   } else if (ta == CF_GEOM_BOX) {
-    c = ca + mul(pile_R(s, a), mk3((sub & 4) ? s.rad[a] : -s.rad[a], (sub & 2) ? s.hl[a] : -s.hl[a],
-                                   (sub & 1) ? s.s2[a] : -s.s2[a]));
+    c = ca + mul(pile_R(s, a), mk3((sub & 4) ? pile_rad(s, a) : -pile_rad(s, a), (sub & 2) ? pile_hl(s, a) : -pile_hl(s, a),
+                                   (sub & 1) ? pile_s2(s, a) : -pile_s2(s, a)));
     r = 0.f;
   }
   return nf_sphere_plane(c, r, o, nz);
@@ -286,8 +293,8 @@ __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int s
 template <bool kExt>
 __device__ __forceinline__ int pile_nsub(const PileView& s, int code) {
   if (code < 0) return 0;
-  const int ta = s.type[code >> 16];
-  if (!(code & kPlaneBit)) return kExt && ta == CF_GEOM_BOX && s.type[code & kBodyMask] == CF_GEOM_BOX ? 8 : 1;
+  const int ta = pile_type(s, code >> 16);
+  if (!(code & kPlaneBit)) return kExt && ta == CF_GEOM_BOX && pile_type(s, code & kBodyMask) == CF_GEOM_BOX ? 8 : 1;
   return ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
 }
 
@@ -316,6 +323,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   const int tid = threadIdx.x - gid * T;
   const int lane = threadIdx.x & 31, wig = tid >> 5;
   PileView s = pile_view(smem, N, NP, gwarps);
+  s.geoms = P.geoms + sc.geom0;
   const float* q = P.q + W.qadr;
   const float* v = P.v + W.vadr;
   const float dt = P.dt;
@@ -324,9 +332,8 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
   for (int i = tid; i < N; i += T) {
     const float* qi = q + 7 * i;
     float px = qi[0], py = qi[1], pz = qi[2];
-    s.qw[i] = qi[3]; s.qx[i] = qi[4]; s.qy[i] = qi[5]; s.qz[i] = qi[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s.v[k * N + i] = v[6 * i + k];
+    const float* vi = v + 6 * i;
+    float4* rc = s.rec + kRec * i;
     float m, i0, i1, i2, ty, r, h, s2;
     if (W.padr >= 0) {
       const float4* pp = reinterpret_cast<const float4*>(P.wparam + W.padr + 8 * i);
@@ -339,12 +346,15 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       ty = (float)gd.type; r = gd.size[0]; h = gd.size[1]; s2 = gd.size[2];
     }
     int t = (int)ty;
-    s.invm[i] = 1.f / m; s.I0[i] = 1.f / i0; s.I1[i] = 1.f / i1; s.I2[i] = 1.f / i2;
-    s.type[i] = t; s.rad[i] = r; s.hl[i] = h; s.s2[i] = s2;
+    rc[0] = make_float4(vi[0], vi[1], vi[2], 1.f / m);
+    rc[1] = make_float4(vi[3], vi[4], vi[5], 1.f / i0);
+    rc[2].w = 1.f / i1;
+    rc[3].w = 1.f / i2;
+    rc[4].w = r;
+    rc[5] = make_float4(h, s2, __int_as_float(t), 0.f);
+    rc[6] = make_float4(qi[3], qi[4], qi[5], qi[6]);
     s.pb[i] = make_float4(px, py, pz,
                           t == CF_GEOM_SPHERE ? r : (t == CF_GEOM_CAPSULE ? r + h : sqrtf(r * r + h * h + s2 * s2)));
-    const DGeom& gd = P.geoms[sc.geom0 + i];
-    s.mu0[i] = gd.mu[0]; s.mu1[i] = gd.mu[1]; s.mu2[i] = gd.mu[2];
   }
   for (int pi = tid; pi < NP; pi += T) {
     PlaneDev pl = load_plane(P.geoms[sc.geom0 + sc.plane0 + pi]);
@@ -360,18 +370,17 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     group_sync(gid, T);
     // ---- A. kinematics and smooth prediction (free body: c = (-m g, w x I w)), v -> v_s ----
     for (int i = tid; i < N; i += T) {
-      M33 R = quat_mat(s.qw[i], s.qx[i], s.qy[i], s.qz[i]);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) s.R[k * N + i] = R.m[k];
-      float w0 = s.v[3 * N + i], w1 = s.v[4 * N + i], w2 = s.v[5 * N + i];
-      float ii0 = s.I0[i], ii1 = s.I1[i], ii2 = s.I2[i];  // inverse principal inertia
+      float4* rc = s.rec + kRec * i;
+      const float4 qq = rc[6], r0 = rc[0], r1 = rc[1];
+      M33 R = quat_mat(qq.x, qq.y, qq.z, qq.w);
+      const float ii0 = r1.w, ii1 = rc[2].w, ii2 = rc[3].w;  // inverse principal inertia
+      rc[2] = make_float4(R.m[0], R.m[1], R.m[2], ii1);
+      rc[3] = make_float4(R.m[3], R.m[4], R.m[5], ii2);
+      rc[4] = make_float4(R.m[6], R.m[7], R.m[8], rc[4].w);
+      float w0 = r1.x, w1 = r1.y, w2 = r1.z;
       f3 gy = cross(mk3(w0, w1, w2), mk3(w0 / ii0, w1 / ii1, w2 / ii2));
-      s.v[i] += g.x * dt;
-      s.v[N + i] += g.y * dt;
-      s.v[2 * N + i] += g.z * dt;
-      s.v[3 * N + i] = w0 - dt * gy.x * ii0;
-      s.v[4 * N + i] = w1 - dt * gy.y * ii1;
-      s.v[5 * N + i] = w2 - dt * gy.z * ii2;
+      rc[0] = make_float4(r0.x + g.x * dt, r0.y + g.y * dt, r0.z + g.z * dt, r0.w);
+      rc[1] = make_float4(w0 - dt * gy.x * ii0, w1 - dt * gy.y * ii1, w2 - dt * gy.z * ii2, ii0);
 #pragma unroll
       for (int k = 0; k < 6; ++k) { s.acch[k * N + i] = 0; s.accl[k * N + i] = 0u; }
     }
@@ -490,14 +499,16 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
 
     // ---- C. velocity correction and semi-implicit Euler ----
     for (int i = tid; i < N; i += T) {
-      float v0 = s.v[i] + fix2_get(s.acch[i], s.accl[i]);
-      float v1 = s.v[N + i] + fix2_get(s.acch[N + i], s.accl[N + i]);
-      float v2 = s.v[2 * N + i] + fix2_get(s.acch[2 * N + i], s.accl[2 * N + i]);
-      float w0 = s.v[3 * N + i] + fix2_get(s.acch[3 * N + i], s.accl[3 * N + i]);
-      float w1 = s.v[4 * N + i] + fix2_get(s.acch[4 * N + i], s.accl[4 * N + i]);
-      float w2 = s.v[5 * N + i] + fix2_get(s.acch[5 * N + i], s.accl[5 * N + i]);
-      s.v[i] = v0; s.v[N + i] = v1; s.v[2 * N + i] = v2;
-      s.v[3 * N + i] = w0; s.v[4 * N + i] = w1; s.v[5 * N + i] = w2;
+      float4* rc = s.rec + kRec * i;
+      const float4 r0 = rc[0], r1 = rc[1];
+      float v0 = r0.x + fix2_get(s.acch[i], s.accl[i]);
+      float v1 = r0.y + fix2_get(s.acch[N + i], s.accl[N + i]);
+      float v2 = r0.z + fix2_get(s.acch[2 * N + i], s.accl[2 * N + i]);
+      float w0 = r1.x + fix2_get(s.acch[3 * N + i], s.accl[3 * N + i]);
+      float w1 = r1.y + fix2_get(s.acch[4 * N + i], s.accl[4 * N + i]);
+      float w2 = r1.z + fix2_get(s.acch[5 * N + i], s.accl[5 * N + i]);
+      rc[0] = make_float4(v0, v1, v2, r0.w);
+      rc[1] = make_float4(w0, w1, w2, r1.w);
       s.pb[i].x += v0 * dt; s.pb[i].y += v1 * dt; s.pb[i].z += v2 * dt;
       float wn = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
       float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
@@ -507,13 +518,14 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
         float sc_ = sn / wn;
         dq0 = cs; dq1 = sc_ * w0; dq2 = sc_ * w1; dq3 = sc_ * w2;
       }
-      float a0 = s.qw[i], a1 = s.qx[i], a2 = s.qy[i], a3 = s.qz[i];
+      const float4 qq = rc[6];
+      float a0 = qq.x, a1 = qq.y, a2 = qq.z, a3 = qq.w;
       float n0 = a0 * dq0 - a1 * dq1 - a2 * dq2 - a3 * dq3;
       float n1 = a0 * dq1 + a1 * dq0 + a2 * dq3 - a3 * dq2;
       float n2 = a0 * dq2 - a1 * dq3 + a2 * dq0 + a3 * dq1;
       float n3 = a0 * dq3 + a1 * dq2 - a2 * dq1 + a3 * dq0;
       float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
-      s.qw[i] = n0 * inv; s.qx[i] = n1 * inv; s.qy[i] = n2 * inv; s.qz[i] = n3 * inv;
+      rc[6] = make_float4(n0 * inv, n1 * inv, n2 * inv, n3 * inv);
     }
   }
   group_sync(gid, T);
@@ -525,11 +537,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     float* qi = qo + 7 * i;
     float4 p4 = s.pb[i];
     qi[0] = p4.x; qi[1] = p4.y; qi[2] = p4.z;
-    qi[3] = s.qw[i]; qi[4] = s.qx[i]; qi[5] = s.qy[i]; qi[6] = s.qz[i];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) vo[6 * i + k] = s.v[k * N + i];
-    float chk = p4.x + p4.y + p4.z + s.qw[i] + s.v[i] + s.v[N + i] + s.v[2 * N + i] + s.v[3 * N + i] +
-                s.v[4 * N + i] + s.v[5 * N + i];
+    const float4* rc = s.rec + kRec * i;
+    const float4 qq = rc[6], r0 = rc[0], r1 = rc[1];
+    qi[3] = qq.x; qi[4] = qq.y; qi[5] = qq.z; qi[6] = qq.w;
+    float* vi = vo + 6 * i;
+    vi[0] = r0.x; vi[1] = r0.y; vi[2] = r0.z; vi[3] = r1.x; vi[4] = r1.y; vi[5] = r1.z;
+    float chk = p4.x + p4.y + p4.z + qq.x + r0.x + r0.y + r0.z + r1.x + r1.y + r1.z;
     if (!isfinite(chk)) bad = true;
   }
   if (bad) {
