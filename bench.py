@@ -192,18 +192,23 @@ def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, ja
                 contacts=int(contact_sum.sum().item()), worlds=nworld, bodies=nbody, sb=sb, batch=b, model=model)
 
 
-def run_e2e(res, steps):
-    """Same workload through the C ABI with pinned host buffers: per step the state goes
-    host -> device, one step, device -> host (the copies are inside the timed region)."""
+def run_e2e(res, steps, blocks=4):
+    """Same workload through the public API with the state in pinned host memory: every step
+    copies q, v host -> device, steps, and copies them device -> host.  Measured twice: serially
+    on one batch, and with comfree.Pipeline, which splits the worlds into `blocks` batches on
+    their own streams so that one block's copies overlap another's step."""
     import torch
+    from paper_2603_12185_gb300 import comfree as CF
     b = res["batch"]
+    sb = res["sb"]
+    dt = sb.dt
     q, v = b.get_state()
+    nbytes = (b.total_nq + b.total_nv) * 4
+    # serial: one batch, synchronous host copies
     hq = torch.empty(b.total_nq, dtype=torch.float32, pin_memory=True)
     hv = torch.empty(b.total_nv, dtype=torch.float32, pin_memory=True)
     hq.copy_(q.cpu())
     hv.copy_(v.cpu())
-    dt = res["sb"].dt
-    # warm-up
     b.set_state(hq, hv)
     b.step(dt, 1)
     b.get_state(hq, hv)
@@ -214,9 +219,32 @@ def run_e2e(res, steps):
         b.step(dt, 1)
         b.get_state(hq, hv)          # device -> host, synchronises and checks device status
     torch.cuda.synchronize()
+    serial = res["worlds"] * steps / (time.perf_counter() - t0)
+    # pipelined: blocks of worlds on their own streams
+    W = res["worlds"]
+    edges = [W * k // blocks for k in range(blocks + 1)]
+    batches, bq, bv = [], [], []
+    qo = vo = 0
+    for k in range(blocks):
+        _, bk = CF.from_scenes(sb.subset(range(edges[k], edges[k + 1])))
+        bk.autotune(dt)
+        batches.append(bk)
+        bq.append(q[qo:qo + bk.total_nq].cpu().pin_memory())
+        bv.append(v[vo:vo + bk.total_nv].cpu().pin_memory())
+        qo += bk.total_nq
+        vo += bk.total_nv
+    pipe = CF.Pipeline(batches)
+    pipe.step(bq, bv, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pipe.step(bq, bv, dt)
+    torch.cuda.synchronize()
     sec = time.perf_counter() - t0
-    nbytes = (b.total_nq + b.total_nv) * 4
-    return dict(value=res["worlds"] * steps / sec, h2d=nbytes, d2h=nbytes)
+    for st, _ in pipe.status():
+        if st != 0:
+            raise RuntimeError(f"device status {st} in the pipelined run")
+    return dict(value=W * steps / sec, serial=serial, blocks=blocks, h2d=nbytes, d2h=nbytes)
 
 
 def run_extras(rank):
@@ -430,7 +458,8 @@ def main():
             "sweep_bodies": sweep,
             "roofline": roofline,
             "e2e": {"value": e2e_v, "unit": "world-steps/s", "h2d_bytes_per_step": e2e["h2d"],
-                    "d2h_bytes_per_step": e2e["d2h"]},
+                    "d2h_bytes_per_step": e2e["d2h"], "api": f"comfree.Pipeline, {e2e['blocks']} blocks",
+                    "serial_value": e2e["serial"]},
             "gpu_launches": res["steps"],
             "clocks": clk}
     if not args.no_extras:

@@ -149,9 +149,11 @@ void cf_batch_destroy(cf_batch* batch);
 /* total floats of q, v and actuated controls over all worlds */
 cf_status cf_batch_sizes(const cf_batch* batch, int64_t* total_nq, int64_t* total_nv, int64_t* total_nu);
 
-/* Copy the full state in (set) or out (get).  q[total_nq], v[total_nv]; on_device != 0 means
- * device pointers (asynchronous on `stream`), else host pointers (the call synchronises and,
- * for get, reports latched device errors). */
+/* Copy the full state in (set) or out (get).  q[total_nq], v[total_nv]; on_device: 1 = device
+ * pointers (asynchronous on `stream`); 0 = host pointers (the call synchronises and, for get,
+ * reports latched device errors); 2 = pinned host pointers, asynchronous: the copy is only
+ * enqueued on `stream`, the buffers must stay valid until the stream passes it, and device
+ * errors wait for the next synchronising call (cf_batch_status). */
 cf_status cf_set_state(cf_batch* batch, const float* q, const float* v, int32_t on_device, void* stream);
 cf_status cf_get_state(const cf_batch* batch, float* q, float* v, int32_t on_device, void* stream);
 

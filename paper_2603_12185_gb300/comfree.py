@@ -217,6 +217,16 @@ class Batch:
             self.h = None
 
     # ---- state ----
+    def set_state_async(self, q, v, stream=None):
+        """Enqueue the copy of pinned host tensors q, v on `stream` and return (cf_set_state mode 2)."""
+        assert q.is_pinned() and v.is_pinned() and q.numel() == self.total_nq and v.numel() == self.total_nv
+        check(lib().cf_set_state(self.h, _ptr(q), _ptr(v), 2, _stream(stream)))
+
+    def get_state_async(self, q, v, stream=None):
+        """Enqueue the copy of the state into pinned host tensors q, v on `stream` and return."""
+        assert q.is_pinned() and v.is_pinned() and q.numel() == self.total_nq and v.numel() == self.total_nv
+        check(lib().cf_get_state(self.h, _ptr(q), _ptr(v), 2, _stream(stream)))
+
     def set_state(self, q, v, stream=None):
         on_dev = isinstance(q, torch.Tensor) and q.is_cuda
         if on_dev:
@@ -316,6 +326,28 @@ class Batch:
         check(lib().cf_step_grad(self.h, int(T), float(dt), _ptr(dqT.contiguous()), _ptr(dvT.contiguous()), _ptr(dq0),
                                  _ptr(dv0), _ptr(dtau), _stream(stream)))
         return dq0, dv0, dtau[:T * self.total_nu].view(T, self.total_nu) if self.total_nu else dtau[:0]
+
+
+class Pipeline:
+    """Steps blocks of worlds (one Batch per block) from and back to pinned host state, each
+    block on its own stream, so that one block's host-to-device copy, step and device-to-host
+    copy overlap the others'.  step() returns when every block's new state is in host memory."""
+
+    def __init__(self, batches):
+        self.batches = list(batches)
+        self.streams = [torch.cuda.Stream() for _ in self.batches]
+
+    def step(self, host_q, host_v, dt, nsteps=1):
+        """host_q, host_v: per-block pinned CPU tensors, read and then overwritten in place."""
+        for b, s, q, v in zip(self.batches, self.streams, host_q, host_v):
+            b.set_state_async(q, v, stream=s)
+            b.step(dt, nsteps, stream=s)
+            b.get_state_async(q, v, stream=s)
+        for s in self.streams:
+            s.synchronize()
+
+    def status(self):
+        return [b.status() for b in self.batches]
 
 
 def step_noalloc(model, scene, n_worlds, q, v, world_params, dt, nsteps, contacts=None, stream=None):

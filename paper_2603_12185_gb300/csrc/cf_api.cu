@@ -582,10 +582,11 @@ extern "C" cf_status cf_batch_sizes(const cf_batch* b, int64_t* nq, int64_t* nv,
 extern "C" cf_status cf_set_state(cf_batch* b, const float* q, const float* v, int32_t on_device, void* stream) {
   if (!b || (!q && !v)) return fail(CF_ERR_INVALID_ARGUMENT, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (on_device < 0 || on_device > 2) return fail(CF_ERR_INVALID_ARGUMENT, "on_device must be 0, 1 or 2");
+  cudaMemcpyKind k = on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (q) CF_CUDA(cudaMemcpyAsync(b->ws + b->L.q, q, sizeof(float) * b->total_nq, k, s), "set q");
   if (v) CF_CUDA(cudaMemcpyAsync(b->ws + b->L.v, v, sizeof(float) * b->total_nv, k, s), "set v");
-  if (!on_device) CF_CUDA(cudaStreamSynchronize(s), "set state");
+  if (on_device == 0) CF_CUDA(cudaStreamSynchronize(s), "set state");
   return CF_OK;
 }
 
@@ -606,10 +607,11 @@ static cf_status status_of_word(int w) {
 extern "C" cf_status cf_get_state(const cf_batch* b, float* q, float* v, int32_t on_device, void* stream) {
   if (!b || (!q && !v)) return fail(CF_ERR_INVALID_ARGUMENT, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (on_device < 0 || on_device > 2) return fail(CF_ERR_INVALID_ARGUMENT, "on_device must be 0, 1 or 2");
+  cudaMemcpyKind k = on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (q) CF_CUDA(cudaMemcpyAsync(q, b->ws + b->L.q, sizeof(float) * b->total_nq, k, s), "get q");
   if (v) CF_CUDA(cudaMemcpyAsync(v, b->ws + b->L.v, sizeof(float) * b->total_nv, k, s), "get v");
-  if (!on_device) {
+  if (on_device == 0) {
     int word = 0;
     cf_status st = read_errword(b, s, &word);
     if (st != CF_OK) return st;

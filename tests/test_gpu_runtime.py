@@ -77,6 +77,33 @@ def test_graph_replay_equals_eager_steps():
     assert st == 0
 
 
+def test_pipeline_matches_one_batch():
+    """comfree.Pipeline (blocks of worlds on their own streams, state in pinned host memory)
+    gives bit-identical states to stepping all worlds in one batch."""
+    sb = S.make_pile(8, 16, seed=21)
+    _, full = CF.from_scenes(sb)
+    full.step(sb.dt, 20)
+    q0, v0 = _state(full)
+    blocks, hq, hv = [], [], []
+    qo = vo = 0
+    for lo, hi in ((0, 3), (3, 8)):
+        _, bk = CF.from_scenes(sb.subset(range(lo, hi)))
+        blocks.append(bk)
+        hq.append(torch.from_numpy(q0[qo:qo + bk.total_nq].copy()).pin_memory())
+        hv.append(torch.from_numpy(v0[vo:vo + bk.total_nv].copy()).pin_memory())
+        qo += bk.total_nq
+        vo += bk.total_nv
+    pipe = CF.Pipeline(blocks)
+    for _ in range(3):
+        pipe.step(hq, hv, sb.dt)
+    for _ in range(3):
+        full.step(sb.dt, 1)
+    q1, v1 = _state(full)
+    assert np.array_equal(np.concatenate([t.numpy() for t in hq]), q1)
+    assert np.array_equal(np.concatenate([t.numpy() for t in hv]), v1)
+    assert all(st == 0 for st, _ in pipe.status())
+
+
 def test_state_round_trip_host_and_device():
     sb = S.make_mixed(8, seed=5)
     _, b = CF.from_scenes(sb)
