@@ -45,11 +45,12 @@ def task_cost(q, goal):
 
 class HandMPPI:
     def __init__(self, template, params, N=1024, H=32, dt=0.005, sigma=1.0, lam=0.1, limit=2.0, mlp=None,
-                 n_prop=0, seed=0, cost=None, device="cuda"):
+                 n_prop=0, seed=0, cost=None, device="cuda", warps=2):
         self.N, self.H, self.dt, self.sigma, self.lam, self.limit = N, H, dt, sigma, lam, limit
         self.mlp, self.n_prop = mlp, (n_prop if mlp is not None else 0)
         self.model = CF.Model([template], params)
         self.rollouts = CF.Batch(self.model, np.zeros(N, np.int32), max_ctrl_steps=H)
+        self.rollouts.set_warps(0, warps)  # warps per rollout world (2: the fastest for 1024 hands)
         self.plant = CF.Batch(self.model, np.zeros(1, np.int32), max_ctrl_steps=1)
         dev = device
         self.goals = torch.zeros(N, 7, device=dev)
