@@ -122,7 +122,7 @@ typedef struct {
 
 namespace orc {
 
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, CYLINDER = 4, ELLIPSOID = 5 };
 enum { FREE = 0, HINGE = 1 };
 
 template <class S> struct V3 {
@@ -622,6 +622,96 @@ static void box_box(const V3<S>& ca, const M3<S>& Ra, const V3<S>& ha, const V3<
   }
 }
 
+/* Ellipsoid (centre c, rotation R, semi-axes e along the body axes) against a plane (point o,
+ * unit normal n), reading 17: the ellipsoid's support point against n,
+ * p = c - R D^2 R^T n / |D R^T n| with D = diag(e), is the lowest point; gap = its height. */
+template <class S>
+static void ellipsoid_plane(const V3<S>& c, const M3<S>& R, const V3<S>& e, const V3<S>& o, const V3<S>& n,
+                            std::vector<RawContact<S>>& out) {
+  const V3<S> nl = mulT(R, n);
+  const V3<S> dn(e.x * nl.x, e.y * nl.y, e.z * nl.z);
+  const S len = norm(dn);
+  const V3<S> pl(e.x * dn.x / len, e.y * dn.y / len, e.z * dn.z / len);
+  const V3<S> p = c - mul(R, pl);
+  RawContact<S> k;
+  const S dist = dot(n, p - o);
+  k.phi = dist;
+  k.p = p - (S(0.5) * dist) * n;
+  k.n = n;
+  out.push_back(k);
+}
+
+/* Cylinder (centre c, rotation R, radius r, half length h along the body z axis) against a
+ * plane, reading 17: each end cap contributes three rim points 120 degrees apart, starting from
+ * the rim's lowest direction w = -(n - (n.u) u)/|.| (the body x axis when the cap is parallel
+ * to the plane): a tilted cylinder touches with its lowest rim point, a lying one along a line,
+ * a standing one on a tripod.  Subs 3 cap + k (cap 0 at -h). */
+template <class S>
+static void cylinder_plane(const V3<S>& c, const M3<S>& R, S r, S h, const V3<S>& o, const V3<S>& n,
+                           std::vector<RawContact<S>>& out) {
+  const V3<S> u = R.col(2);
+  V3<S> w = -(n - dot(n, u) * u);
+  const S wl = norm(w);
+  w = wl > S(1e-6) ? (S(1.0) / wl) * w : R.col(0);
+  const V3<S> w2 = cross(u, w);
+  for (int cap = 0; cap < 2; ++cap) {
+    const V3<S> ce = c + (cap ? h : -h) * u;
+    for (int k = 0; k < 3; ++k) {
+      const double th = 2.0 * M_PI * k / 3.0;
+      const V3<S> p = ce + (r * S(std::cos(th))) * w + (r * S(std::sin(th))) * w2;
+      RawContact<S> kc;
+      const S dist = dot(n, p - o);
+      kc.phi = dist;
+      kc.p = p - (S(0.5) * dist) * n;
+      kc.n = n;
+      out.push_back(kc);
+    }
+  }
+}
+
+/* Sphere (centre s, radius rs) against a solid cylinder (centre c, axis u, radius r, half
+ * length h), reading 17: with t = u.(s - c) and the radial offset d = (s - c) - t u, a centre
+ * outside the cylinder is pushed from the closest point c + clamp(t) u + min(|d|, r) d/|d|; a
+ * centre inside leaves through the nearer of the side (depth r - |d|) and the cap (depth
+ * h - |t|).  The normal points from the cylinder toward the sphere. */
+template <class S>
+static void sphere_cylinder(const V3<S>& sc, S rs, const V3<S>& c, const M3<S>& R, S r, S h, bool sphere_is_a,
+                            std::vector<RawContact<S>>& out) {
+  const V3<S> u = R.col(2);
+  const V3<S> rel = sc - c;
+  const S t = dot(u, rel);
+  const V3<S> d = rel - t * u;
+  const S rho = norm(d);
+  const V3<S> dr = rho > S(1e-12) ? (S(1.0) / rho) * d : R.col(0);
+  V3<S> nb, q;
+  S dist;
+  if (fabs(t) <= h && rho <= r) {
+    const S side = r - rho, cap = h - fabs(t);
+    if (side <= cap) {
+      nb = dr;
+      dist = -side;
+      q = c + t * u + r * dr;
+    } else {
+      const S sg = t >= S(0.0) ? S(1.0) : S(-1.0);
+      nb = sg * u;
+      dist = -cap;
+      q = c + (sg * h) * u + d;
+    }
+  } else {
+    const S tc = clampv(t, -h, h);
+    const S rc = rho < r ? rho : r;
+    q = c + tc * u + rc * dr;
+    const V3<S> g = sc - q;
+    dist = norm(g);
+    nb = (S(1.0) / dist) * g;
+  }
+  RawContact<S> k;
+  k.phi = dist - rs;
+  k.p = S(0.5) * ((sc - rs * nb) + q);
+  k.n = sphere_is_a ? nb : -nb;
+  out.push_back(k);
+}
+
 /* Box signed distance along the capsule axis: f(t) = sdf_box(x0 + t w), t in [-h, h], in box
  * coordinates.  f is convex; t* = argmin f.  If the axis stays outside the box, f^2 is the
  * C1 piecewise quadratic sum_k max(|x_k(t)| - s_k, 0)^2, and t* is the root of its
@@ -820,6 +910,10 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         else if (ta == CAPSULE) {
           sphere_plane(G[ga].c - S(sa[1]) * axa, S(sa[0]), o, nz, raw);
           sphere_plane(G[ga].c + S(sa[1]) * axa, S(sa[0]), o, nz, raw);
+        } else if (ta == ELLIPSOID) {
+          ellipsoid_plane(G[ga].c, G[ga].R, vload<S>(sa), o, nz, raw);
+        } else if (ta == CYLINDER) {
+          cylinder_plane(G[ga].c, G[ga].R, S(sa[0]), S(sa[1]), o, nz, raw);
         } else if (ta == BOX) {
           for (int cx = -1; cx <= 1; cx += 2)
             for (int cy = -1; cy <= 1; cy += 2)
@@ -863,6 +957,13 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         V3<S> x0 = mulT(bg.R, cg.c - bg.c), wl = mulT(bg.R, cg.R.col(2));
         S t = capsule_box_param(x0, wl, S(cs[1]), vload<S>(bs));
         sphere_box(cg.c + t * cg.R.col(2), S(cs[0]), bg.c, bg.R, vload<S>(bs), capA, raw);
+      } else if ((ta == SPHERE && tb == CYLINDER) || (ta == CYLINDER && tb == SPHERE)) {
+        const bool sphA = ta == SPHERE;
+        const GeomPose<S>& sg = sphA ? G[ga] : G[gb];
+        const GeomPose<S>& cg = sphA ? G[gb] : G[ga];
+        const double* ss = sphA ? sa : sb;
+        const double* cs = sphA ? sb : sa;
+        sphere_cylinder(sg.c, S(ss[0]), cg.c, cg.R, S(cs[0]), S(cs[1]), sphA, raw);
       } else if (ta == BOX && tb == BOX) {
         box_box(G[ga].c, G[ga].R, vload<S>(sa), G[gb].c, G[gb].R, vload<S>(sb), raw);
       } else {

@@ -35,7 +35,7 @@ import dataclasses
 from dataclasses import dataclass, field
 import numpy as np
 
-PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+PLANE, SPHERE, CAPSULE, BOX, CYLINDER, ELLIPSOID = 0, 1, 2, 3, 4, 5
 FREE, HINGE = 0, 1
 PARAM_STRIDE = 8  # per-body override block: mass, I1, I2, I3, type, s0, s1, s2
 
@@ -61,6 +61,19 @@ def capsule_mass_inertia(r, h, rho):
 def box_mass_inertia(half, m):
     a, b, c = 2.0 * np.asarray(half, dtype=np.float64)
     return m, np.array([m * (b * b + c * c) / 12.0, m * (a * a + c * c) / 12.0, m * (a * a + b * b) / 12.0])
+
+
+def cylinder_mass_inertia(r, h, rho):
+    """Solid cylinder of radius r, half length h along z."""
+    m = rho * np.pi * r * r * 2.0 * h
+    return m, np.array([m * (3 * r * r + 4 * h * h) / 12.0, m * (3 * r * r + 4 * h * h) / 12.0, 0.5 * m * r * r])
+
+
+def ellipsoid_mass_inertia(e, rho):
+    """Solid ellipsoid with semi-axes e = (a, b, c)."""
+    a, b, c = np.asarray(e, dtype=np.float64)
+    m = rho * 4.0 / 3.0 * np.pi * a * b * c
+    return m, np.array([m * (b * b + c * c) / 5.0, m * (a * a + c * c) / 5.0, m * (a * a + b * b) / 5.0])
 
 
 def random_quats(rng, n):

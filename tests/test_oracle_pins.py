@@ -645,6 +645,87 @@ def test_box_box_stack_settles_in_place(oracle):
         assert np.hypot(*(q1[i, :2] - q.reshape(3, 7)[i, :2])) < 0.005
 
 
+def _plane_contacts(oracle, geom, q):
+    d = Wd.world([dict(mass=1.0)], [dict(type=S.PLANE, body=-1), dict(geom, body=0)])
+    rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=1.0), DT, q, np.zeros(6))
+    return {c["sub"]: c for c in rec["contacts"]}
+
+
+def test_ellipsoid_plane_is_the_lowest_surface_point(oracle):
+    """Reading 17: the gap of an ellipsoid over the floor is its lowest surface point's height
+    (dense surface samples), at any orientation; unrotated it is z - c."""
+    rng = np.random.default_rng(31)
+    e = np.array([0.05, 0.03, 0.02])
+    cs = _plane_contacts(oracle, dict(type=S.ELLIPSOID, size=tuple(e)), np.array([0, 0, 0.1, 1, 0, 0, 0.0]))
+    assert cs[0]["phi"] == pytest.approx(0.08, abs=1e-12)
+    u = rng.standard_normal((200000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    for trial in range(5):
+        qu = S.random_quats(rng, 1)[0]
+        cs = _plane_contacts(oracle, dict(type=S.ELLIPSOID, size=tuple(e)), np.concatenate([[0.01, 0.02, 0.1], qu]))
+        pts = (u * e) @ _quat_mat(qu).T + np.array([0.01, 0.02, 0.1])
+        assert cs[0]["phi"] == pytest.approx(pts[:, 2].min(), abs=2e-6)
+        assert cs[0]["phi"] <= pts[:, 2].min() + 1e-12
+
+
+def test_cylinder_plane_rim_points(oracle):
+    """Reading 17: standing, the bottom rim's three points carry the cylinder (gap z - h); lying,
+    each cap's lowest rim point (gap z - r); tilted, the lowest of the six is the lowest point of
+    the solid (dense rim samples)."""
+    r, h = 0.03, 0.05
+    g = dict(type=S.CYLINDER, size=(r, h, 0))
+    cs = _plane_contacts(oracle, g, np.array([0, 0, 0.2, 1, 0, 0, 0.0]))
+    for k in (0, 1, 2):
+        assert cs[k]["phi"] == pytest.approx(0.2 - h, abs=1e-12)
+    qy = S.quat_about((1, 0, 0), np.pi / 2)
+    cs = _plane_contacts(oracle, g, np.concatenate([[0, 0, 0.2], qy]))
+    assert cs[0]["phi"] == pytest.approx(0.2 - r, abs=1e-12) and cs[3]["phi"] == pytest.approx(0.2 - r, abs=1e-12)
+    rng = np.random.default_rng(32)
+    th = np.linspace(0, 2 * np.pi, 100001)
+    for trial in range(5):
+        qu = S.random_quats(rng, 1)[0]
+        cs = _plane_contacts(oracle, g, np.concatenate([[0, 0, 0.2], qu]))
+        R = _quat_mat(qu)
+        rim = np.concatenate([np.stack([r * np.cos(th), r * np.sin(th), np.full_like(th, z)], 1) for z in (-h, h)])
+        low = (rim @ R.T)[:, 2].min() + 0.2
+        assert min(c["phi"] for c in cs.values()) == pytest.approx(low, abs=1e-8)
+
+
+def test_sphere_cylinder_distance_brute_force(oracle):
+    """Reading 17: separated sphere-cylinder pairs: the gap is the distance from the sphere centre
+    to the solid cylinder (dense surface samples) minus the radius; for centres inside, the
+    smaller of the side and cap depths."""
+    rng = np.random.default_rng(33)
+    r, h, rs = 0.03, 0.05, 0.02
+    th = rng.uniform(0, 2 * np.pi, 300000)
+    zz = rng.uniform(-h, h, 300000)
+    side = np.stack([r * np.cos(th), r * np.sin(th), zz], 1)
+    rr = r * np.sqrt(rng.uniform(0, 1, 200000))
+    t2 = rng.uniform(0, 2 * np.pi, 200000)
+    caps = np.concatenate([np.stack([rr * np.cos(t2), rr * np.sin(t2), np.full_like(rr, z)], 1) for z in (-h, h)])
+    surf = np.concatenate([side, caps])
+    from scipy.spatial import cKDTree
+    done = 0
+    for trial in range(30):
+        qc = np.concatenate([[0, 0, 0], S.random_quats(rng, 1)[0]])
+        ps = rng.uniform(-0.09, 0.09, 3)
+        d = Wd.world([dict(mass=1.0), dict(mass=1.0)], [dict(type=S.SPHERE, body=0, size=(rs, 0, 0)),
+                                                         dict(type=S.CYLINDER, body=1, size=(r, h, 0))])
+        rec = oracle.step_record(d, Wd.params(gravity=(0.0, 0.0, 0.0), margin=1.0), DT,
+                                 np.concatenate([ps, [1, 0, 0, 0], qc]), np.zeros(12))
+        c = rec["contacts"][0]
+        R = _quat_mat(qc[3:])
+        loc = R.T @ ps
+        inside = abs(loc[2]) <= h and np.hypot(loc[0], loc[1]) <= r
+        if inside:
+            want = -min(r - np.hypot(loc[0], loc[1]), h - abs(loc[2])) - rs
+        else:
+            want = cKDTree(surf @ R.T).query(ps)[0] - rs
+        assert c["phi"] == pytest.approx(want, abs=2e-4 if not inside else 1e-12)
+        done += 1
+    assert done == 30
+
+
 def test_box_plane_corners_and_capsule_plane_endpoints(oracle):
     """Box-plane emits every corner below the margin; capsule-plane both end spheres."""
     d = Wd.world([dict(mass=1.0), dict(mass=1.0)],
