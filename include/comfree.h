@@ -60,6 +60,9 @@ typedef enum {
 #define CF_GEOM_SPHERE 1  /* size[0] = radius                                           */
 #define CF_GEOM_CAPSULE 2 /* size[0] = radius, size[1] = half length along local z      */
 #define CF_GEOM_BOX 3     /* size = half extents                                        */
+#define CF_GEOM_CYLINDER 4  /* size[0] = radius, size[1] = half length along local z; touches
+                               planes and spheres only (reading 17)                         */
+#define CF_GEOM_ELLIPSOID 5 /* size = semi-axes; touches planes only (reading 17)          */
 #define CF_JOINT_FREE 0
 #define CF_JOINT_HINGE 1
 
@@ -138,7 +141,8 @@ cf_status cf_batch_workspace_bytes(const cf_model* model, int32_t n_worlds, cons
 /* Create a batch inside the caller's device workspace (at least cf_batch_workspace_bytes,
  * 256-byte aligned).  world_params (host, nullable) holds, in world order, one block of 8
  * floats per body for every world of a pile scene: mass, I1, I2, I3, geom type (sphere,
- * capsule or box), size0, size1, size2; worlds of other scenes contribute nothing.  NULL keeps the
+ * capsule, box, cylinder or ellipsoid), size0, size1, size2; worlds of other scenes contribute
+ * nothing.  NULL keeps the
  * scene defaults.  The initial state is the scene's zero state (identity poses) until
  * cf_set_state.  The workspace must outlive the batch.  Synchronises `stream`. */
 cf_status cf_batch_create(const cf_model* model, int32_t n_worlds, const int32_t* scene_of_world,

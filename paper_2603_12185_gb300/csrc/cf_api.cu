@@ -164,12 +164,13 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
   int nplane = 0, plane0 = -1;
   for (int g = 0; g < d.ngeom; ++g) {
     int ty = d.geom_type[g], bd = d.geom_body[g];
-    if (ty < CF_GEOM_PLANE || ty > CF_GEOM_BOX) return fail(CF_ERR_INVALID_ARGUMENT, "scene %d geom %d: type %d", si, g, ty);
+    if (ty < CF_GEOM_PLANE || ty > CF_GEOM_ELLIPSOID)
+      return fail(CF_ERR_INVALID_ARGUMENT, "scene %d geom %d: type %d", si, g, ty);
     if (bd < -1 || bd >= d.nbody) return fail(CF_ERR_INVALID_ARGUMENT, "scene %d geom %d: body %d", si, g, bd);
     if (ty == CF_GEOM_PLANE && bd != -1)
       return fail(CF_ERR_UNSUPPORTED, "scene %d geom %d: planes must be static", si, g);
     if (ty != CF_GEOM_PLANE) {
-      int need = ty == CF_GEOM_SPHERE ? 1 : (ty == CF_GEOM_CAPSULE ? 2 : 3);
+      int need = ty == CF_GEOM_SPHERE ? 1 : (ty == CF_GEOM_CAPSULE || ty == CF_GEOM_CYLINDER ? 2 : 3);
       for (int k = 0; k < need; ++k)
         if (!(d.geom_size[3 * g + k] > 0.0))
           return fail(CF_ERR_INVALID_ARGUMENT, "scene %d geom %d: size must be positive", si, g);
@@ -224,8 +225,12 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
   }
   {
     int nbox = 0;
-    for (int g = 0; g < d.ngeom; ++g) nbox += G[g].type == CF_GEOM_BOX && G[g].body >= 0;
-    sc.boxbox = nbox >= 2 ? 1 : 0;
+    int nextra = 0;
+    for (int g = 0; g < d.ngeom; ++g) {
+      nbox += G[g].type == CF_GEOM_BOX && G[g].body >= 0;
+      nextra += G[g].type >= CF_GEOM_CYLINDER;
+    }
+    sc.boxbox = (nbox >= 2 || nextra > 0) ? 1 : 0;
   }
   sc.npair = (int)m->pairs.size() - sc.pair0;
   sc.nq = nq;
@@ -491,8 +496,8 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
         const float* p = params.data() + d.padr + 8 * i;
         int ty = (int)p[4];
         bool ok = p[0] > 0.f && p[1] > 0.f && p[2] > 0.f && p[3] > 0.f &&
-                  (ty == CF_GEOM_SPHERE || ty == CF_GEOM_CAPSULE || ty == CF_GEOM_BOX) && p[5] > 0.f &&
-                  (ty == CF_GEOM_SPHERE || p[6] > 0.f) && (ty != CF_GEOM_BOX || p[7] > 0.f) && (float)ty == p[4];
+                  ty >= CF_GEOM_SPHERE && ty <= CF_GEOM_ELLIPSOID && p[5] > 0.f && (ty == CF_GEOM_SPHERE || p[6] > 0.f) &&
+                  ((ty != CF_GEOM_BOX && ty != CF_GEOM_ELLIPSOID) || p[7] > 0.f) && (float)ty == p[4];
         if (!ok) {
           delete b;
           return fail(CF_ERR_INVALID_ARGUMENT, "world %d body %d: bad override block", w, i);
@@ -524,8 +529,13 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
       continue;
     }
     int nbox = 0;
-    for (int i = 0; i < sc.nbody; ++i) nbox += (int)params[d.padr + 8 * i + 4] == CF_GEOM_BOX;
-    if (nbox >= 2) b->ext = true;
+    int nextra = 0;
+    for (int i = 0; i < sc.nbody; ++i) {
+      const int ty = (int)params[d.padr + 8 * i + 4];
+      nbox += ty == CF_GEOM_BOX;
+      nextra += ty >= CF_GEOM_CYLINDER;
+    }
+    if (nbox >= 2 || nextra > 0) b->ext = true;
   }
   // zero state with identity orientations
   std::vector<float> q0(b->total_nq, 0.f);

@@ -377,6 +377,80 @@ static __device__ __noinline__ Raw nf_box_box(f3 ca, M33 Ra, f3 ha, f3 cb, M33 R
   return o;
 }
 
+// Ellipsoid (centre c, rotation R, semi-axes e) against a plane (point o, normal n): the
+// support point against n, c - R D^2 R^T n / |D R^T n| (D = diag(e)), is the lowest point.
+__device__ __forceinline__ Raw nf_ellipsoid_plane(f3 c, const M33& R, f3 e, f3 o, f3 n) {
+  const f3 nl = mulT(R, n);
+  const f3 dn = mk3(e.x * nl.x, e.y * nl.y, e.z * nl.z);
+  const float il = rsqrtf(dot(dn, dn));
+  const f3 p = c - mul(R, mk3(e.x * dn.x * il, e.y * dn.y * il, e.z * dn.z * il));
+  Raw k;
+  k.phi = dot(n, p - o);
+  k.p = p - (0.5f * k.phi) * n;
+  k.n = n;
+  return k;
+}
+
+// Cylinder (centre c, rotation R, radius r, half length h along body z) against a plane: rim
+// point `sub` = 3 cap + k of the cap at -h (cap 0) or +h (cap 1), at 120 k degrees from the
+// rim's lowest direction -(n - (n.u) u)/|.| (the body x axis when the cap is parallel).
+__device__ __forceinline__ Raw nf_cylinder_plane(f3 c, const M33& R, float r, float h, f3 o, f3 n, int sub) {
+  const f3 u = col(R, 2);
+  // -(n - (n.u) u) written as u x (u x n): the direct form cancels in 1 - (n.u)^2 when the
+  // cylinder stands nearly upright, which FP32 resolves too coarsely
+  f3 w = cross(u, cross(u, n));
+  const float wl2 = dot(w, w);
+  w = wl2 > 1e-12f ? rsqrtf(wl2) * w : col(R, 0);
+  const f3 w2 = cross(u, w);
+  const int k = sub % 3;
+  const float cs = k == 0 ? 1.f : -0.5f, sn = k == 0 ? 0.f : (k == 1 ? 0.8660254f : -0.8660254f);
+  const f3 p = c + (sub >= 3 ? h : -h) * u + (r * cs) * w + (r * sn) * w2;
+  Raw o2;
+  o2.phi = dot(n, p - o);
+  o2.p = p - (0.5f * o2.phi) * n;
+  o2.n = n;
+  return o2;
+}
+
+// Sphere (centre sc, radius rs) against a solid cylinder (centre c, rotation R, radius r, half
+// length h): a centre outside meets the closest point; one inside leaves through the nearer of
+// the side and the cap.  The normal points from B to A (sphere_is_a: the sphere is A).
+__device__ __forceinline__ Raw nf_sphere_cylinder(f3 sc, float rs, f3 c, const M33& R, float r, float h,
+                                                  bool sphere_is_a) {
+  const f3 u = col(R, 2);
+  const f3 rel = sc - c;
+  const float t = dot(u, rel);
+  const f3 d = rel - t * u;
+  const float rho = sqrtf(dot(d, d));
+  const f3 dr = rho > 1e-12f ? (1.f / rho) * d : col(R, 0);
+  f3 nb, q;
+  float dist;
+  if (fabsf(t) <= h && rho <= r) {
+    const float side = r - rho, cap = h - fabsf(t);
+    if (side <= cap) {
+      nb = dr;
+      dist = -side;
+      q = c + t * u + r * dr;
+    } else {
+      const float sg = t >= 0.f ? 1.f : -1.f;
+      nb = sg * u;
+      dist = -cap;
+      q = c + (sg * h) * u + d;
+    }
+  } else {
+    const float tc = fminf(fmaxf(t, -h), h), rc = fminf(rho, r);
+    q = c + tc * u + rc * dr;
+    const f3 g = sc - q;
+    dist = sqrtf(dot(g, g));
+    nb = (1.f / dist) * g;
+  }
+  Raw k;
+  k.phi = dist - rs;
+  k.p = 0.5f * ((sc - rs * nb) + q);
+  k.n = sphere_is_a ? nb : -1.f * nb;
+  return k;
+}
+
 // Gram matrix, through M~^-1, of a contact's six basis rows: point velocity along n, t1, t2
 // (0..2) and relative angular velocity about n, t1, t2 (3..5) -- the entries the facet rows
 // J~_j = J_n - mu d_j^T J_s need for their diagonals w_j = J~_j M~^-1 J~_j^T.

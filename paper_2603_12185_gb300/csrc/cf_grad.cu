@@ -795,6 +795,7 @@ __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float
 bool grad_scene_supported(const DScene& s, const char** why) {
   if (s.pile) { *why = "pile scenes are not differentiable here"; return false; }
   if (s.joints) { *why = "the adjoint does not cover joint limits or dry joint friction"; return false; }
+  if (s.boxbox) { *why = "the adjoint does not cover box-box pairs, cylinders or ellipsoids"; return false; }
   if (s.nbody > kG1Body || s.ngeom > kG1Geom || s.nq > kG1Q || s.nv > kG1V || s.ntree > kG1Tree) {
     *why = "scene exceeds the adjoint's per-world limits (24 bodies, 32 geoms, 48 q, 48 v, 8 trees)";
     return false;

@@ -30,7 +30,7 @@ struct alignas(16) DScene {
   int nu, ntree, pile, nplane;
   int body0, geom0, tree0, pair0;
   int npair, plane0, maxdepth, joints;  // joints: some hinge is limited or has dry friction
-  int boxbox, pad1, pad2, pad3;         // boxbox: two box geoms may touch (extended kernel)
+  int boxbox, pad1, pad2, pad3;         // boxbox: needs the extended kernel (two boxes, cylinders, ellipsoids)
 };
 
 struct alignas(16) DBody {

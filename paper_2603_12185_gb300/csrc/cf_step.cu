@@ -238,7 +238,12 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
-  if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
+  if (kExt && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
+    if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER)
+      k = nf_sphere_cylinder(ca, pile_rad(s, a), cb, pile_R(s, b), pile_rad(s, b), pile_hl(s, b), true);
+    else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE)
+      k = nf_sphere_cylinder(cb, pile_rad(s, b), ca, pile_R(s, a), pile_rad(s, a), pile_hl(s, a), false);
+  } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
     f3 ua = pile_axis(s, a), ub = pile_axis(s, b);
     f3 p1 = ca - pile_hl(s, a) * ua, q1 = ca + pile_hl(s, a) * ua, p2 = cb - pile_hl(s, b) * ub, q2 = cb + pile_hl(s, b) * ub;
     float ss, tt;
@@ -275,8 +280,12 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
 }
 
 // narrowphase of body a against a plane: sphere (sub 0), capsule end sphere sub, box corner sub
+template <bool kExt>
 __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int sub, f3 ca, f3 o, f3 nz) {
   const int ta = pile_type(s, a);
+  if (kExt && ta == CF_GEOM_CYLINDER) return nf_cylinder_plane(ca, pile_R(s, a), pile_rad(s, a), pile_hl(s, a), o, nz, sub);
+  if (kExt && ta == CF_GEOM_ELLIPSOID)
+    return nf_ellipsoid_plane(ca, pile_R(s, a), mk3(pile_rad(s, a), pile_hl(s, a), pile_s2(s, a)), o, nz);
   f3 c = ca;
   float r = pile_rad(s, a);
   if (ta == CF_GEOM_CAPSULE) {
@@ -295,6 +304,7 @@ __device__ __forceinline__ int pile_nsub(const PileView& s, int code) {
   if (code < 0) return 0;
   const int ta = pile_type(s, code >> 16);
   if (!(code & kPlaneBit)) return kExt && ta == CF_GEOM_BOX && pile_type(s, code & kBodyMask) == CF_GEOM_BOX ? 8 : 1;
+  if (kExt && ta >= CF_GEOM_CYLINDER) return ta == CF_GEOM_CYLINDER ? 6 : 1;
   return ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
 }
 
@@ -307,7 +317,7 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
   const f3 ca = mk3(pa4.x, pa4.y, pa4.z);
   if (bc & kPlaneBit) {
     const float* pl = s.planes + 12 * (bc & kPlaneMask);
-    k = pile_narrow_plane(s, a, sub, ca, mk3(pl[0], pl[1], pl[2]), mk3(pl[3], pl[4], pl[5]));
+    k = pile_narrow_plane<kExt>(s, a, sub, ca, mk3(pl[0], pl[1], pl[2]), mk3(pl[3], pl[4], pl[5]));
   } else {
     k = pile_narrow_pair<kExt>(s, a, bc, ca, sub);
   }
@@ -353,8 +363,12 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     rc[4].w = r;
     rc[5] = make_float4(h, s2, __int_as_float(t), 0.f);
     rc[6] = make_float4(qi[3], qi[4], qi[5], qi[6]);
-    s.pb[i] = make_float4(px, py, pz,
-                          t == CF_GEOM_SPHERE ? r : (t == CF_GEOM_CAPSULE ? r + h : sqrtf(r * r + h * h + s2 * s2)));
+    const float bound = t == CF_GEOM_SPHERE ? r
+                        : t == CF_GEOM_CAPSULE ? r + h
+                        : t == CF_GEOM_CYLINDER ? sqrtf(r * r + h * h)
+                        : t == CF_GEOM_ELLIPSOID ? fmaxf(r, fmaxf(h, s2))
+                                                 : sqrtf(r * r + h * h + s2 * s2);
+    s.pb[i] = make_float4(px, py, pz, bound);
   }
   for (int pi = tid; pi < NP; pi += T) {
     PlaneDev pl = load_plane(P.geoms[sc.geom0 + sc.plane0 + pi]);
@@ -1051,6 +1065,14 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
         Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
         if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, e, k, true, px);
       }
+    } else if (kExact && ta == CF_GEOM_CYLINDER) {
+      for (int sub = 0; sub < 6; ++sub) {
+        Raw k = nf_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
+        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, sub, k, true, px);
+      }
+    } else if (kExact && ta == CF_GEOM_ELLIPSOID) {
+      Raw k = nf_ellipsoid_plane(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, nz);
+      if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, true, px);
     } else if (ta == CF_GEOM_BOX) {
       for (int ci = 0; ci < 8; ++ci) {
         f3 corner = ca + mul(Ra, mk3((ci & 4) ? sa[0] : -sa[0], (ci & 2) ? sa[1] : -sa[1], (ci & 1) ? sa[2] : -sa[2]));
@@ -1062,7 +1084,10 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
   }
   Raw k;
   k.phi = 3.0e38f;
-  if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
+  if (kExact && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
+    if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER) k = nf_sphere_cylinder(ca, sa[0], cb, Rb, sb[0], sb[1], true);
+    else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE) k = nf_sphere_cylinder(cb, sb[0], ca, Ra, sa[0], sa[1], false);
+  } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
     k = nf_sphere_sphere(ca, sa[0], cb, sb[0]);
   } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
     f3 ua = col(Ra, 2), ub = col(Rb, 2);
@@ -1182,6 +1207,8 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
       for (int k = 0; k < 9; ++k) s.gR[9 * g + k] = R.m[k];
       s.gb[g] = gd.type == CF_GEOM_SPHERE ? gd.size[0]
                 : gd.type == CF_GEOM_CAPSULE ? gd.size[0] + gd.size[1]
+                : gd.type == CF_GEOM_CYLINDER ? sqrtf(gd.size[0] * gd.size[0] + gd.size[1] * gd.size[1])
+                : gd.type == CF_GEOM_ELLIPSOID ? fmaxf(gd.size[0], fmaxf(gd.size[1], gd.size[2]))
                 : sqrtf(gd.size[0] * gd.size[0] + gd.size[1] * gd.size[1] + gd.size[2] * gd.size[2]);
     }
     group_sync(gid, T);
@@ -1300,8 +1327,8 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
 // kArtic: articulated worlds compiled in; kExact: the extended instantiation, with the exact
-// diagonal impedance (trace_mode 2) and box-box contacts compiled in, so that the other
-// instantiations keep their register budget.
+// diagonal impedance (trace_mode 2), box-box contacts, cylinders and ellipsoids compiled in, so
+// that the other instantiations keep their register budget.
 template <bool kArtic, int kMinBlocks, bool kExact>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];

@@ -268,7 +268,7 @@ def make_spheres_on_plane(nworld=64, nbody=8, seed=0, radius=0.05, mass=1.0, mu=
                  {"workload": f"spheres_on_plane_{nworld}x{nbody}"})
 
 
-def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False, box_frac=0.0):
+def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False, box_frac=0.0, round_frac=0.0):
     """Per-world sphere/capsule mixes placed without overlap of their bounding spheres.
 
     Random sequential deposition, vectorised across worlds: body k draws x, y uniformly inside
@@ -287,6 +287,18 @@ def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False, 
         hs = rng.uniform(0.02, 0.045, size=(nworld, n, 3))
         is_caps = is_caps & ~is_box
         bound = np.where(is_box, np.linalg.norm(hs, axis=2), bound)
+    kind = np.zeros((nworld, n), np.int32)    # 1: cylinder, 2: ellipsoid (replacing spheres/capsules)
+    ext = np.zeros((nworld, n, 3))
+    if round_frac > 0.0:  # cylinders r U[0.02, 0.04], h U[0.02, 0.05]; ellipsoids semi-axes U[0.02, 0.05]
+        pick = (rng.random((nworld, n)) < round_frac) & ~is_box
+        kind = np.where(pick, 1 + (rng.random((nworld, n)) < 0.5), 0)
+        cyl = np.stack([rng.uniform(0.02, 0.04, (nworld, n)), rng.uniform(0.02, 0.05, (nworld, n)),
+                        np.zeros((nworld, n))], axis=2)
+        ell = rng.uniform(0.02, 0.05, size=(nworld, n, 3))
+        ext = np.where((kind == 1)[..., None], cyl, ell)
+        is_caps = is_caps & (kind == 0)
+        bound = np.where(kind == 1, np.hypot(cyl[..., 0], cyl[..., 1]),
+                         np.where(kind == 2, ell.max(axis=2), bound))
     pos = np.zeros((nworld, n, 3))
     for k in range(n):
         bk = bound[:, k]
@@ -307,6 +319,17 @@ def _pile_worlds(rng, nworld, n, rho=1000.0, half=0.3, box_h=0.6, jammed=False, 
     for w in range(nworld):
         blk = np.zeros((n, PARAM_STRIDE))
         for i in range(n):
+            if kind[w, i]:
+                if kind[w, i] == 1:
+                    m, inertia = cylinder_mass_inertia(ext[w, i, 0], ext[w, i, 1], rho)
+                    blk[i, 4] = CYLINDER
+                else:
+                    m, inertia = ellipsoid_mass_inertia(ext[w, i], rho)
+                    blk[i, 4] = ELLIPSOID
+                blk[i, 0] = m
+                blk[i, 1:4] = inertia
+                blk[i, 5:8] = ext[w, i]
+                continue
             if is_box[w, i]:
                 m, inertia = box_mass_inertia(hs[w, i], rho * 8.0 * float(np.prod(hs[w, i])))
                 blk[i, 0] = m
@@ -334,7 +357,7 @@ PILE_PARAMS = dict(k_user=0.1, d_user=0.001, n_t=8, n_tor=2, n_rol=8)
 PILE_MU = (0.8, 0.005, 0.005)
 
 
-def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False, box_frac=0.0):
+def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False, box_frac=0.0, round_frac=0.0):
     """Walled bins (floor + 4 walls at +-0.3 m) with a seeded 50/50 sphere/capsule mix.
 
     Spheres r ~ U[0.03, 0.06] m; capsules r = 0.03 m, half length ~ U[0.03, 0.08] m; density
@@ -347,10 +370,11 @@ def make_pile(nworld=4096, nbody=16, seed=0, dt=0.002, nsteps=1000, jammed=False
     rng = np.random.default_rng(seed)
     pp, pq = _planes(True)
     t = _pile_template(f"pile{nbody}", nbody, pp, pq, PILE_MU)
-    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody, jammed=jammed, box_frac=box_frac)
+    blocks, q0, v0 = _pile_worlds(rng, nworld, nbody, jammed=jammed, box_frac=box_frac, round_frac=round_frac)
     return Batch([t], Params(**PILE_PARAMS), np.zeros(nworld, np.int32), blocks, q0, v0, dt, nsteps,
                  {"workload": f"pile_{nworld}x{nbody}" + ("_jammed" if jammed else "") +
-                  (f"_boxes{box_frac:g}" if box_frac > 0 else "")})
+                  (f"_boxes{box_frac:g}" if box_frac > 0 else "") +
+                  (f"_cylell{round_frac:g}" if round_frac > 0 else "")})
 
 
 # ----------------------------------------------------------------------------------------
