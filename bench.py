@@ -39,7 +39,7 @@ METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of
 # 4096 x 256 pile workload late in the episode, from one ncu capture of the kernel sources
 # whose digest is given; reported as null once the sources differ from the ones measured.
 STEP_SOURCES = ("cf_step.cu", "cf_device_math.cuh", "cf_internal.cuh")
-TRAFFIC = {"digest": "98a7d9ea0e5734a3", "bytes": 107.70e6}
+TRAFFIC = {"digest": "ba913384c8d363c6", "bytes": 93.32e6}
 
 
 def step_digest():
@@ -192,7 +192,7 @@ def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, ja
                 contacts=int(contact_sum.sum().item()), worlds=nworld, bodies=nbody, sb=sb, batch=b, model=model)
 
 
-def run_e2e(res, steps, blocks=4):
+def run_e2e(res, steps, blocks=8):
     """Same workload through the public API with the state in pinned host memory: every step
     copies q, v host -> device, steps, and copies them device -> host.  Measured twice: serially
     on one batch, and with comfree.Pipeline, which splits the worlds into `blocks` batches on
