@@ -698,7 +698,7 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
 
 static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t smem, cudaStream_t s) {
   if (p.nunits <= 0) return CF_OK;
-  const int var = b->ext ? kExactVariant : b->variant;
+  const int var = b->ext ? kExtVariant : b->variant;
   int per_sm = step_max_blocks_per_sm(artic, var, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
   cudaError_t e = launch_step(p, artic, var, grid, smem, s);
@@ -1111,7 +1111,7 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
   }
   const bool artic = !sc.pile;
   // per-world override blocks live on the device here, so a pile with overrides may hold boxes
-  const int var = (m->trace_mode == 2 || sc.boxbox || (sc.pile && world_params)) ? kExactVariant : 0;
+  const int var = (m->trace_mode == 2 || sc.boxbox || (sc.pile && world_params)) ? kExtVariant : 0;
   const size_t smem = world_smem_bytes(sc, warps) * per;
   if (smem > step_max_dynamic_smem()) return fail(CF_ERR_UNSUPPORTED, "a world needs %zu bytes of shared memory", smem);
   int nsm = 0;

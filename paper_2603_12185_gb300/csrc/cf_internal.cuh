@@ -113,7 +113,7 @@ size_t world_smem_bytes(const DScene& s, int warps);
 // variant 0..2 = pile-only kernel compiled for 2, 3 or 4 resident CTAs per SM
 constexpr int kStepVariants = 5;
 constexpr int kPileVariants = 3;
-constexpr int kExactVariant = 99;  // the extended kernel: exact diagonal impedance, box-box contacts
+constexpr int kExtVariant = 99;  // the extended kernel: exact diagonal impedance, box-box contacts
 cudaError_t launch_step(const StepParams& p, bool artic, int variant, int grid, size_t smem, cudaStream_t stream);
 int step_max_blocks_per_sm(bool artic, int variant, size_t smem);
 size_t step_max_dynamic_smem();

@@ -73,13 +73,13 @@ struct PileView {
 };
 
 // Codes (pile bodies <= 4096, planes <= 4096): a candidate is (a << 16) | b for a body pair and
-// (a << 16) | 0x8000 | plane for a body-plane pair; a queued contact adds its sub-contact (box
-// corners and clipped box-box vertices: 0..7) as (sub & 7) << 12, and (sub >> 3) << 28.
+// (a << 16) | 0x8000 | plane for a body-plane pair; a queued contact adds its sub-contact (0..7:
+// capsule ends, box corners, cylinder rim points, clipped box-box vertices) as sub << 12.
 constexpr int kPlaneBit = 0x8000;
 constexpr int kPlaneMask = 0xfff;
 constexpr int kBodyMask = 0xfff;
 
-__device__ __forceinline__ int code_with_sub(int code, int sub) { return code | ((sub & 7) << 12) | ((sub >> 3) << 28); }
+__device__ __forceinline__ int code_with_sub(int code, int sub) { return code | (sub << 12); }
 constexpr int kCqWords = 8;
 
 // Body record of a pile body, 7 float4 (one vector load each):
@@ -148,9 +148,9 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, 
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
-// (a plane contributes nothing).  kGeneral: the extended instantiation (exact diagonal
-// impedance, box-box contacts).
-template <bool kGeneral>
+// (a plane contributes nothing).  kExt: the extended instantiation (exact diagonal
+// impedance, box-box contacts, cylinders and ellipsoids).
+template <bool kExt>
 __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
                                            const float* cq, int slot, bool& range) {
   Raw k;
@@ -161,7 +161,7 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   const int a = (code >> 16) & kBodyMask, bc = code & 0xffff;
   const bool plane = (bc & kPlaneBit) != 0;
   const int b = plane ? -1 : (bc & kBodyMask);
-  const int sub = ((bc >> 12) & 7) | (((code >> 28) & 1) << 3);
+  const int sub = (bc >> 12) & 7;
   f3 px = mk3(0.f, 0.f, 0.f);
   float mub0, mub1, mub2;
   int gb;
@@ -207,7 +207,7 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   const float mu_t = fmaxf(ma[0], mub0), mu_tor = fmaxf(ma[1], mub1), mu_rol = fmaxf(ma[2], mub2);
   float mphi = 0.f;
   float w[6];
-  if (kGeneral && P.trace_mode == 2) {
+  if (kExt && P.trace_mode == 2) {
     Gram g;
     gram_zero(g);
     gram_add_free(g, ima, iia, Ra, ra, k.n, t1, t2);
@@ -324,7 +324,7 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
   return k.phi < P.margin;
 }
 
-template <bool kGeneral>
+template <bool kExt>
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -482,11 +482,11 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
           const int nb = min(qn, 32);
           const int mine = lane < nb ? queue[qn - nb + lane] : -1;
           qn -= nb;
-          const int my_nsub = pile_nsub<kGeneral>(s, mine);
+          const int my_nsub = pile_nsub<kExt>(s, mine);
           const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
           for (int sub = 0; sub < nsub; ++sub) {
             Raw kc;
-            const bool hit = sub < my_nsub && pile_narrow<kGeneral>(P, s, mine, sub, kc);
+            const bool hit = sub < my_nsub && pile_narrow<kExt>(P, s, mine, sub, kc);
             const unsigned hm = __ballot_sync(0xffffffffu, hit);
             if (hit) {
               const int slot = cn + __popc(hm & lt);
@@ -500,7 +500,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
             while (cn >= 32 || (last && cn > 0)) {
               __syncwarp();
               const int ns = min(cn, 32);
-              if (lane < ns) pile_solve<kGeneral>(P, s, sc, world, cq, cn - ns + lane, range);
+              if (lane < ns) pile_solve<kExt>(P, s, sc, world, cq, cn - ns + lane, range);
               cn -= ns;
               __syncwarp();
             }
@@ -960,7 +960,7 @@ __device__ __noinline__ void artic_gram(const StepParams& P, const ArticView& s,
   }
 }
 
-template <bool kExact>
+template <bool kExt>
 __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world, int ga,
                                            int gb, int sub, const Raw& k, bool plane, f3 px) {
   const DGeom& GA = P.geoms[sc.geom0 + ga];
@@ -980,7 +980,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
   }
   float mphi = 0.f;
   float w[6];
-  if (kExact && P.trace_mode == 2) {
+  if (kExt && P.trace_mode == 2) {
     Gram g;
     artic_gram(P, s, sc, ba, bb, k.p, k.n, t1, t2, g);
     facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
@@ -1044,7 +1044,7 @@ __device__ void artic_joint_constraints(const StepParams& P, ArticView& s, const
 }
 
 // narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
-template <bool kExact>
+template <bool kExt>
 __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
   int ga = code >> 16, gb = code & 0xffff;
   const DGeom* G = P.geoms + sc.geom0;
@@ -1058,33 +1058,33 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     f3 nz = col(Rb, 2), px = col(Rb, 0);
     if (ta == CF_GEOM_SPHERE) {
       Raw k = nf_sphere_plane(ca, sa[0], cb, nz);
-      if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, true, px);
+      if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, true, px);
     } else if (ta == CF_GEOM_CAPSULE) {
       f3 ax = col(Ra, 2);
       for (int e = 0; e < 2; ++e) {
         Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
-        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, e, k, true, px);
+        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, e, k, true, px);
       }
-    } else if (kExact && ta == CF_GEOM_CYLINDER) {
+    } else if (kExt && ta == CF_GEOM_CYLINDER) {
       for (int sub = 0; sub < 6; ++sub) {
         Raw k = nf_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
-        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, sub, k, true, px);
+        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, k, true, px);
       }
-    } else if (kExact && ta == CF_GEOM_ELLIPSOID) {
+    } else if (kExt && ta == CF_GEOM_ELLIPSOID) {
       Raw k = nf_ellipsoid_plane(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, nz);
-      if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, true, px);
+      if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, true, px);
     } else if (ta == CF_GEOM_BOX) {
       for (int ci = 0; ci < 8; ++ci) {
         f3 corner = ca + mul(Ra, mk3((ci & 4) ? sa[0] : -sa[0], (ci & 2) ? sa[1] : -sa[1], (ci & 1) ? sa[2] : -sa[2]));
         Raw k = nf_sphere_plane(corner, 0.f, cb, nz);
-        if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, ci, k, true, px);
+        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, ci, k, true, px);
       }
     }
     return;
   }
   Raw k;
   k.phi = 3.0e38f;
-  if (kExact && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
+  if (kExt && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
     if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER) k = nf_sphere_cylinder(ca, sa[0], cb, Rb, sb[0], sb[1], true);
     else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE) k = nf_sphere_cylinder(cb, sb[0], ca, Ra, sa[0], sa[1], false);
   } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
@@ -1105,9 +1105,9 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     k = nf_sphere_sphere(ca, sa[0], cb + t * u, sb[0]);
   } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
     if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertices, subs 0..7
-      for (int sub = 0; kExact && sub < 8; ++sub) {
+      for (int sub = 0; kExt && sub < 8; ++sub) {
         const Raw kb = nf_box_box(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, Rb, mk3(sb[0], sb[1], sb[2]), sub);
-        if (kb.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, sub, kb, false, mk3(0.f, 0.f, 0.f));
+        if (kb.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, kb, false, mk3(0.f, 0.f, 0.f));
       }
       return;
     }
@@ -1126,7 +1126,7 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
       k = nf_sphere_box(co + t * u, os[0], cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < P.margin) artic_contact<kExact>(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
+  if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
 }
 
 // MPC running cost of the state at the start of a step (Sec. V, Eq. mpc cost terms): object
@@ -1167,7 +1167,7 @@ __device__ float artic_running_cost(const StepParams& P, const ArticView& s, con
   return c;
 }
 
-template <bool kExact>
+template <bool kExt>
 __device__ void artic_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -1238,12 +1238,12 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
       qn += __popc(m);
       __syncwarp();
       if (qn >= 32) {
-        artic_candidate<kExact>(P, s, sc, world, queue[qn - 32 + lane]);
+        artic_candidate<kExt>(P, s, sc, world, queue[qn - 32 + lane]);
         qn -= 32;
         __syncwarp();
       }
     }
-    if (lane < qn) artic_candidate<kExact>(P, s, sc, world, queue[lane]);
+    if (lane < qn) artic_candidate<kExt>(P, s, sc, world, queue[lane]);
     if (sc.joints)
       for (int t = tid; t < sc.ntree; t += T) artic_joint_constraints(P, s, sc, P.trees[sc.tree0 + t], t);
     group_sync(gid, T);
@@ -1326,10 +1326,10 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
-// kArtic: articulated worlds compiled in; kExact: the extended instantiation, with the exact
+// kArtic: articulated worlds compiled in; kExt: the extended instantiation, with the exact
 // diagonal impedance (trace_mode 2), box-box contacts, cylinders and ellipsoids compiled in, so
 // that the other instantiations keep their register budget.
-template <bool kArtic, int kMinBlocks, bool kExact>
+template <bool kArtic, int kMinBlocks, bool kExt>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_unit;
@@ -1347,8 +1347,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) 
       size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, U.warps)
                            : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, U.warps);
       float* base = smem + per * gid;
-      if (!kArtic || sc.pile) pile_world<kExact>(P, base, world, gid, U.warps);
-      else artic_world<kExact>(P, base, world, gid, U.warps);
+      if (!kArtic || sc.pile) pile_world<kExt>(P, base, world, gid, U.warps);
+      else artic_world<kExt>(P, base, world, gid, U.warps);
     }
     __syncthreads();
   }
@@ -1378,7 +1378,7 @@ static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2, false>, st
 static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0, 0};
 
 static int variant_index(bool artic, int variant) {
-  if (variant == kExactVariant) return 4;
+  if (variant == kExtVariant) return 4;
   return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant));
 }
 
