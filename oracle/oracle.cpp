@@ -17,7 +17,9 @@
  *   4. all-pairs narrowphase -> contacts (phi, point, normal)
  *   5. per contact: frame, relative Jacobian blocks J_n, J_t, J_tor, J_rol      (Sec. III-A)
  *      and the constraint-space impedance M(phi)                    (Eqs. k_d_setting, r_scaling)
- *      (or, trace_mode 2, the exact diagonal impedance of each facet, Sec. III-B)
+ *      (or, trace_mode 2, the exact diagonal impedance of each facet, Sec. III-B; or,
+ *      trace_mode 3, M(phi) scaled by a learned function of the contact's configuration,
+ *      the learning-based K(q), D(q) that Sec. III-B allows)
  *   6. per facet: J~ = J_n - mu_s d_j^T J_s, s = J~ v_s,
  *      lambda dt = ( -k M(phi) (s dt + phi) - d M(phi) s )_+        (Eqs. tilde_defs, cf_wrench)
  *   7. p = sum J~^T lambda dt                                         (Algorithm 1, Kernel III)
@@ -68,6 +70,8 @@ static inline Dual pow(Dual a, double p) {
   double r = std::pow(a.v, p);
   return Dual(r, a.v != 0 ? p * std::pow(a.v, p - 1) * a.d : 0.0);
 }
+static inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, e * a.d); }
+static inline Dual tanh(Dual a) { double t = std::tanh(a.v); return Dual(t, (1.0 - t * t) * a.d); }
 static inline double val(double a) { return a; }
 static inline double val(Dual a) { return a.v; }
 using std::sqrt; using std::sin; using std::cos; using std::fabs; using std::pow;
@@ -104,7 +108,9 @@ typedef struct {
   double margin;
   int n_t, n_tor, n_rol;
   int trace_mode; /* 0: tr(J_i M~^-1 J_i^T) of the translational point Jacobian, 1: 1/m_i,
-                     2: the exact diagonal impedance of Sec. III-B, one value per facet */
+                     2: the exact diagonal impedance of Sec. III-B, one value per facet,
+                     3: the mode-0 M(phi) times exp(g(x)), g the impedance network below */
+  const double* impnet; /* trace_mode 3: the network's IMP_PARAMS parameters */
 } ow_params;
 
 /* one detected contact, for tests */
@@ -117,6 +123,9 @@ typedef struct {
                             normal, t1, t2, torsional, rolling t1, rolling t2 */
   int nfacet;
   int nactive;
+  double feat[4];        /* the impedance network's input x (see impnet_features)     */
+  double m_exact;        /* mean over the facets of the exact diagonal impedance
+                            M_j = 1 / ((k dt + d) J~_j M~^-1 J~_j^T) (Sec. III-B)       */
 } ow_contact;
 }
 
@@ -837,11 +846,53 @@ template <class S> static S solimp_r(S aphi, const double* si) {
 }
 
 /* ------------------------------------------------------------------------------------------
+ * learned impedance (Sec. III-B: K(q) and D(q) may be learned instead of set by the
+ * heuristic).  The paper fixes neither the model nor its inputs; the readings here:
+ * K = k M_theta / dt, D = d M_theta / dt as in Eq. k_d_setting, with
+ *   M_theta = M(phi) exp(clamp(g(x), -IMP_CLAMP, IMP_CLAMP)),
+ *   g(x) = b2 + sum_h w2_h tanh(b1_h + sum_i W1_hi x_i)   (IMP_HIDDEN tanh units),
+ * theta = [W1 (IMP_HIDDEN x IMP_IN, row-major), b1, w2, b2], and the contact's configuration
+ * features
+ *   x0 = clamp(phi / solimp width, -1, 1)            (where r(|phi|) of Eq. r_scaling moves)
+ *   x1 = clamp(1 - 3 (1/m_A + 1/m_B) / (tr_A + tr_B), -1, 1)
+ *        (the share of the point-Jacobian trace that comes from rotation; 1/m of a static
+ *        side is 0, tr is the mode-0 trace)
+ *   x2 = n_z, the vertical component of the contact normal
+ *   x3 = 1 if side B is static, else 0.
+ * g = 0 gives back the heuristic exactly.
+ * ---------------------------------------------------------------------------------------- */
+enum { IMP_IN = 4, IMP_HIDDEN = 8, IMP_PARAMS = IMP_HIDDEN * IMP_IN + 2 * IMP_HIDDEN + 1 };
+static const double IMP_CLAMP = 8.0;
+
+template <class S> static S impnet_g(const double* th, const S* x) {
+  const double* W1 = th;
+  const double* b1 = th + IMP_HIDDEN * IMP_IN;
+  const double* w2 = b1 + IMP_HIDDEN;
+  const double b2 = w2[IMP_HIDDEN];
+  S g(b2);
+  for (int h = 0; h < IMP_HIDDEN; ++h) {
+    S a(b1[h]);
+    for (int i = 0; i < IMP_IN; ++i) a += S(W1[h * IMP_IN + i]) * x[i];
+    g += S(w2[h]) * tanh(a);
+  }
+  return g;
+}
+
+template <class S>
+static void impnet_features(S phi, double width, S trace_sum, double im_sum, S nz, bool b_static, S* x) {
+  x[0] = clampv(phi / S(width), S(-1.0), S(1.0));
+  x[1] = clampv(S(1.0) - S(3.0 * im_sum) / trace_sum, S(-1.0), S(1.0));
+  x[2] = nz;
+  x[3] = S(b_static ? 1.0 : 0.0);
+}
+
+/* ------------------------------------------------------------------------------------------
  * the step
  * ---------------------------------------------------------------------------------------- */
 template <class S> struct StepRecord {
   std::vector<S> vs, p, c;
   std::vector<ow_contact> contacts;
+  bool detail = false;  /* also the mean exact facet impedance of every contact */
 };
 
 template <class S>
@@ -990,8 +1041,10 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           S sgn(side == 0 ? 1.0 : -1.0);
           for (int r = 0; r < 3; ++r)
             for (int i = 0; i < st.nv; ++i) { Jl[r][i] += sgn * jl[r][i]; Ja[r][i] += sgn * ja[r][i]; }
-          /* trace of J_i M~^-1 J_i^T over the translational point Jacobian of body i */
-          if (prm->trace_mode == 0) {
+          /* trace of J_i M~^-1 J_i^T over the translational point Jacobian of body i (also the
+             input of the learned impedance's features, and of the heuristic that the exact
+             impedance is compared with) */
+          if (prm->trace_mode != 1) {
             for (int r = 0; r < 3; ++r) {
               tmp = jl[r];
               solve_all(st, L, tmp);
@@ -1012,6 +1065,13 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         /* impedance: Eq. k_d_setting with M(phi) = r/(1-r) / (tr_i + tr_j), Eq. r_scaling */
         S r = solimp_r(fabs(k.phi), prm->solimp);
         S mphi = r / (S(1.0) - r) / (trace[0] + trace[1]);
+        /* the learned impedance's inputs, and (trace_mode 3) its scaling of M(phi) */
+        S feat[4];
+        {
+          double im_sum = (ba >= 0 ? 1.0 / w->body_mass[ba] : 0.0) + (bb >= 0 ? 1.0 / w->body_mass[bb] : 0.0);
+          impnet_features(k.phi, prm->solimp[2], trace[0] + trace[1], im_sum, k.n.z, bb < 0, feat);
+        }
+        if (prm->trace_mode == 3) mphi *= exp(clampv(impnet_g(prm->impnet, feat), S(-IMP_CLAMP), S(IMP_CLAMP)));
         S kM = S(prm->k_user) * mphi, dM = S(prm->d_user) * mphi;
         /* friction coefficients of the pair: the larger of the two geoms' */
         S mu[3];
@@ -1019,6 +1079,7 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         ow_contact rc;
         std::memset(&rc, 0, sizeof(rc));
         S wrench[6] = {S(0.0), S(0.0), S(0.0), S(0.0), S(0.0), S(0.0)};
+        S m_exact_sum(0.0);
         int nf = 0, nact = 0;
         /* facets, Eqs. dual_polyhedral, tilde_defs, cf_wrench */
         auto facet = [&](int sub, S ca, S sa_) {
@@ -1034,7 +1095,8 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           S sv(0.0);
           for (int i = 0; i < st.nv; ++i) sv += Jf[i] * vs[i];
           S lam;
-          if (prm->trace_mode == 2) {
+          S Mj(0.0);
+          if (prm->trace_mode == 2 || (rec && rec->detail)) {
             /* Sec. III-B, the diagonal form K dt + D = 1/(dt w_j), w_j = J~_j M~^-1 J~_j^T; the
                user's (k, d) keep splitting it between the gap and the velocity term:
                M_j = 1 / ((k dt + d) w_j) in place of M(phi) */
@@ -1042,7 +1104,10 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
             solve_all(st, L, tmp);
             S wj(0.0);
             for (int i = 0; i < st.nv; ++i) wj += Jf[i] * tmp[i];
-            S Mj = S(1.0) / ((S(prm->k_user) * DT + S(prm->d_user)) * wj);
+            Mj = S(1.0) / ((S(prm->k_user) * DT + S(prm->d_user)) * wj);
+            m_exact_sum += Mj;
+          }
+          if (prm->trace_mode == 2) {
             lam = -S(prm->k_user) * Mj * (sv * DT + k.phi) - S(prm->d_user) * Mj * sv;
           } else {
             lam = -kM * (sv * DT + k.phi) - dM * sv;
@@ -1076,6 +1141,8 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
           rc.r = val(r); rc.mphi = prm->trace_mode == 2 ? 0.0 : val(mphi); rc.lam_sum = val(wrench[0]);
           for (int i = 0; i < 6; ++i) rc.wrench[i] = val(wrench[i]);
           rc.nfacet = nf; rc.nactive = nact;
+          for (int i = 0; i < 4; ++i) rc.feat[i] = val(feat[i]);
+          rc.m_exact = nf ? val(m_exact_sum) / nf : 0.0;
           rec->contacts.push_back(rc);
         }
       }
@@ -1223,6 +1290,7 @@ int ow_step_record(const ow_world* w, const ow_params* prm, double dt, double* q
   Structure st;
   if (!build_structure(w, st)) return -1;
   StepRecord<double> rec;
+  rec.detail = true;
   int rc = step_world<double>(w, prm, st, dt, q, v, tau, &rec);
   if (rc) return rc;
   for (int i = 0; i < st.nv; ++i) {
@@ -1284,6 +1352,45 @@ double ow_capsule_box_param(const double* x0, const double* w, double h, const d
 }
 
 double ow_solimp_r(double aphi, const double* solimp) { return solimp_r(aphi, solimp); }
+
+int ow_impnet_params(void) { return IMP_PARAMS; }
+
+/* The learned impedance network at n inputs x[n][IMP_IN]: out[n] = g(x) (unclamped). */
+void ow_impnet_eval(const double* theta, const double* x, int n, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = impnet_g(theta, x + (size_t)i * IMP_IN);
+}
+
+/* Mean squared error of the network on (x[n][IMP_IN], y[n]), L = (1/n) sum_i (g(x_i) - y_i)^2,
+ * and its gradient by the chain rule through g: grad[IMP_PARAMS]. */
+double ow_impnet_loss_grad(const double* theta, const double* x, const double* y, int n, double* grad) {
+  const double* W1 = theta;
+  const double* b1 = theta + IMP_HIDDEN * IMP_IN;
+  const double* w2 = b1 + IMP_HIDDEN;
+  for (int p = 0; p < IMP_PARAMS; ++p) grad[p] = 0.0;
+  double loss = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double* xi = x + (size_t)i * IMP_IN;
+    double hid[IMP_HIDDEN];
+    double g = w2[IMP_HIDDEN];
+    for (int h = 0; h < IMP_HIDDEN; ++h) {
+      double a = b1[h];
+      for (int k = 0; k < IMP_IN; ++k) a += W1[h * IMP_IN + k] * xi[k];
+      hid[h] = std::tanh(a);
+      g += w2[h] * hid[h];
+    }
+    const double e = g - y[i];
+    loss += e * e;
+    const double dg = 2.0 * e / n;                      /* dL/dg_i */
+    grad[IMP_PARAMS - 1] += dg;                         /* b2 */
+    for (int h = 0; h < IMP_HIDDEN; ++h) {
+      grad[IMP_HIDDEN * IMP_IN + IMP_HIDDEN + h] += dg * hid[h];        /* w2_h */
+      const double da = dg * w2[h] * (1.0 - hid[h] * hid[h]);         /* through tanh */
+      grad[IMP_HIDDEN * IMP_IN + h] += da;                             /* b1_h */
+      for (int k = 0; k < IMP_IN; ++k) grad[h * IMP_IN + k] += da * xi[k];  /* W1_hk */
+    }
+  }
+  return loss / n;
+}
 
 /* Rollout loss of body `body` after T steps, L = |x_T - x*|^2 + (1 - (quat*^T quat_T)^2), and
  * its directional derivative along (dq0, dv0, dtau) by forward-mode dual numbers.

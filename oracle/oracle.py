@@ -46,7 +46,7 @@ class OWorld(C.Structure):
 class OParams(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("k_user", C.c_double), ("d_user", C.c_double),
                 ("solimp", C.c_double * 5), ("margin", C.c_double), ("n_t", C.c_int), ("n_tor", C.c_int),
-                ("n_rol", C.c_int), ("trace_mode", C.c_int)]
+                ("n_rol", C.c_int), ("trace_mode", C.c_int), ("impnet", C.c_void_p)]
 
 
 class OContact(C.Structure):
@@ -54,7 +54,8 @@ class OContact(C.Structure):
                 ("sub", C.c_int), ("phi", C.c_double), ("pos", C.c_double * 3), ("normal", C.c_double * 3),
                 ("t1", C.c_double * 3), ("t2", C.c_double * 3), ("trace_a", C.c_double),
                 ("trace_b", C.c_double), ("r", C.c_double), ("mphi", C.c_double), ("lam_sum", C.c_double),
-                ("wrench", C.c_double * 6), ("nfacet", C.c_int), ("nactive", C.c_int)]
+                ("wrench", C.c_double * 6), ("nfacet", C.c_int), ("nactive", C.c_int), ("feat", C.c_double * 4),
+                ("m_exact", C.c_double)]
 
 
 def lib():
@@ -81,6 +82,10 @@ def lib():
             L.ow_rollout_loss_dir.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_int] + [C.c_void_p] * 6 + [
                 C.c_int, C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_double)]
             L.ow_max_threads.restype = C.c_int
+            L.ow_impnet_params.restype = C.c_int
+            L.ow_impnet_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+            L.ow_impnet_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+            L.ow_impnet_loss_grad.restype = C.c_double
             _lib = L
     return _lib
 
@@ -115,24 +120,37 @@ class World:
         self.nq, self.nv = nq.value, nv.value
 
 
-def params_struct(p):
-    s = OParams()
+class _ParamsStruct(OParams):
+    """OParams that also keeps the learned impedance's parameter array alive."""
+
+
+def params_struct(p, impnet=None):
+    """impnet: the learned impedance's parameters (trace_mode 3), else None."""
+    s = _ParamsStruct()
     s.gravity[:] = list(p.gravity)
     s.k_user, s.d_user = p.k_user, p.d_user
     s.solimp[:] = list(p.solimp)
     s.margin = p.margin
     s.n_t, s.n_tor, s.n_rol, s.trace_mode = p.n_t, p.n_tor, p.n_rol, p.trace_mode
+    if p.trace_mode == 3:
+        if impnet is None:
+            raise ValueError("trace_mode 3 needs the impedance network's parameters")
+        s._theta = np.ascontiguousarray(impnet, np.float64).reshape(-1)
+        if s._theta.size != impnet_params():
+            raise ValueError("wrong number of impedance network parameters")
+        s.impnet = s._theta.ctypes.data
     return s
 
 
-def step(desc, params, dt, nsteps, q, v, tau=None):
-    """Advance one world; returns (q, v, total contacts over the steps).  tau: [nsteps, nv] or None."""
+def step(desc, params, dt, nsteps, q, v, tau=None, impnet=None):
+    """Advance one world; returns (q, v, total contacts over the steps).  tau: [nsteps, nv] or None;
+    impnet: the learned impedance's parameters when params.trace_mode == 3."""
     w = desc if isinstance(desc, World) else World(desc)
     q = np.array(q, dtype=np.float64).copy()
     v = np.array(v, dtype=np.float64).copy()
     t = None if tau is None else np.ascontiguousarray(np.asarray(tau, np.float64).reshape(nsteps, w.nv))
     nc = C.c_int()
-    ps = params_struct(params)
+    ps = params_struct(params, impnet)
     rc = lib().ow_step(C.byref(w.s), C.byref(ps), dt, nsteps, _p(q), _p(v), None if t is None else _p(t),
                        C.byref(nc))
     if rc:
@@ -140,8 +158,9 @@ def step(desc, params, dt, nsteps, q, v, tau=None):
     return q, v, nc.value
 
 
-def step_record(desc, params, dt, q, v, tau=None, cap=20000):
-    """One step with its intermediates: dict(q, v, vs, p, c, contacts=[dict])."""
+def step_record(desc, params, dt, q, v, tau=None, cap=20000, impnet=None):
+    """One step with its intermediates: dict(q, v, vs, p, c, contacts=[dict]).  Each contact also
+    carries the learned impedance's inputs `feat` and the mean exact facet impedance `m_exact`."""
     w = desc if isinstance(desc, World) else World(desc)
     q = np.array(q, dtype=np.float64).copy()
     v = np.array(v, dtype=np.float64).copy()
@@ -149,7 +168,7 @@ def step_record(desc, params, dt, q, v, tau=None, cap=20000):
     cs = (OContact * cap)()
     n = C.c_int()
     t = None if tau is None else np.ascontiguousarray(np.asarray(tau, np.float64))
-    ps = params_struct(params)
+    ps = params_struct(params, impnet)
     rc = lib().ow_step_record(C.byref(w.s), C.byref(ps), dt, _p(q), _p(v), None if t is None else _p(t), _p(vs),
                               _p(pg), _p(cb), cs, cap, C.byref(n))
     if rc:
@@ -161,7 +180,7 @@ def step_record(desc, params, dt, q, v, tau=None, cap=20000):
                              pos=np.array(k.pos[:]), normal=np.array(k.normal[:]), t1=np.array(k.t1[:]),
                              t2=np.array(k.t2[:]), trace_a=k.trace_a, trace_b=k.trace_b, r=k.r, mphi=k.mphi,
                              lam_sum=k.lam_sum, wrench=np.array(k.wrench[:]), nfacet=k.nfacet,
-                             nactive=k.nactive))
+                             nactive=k.nactive, feat=np.array(k.feat[:]), m_exact=k.m_exact))
     return dict(q=q, v=v, vs=vs, p=pg, c=cb, contacts=contacts)
 
 
@@ -216,10 +235,10 @@ def rollout_loss_dir(desc, params, dt, q0, v0, tau, dq0, dv0, dtau, body, target
 class BatchRunner:
     """Steps many worlds in parallel with OpenMP (the timed CPU baseline)."""
 
-    def __init__(self, descs, params):
+    def __init__(self, descs, params, impnet=None):
         self.worlds = [d if isinstance(d, World) else World(d) for d in descs]
         self.ptrs = (C.c_void_p * len(self.worlds))(*[C.cast(C.pointer(w.s), C.c_void_p) for w in self.worlds])
-        self.params = params_struct(params)
+        self.params = params_struct(params, impnet)
         self.qadr = np.cumsum([0] + [w.nq for w in self.worlds[:-1]]).astype(np.int64)
         self.vadr = np.cumsum([0] + [w.nv for w in self.worlds[:-1]]).astype(np.int64)
 
@@ -234,3 +253,49 @@ class BatchRunner:
 
 def max_threads():
     return lib().ow_max_threads()
+
+
+# ---------------------------------------------------------------------------------------------
+# learned impedance (Sec. III-B): the network, its loss and the optimiser that fits it
+# ---------------------------------------------------------------------------------------------
+def impnet_params():
+    """Number of parameters of the learned impedance network."""
+    return lib().ow_impnet_params()
+
+
+def impnet_eval(theta, x):
+    """g(x) for x[n, 4] (unclamped)."""
+    th = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 4)
+    out = np.zeros(len(x))
+    lib().ow_impnet_eval(_p(th), _p(x), len(x), _p(out))
+    return out
+
+
+def impnet_loss_grad(theta, x, y):
+    """(L, dL/dtheta) of the mean squared error (1/n) sum (g(x_i) - y_i)^2."""
+    th = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 4)
+    y = np.ascontiguousarray(y, np.float64)
+    g = np.zeros(th.size)
+    L = lib().ow_impnet_loss_grad(_p(th), _p(x), _p(y), len(x), _p(g))
+    return L, g
+
+
+def impnet_adam(theta, x, y, iters, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Full-batch Adam (Kingma and Ba, ICLR 2015, Algorithm 1, with the bias corrections
+    applied to the moments) on the mean squared error; returns (theta, losses before each
+    update)."""
+    th = np.array(theta, np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    losses = []
+    for t in range(1, iters + 1):
+        L, g = impnet_loss_grad(th, x, y)
+        losses.append(L)
+        m = beta1 * m + (1 - beta1) * g
+        v = beta2 * v + (1 - beta2) * g * g
+        mh = m / (1 - beta1 ** t)
+        vh = v / (1 - beta2 ** t)
+        th = th - lr * mh / (np.sqrt(vh) + eps)
+    return th, np.array(losses)
