@@ -857,7 +857,10 @@ template <class S> static S solimp_r(S aphi, const double* si) {
  *   x1 = clamp(1 - 3 (1/m_A + 1/m_B) / (tr_A + tr_B), -1, 1)
  *        (the share of the point-Jacobian trace that comes from rotation; 1/m of a static
  *        side is 0, tr is the mode-0 trace)
- *   x2 = n_z, the vertical component of the contact normal
+ *   x2 = clamp(w_n / (tr_A + tr_B), 0, 4), w_n = sum over the dynamic sides of
+ *        1/m_b + (l_b x n)^T I_b^-1 (l_b x n) with l_b the lever from body b's centre of mass
+ *        and I_b its world inertia: the normal row's J M^-1 J^T with every body taken as a
+ *        free body (exact for free bodies, a cheap stand-in for links of a tree)
  *   x3 = 1 if side B is static, else 0.
  * g = 0 gives back the heuristic exactly.
  * ---------------------------------------------------------------------------------------- */
@@ -879,11 +882,20 @@ template <class S> static S impnet_g(const double* th, const S* x) {
 }
 
 template <class S>
-static void impnet_features(S phi, double width, S trace_sum, double im_sum, S nz, bool b_static, S* x) {
+static void impnet_features(S phi, double width, S trace_sum, double im_sum, S w_n, bool b_static, S* x) {
   x[0] = clampv(phi / S(width), S(-1.0), S(1.0));
   x[1] = clampv(S(1.0) - S(3.0 * im_sum) / trace_sum, S(-1.0), S(1.0));
-  x[2] = nz;
+  x[2] = clampv(w_n / trace_sum, S(0.0), S(4.0));
   x[3] = S(b_static ? 1.0 : 0.0);
+}
+
+/* 1/m + (l x n)^T I^-1 (l x n) of body b taken as a free body, l = p - its centre of mass */
+template <class S>
+static S free_normal_inverse_mass(const ow_world* w, const std::vector<Pose<S>>& P, int b, const V3<S>& p,
+                                  const V3<S>& n) {
+  V3<S> u = mulT(P[b].R, cross(p - P[b].com, n));
+  const double* I = w->body_inertia + 3 * b;
+  return S(1.0 / w->body_mass[b]) + u.x * u.x / S(I[0]) + u.y * u.y / S(I[1]) + u.z * u.z / S(I[2]);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -1069,7 +1081,10 @@ static int step_world(const ow_world* w, const ow_params* prm, const Structure& 
         S feat[4];
         {
           double im_sum = (ba >= 0 ? 1.0 / w->body_mass[ba] : 0.0) + (bb >= 0 ? 1.0 / w->body_mass[bb] : 0.0);
-          impnet_features(k.phi, prm->solimp[2], trace[0] + trace[1], im_sum, k.n.z, bb < 0, feat);
+          S w_n(0.0);
+          if (ba >= 0) w_n += free_normal_inverse_mass(w, P, ba, k.p, k.n);
+          if (bb >= 0) w_n += free_normal_inverse_mass(w, P, bb, k.p, k.n);
+          impnet_features(k.phi, prm->solimp[2], trace[0] + trace[1], im_sum, w_n, bb < 0, feat);
         }
         if (prm->trace_mode == 3) mphi *= exp(clampv(impnet_g(prm->impnet, feat), S(-IMP_CLAMP), S(IMP_CLAMP)));
         S kM = S(prm->k_user) * mphi, dM = S(prm->d_user) * mphi;

@@ -89,7 +89,8 @@ def test_constant_network_is_scaled_k_and_d(oracle, scene):
 def test_features_of_a_uniform_sphere_on_a_plane(oracle):
     """A uniform sphere (I = 0.4 m r^2) touching a plane: its lever is parallel to the normal,
     tr(J M^-1 J^T) = 3/m + 2 r_c^2 / I with r_c the lever length, so the rotational share is
-    x1 = 1 - (3/m) / tr.  x0 = phi / width, x2 = n_z = 1, x3 = 1 (a static plane)."""
+    x1 = 1 - (3/m) / tr, and the normal row n^T J M^-1 J^T n = 1/m (no rotation) gives
+    x2 = (1/m) / tr.  x0 = phi / width, x3 = 1 (a static plane)."""
     m, r = 2.0, 0.05
     I = 0.4 * m * r * r
     d = Wd.sphere_on_plane(r=r, m=m, inertia=I)
@@ -99,14 +100,15 @@ def test_features_of_a_uniform_sphere_on_a_plane(oracle):
     c, = rec["contacts"]
     lever = r + phi / 2                     # the contact point sits mid-way through the overlap
     tr = 3 / m + 2 * lever ** 2 / I
-    np.testing.assert_allclose(c["feat"], [phi / 0.001, 1 - 3 / m / tr, 1.0, 1.0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(c["feat"], [phi / 0.001, 1 - 3 / m / tr, 1 / m / tr, 1.0], rtol=1e-12, atol=1e-15)
     assert c["trace_a"] + c["trace_b"] == pytest.approx(tr, rel=1e-12)
 
 
 def test_features_of_a_capsule_end_on_a_capsule(oracle):
-    """Two free bodies, no static side (x3 = 0), a slanted normal (x2 = n_z) and levers that
-    are not parallel to the normal: the trace is worked from the definition
-    J M^-1 J^T = I/m + [l]x I^-1 [l]x^T of a free body's translational point Jacobian."""
+    """Two free bodies, no static side (x3 = 0), a slanted normal and levers that are not
+    parallel to the normal: the trace (x1) and the normal row (x2) are worked from the
+    definition J M^-1 J^T = I/m + [l]x I^-1 [l]x^T of a free body's translational point
+    Jacobian, summed over the two bodies."""
     r, h = 0.02, 0.05
     ma, mb = 0.3, 0.7
     Ia, Ib = np.array([2e-4, 3e-4, 1e-4]), np.array([5e-4, 4e-4, 6e-4])
@@ -126,18 +128,37 @@ def test_features_of_a_capsule_end_on_a_capsule(oracle):
     p = np.array(c["pos"])
     n = np.array(c["normal"])
 
-    def trace(m, I, R, x):
+    def delassus(m, I, R, x):
         lx = p - x
         K = np.array([[0, -lx[2], lx[1]], [lx[2], 0, -lx[0]], [-lx[1], lx[0], 0]])
         Iinv = R @ np.diag(1 / I) @ R.T
-        return np.trace(np.eye(3) / m + K @ Iinv @ K.T)
+        return np.eye(3) / m + K @ Iinv @ K.T
 
-    tr = trace(ma, Ia, Ra, np.array([0, 0, 1.0])) + trace(mb, Ib, np.eye(3), xb + [0, 0, 1.0])
+    W = delassus(ma, Ia, Ra, np.array([0, 0, 1.0])) + delassus(mb, Ib, np.eye(3), xb + [0, 0, 1.0])
+    tr = np.trace(W)
     phi = c["phi"]
     assert phi == pytest.approx(-0.003, abs=1e-12)
-    x_exp = [max(-1.0, phi / 0.001), 1 - 3 * (1 / ma + 1 / mb) / tr, n[2], 0.0]
+    x_exp = [max(-1.0, phi / 0.001), 1 - 3 * (1 / ma + 1 / mb) / tr, n @ W @ n / tr, 0.0]
     np.testing.assert_allclose(c["feat"], x_exp, rtol=1e-12, atol=1e-14)
-    assert abs(n[2]) > 0.5 and 0.0 < x_exp[1] < 1.0
+    assert 0.0 < x_exp[1] < 1.0 and n @ W @ n > 1 / ma + 1 / mb
+
+
+def test_features_of_a_hinged_link(oracle):
+    """A link on a vertical hinge (anchor 0.3 m up, 1 kg, centre of mass 0.1 m out, I_zz =
+    2e-3) carrying a sphere that touches the floor below its centre of mass.  Its point
+    Jacobian is a x (p - anchor) = (0, 0.1, 0), so tr = 0.1^2 / (2e-3 + 1 * 0.1^2) = 5/6 and the
+    rotational share 1 - 3 (1/m) / tr = -2.6 clamps to -1.  Taken as a free body the link's lever
+    from its centre of mass is parallel to the normal: w_n = 1/m = 1, x2 = 1 / (5/6) = 1.2."""
+    r = 0.02
+    d = Wd.world([dict(parent=-1, jnt=S.HINGE, pos=(0, 0, 0.3), axis=(0, 0, 1), ipos=(0.1, 0, 0), mass=1.0,
+                       inertia=(1e-3, 1e-3, 2e-3))],
+                 [dict(type=S.PLANE, body=-1), dict(type=S.SPHERE, body=0, pos=(0.1, 0, -0.3 + r - 0.0002),
+                                                    size=(r, 0, 0))])
+    rec = oracle.step_record(d, Wd.params(n_t=4), DT, [0.0], [0.0])
+    c, = rec["contacts"]
+    tr = 0.01 / 0.012
+    assert c["trace_a"] + c["trace_b"] == pytest.approx(tr, rel=1e-12)
+    np.testing.assert_allclose(c["feat"], [-0.2, -1.0, 1.0 / tr, 1.0], rtol=1e-10, atol=1e-12)
 
 
 def test_network_layout_against_a_hand_evaluation(oracle):
