@@ -39,7 +39,7 @@ METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of
 # 4096 x 256 pile workload late in the episode, from one ncu capture of the kernel sources
 # whose digest is given; reported as null once the sources differ from the ones measured.
 STEP_SOURCES = ("cf_step.cu", "cf_device_math.cuh", "cf_internal.cuh")
-TRAFFIC = {"digest": "54c9313ddce03dd5", "bytes": 92.58e6}
+TRAFFIC = {"digest": "90d17e8fff253edc", "bytes": 92.21e6}
 
 
 def step_digest():
@@ -296,15 +296,33 @@ def run_extras(rank):
                          "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
     del g
     del b
-    # exact diagonal impedance (trace_mode 2) against the heuristic: one step of the jammed
+    # exact diagonal impedance (trace_mode 2) and the learned impedance (trace_mode 3, fitted
+    # here to exact-mode contacts of other piles) against the heuristic: one step of the jammed
     # 4096 x 256 pile from the same state (events around the step only)
     import dataclasses
+    from paper_2603_12185_gb300 import impedance as IMP
+    train = [IMP.advanced(S.make_pile(96, 64, seed=R.rank_seed(1960, rank)), 300),
+             S.make_pile(32, 256, seed=R.rank_seed(1961, rank), jammed=True)]
+    xs, ys = zip(*[IMP.exact_dataset(t)[:2] for t in train])
+    x, y = torch.cat(xs), torch.cat(ys)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net, losses = IMP.fit(x, y, iters=3000, lr=0.02)
+    fit_s = time.perf_counter() - t0
+    held = S.make_pile(8, 256, seed=R.rank_seed(1962, rank), jammed=True)
+    xh, yh, _ = IMP.exact_dataset(held)
+    r2, _, _ = IMP.r2(net, xh, yh, float(y.mean()))
+    errs = IMP.impulse_errors(held, {"learned": net, "constant": IMP.constant_net(y)})
     sbj = S.make_pile(4096, 256, seed=R.rank_seed(1950, rank), jammed=True)
-    res = {}
-    for mode in (0, 2):
+    res = {"learned_fit": {"train_contacts": int(len(y)), "adam_steps": 3000, "fit_s": fit_s,
+                           "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                           "held_out_r2": r2, "median_rel_impulse_err_vs_exact": errs}}
+    for mode in (0, 2, 3):
         sbj.params = dataclasses.replace(sbj.params, trace_mode=mode)
         _, bj = CF.from_scenes(sbj)
         bj.set_warps(0, 4)
+        if mode == 3:
+            bj.set_impedance_net(net.theta.view(1, -1), 1)
         q0, v0 = bj.get_state()
         q0, v0 = q0.clone(), v0.clone()
         ts = []
@@ -317,10 +335,10 @@ def run_extras(rank):
             torch.cuda.synchronize()
             if i:
                 ts.append(e0.elapsed_time(e1))
-        res["heuristic" if mode == 0 else "exact"] = {"ms_per_step": float(np.mean(ts)),
-                                                      "contacts_per_world": float(bj.contact_counts().mean())}
+        res[{0: "heuristic", 2: "exact", 3: "learned"}[mode]] = {
+            "ms_per_step": float(np.mean(ts)), "contacts_per_world": float(bj.contact_counts().mean())}
         del bj
-    out["exact_impedance_jammed_pile_4096x256"] = res
+    out["impedance_modes_jammed_pile_4096x256"] = res
     # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
     T = 100
     sb = S.make_hand(1024, seed=R.rank_seed(2100, rank))

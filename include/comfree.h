@@ -112,7 +112,11 @@ typedef struct {
                               point Jacobian; 1: 1/m_i per body; 2: the exact diagonal
                               impedance of Sec. III-B instead of M(phi): per facet j,
                               M_j = 1 / ((k_user dt + d_user) J~_j M~^-1 J~_j^T) (solimp
-                              unused; cf_step_grad answers CF_ERR_UNSUPPORTED)           */
+                              unused; cf_step_grad answers CF_ERR_UNSUPPORTED); 3: the
+                              learned impedance of Sec. III-B's learning-based K(q), D(q):
+                              mode 0's M(phi) times exp(clamp(g(x), -8, 8)), g the network
+                              of cf_batch_set_impedance_net (joint limits keep mode 0;
+                              cf_step_grad and cf_step_noalloc answer CF_ERR_UNSUPPORTED) */
 } cf_model_desc;
 
 /* Validate a description and build the host model.  Errors: CF_ERR_INVALID_ARGUMENT for a
@@ -181,11 +185,19 @@ cf_status cf_get_contact_counts(const cf_batch* batch, int32_t* counts, int32_t 
 
 /* One captured contact (contact_capture > 0): geoms (a, b) with a the geom the normal points
  * to, sub = contact index within the pair (capsule end / box corner), phi, point, normal,
- * the summed facet impulse (lambda dt) and M(phi). */
+ * the summed facet impulse (lambda dt) and M(phi) (trace_mode 3: the learned impedance;
+ * trace_mode 2: 0). */
 typedef struct {
-  int32_t geom_a, geom_b, sub, pad;
-  float phi, pos[3], normal[3], lam_sum, mphi, pad2[3];
+  int32_t geom_a, geom_b, sub, flags;  /* flags: CF_CONTACT_B_STATIC when geom_b has no body   */
+  float phi, pos[3], normal[3], lam_sum, mphi;
+  float rho;      /* trace_mode 2 and 3: the learned impedance's input x1 (below), else 0      */
+  float wn;       /* trace_mode 2 and 3: the learned impedance's input x2 (below), else 0      */
+  float target;   /* trace_mode 2: ln(M_exact / M(phi)), the learned impedance's regression
+                     target, M_exact the mean over the facets of the exact diagonal impedance
+                     1 / ((k_user dt + d_user) J~_j M~^-1 J~_j^T), M(phi) the mode-0 heuristic;
+                     else 0                                                                    */
 } cf_contact;
+#define CF_CONTACT_B_STATIC 1
 
 /* Copy the contacts captured in the last step: out[n_worlds][capacity], counts[n_worlds]
  * (host).  Order within a world is unspecified.  CF_ERR_CONTACT_OVERFLOW if a world had more
@@ -301,6 +313,48 @@ cf_status cf_mlp_status(cf_mlp* mlp, void* stream);
  * Device-side flags (non-finite state) are not reported by this entry point. */
 cf_status cf_step_noalloc(const cf_model* model, int32_t scene, int32_t n_worlds, float* q, float* v,
                           const float* world_params, float dt, int32_t nsteps, int32_t* contacts, void* stream);
+
+/* ---- learned impedance (trace_mode 3) -------------------------------------------------------
+ * Sec. III-B lets K(q) and D(q) be learned instead of set by the heuristic and fixes no model.
+ * Here K = k_user M_theta / dt and D = d_user M_theta / dt as in Eq. k_d_setting, with
+ * M_theta = M(phi) exp(clamp(g(x), -8, 8)) per contact and
+ *   g(x) = b2 + sum_h w2_h tanh(b1_h + sum_i W1_hi x_i),  h < 8,  i < 4,
+ *   theta = [W1 (8 x 4, row-major), b1[8], w2[8], b2]  (CF_IMPNET_PARAMS floats),
+ *   x = (clamp(phi / solimp width, -1, 1), clamp(1 - 3 (1/m_A + 1/m_B) / (tr_A + tr_B), -1, 1),
+ *        clamp(w_n / (tr_A + tr_B), 0, 4), 1 if side B is static else 0),
+ * tr the mode-0 point-Jacobian trace, 1/m of a static side 0, and w_n = sum over the dynamic
+ * sides of 1/m_b + (l_b x n)^T I_b^-1 (l_b x n), l_b the lever from body b's centre of mass and
+ * I_b its world inertia (the normal row of J M^-1 J^T with every body taken as free).  g = 0 is
+ * the heuristic. */
+#define CF_IMPNET_INPUTS 4
+#define CF_IMPNET_PARAMS 49
+
+/* Use the network theta (device, [n_sets][CF_IMPNET_PARAMS]; n_sets = 1: every world, n_sets =
+ * n_worlds: world w uses set w) in trace_mode 3 steps of this batch.  The batch keeps the
+ * pointer: theta must stay valid while steps (or graphs captured after this call) run; the
+ * values may change between steps.  theta = NULL detaches it.  CF_ERR_INVALID_ARGUMENT for
+ * another n_sets.  A trace_mode 3 step without a network answers CF_ERR_INVALID_ARGUMENT. */
+cf_status cf_batch_set_impedance_net(cf_batch* batch, const float* theta, int32_t n_sets);
+
+/* g(x) (unclamped) at x[n][CF_IMPNET_INPUTS] (device, 16-byte aligned) into g[n] (device). */
+cf_status cf_impnet_eval(const float* theta, const float* x, int32_t n, float* g, void* stream);
+
+/* Device floats of the fitting state: Adam's two moments and the reduction scratch.  Zero it
+ * before the first cf_impnet_fit of a run. */
+size_t cf_impnet_state_floats(void);
+
+/* Mean squared error L = (1/n) sum_i (g(x_i) - y_i)^2 and its gradient grad[CF_IMPNET_PARAMS]
+ * (device; either may be NULL) at x[n][4] (16-byte aligned), y[n], all device.  Uses state's
+ * scratch.  Deterministic: the sums run in a fixed order. */
+cf_status cf_impnet_loss_grad(const float* theta, const float* x, const float* y, int32_t n, float* state,
+                              float* grad, float* loss, void* stream);
+
+/* iters steps of full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected moments) on
+ * that loss, updating theta (device) in place; step0 = Adam steps already taken with this
+ * state.  losses[iters] (device, nullable) receives the loss before each step.  Enqueued on
+ * `stream`, no synchronisation. */
+cf_status cf_impnet_fit(float* theta, float* state, int32_t step0, const float* x, const float* y, int32_t n,
+                        int32_t iters, float lr, float* losses, void* stream);
 
 const char* cf_status_string(cf_status status);
 const char* cf_last_error(void);

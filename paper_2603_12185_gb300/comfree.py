@@ -46,9 +46,16 @@ class BatchOpts(C.Structure):
 
 
 class Contact(C.Structure):
-    _fields_ = [("geom_a", C.c_int32), ("geom_b", C.c_int32), ("sub", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("geom_a", C.c_int32), ("geom_b", C.c_int32), ("sub", C.c_int32), ("flags", C.c_int32),
                 ("phi", C.c_float), ("pos", C.c_float * 3), ("normal", C.c_float * 3), ("lam_sum", C.c_float),
-                ("mphi", C.c_float), ("pad2", C.c_float * 3)]
+                ("mphi", C.c_float), ("rho", C.c_float), ("wn", C.c_float), ("target", C.c_float)]
+
+
+CONTACT_DTYPE = np.dtype([("geom_a", np.int32), ("geom_b", np.int32), ("sub", np.int32), ("flags", np.int32),
+                          ("phi", np.float32), ("pos", np.float32, 3), ("normal", np.float32, 3),
+                          ("lam_sum", np.float32), ("mphi", np.float32), ("rho", np.float32),
+                          ("wn", np.float32), ("target", np.float32)])
+CONTACT_B_STATIC = 1
 
 
 class CostDesc(C.Structure):
@@ -63,7 +70,9 @@ EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_wo
            "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error", "cf_mlp_workspace_bytes",
            "cf_mlp_create", "cf_mlp_destroy", "cf_mlp_param_count", "cf_mlp_forward", "cf_mlp_gradients",
            "cf_mlp_train_step", "cf_mlp_get_params", "cf_mlp_status", "cf_set_cost", "cf_mppi_sample",
-           "cf_mppi_update", "cf_mppi_shift", "cf_broadcast_state", "cf_mppi_features")
+           "cf_mppi_update", "cf_mppi_shift", "cf_broadcast_state", "cf_mppi_features",
+           "cf_batch_set_impedance_net", "cf_impnet_eval", "cf_impnet_state_floats", "cf_impnet_loss_grad",
+           "cf_impnet_fit")
 
 _lib = None
 
@@ -113,6 +122,12 @@ def lib():
     L.cf_mppi_shift.argtypes = [I32, I32, V, V]
     L.cf_broadcast_state.argtypes = [V, V, I32, I32, I32, V, V, V]
     L.cf_mppi_features.argtypes = [V, I32, V, I32, C.c_float, V, I32, C.c_float, V, V]
+    L.cf_batch_set_impedance_net.argtypes = [V, V, I32]
+    L.cf_impnet_eval.argtypes = [V, V, I32, V, V]
+    L.cf_impnet_state_floats.argtypes = []
+    L.cf_impnet_state_floats.restype = C.c_size_t
+    L.cf_impnet_loss_grad.argtypes = [V, V, V, I32, V, V, V, V]
+    L.cf_impnet_fit.argtypes = [V, V, I32, V, V, I32, I32, C.c_float, V, V]
     L.cf_status_string.argtypes = [I32]
     L.cf_status_string.restype = C.c_char_p
     L.cf_last_error.argtypes = []
@@ -282,6 +297,29 @@ class Batch:
         check(lib().cf_get_contact_counts(self.h, _ptr(out), 1, _stream(stream)))
         return out
 
+    def set_impedance_net(self, theta, n_sets=1):
+        """Learned impedance of trace_mode 3 (cf_batch_set_impedance_net): theta is a device
+        tensor [n_sets, 49] (n_sets 1 or the number of worlds), kept referenced here; None
+        detaches it."""
+        if theta is None:
+            self._impnet = None
+            check(lib().cf_batch_set_impedance_net(self.h, None, 0))
+            return
+        assert theta.is_cuda and theta.dtype == torch.float32 and theta.is_contiguous()
+        assert theta.numel() == n_sets * IMPNET_PARAMS
+        self._impnet = theta
+        check(lib().cf_batch_set_impedance_net(self.h, _ptr(theta), int(n_sets)))
+
+    def contacts_array(self, stream=None):
+        """The captured contacts as one numpy record array (CONTACT_DTYPE) and the per-world
+        counts (needs contact_capture > 0)."""
+        cap = self.opts.contact_capture
+        buf = np.zeros(self.W * cap, CONTACT_DTYPE)
+        counts = np.zeros(self.W, np.int32)
+        check(lib().cf_get_contacts(self.h, buf.ctypes.data_as(C.c_void_p), _ptr(counts), _stream(stream)))
+        keep = (np.arange(cap)[None, :] < np.minimum(counts, cap)[:, None]).reshape(-1)
+        return buf[keep], counts
+
     def contacts(self, stream=None):
         """List (per world) of captured contacts as dicts (needs contact_capture > 0)."""
         cap = self.opts.contact_capture
@@ -294,7 +332,8 @@ class Batch:
             for i in range(counts[w]):
                 c = buf[w * cap + i]
                 lst.append(dict(geom_a=c.geom_a, geom_b=c.geom_b, sub=c.sub, phi=c.phi, pos=np.array(c.pos[:]),
-                                normal=np.array(c.normal[:]), lam_sum=c.lam_sum, mphi=c.mphi))
+                                normal=np.array(c.normal[:]), lam_sum=c.lam_sum, mphi=c.mphi, rho=c.rho,
+                                wn=c.wn, target=c.target, b_static=bool(c.flags & CONTACT_B_STATIC)))
             out.append(lst)
         return out
 
@@ -400,6 +439,74 @@ def mlp_init(fin, hidden, fout, seed=0, out_scale=0.1):
         else:
             parts.append(np.zeros(shape))
     return np.concatenate(parts).astype(np.float32)
+
+
+IMPNET_PARAMS = 49
+IMPNET_INPUTS = 4
+
+
+def impnet_init(seed=0, scale=0.5):
+    """Initial learned-impedance parameters: first-layer weights ~ N(0, scale^2) (seeded),
+    biases and output layer 0, so g = 0 (the heuristic) until it is fitted."""
+    th = np.zeros(IMPNET_PARAMS, np.float32)
+    th[:32] = np.random.default_rng(seed).normal(scale=scale, size=32)
+    return th
+
+
+def impedance_features(rec, solimp_width):
+    """Inputs x[n, 4] of the learned impedance from captured contact records (CONTACT_DTYPE),
+    the same features the step kernel forms: clamp(phi / width, -1, 1), the trace's rotational
+    share rho, the free-body normal row over the trace wn, side B static."""
+    x = np.empty((len(rec), IMPNET_INPUTS), np.float32)
+    x[:, 0] = np.clip(rec["phi"] / np.float32(solimp_width), -1.0, 1.0)
+    x[:, 1] = rec["rho"]
+    x[:, 2] = rec["wn"]
+    x[:, 3] = (rec["flags"] & CONTACT_B_STATIC) != 0
+    return x
+
+
+class ImpedanceNet:
+    """Parameters of the learned impedance (trace_mode 3) on the device, with its Adam state
+    (cf_impnet_*)."""
+
+    def __init__(self, theta=None, seed=0, device="cuda"):
+        th = impnet_init(seed) if theta is None else np.asarray(theta, np.float32).reshape(IMPNET_PARAMS)
+        self.theta = torch.from_numpy(np.ascontiguousarray(th)).to(device)
+        self.state = torch.zeros(int(lib().cf_impnet_state_floats()), dtype=torch.float32, device=device)
+        self.steps = 0
+        self.device = device
+
+    @staticmethod
+    def _x(x):
+        x = x.contiguous().float()
+        assert x.dim() == 2 and x.shape[1] == IMPNET_INPUTS and x.data_ptr() % 16 == 0
+        return x
+
+    def eval(self, x, stream=None):
+        """g(x) (unclamped) at device inputs x[n, 4]."""
+        x = self._x(x)
+        g = torch.empty(x.shape[0], dtype=torch.float32, device=self.device)
+        check(lib().cf_impnet_eval(_ptr(self.theta), _ptr(x), x.shape[0], _ptr(g), _stream(stream)))
+        return g
+
+    def loss_grad(self, x, y, stream=None):
+        x = self._x(x)
+        y = y.contiguous().float()
+        g = torch.empty(IMPNET_PARAMS, dtype=torch.float32, device=self.device)
+        L = torch.empty(1, dtype=torch.float32, device=self.device)
+        check(lib().cf_impnet_loss_grad(_ptr(self.theta), _ptr(x), _ptr(y), x.shape[0], _ptr(self.state), _ptr(g),
+                                        _ptr(L), _stream(stream)))
+        return L, g
+
+    def fit(self, x, y, iters, lr=0.02, stream=None):
+        """iters full-batch Adam steps on the mean squared error; returns the losses (device)."""
+        x = self._x(x)
+        y = y.contiguous().float()
+        losses = torch.empty(max(iters, 1), dtype=torch.float32, device=self.device)
+        check(lib().cf_impnet_fit(_ptr(self.theta), _ptr(self.state), self.steps, _ptr(x), _ptr(y), x.shape[0],
+                                  int(iters), float(lr), _ptr(losses), _stream(stream)))
+        self.steps += iters
+        return losses[:iters]
 
 
 class Mlp:

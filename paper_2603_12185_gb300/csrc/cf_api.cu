@@ -258,7 +258,8 @@ extern "C" cf_status cf_model_create(const cf_model_desc* desc, cf_model** out) 
   const double* si = desc->solimp;
   if (!(si[0] > 0.0 && si[0] <= si[1] && si[1] < 1.0 && si[2] > 0.0 && si[3] > 0.0 && si[3] < 1.0 && si[4] >= 1.0))
     return fail(CF_ERR_INVALID_ARGUMENT, "solimp must satisfy 0 < r_min <= r_max < 1, width > 0, 0 < mid < 1, power >= 1");
-  if (desc->trace_mode < 0 || desc->trace_mode > 2) return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode must be 0, 1 or 2");
+  if (desc->trace_mode < 0 || desc->trace_mode > 3)
+    return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode must be 0, 1, 2 or 3");
   cf_model* m = new (std::nothrow) cf_model();
   if (!m) return fail(CF_ERR_OUT_OF_MEMORY, "model allocation");
   for (int s = 0; s < desc->nscene; ++s) {
@@ -312,7 +313,9 @@ struct cf_batch {
   int nunits = 0;
   size_t smem_all = 0;
   bool artic_all = false;
-  bool ext = false;  // needs the extended kernel: exact impedance or possible box-box contacts
+  bool ext = false;  // needs the extended kernel: exact or learned impedance, or possible box-box contacts
+  const float* impnet = nullptr;  // learned impedance network (trace_mode 3)
+  int impnet_stride = 0;
   int variant = 0;             // pile kernel occupancy variant (autotuned)
   // fused MPC cost (cf_set_cost)
   float* cost = nullptr;
@@ -519,8 +522,8 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
       }
     }
   }
-  // the extended kernel serves the exact impedance and worlds where two boxes may touch
-  b->ext = m->trace_mode == 2;
+  // the extended kernel serves the exact and learned impedances and worlds where two boxes may touch
+  b->ext = m->trace_mode >= 2;
   for (int w = 0; w < n_worlds && !b->ext; ++w) {
     const DWorld& d = b->worlds[w];
     const DScene& sc = m->scenes[d.scene];
@@ -678,6 +681,8 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
   p.n_tor = m.n_tor;
   p.n_rol = m.n_rol;
   p.trace_mode = m.trace_mode;
+  p.impnet = b->impnet;
+  p.impnet_stride = b->impnet_stride;
   for (int j = 0; j < m.n_t; ++j) {
     double th = 2.0 * M_PI * j / m.n_t;
     p.tcos[j] = (float)std::cos(th);
@@ -698,6 +703,8 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
 
 static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t smem, cudaStream_t s) {
   if (p.nunits <= 0) return CF_OK;
+  if (p.trace_mode == 3 && !p.impnet)
+    return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode 3 needs an impedance network (cf_batch_set_impedance_net)");
   const int var = b->ext ? kExtVariant : b->variant;
   int per_sm = step_max_blocks_per_sm(artic, var, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
@@ -905,11 +912,26 @@ extern "C" cf_status cf_set_cost(cf_batch* b, const cf_cost_desc* desc, const fl
   return CF_OK;
 }
 
+extern "C" cf_status cf_batch_set_impedance_net(cf_batch* b, const float* theta, int32_t n_sets) {
+  if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
+  if (!theta) {
+    b->impnet = nullptr;
+    b->impnet_stride = 0;
+    return CF_OK;
+  }
+  if (n_sets != 1 && n_sets != b->W)
+    return fail(CF_ERR_INVALID_ARGUMENT, "n_sets must be 1 or the number of worlds (%d), got %d", b->W, n_sets);
+  if (reinterpret_cast<uintptr_t>(theta) & 3u) return fail(CF_ERR_INVALID_ARGUMENT, "theta not 4-byte aligned");
+  b->impnet = theta;
+  b->impnet_stride = n_sets == 1 ? 0 : kImpParams;
+  return CF_OK;
+}
+
 extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                                   float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream) {
   if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
   if (b->opts.grad_steps <= 0) return fail(CF_ERR_UNSUPPORTED, "batch created without an adjoint tape (grad_steps = 0)");
-  if (b->model.trace_mode == 2) return fail(CF_ERR_UNSUPPORTED, "the adjoint covers the heuristic impedance only");
+  if (b->model.trace_mode >= 2) return fail(CF_ERR_UNSUPPORTED, "the adjoint covers the heuristic impedance only");
   if (T < 1 || T > b->opts.grad_steps || T > b->opts.max_ctrl_steps)
     return fail(CF_ERR_INVALID_ARGUMENT, "T = %d outside [1, min(grad_steps, max_ctrl_steps)]", T);
   if (!(dt > 0.f)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
@@ -988,6 +1010,7 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
   if (nsteps < 1) return fail(CF_ERR_INVALID_ARGUMENT, "nsteps must be >= 1");
   const DScene& sc = m->scenes[scene];
   if (!sc.pile && world_params) return fail(CF_ERR_INVALID_ARGUMENT, "per-world parameters need a pile scene");
+  if (m->trace_mode == 3) return fail(CF_ERR_UNSUPPORTED, "cf_step_noalloc has no impedance network (trace_mode 3)");
 
   // layout of the static scratch for this call
   size_t off = 0;

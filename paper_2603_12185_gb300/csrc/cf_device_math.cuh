@@ -518,6 +518,62 @@ __device__ __forceinline__ void facet_impulses_exact(const StepParams& P, float 
   w[0] = N; w[1] = -mu_t * F1; w[2] = -mu_t * F2; w[3] = -mu_tor * T; w[4] = -mu_rol * R1; w[5] = -mu_rol * R2;
 }
 
+// Mean over the facets of the exact diagonal impedance M_j = 1 / ((k dt + d) w_j) of Sec. III-B
+// (the learned impedance's regression target), from the contact's Gram blocks.
+__device__ __forceinline__ float facet_mean_exact_impedance(const StepParams& P, float mu_t, float mu_tor,
+                                                            float mu_rol, const Gram& g) {
+  const float kd = fmaf(P.k_user, P.dt, P.d_user);
+  float sum = 0.f;
+  for (int j = 0; j < P.n_t; ++j)
+    sum += 1.f / (kd * gram_facet(g.nn, g.n1, g.n2, g.t11, g.t12, g.t22, mu_t, P.tcos[j], P.tsin[j]));
+  for (int j = 0; j < P.n_tor; ++j) {
+    const float sg = (j & 1) ? -1.f : 1.f;
+    sum += 1.f / (kd * (g.nn - 2.f * mu_tor * sg * g.n3 + mu_tor * mu_tor * g.r33));
+  }
+  for (int j = 0; j < P.n_rol; ++j)
+    sum += 1.f / (kd * gram_facet(g.nn, g.n4, g.n5, g.r44, g.r45, g.r55, mu_rol, P.rcos[j], P.rsin[j]));
+  const int nf = P.n_t + P.n_tor + P.n_rol;
+  return nf ? sum / (float)nf : 0.f;
+}
+
+// Learned impedance (Sec. III-B allows K(q), D(q) to be learned): the contact's configuration
+// features x = (clamp(phi / solimp width, -1, 1), clamp(1 - 3 (1/m_A + 1/m_B) / (tr_A + tr_B),
+// -1, 1), clamp(w_n / (tr_A + tr_B), 0, 4), side B static), tr the mode-0 trace and w_n the
+// normal row n^T J M^-1 J^T n with every body taken as a free body.
+struct ImpFeat {
+  float x[kImpIn];
+};
+__device__ __forceinline__ ImpFeat impnet_features(const StepParams& P, float phi, float tr, float im_sum, float w_n,
+                                                   bool b_static) {
+  ImpFeat f;
+  f.x[0] = fminf(fmaxf(phi / P.solimp[2], -1.f), 1.f);
+  f.x[1] = fminf(fmaxf(1.f - 3.f * im_sum / tr, -1.f), 1.f);
+  f.x[2] = fminf(fmaxf(w_n / tr, 0.f), 4.f);
+  f.x[3] = b_static ? 1.f : 0.f;
+  return f;
+}
+
+// 1/m + (l x n)^T I^-1 (l x n) of a free body with orientation R, inverse principal inertia ii
+// and lever l from its centre of mass
+__device__ __forceinline__ float free_normal_inverse_mass(float im, f3 ii, const M33& R, f3 l, f3 n) {
+  const f3 u = mulT(R, cross(l, n));
+  return im + u.x * u.x * ii.x + u.y * u.y * ii.y + u.z * u.z * ii.z;
+}
+
+// The factor exp(clamp(g(x), -8, 8)) that scales M(phi), g(x) = b2 + sum_h w2_h
+// tanh(b1_h + sum_i W1_hi x_i), parameters [W1 (8 x 4, row-major), b1, w2, b2].
+__device__ __forceinline__ float impnet_scale(const float* __restrict__ th, const ImpFeat& f) {
+  float g = __ldg(th + kImpParams - 1);
+#pragma unroll
+  for (int h = 0; h < kImpHidden; ++h) {
+    float a = __ldg(th + kImpHidden * kImpIn + h);
+#pragma unroll
+    for (int i = 0; i < kImpIn; ++i) a = fmaf(__ldg(th + h * kImpIn + i), f.x[i], a);
+    g = fmaf(__ldg(th + kImpHidden * kImpIn + kImpHidden + h), tanhf(a), g);
+  }
+  return expf(fminf(fmaxf(g, -kImpClamp), kImpClamp));
+}
+
 // Closed-form facet impulses of one contact (Eqs. tilde_defs, cf_wrench with
 // K = k M(phi)/dt, D = d M(phi)/dt, impulse lambda dt = (-kM (s dt + phi) - dM s)_+).
 // In: the contact-space velocities of the smooth prediction (normal, tangential pair,

@@ -21,6 +21,11 @@ constexpr float kFix2Lo = 1048576.0f;                  // 2^20 (fraction bits of
 constexpr float kFix2HiInv = 1.52587890625e-05f;       // 2^-16
 constexpr float kFix2LoInv = 1.4551915228366852e-11f;  // 2^-36
 constexpr float kFix2Range = 4096.0f;                  // |dv| per contribution; larger raises CF_FLAG_RANGE
+// learned impedance network (trace_mode 3): inputs, tanh hidden units, parameters, output clamp
+constexpr int kImpIn = 4;
+constexpr int kImpHidden = 8;
+constexpr int kImpParams = kImpHidden * kImpIn + 2 * kImpHidden + 1;
+constexpr float kImpClamp = 8.0f;
 
 // ---------------------------------------------------------------------------------------
 // scene templates (uploaded once per batch into the workspace)
@@ -93,6 +98,8 @@ struct StepParams {
   float solimp[5];
   float margin;
   int n_t, n_tor, n_rol, trace_mode;
+  const float* impnet;       // trace_mode 3: [sets][kImpParams] network parameters
+  int impnet_stride;         // floats between worlds' parameter sets (0: one shared set)
   float tcos[kMaxFacetDirs], tsin[kMaxFacetDirs];
   float rcos[kMaxFacetDirs], rsin[kMaxFacetDirs];
   // fused MPC cost of articulated worlds (cost == nullptr: off)

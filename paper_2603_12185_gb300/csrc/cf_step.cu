@@ -42,16 +42,17 @@ __device__ __forceinline__ PlaneDev load_plane(const DGeom& g) {
 }
 
 __device__ __forceinline__ void capture_contact(const StepParams& P, int world, int* s_count, int ga, int gb, int sub,
-                                                float phi, f3 p, f3 n, float lam, float mphi) {
+                                                float phi, f3 p, f3 n, float lam, float mphi, float rho,
+                                                float wn, float target, bool b_static) {
   int slot = atomicAdd(s_count + 1, 1);
   if (slot < P.capture_cap) {
     cf_contact c;
-    c.geom_a = ga; c.geom_b = gb; c.sub = sub; c.pad = 0;
+    c.geom_a = ga; c.geom_b = gb; c.sub = sub; c.flags = b_static ? CF_CONTACT_B_STATIC : 0;
     c.phi = phi;
     c.pos[0] = p.x; c.pos[1] = p.y; c.pos[2] = p.z;
     c.normal[0] = n.x; c.normal[1] = n.y; c.normal[2] = n.z;
     c.lam_sum = lam; c.mphi = mphi;
-    c.pad2[0] = c.pad2[1] = c.pad2[2] = 0.f;
+    c.rho = rho; c.wn = wn; c.target = target;
     P.capture[(size_t)world * P.capture_cap + slot] = c;
   }
 }
@@ -127,7 +128,7 @@ __device__ __forceinline__ float pile_s2(const PileView& s, int i) { return s.re
 // translational trace tr(J_i M^-1 J_i^T) of a free body at lever r (world) or 1/m;
 // im = 1/m, ii = inverse principal inertia
 __device__ __forceinline__ float pile_trace(const StepParams& P, float im, f3 ii, const M33& R, f3 r) {
-  if (P.trace_mode) return im;
+  if (P.trace_mode == 1) return im;
   f3 l = mulT(R, r);
   return 3.f * im + dot(r, r) * (ii.x + ii.y + ii.z) - (l.x * l.x * ii.x + l.y * l.y * ii.y + l.z * l.z * ii.z);
 }
@@ -205,8 +206,14 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   // pair friction: the larger of the two geoms' coefficients
   const float* ma = s.geoms[a].mu;
   const float mu_t = fmaxf(ma[0], mub0), mu_tor = fmaxf(ma[1], mub1), mu_rol = fmaxf(ma[2], mub2);
-  float mphi = 0.f;
+  float mphi = 0.f, target = 0.f;
   float w[6];
+  ImpFeat feat;
+  if (kExt && P.trace_mode >= 2) {
+    float w_n = free_normal_inverse_mass(ima, iia, Ra, ra, k.n);
+    if (b >= 0) w_n += free_normal_inverse_mass(imb, iib, Rb, rb, k.n);
+    feat = impnet_features(P, k.phi, tr, ima + imb, w_n, b < 0);
+  }
   if (kExt && P.trace_mode == 2) {
     Gram g;
     gram_zero(g);
@@ -214,9 +221,14 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
     if (b >= 0) gram_add_free(g, imb, iib, Rb, rb, k.n, t1, t2);
     facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                          mu_t, mu_tor, mu_rol, g, w);
+    if (P.capture_cap > 0) {  // the learned impedance's target: ln(mean exact impedance / M(phi))
+      const float r = solimp_r(P, fabsf(k.phi));
+      target = logf(facet_mean_exact_impedance(P, mu_t, mu_tor, mu_rol, g) * (1.f - r) * tr / r);
+    }
   } else {
     float r = solimp_r(P, fabsf(k.phi));
     mphi = __fdividef(r, (1.f - r) * tr);
+    if (kExt && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
     facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                    P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
   }
@@ -225,7 +237,10 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   pile_apply(s, a, ima, iia, Ra, ra, f, m, 1.f, range);
   if (b >= 0) pile_apply(s, b, imb, iib, Rb, rb, f, m, -1.f, range);
   atomicAdd(s.count, 1);
-  if (P.capture_cap > 0) capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi);
+  if (P.capture_cap > 0)
+    capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi,
+                    kExt && P.trace_mode >= 2 ? feat.x[1] : 0.f, kExt && P.trace_mode >= 2 ? feat.x[2] : 0.f,
+                    target, b < 0);
 }
 
 // narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none.
@@ -860,7 +875,7 @@ __device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DSce
 __device__ float artic_trace(const StepParams& P, const ArticView& s, const DScene& sc, int b, f3 p) {
   const DBody* B = P.bodies + sc.body0;
   const DBody& bd = B[b];
-  if (P.trace_mode) return 1.f / bd.mass;
+  if (P.trace_mode == 1) return 1.f / bd.mass;
   const DTree& tr = P.trees[sc.tree0 + bd.tree];
   if (tr.free) {
     M33 R = ld33(s.bR + 9 * b);
@@ -978,19 +993,38 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
     wc = wc - omb;
     tr += artic_trace(P, s, sc, bb, k.p);
   }
-  float mphi = 0.f;
+  float mphi = 0.f, target = 0.f;
   float w[6];
+  const float mu_t = fmaxf(GA.mu[0], GB.mu[0]), mu_tor = fmaxf(GA.mu[1], GB.mu[1]), mu_rol = fmaxf(GA.mu[2], GB.mu[2]);
+  ImpFeat feat;
+  if (kExt && P.trace_mode >= 2) {
+    const DBody* B = P.bodies + sc.body0;
+    auto side = [&](int b) {  // the link taken as a free body about its centre of mass
+      const DBody& bd = B[b];
+      const M33 R = ld33(s.bR + 9 * b);
+      const f3 com = ld3(s.bx + 3 * b) + mul(R, mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]));
+      return free_normal_inverse_mass(1.f / bd.mass, mk3(1.f / bd.inertia[0], 1.f / bd.inertia[1], 1.f / bd.inertia[2]),
+                                      R, k.p - com, k.n);
+    };
+    const float im_sum = 1.f / B[ba].mass + (bb >= 0 ? 1.f / B[bb].mass : 0.f);
+    const float w_n = side(ba) + (bb >= 0 ? side(bb) : 0.f);
+    feat = impnet_features(P, k.phi, tr, im_sum, w_n, bb < 0);
+  }
   if (kExt && P.trace_mode == 2) {
     Gram g;
     artic_gram(P, s, sc, ba, bb, k.p, k.n, t1, t2, g);
     facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
-                         fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]), fmaxf(GA.mu[2], GB.mu[2]), g, w);
+                         mu_t, mu_tor, mu_rol, g, w);
+    if (P.capture_cap > 0) {  // the learned impedance's target: ln(mean exact impedance / M(phi))
+      const float r = solimp_r(P, fabsf(k.phi));
+      target = logf(facet_mean_exact_impedance(P, mu_t, mu_tor, mu_rol, g) * (1.f - r) * tr / r);
+    }
   } else {
     float r = solimp_r(P, fabsf(k.phi));
     mphi = __fdividef(r, (1.f - r) * tr);
+    if (kExt && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
     facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
-                   P.k_user * mphi, P.d_user * mphi, fmaxf(GA.mu[0], GB.mu[0]), fmaxf(GA.mu[1], GB.mu[1]),
-                   fmaxf(GA.mu[2], GB.mu[2]), w);
+                   P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
   }
   f3 f = w[0] * k.n + w[1] * t1 + w[2] * t2;
   f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
@@ -998,7 +1032,9 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
   if (bb >= 0) artic_apply(P, s, sc, bb, k.p, -f, -m);
   atomicAdd(s.count, 1);
   if (P.capture_cap > 0)
-    capture_contact(P, world, s.count, sc.geom0 + ga, sc.geom0 + gb, sub, k.phi, k.p, k.n, w[0], mphi);
+    capture_contact(P, world, s.count, sc.geom0 + ga, sc.geom0 + gb, sub, k.phi, k.p, k.n, w[0], mphi,
+                    kExt && P.trace_mode >= 2 ? feat.x[1] : 0.f, kExt && P.trace_mode >= 2 ? feat.x[2] : 0.f,
+                    target, bb < 0);
 }
 
 // Joint limits and dry joint friction of one hinge tree (Sec. III-A's system model), closed

@@ -115,7 +115,8 @@ class Params:
     n_tor: int = 0
     n_rol: int = 0
     trace_mode: int = 0  # 0: translational point-Jacobian trace, 1: sum of 1/m of the bodies,
-    #                      2: exact diagonal impedance per facet (Sec. III-B)
+    #                      2: exact diagonal impedance per facet (Sec. III-B),
+    #                      3: mode 0 scaled by the learned impedance network (Sec. III-B)
 
 
 @dataclass

@@ -79,3 +79,27 @@ def test_workspace_size_grows_with_worlds(cf):
         sizes.append(n.value)
     assert sizes[0] < sizes[1] < sizes[2]
     assert sizes[2] > 100 * (16 * 13 * 4)
+
+
+def test_impedance_modes_and_network_sizes(cf):
+    """trace_mode 0..3 build a model (3: the learned impedance), 4 does not; the fitting state
+    holds at least Adam's two moments of the 49 parameters."""
+    from paper_2603_12185_gb300 import scenes as S
+    sb = S.make_pile(2, 16)
+    for mode in (0, 1, 2, 3):
+        cf.Model(sb.templates, S.Params(trace_mode=mode))
+    with pytest.raises(cf.CfError):
+        cf.Model(sb.templates, S.Params(trace_mode=4))
+    assert cf.lib().cf_impnet_state_floats() >= 2 * cf.IMPNET_PARAMS
+    assert cf.IMPNET_PARAMS == 8 * 4 + 8 + 8 + 1
+
+
+def test_impedance_features_from_records(cf):
+    """The host-side feature assembly of the training data matches the kernel's definition."""
+    rec = np.zeros(3, cf.CONTACT_DTYPE)
+    rec["phi"] = [-0.0005, 0.004, -0.01]
+    rec["rho"] = [0.625, 0.1, -0.3]
+    rec["wn"] = [0.125, 0.3, 1.2]
+    rec["flags"] = [cf.CONTACT_B_STATIC, 0, 0]
+    x = cf.impedance_features(rec, 0.001)
+    np.testing.assert_allclose(x, [[-0.5, 0.625, 0.125, 1], [1, 0.1, 0.3, 0], [-1, -0.3, 1.2, 0]], rtol=1e-6)
