@@ -39,7 +39,7 @@ METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of
 # 4096 x 256 pile workload late in the episode, from one ncu capture of the kernel sources
 # whose digest is given; reported as null once the sources differ from the ones measured.
 STEP_SOURCES = ("cf_step.cu", "cf_device_math.cuh", "cf_internal.cuh")
-TRAFFIC = {"digest": "90d17e8fff253edc", "bytes": 92.21e6}
+TRAFFIC = {"digest": "0b1c8021b8903d67", "bytes": 92.41e6}
 
 
 def step_digest():
@@ -61,13 +61,16 @@ def parse():
     ap.add_argument("--bodies", type=int, default=BODIES)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10, help="end-to-end steps (0: skip, for profiles)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--episode", type=int, default=EPISODE, help="episode length (the timed steps are its last)")
     ap.add_argument("--warps", type=int, default=0,
                     help="warps per world (0: autotune); a fixed shape makes profiles comparable")
     ap.add_argument("--jammed", action="store_true",
                     help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
+    ap.add_argument("--impedance", default="heuristic", choices=sorted(IMPEDANCE_MODES),
+                    help="impedance mode of the headline workload (the exact and learned forms of Sec. III-B; "
+                         "for profiles)")
     return ap.parse_args()
 
 
@@ -154,15 +157,50 @@ def barrier_sum(x, world):
     return R.reduce_scalar(x, "sum")
 
 
-def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, jammed=False, warps=0):
+IMPEDANCE_MODES = {"heuristic": 0, "exact": 2, "learned": 3}
+
+
+def learned_impedance(rank, evaluate=False):
+    """A learned impedance network (trace_mode 3) fitted to exact-mode contacts of 96 settled
+    pile64 worlds and 32 jammed pile256 worlds: (net, fit statistics); evaluate=True adds the
+    held-out R^2 and impulse errors on 8 other jammed pile256 worlds."""
+    import torch
+    from paper_2603_12185_gb300 import impedance as IMP
+    from paper_2603_12185_gb300 import scenes as S
+    train = [IMP.advanced(S.make_pile(96, 64, seed=R.rank_seed(1960, rank)), 300),
+             S.make_pile(32, 256, seed=R.rank_seed(1961, rank), jammed=True)]
+    xs, ys = zip(*[IMP.exact_dataset(t)[:2] for t in train])
+    x, y = torch.cat(xs), torch.cat(ys)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net, losses = IMP.fit(x, y, iters=3000, lr=0.02)
+    fit = {"train_contacts": int(len(y)), "adam_steps": 3000, "fit_s": time.perf_counter() - t0,
+           "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+    if evaluate:
+        held = S.make_pile(8, 256, seed=R.rank_seed(1962, rank), jammed=True)
+        xh, yh, _ = IMP.exact_dataset(held)
+        fit["held_out_r2"] = IMP.r2(net, xh, yh, float(y.mean()))[0]
+        fit["median_rel_impulse_err_vs_exact"] = IMP.impulse_errors(
+            held, {"learned": net, "constant": IMP.constant_net(y)})
+    return net, fit
+
+
+def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, jammed=False, warps=0,
+             impedance="heuristic"):
     """Simulate the episode; time the last `steps` steps with CUDA events on the launch stream,
     flushing L2 (256 MB write) between timed steps outside the timed intervals.  The autotuner
-    runs half way through the untimed part, on a state like the timed one (it restores it)."""
+    runs half way through the untimed part, on a state like the timed one (it restores it).
+    impedance: the impedance mode of the whole run (the learned one is fitted first)."""
+    import dataclasses
     import torch
     from paper_2603_12185_gb300 import comfree as CF
     from paper_2603_12185_gb300 import scenes as S
     sb = S.make_pile(nworld, nbody, seed=R.rank_seed(1000, rank), jammed=jammed)
+    sb.params = dataclasses.replace(sb.params, trace_mode=IMPEDANCE_MODES[impedance])
+    net = learned_impedance(rank)[0] if impedance == "learned" else None
     model, b = CF.from_scenes(sb)
+    if net is not None:
+        b.set_impedance_net(net.theta.view(1, -1), 1)
     stream = torch.cuda.current_stream()
     preroll = max(warmup, episode - steps)
     if warps > 0:
@@ -189,7 +227,8 @@ def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, ja
     if st != 0:
         raise RuntimeError(f"device status {st} after the episode")
     return dict(ms=float(np.sum(times)), per_launch_ms=float(np.mean(times)), steps=steps, preroll=preroll,
-                contacts=int(contact_sum.sum().item()), worlds=nworld, bodies=nbody, sb=sb, batch=b, model=model)
+                contacts=int(contact_sum.sum().item()), worlds=nworld, bodies=nbody, sb=sb, batch=b, model=model,
+                net=net)
 
 
 def run_e2e(res, steps, blocks=8):
@@ -227,6 +266,8 @@ def run_e2e(res, steps, blocks=8):
     qo = vo = 0
     for k in range(blocks):
         _, bk = CF.from_scenes(sb.subset(range(edges[k], edges[k + 1])))
+        if res["net"] is not None:
+            bk.set_impedance_net(res["net"].theta.view(1, -1), 1)
         bk.autotune(dt)
         batches.append(bk)
         bq.append(q[qo:qo + bk.total_nq].cpu().pin_memory())
@@ -300,23 +341,9 @@ def run_extras(rank):
     # here to exact-mode contacts of other piles) against the heuristic: one step of the jammed
     # 4096 x 256 pile from the same state (events around the step only)
     import dataclasses
-    from paper_2603_12185_gb300 import impedance as IMP
-    train = [IMP.advanced(S.make_pile(96, 64, seed=R.rank_seed(1960, rank)), 300),
-             S.make_pile(32, 256, seed=R.rank_seed(1961, rank), jammed=True)]
-    xs, ys = zip(*[IMP.exact_dataset(t)[:2] for t in train])
-    x, y = torch.cat(xs), torch.cat(ys)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    net, losses = IMP.fit(x, y, iters=3000, lr=0.02)
-    fit_s = time.perf_counter() - t0
-    held = S.make_pile(8, 256, seed=R.rank_seed(1962, rank), jammed=True)
-    xh, yh, _ = IMP.exact_dataset(held)
-    r2, _, _ = IMP.r2(net, xh, yh, float(y.mean()))
-    errs = IMP.impulse_errors(held, {"learned": net, "constant": IMP.constant_net(y)})
+    net, fit = learned_impedance(rank, evaluate=True)
     sbj = S.make_pile(4096, 256, seed=R.rank_seed(1950, rank), jammed=True)
-    res = {"learned_fit": {"train_contacts": int(len(y)), "adam_steps": 3000, "fit_s": fit_s,
-                           "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-                           "held_out_r2": r2, "median_rel_impulse_err_vs_exact": errs}}
+    res = {"learned_fit": fit}
     for mode in (0, 2, 3):
         sbj.params = dataclasses.replace(sbj.params, trace_mode=mode)
         _, bj = CF.from_scenes(sbj)
@@ -444,14 +471,15 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     res = run_pile(args.bodies, args.worlds, args.steps, args.warmup, rank, flush=flush, episode=args.episode,
-                   jammed=args.jammed, warps=args.warps)
+                   jammed=args.jammed, warps=args.warps, impedance=args.impedance)
     torch.cuda.synchronize()
     clk = clocks.stop()
     sec = barrier_max(res["ms"] / 1e3, world)
     total_contacts = barrier_sum(res["contacts"], world)
     value = world * res["worlds"] * res["steps"] / sec
-    e2e = run_e2e(res, args.e2e_steps)
-    e2e_v = barrier_sum(e2e["value"], world) if world > 1 else e2e["value"]
+    e2e = run_e2e(res, args.e2e_steps) if args.e2e_steps > 0 else None
+    if e2e is not None:
+        e2e_v = barrier_sum(e2e["value"], world) if world > 1 else e2e["value"]
 
     pk, src = peaks()
     launch_s = res["per_launch_ms"] / 1e3
@@ -459,13 +487,15 @@ def main():
     achieved = alg_bytes / launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": TRAFFIC["bytes"] if TRAFFIC["digest"] == step_digest() else None,
+                "traffic": (TRAFFIC["bytes"] if TRAFFIC["digest"] == step_digest() and args.impedance == "heuristic"
+                            else None),
                 "kernel_digest": step_digest(), "peak_source": src,
                 "kernel": "cf::step_kernel", "algorithmic_bytes_per_launch": alg_bytes}
     line = {"metric": METRIC, "value": value, "unit": "world-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / res["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"pile_{res['worlds']}x{res['bodies']}" + ("_jammed" if args.jammed else ""),
+            "config": {"workload": f"pile_{res['worlds']}x{res['bodies']}" + ("_jammed" if args.jammed else "") +
+                       ("" if args.impedance == "heuristic" else f"_{args.impedance}_impedance"),
                        "worlds_per_gpu": res["worlds"],
                        "bodies_per_world": res["bodies"], "facets_per_contact": 18, "dt": 0.002,
                        "episode_steps": args.episode, "timed_steps": f"last {res['steps']} of the episode",
@@ -475,9 +505,10 @@ def main():
             "contacts_per_world": res["contacts"] / (res["worlds"] * res["steps"]),
             "sweep_bodies": sweep,
             "roofline": roofline,
-            "e2e": {"value": e2e_v, "unit": "world-steps/s", "h2d_bytes_per_step": e2e["h2d"],
-                    "d2h_bytes_per_step": e2e["d2h"], "api": f"comfree.Pipeline, {e2e['blocks']} blocks",
-                    "serial_value": e2e["serial"]},
+            "e2e": None if e2e is None else {
+                "value": e2e_v, "unit": "world-steps/s", "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"], "api": f"comfree.Pipeline, {e2e['blocks']} blocks",
+                "serial_value": e2e["serial"]},
             "gpu_launches": res["steps"],
             "clocks": clk}
     if not args.no_extras:

@@ -313,7 +313,8 @@ struct cf_batch {
   int nunits = 0;
   size_t smem_all = 0;
   bool artic_all = false;
-  bool ext = false;  // needs the extended kernel: exact or learned impedance, or possible box-box contacts
+  bool ext = false;  // needs the extended kernel: possible box-box contacts, cylinders or ellipsoids
+  bool imp = false;  // exact or learned impedance (trace_mode 2, 3)
   const float* impnet = nullptr;  // learned impedance network (trace_mode 3)
   int impnet_stride = 0;
   int variant = 0;             // pile kernel occupancy variant (autotuned)
@@ -522,8 +523,10 @@ extern "C" cf_status cf_batch_create(const cf_model* m, int32_t n_worlds, const 
       }
     }
   }
-  // the extended kernel serves the exact and learned impedances and worlds where two boxes may touch
-  b->ext = m->trace_mode >= 2;
+  // the extended kernel serves worlds where two boxes may touch or that hold cylinders or
+  // ellipsoids; the impedance modes have a lighter pile-only kernel of their own
+  b->imp = m->trace_mode >= 2;
+  b->ext = false;
   for (int w = 0; w < n_worlds && !b->ext; ++w) {
     const DWorld& d = b->worlds[w];
     const DScene& sc = m->scenes[d.scene];
@@ -705,7 +708,7 @@ static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t sme
   if (p.nunits <= 0) return CF_OK;
   if (p.trace_mode == 3 && !p.impnet)
     return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode 3 needs an impedance network (cf_batch_set_impedance_net)");
-  const int var = b->ext ? kExtVariant : b->variant;
+  const int var = b->ext ? kExtVariant : (b->imp ? kImpVariant : b->variant);
   int per_sm = step_max_blocks_per_sm(artic, var, smem);
   int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
   cudaError_t e = launch_step(p, artic, var, grid, smem, s);
@@ -854,7 +857,7 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
   {
     cf_status st = upload_units(b, s);
     if (st != CF_OK) return st;
-    if (!b->artic_all && !b->ext) {
+    if (!b->artic_all && !b->ext && !b->imp) {
       float best = 3e38f;
       int best_v = 0, prev_blocks = 0;
       for (int var = 0; var < kPileVariants; ++var) {
@@ -1134,7 +1137,7 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
   }
   const bool artic = !sc.pile;
   // per-world override blocks live on the device here, so a pile with overrides may hold boxes
-  const int var = (m->trace_mode == 2 || sc.boxbox || (sc.pile && world_params)) ? kExtVariant : 0;
+  const int var = (sc.boxbox || (sc.pile && world_params)) ? kExtVariant : (m->trace_mode == 2 ? kImpVariant : 0);
   const size_t smem = world_smem_bytes(sc, warps) * per;
   if (smem > step_max_dynamic_smem()) return fail(CF_ERR_UNSUPPORTED, "a world needs %zu bytes of shared memory", smem);
   int nsm = 0;

@@ -118,9 +118,13 @@ size_t world_smem_bytes(const DScene& s, int warps);
 
 // artic = the launch contains worlds of non-pile scenes (selects the kernel instantiation);
 // variant 0..2 = pile-only kernel compiled for 2, 3 or 4 resident CTAs per SM
-constexpr int kStepVariants = 5;
+constexpr int kStepVariants = 6;
 constexpr int kPileVariants = 3;
-constexpr int kExtVariant = 99;  // the extended kernel: exact diagonal impedance, box-box contacts
+constexpr int kExtImp = 1;       // step-kernel feature: exact and learned impedances (trace_mode 2, 3)
+constexpr int kExtGeo = 2;       // step-kernel feature: box-box contacts, cylinders, ellipsoids
+constexpr int kExtVariant = 99;  // the extended kernel: articulated worlds and every feature
+constexpr int kImpVariant = 98;  // the impedance modes without the extra geometry (pile-only
+                                 // kernel unless the launch holds articulated worlds)
 cudaError_t launch_step(const StepParams& p, bool artic, int variant, int grid, size_t smem, cudaStream_t stream);
 int step_max_blocks_per_sm(bool artic, int variant, size_t smem);
 size_t step_max_dynamic_smem();

@@ -149,9 +149,9 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, 
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
-// (a plane contributes nothing).  kExt: the extended instantiation (exact diagonal
-// impedance, box-box contacts, cylinders and ellipsoids).
-template <bool kExt>
+// (a plane contributes nothing).  kExt: the step kernel's optional features (kExtImp: the
+// exact and learned impedances; kExtGeo: box-box contacts, cylinders and ellipsoids).
+template <int kExt>
 __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, const DScene& sc, int world,
                                            const float* cq, int slot, bool& range) {
   Raw k;
@@ -209,12 +209,13 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   float mphi = 0.f, target = 0.f;
   float w[6];
   ImpFeat feat;
-  if (kExt && P.trace_mode >= 2) {
+  const bool imp = (kExt & kExtImp) && P.trace_mode >= 2;  // exact or learned impedance
+  if (imp) {
     float w_n = free_normal_inverse_mass(ima, iia, Ra, ra, k.n);
     if (b >= 0) w_n += free_normal_inverse_mass(imb, iib, Rb, rb, k.n);
     feat = impnet_features(P, k.phi, tr, ima + imb, w_n, b < 0);
   }
-  if (kExt && P.trace_mode == 2) {
+  if ((kExt & kExtImp) && P.trace_mode == 2) {
     Gram g;
     gram_zero(g);
     gram_add_free(g, ima, iia, Ra, ra, k.n, t1, t2);
@@ -228,7 +229,7 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   } else {
     float r = solimp_r(P, fabsf(k.phi));
     mphi = __fdividef(r, (1.f - r) * tr);
-    if (kExt && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
+    if ((kExt & kExtImp) && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
     facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                    P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
   }
@@ -238,22 +239,21 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   if (b >= 0) pile_apply(s, b, imb, iib, Rb, rb, f, m, -1.f, range);
   atomicAdd(s.count, 1);
   if (P.capture_cap > 0)
-    capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi,
-                    kExt && P.trace_mode >= 2 ? feat.x[1] : 0.f, kExt && P.trace_mode >= 2 ? feat.x[2] : 0.f,
-                    target, b < 0);
+    capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi, imp ? feat.x[1] : 0.f,
+                    imp ? feat.x[2] : 0.f, target, b < 0);
 }
 
 // narrowphase of body a against body b (sub-contact 0 only); phi = +inf when there is none.
 // Spheres are handled as capsules of zero half length, so sphere-sphere and sphere-capsule
 // in either order share one branch.
-template <bool kExt>
+template <int kExt>
 __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b, f3 ca, int sub) {
   const int ta = pile_type(s, a), tb = pile_type(s, b);
   const float4 pb4 = s.pb[b];
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
-  if (kExt && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
+  if ((kExt & kExtGeo) && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
     if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER)
       k = nf_sphere_cylinder(ca, pile_rad(s, a), cb, pile_R(s, b), pile_rad(s, b), pile_hl(s, b), true);
     else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE)
@@ -274,7 +274,7 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
     const f3 pc = cc + t * u;
     k = nf_sphere_sphere(capA ? pc : ca, pile_rad(s, a), capA ? cb : pc, pile_rad(s, b));
   } else if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertex `sub`
-    if (kExt)
+    if (kExt & kExtGeo)
       k = nf_box_box(ca, pile_R(s, a), mk3(pile_rad(s, a), pile_hl(s, a), pile_s2(s, a)), cb, pile_R(s, b), mk3(pile_rad(s, b), pile_hl(s, b), pile_s2(s, b)),
                    sub);
   } else if ((ta == CF_GEOM_BOX) != (tb == CF_GEOM_BOX)) {
@@ -295,11 +295,11 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
 }
 
 // narrowphase of body a against a plane: sphere (sub 0), capsule end sphere sub, box corner sub
-template <bool kExt>
+template <int kExt>
 __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int sub, f3 ca, f3 o, f3 nz) {
   const int ta = pile_type(s, a);
-  if (kExt && ta == CF_GEOM_CYLINDER) return nf_cylinder_plane(ca, pile_R(s, a), pile_rad(s, a), pile_hl(s, a), o, nz, sub);
-  if (kExt && ta == CF_GEOM_ELLIPSOID)
+  if ((kExt & kExtGeo) && ta == CF_GEOM_CYLINDER) return nf_cylinder_plane(ca, pile_R(s, a), pile_rad(s, a), pile_hl(s, a), o, nz, sub);
+  if ((kExt & kExtGeo) && ta == CF_GEOM_ELLIPSOID)
     return nf_ellipsoid_plane(ca, pile_R(s, a), mk3(pile_rad(s, a), pile_hl(s, a), pile_s2(s, a)), o, nz);
   f3 c = ca;
   float r = pile_rad(s, a);
@@ -314,17 +314,17 @@ __device__ __forceinline__ Raw pile_narrow_plane(const PileView& s, int a, int s
 }
 
 // number of sub-contacts a candidate can produce (a plane: per end sphere or box corner)
-template <bool kExt>
+template <int kExt>
 __device__ __forceinline__ int pile_nsub(const PileView& s, int code) {
   if (code < 0) return 0;
   const int ta = pile_type(s, code >> 16);
-  if (!(code & kPlaneBit)) return kExt && ta == CF_GEOM_BOX && pile_type(s, code & kBodyMask) == CF_GEOM_BOX ? 8 : 1;
-  if (kExt && ta >= CF_GEOM_CYLINDER) return ta == CF_GEOM_CYLINDER ? 6 : 1;
+  if (!(code & kPlaneBit)) return (kExt & kExtGeo) && ta == CF_GEOM_BOX && pile_type(s, code & kBodyMask) == CF_GEOM_BOX ? 8 : 1;
+  if ((kExt & kExtGeo) && ta >= CF_GEOM_CYLINDER) return ta == CF_GEOM_CYLINDER ? 6 : 1;
   return ta == CF_GEOM_SPHERE ? 1 : (ta == CF_GEOM_CAPSULE ? 2 : 8);
 }
 
 // narrowphase of candidate `code` (-1: none), sub-contact `sub`; true when it is a contact
-template <bool kExt>
+template <int kExt>
 __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView& s, int code, int sub, Raw& k) {
   if (code < 0) return false;
   const int a = code >> 16, bc = code & 0xffff;
@@ -339,7 +339,7 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
   return k.phi < P.margin;
 }
 
-template <bool kExt>
+template <int kExt>
 __device__ void pile_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -975,7 +975,7 @@ __device__ __noinline__ void artic_gram(const StepParams& P, const ArticView& s,
   }
 }
 
-template <bool kExt>
+template <int kExt>
 __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world, int ga,
                                            int gb, int sub, const Raw& k, bool plane, f3 px) {
   const DGeom& GA = P.geoms[sc.geom0 + ga];
@@ -997,7 +997,8 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
   float w[6];
   const float mu_t = fmaxf(GA.mu[0], GB.mu[0]), mu_tor = fmaxf(GA.mu[1], GB.mu[1]), mu_rol = fmaxf(GA.mu[2], GB.mu[2]);
   ImpFeat feat;
-  if (kExt && P.trace_mode >= 2) {
+  const bool imp = (kExt & kExtImp) && P.trace_mode >= 2;  // exact or learned impedance
+  if (imp) {
     const DBody* B = P.bodies + sc.body0;
     auto side = [&](int b) {  // the link taken as a free body about its centre of mass
       const DBody& bd = B[b];
@@ -1010,7 +1011,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
     const float w_n = side(ba) + (bb >= 0 ? side(bb) : 0.f);
     feat = impnet_features(P, k.phi, tr, im_sum, w_n, bb < 0);
   }
-  if (kExt && P.trace_mode == 2) {
+  if ((kExt & kExtImp) && P.trace_mode == 2) {
     Gram g;
     artic_gram(P, s, sc, ba, bb, k.p, k.n, t1, t2, g);
     facet_impulses_exact(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
@@ -1022,7 +1023,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
   } else {
     float r = solimp_r(P, fabsf(k.phi));
     mphi = __fdividef(r, (1.f - r) * tr);
-    if (kExt && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
+    if ((kExt & kExtImp) && P.trace_mode == 3) mphi *= impnet_scale(P.impnet + (size_t)world * P.impnet_stride, feat);
     facet_impulses(P, dot(k.n, vc), dot(t1, vc), dot(t2, vc), dot(k.n, wc), dot(t1, wc), dot(t2, wc), k.phi,
                    P.k_user * mphi, P.d_user * mphi, mu_t, mu_tor, mu_rol, w);
   }
@@ -1033,8 +1034,7 @@ __device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, co
   atomicAdd(s.count, 1);
   if (P.capture_cap > 0)
     capture_contact(P, world, s.count, sc.geom0 + ga, sc.geom0 + gb, sub, k.phi, k.p, k.n, w[0], mphi,
-                    kExt && P.trace_mode >= 2 ? feat.x[1] : 0.f, kExt && P.trace_mode >= 2 ? feat.x[2] : 0.f,
-                    target, bb < 0);
+                    imp ? feat.x[1] : 0.f, imp ? feat.x[2] : 0.f, target, bb < 0);
 }
 
 // Joint limits and dry joint friction of one hinge tree (Sec. III-A's system model), closed
@@ -1080,7 +1080,7 @@ __device__ void artic_joint_constraints(const StepParams& P, ArticView& s, const
 }
 
 // narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
-template <bool kExt>
+template <int kExt>
 __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
   int ga = code >> 16, gb = code & 0xffff;
   const DGeom* G = P.geoms + sc.geom0;
@@ -1101,12 +1101,12 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
         Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
         if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, e, k, true, px);
       }
-    } else if (kExt && ta == CF_GEOM_CYLINDER) {
+    } else if ((kExt & kExtGeo) && ta == CF_GEOM_CYLINDER) {
       for (int sub = 0; sub < 6; ++sub) {
         Raw k = nf_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
         if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, k, true, px);
       }
-    } else if (kExt && ta == CF_GEOM_ELLIPSOID) {
+    } else if ((kExt & kExtGeo) && ta == CF_GEOM_ELLIPSOID) {
       Raw k = nf_ellipsoid_plane(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, nz);
       if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, true, px);
     } else if (ta == CF_GEOM_BOX) {
@@ -1120,7 +1120,7 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
   }
   Raw k;
   k.phi = 3.0e38f;
-  if (kExt && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
+  if ((kExt & kExtGeo) && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
     if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER) k = nf_sphere_cylinder(ca, sa[0], cb, Rb, sb[0], sb[1], true);
     else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE) k = nf_sphere_cylinder(cb, sb[0], ca, Ra, sa[0], sa[1], false);
   } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
@@ -1141,7 +1141,7 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     k = nf_sphere_sphere(ca, sa[0], cb + t * u, sb[0]);
   } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
     if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertices, subs 0..7
-      for (int sub = 0; kExt && sub < 8; ++sub) {
+      for (int sub = 0; (kExt & kExtGeo) && sub < 8; ++sub) {
         const Raw kb = nf_box_box(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, Rb, mk3(sb[0], sb[1], sb[2]), sub);
         if (kb.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, kb, false, mk3(0.f, 0.f, 0.f));
       }
@@ -1203,7 +1203,7 @@ __device__ float artic_running_cost(const StepParams& P, const ArticView& s, con
   return c;
 }
 
-template <bool kExt>
+template <int kExt>
 __device__ void artic_world(const StepParams& P, float* smem, int world, int gid, int gwarps) {
   const DWorld W = P.worlds[world];
   const DScene sc = P.scenes[W.scene];
@@ -1362,10 +1362,10 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 // persistent kernel: CTAs pull work units (sorted by decreasing cost); a unit holds
 // kWarps / warps worlds, one per group of `warps` warps
 // =======================================================================================
-// kArtic: articulated worlds compiled in; kExt: the extended instantiation, with the exact
-// diagonal impedance (trace_mode 2), box-box contacts, cylinders and ellipsoids compiled in, so
-// that the other instantiations keep their register budget.
-template <bool kArtic, int kMinBlocks, bool kExt>
+// kArtic: articulated worlds compiled in; kExt: the optional features compiled in, a mask of
+// kExtImp (the exact and learned impedances, trace_mode 2 and 3) and kExtGeo (box-box
+// contacts, cylinders, ellipsoids), so that the other instantiations keep their register budget.
+template <bool kArtic, int kMinBlocks, int kExt>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_unit;
@@ -1405,16 +1405,21 @@ size_t world_smem_bytes(const DScene& s, int warps) {
   return f * sizeof(float);
 }
 
-// kernel variants: pile-only with 2, 3 or 4 resident CTAs per SM (register budget), and the
-// mixed (articulated) instantiation
+// kernel variants: pile-only with 2, 3 or 4 resident CTAs per SM (register budget), the mixed
+// (articulated) instantiation, the extended one (articulated, every optional feature) and the
+// pile-only one with the exact and learned impedances
 using StepFn = void (*)(StepParams);
-static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2, false>, step_kernel<false, 3, false>,
-                                                step_kernel<false, 4, false>, step_kernel<true, 2, false>,
-                                                step_kernel<true, 2, true>};
-static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0, 0};
+static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2, 0>,
+                                                step_kernel<false, 3, 0>,
+                                                step_kernel<false, 4, 0>,
+                                                step_kernel<true, 2, 0>,
+                                                step_kernel<true, 2, kExtImp | kExtGeo>,
+                                                step_kernel<false, 2, kExtImp>};
+static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0, 0, 0};
 
 static int variant_index(bool artic, int variant) {
   if (variant == kExtVariant) return 4;
+  if (variant == kImpVariant) return artic ? 4 : 5;
   return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant));
 }
 

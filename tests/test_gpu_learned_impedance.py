@@ -215,3 +215,33 @@ def test_fit_explains_the_exact_impedance_and_moves_impulses_toward_it():
         errs = IMP.impulse_errors(sb, {"learned": net, "constant": const})
         print("median relative impulse error vs exact:", errs)
         assert errs["learned"] < 0.5 * errs["constant"] and errs["learned"] < 0.5 * errs["heuristic"]
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_jammed_pile256_full_size_sampled(mode):
+    """4096 worlds x 256 interpenetrating bodies, the bench's impedance-mode launch (one
+    shared network for mode 3); one step compared with the oracle on sampled worlds.  The exact
+    mode answers with velocities of tens of m/s, so positions get dt times the velocity
+    tolerance on top of the usual 2e-6 m."""
+    sb = S.make_pile(4096, 256, seed=5, jammed=True)
+    sb.params = dataclasses.replace(sb.params, trace_mode=mode)
+    th = random_theta(5)
+    m, b = CF.from_scenes(sb)
+    b.set_warps(0, 4)
+    thd = torch.from_numpy(th[None]).cuda().contiguous()
+    if mode == 3:
+        b.set_impedance_net(thd, 1)
+    b.step(sb.dt, 1)
+    q, v = b.get_state()
+    q, v = q.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    assert b.contact_counts().mean() > 300
+    nq, nv = 7 * 256, 6 * 256
+    for w in (0, 1234, 4095):
+        sub = sb.subset([w])
+        if mode == 3:
+            qo, vo = oracle_run(sub, th, 1)
+        else:
+            qo, vo = PR.oracle_run(sub, nsteps=1)
+        vg, qg = v[w * nv:(w + 1) * nv], q[w * nq:(w + 1) * nq]
+        assert PR.vel_err(vg, vo[0], sb.dt) <= GP.TOL1
+        np.testing.assert_allclose(qg, qo[0], rtol=0, atol=2e-6 + sb.dt * GP.TOL1 * np.abs(vo[0]).max())
