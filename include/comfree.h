@@ -336,7 +336,9 @@ cf_status cf_step_noalloc(const cf_model* model, int32_t scene, int32_t n_worlds
  * another n_sets.  A trace_mode 3 step without a network answers CF_ERR_INVALID_ARGUMENT. */
 cf_status cf_batch_set_impedance_net(cf_batch* batch, const float* theta, int32_t n_sets);
 
-/* g(x) (unclamped) at x[n][CF_IMPNET_INPUTS] (device, 16-byte aligned) into g[n] (device). */
+/* g(x) (unclamped) at x[n][CF_IMPNET_INPUTS] (device, 16-byte aligned) into g[n] (device).
+ * n = 0 does nothing (the pointers are then not read); CF_ERR_INVALID_ARGUMENT for a null
+ * pointer, n < 0 or a misaligned x. */
 cf_status cf_impnet_eval(const float* theta, const float* x, int32_t n, float* g, void* stream);
 
 /* Device floats of the fitting state: Adam's two moments and the reduction scratch.  Zero it

@@ -156,9 +156,9 @@ cf_status launched(const char* what) {
 extern "C" size_t cf_impnet_state_floats(void) { return 2 * kImpParams + (size_t)kFitBlocks * kRow; }
 
 extern "C" cf_status cf_impnet_eval(const float* theta, const float* x, int32_t n, float* g, void* stream) {
+  if (n == 0) return CF_OK;
   if (!theta || !x || !g || n < 0 || !aligned16(x))
     return ifail(CF_ERR_INVALID_ARGUMENT, "impnet eval: null pointer, negative count or x not 16-byte aligned");
-  if (n == 0) return CF_OK;
   const int grid = std::min((n + kFitThreads - 1) / kFitThreads, 8 * kFitBlocks);
   impnet_eval_kernel<<<grid, kFitThreads, 0, (cudaStream_t)stream>>>(theta, x, n, g);
   return launched("impnet eval launch");

@@ -245,3 +245,53 @@ def test_jammed_pile256_full_size_sampled(mode):
         vg, qg = v[w * nv:(w + 1) * nv], q[w * nq:(w + 1) * nq]
         assert PR.vel_err(vg, vo[0], sb.dt) <= GP.TOL1
         np.testing.assert_allclose(qg, qo[0], rtol=0, atol=2e-6 + sb.dt * GP.TOL1 * np.abs(vo[0]).max())
+
+
+def test_network_api_edges():
+    """Empty evaluation, a misaligned input, a bad rate and a wrong number of sets are refused
+    or handled without a launch; the library stays usable afterwards."""
+    net = CF.ImpedanceNet(theta=random_theta(6))
+    assert net.eval(torch.zeros(0, 4, device="cuda")).numel() == 0
+    x = torch.zeros(33 * 4 + 1, device="cuda")
+    with pytest.raises((CF.CfError, AssertionError)):
+        net.eval(x[1:].view(33, 4))                       # 4-byte offset: not 16-byte aligned
+    xt = torch.rand(100, 4, device="cuda")
+    yt = torch.rand(100, device="cuda")
+    with pytest.raises(CF.CfError):
+        CF.check(CF.lib().cf_impnet_fit(CF._ptr(net.theta), CF._ptr(net.state), 0, CF._ptr(xt), CF._ptr(yt), 100, 1,
+                                        0.0, None, None))
+    sb = learned(S.make_pile(3, 16, seed=2))
+    _, b = CF.from_scenes(sb)
+    with pytest.raises(CF.CfError):
+        b.set_impedance_net(torch.zeros(2 * NP, device="cuda"), 2)
+    b.set_impedance_net(net.theta.view(1, -1), 1)
+    b.step(sb.dt, 2)
+    assert b.status()[0] == 0
+    b.set_impedance_net(None)
+    with pytest.raises(CF.CfError, match="impedance network"):
+        b.step(sb.dt, 1)
+
+
+def test_learned_steps_replay_from_a_cuda_graph():
+    """A graph captured after the network is attached replays the learned step bit for bit,
+    and picks up new parameter values written into the same buffer."""
+    sb = learned(GP._advanced(S.make_pile(4, 16, seed=17), lambda w: 200))
+    th = torch.from_numpy(random_theta(7)[None]).cuda().contiguous()
+    _, ref = CF.from_scenes(sb)
+    ref.set_impedance_net(th, 1)
+    _, b = CF.from_scenes(sb)
+    b.set_impedance_net(th, 1)
+    g = b.graph(sb.dt, 1, repeat=3)          # one eager step, then three captured ones
+    g.replay()
+    for _ in range(4):
+        ref.step(sb.dt, 1)
+    torch.cuda.synchronize()
+    q1, v1 = b.get_state()
+    q2, v2 = ref.get_state()
+    assert torch.equal(q1, q2) and torch.equal(v1, v2)
+    th.mul_(0.5)                             # new values in the same buffer
+    g.replay()
+    for _ in range(3):
+        ref.step(sb.dt, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(b.get_state()[1], ref.get_state()[1])
