@@ -26,8 +26,8 @@
  *   8. v+ = v_s + M~^-1 p                                              (Eq. vel_correction)
  *   9. semi-implicit Euler with the exact quaternion exponential.
  *
- * Readings taken where the paper is silent or garbled are listed in the design doc; the ones that
- * change numbers are restated at the function that applies them.
+ * Where the paper is silent or garbled, the reading taken is restated at the function that
+ * applies it.
  *
  * Parity pins (tests/test_oracle_pins.py) tie every stage to closed forms, hand-derived
  * worked examples, invariants, brute force or finite differences.
