@@ -68,6 +68,8 @@ def parse():
                     help="warps per world (0: autotune); a fixed shape makes profiles comparable")
     ap.add_argument("--jammed", action="store_true",
                     help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="time only the proposal MLP's tensor-core training step and forward pass (for profiles)")
     ap.add_argument("--impedance", default="heuristic", choices=sorted(IMPEDANCE_MODES),
                     help="impedance mode of the headline workload (the exact and learned forms of Sec. III-B; "
                          "for profiles)")
@@ -288,6 +290,46 @@ def run_e2e(res, steps, blocks=8):
     return dict(value=W * steps / sec, serial=serial, blocks=blocks, h2d=nbytes, d2h=nbytes)
 
 
+def mlp_throughput(batch=16384, reps=20):
+    """The learned MPPI proposal's MLP (49 -> 256 -> 256 -> 1024, GELU; BF16 operands on the
+    tcgen05 tensor cores, FP32 accumulation): CUDA-event time of a forward pass and of one
+    training step (forward, backward, Adam) at `batch` rows, with the dense FLOPs of the GEMMs
+    (the first layer's K padded to 64) and their fraction of the measured bf16 peak."""
+    import torch
+    from paper_2603_12185_gb300 import comfree as CF
+    fin, H, O = 49, 256, 1024
+    kin = (fin + 63) // 64 * 64
+    mlp = CF.Mlp(fin, H, O, max_batch=batch, seed=0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn(batch, fin, device="cuda", generator=g)
+    y = 0.1 * torch.randn(batch, O // 2, device="cuda", generator=g)
+    out = torch.empty(batch, O, device="cuda")
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_f = timed(lambda: mlp.forward(x, out))
+    ms_t = timed(lambda: mlp.train_step(x, y, lr=1e-5))
+    mlp.status()
+    flop_f = 2.0 * batch * (kin * H + H * H + H * O)
+    flop_t = flop_f + 2.0 * batch * (kin * H + 2 * H * H + 2 * H * O)   # weight and activation gradients
+    pk, src = peaks()
+    tf_f, tf_t = flop_f / ms_f / 1e9, flop_t / ms_t / 1e9
+    return {"batch": batch, "forward_ms": ms_f, "forward_tflops": tf_f, "train_step_ms": ms_t, "train_tflops": tf_t,
+            "frac_of_bf16_peak": {"forward": tf_f / pk["bf16_tflops"], "train": tf_t / pk["bf16_tflops"]},
+            "peak_source": src}
+
+
 def run_extras(rank):
     """The other workloads, each timed with CUDA events after warm-up (reported beside the headline):
     mixed batches of uneven worlds in one persistent launch, the hand adjoint, an MPPI tick."""
@@ -392,6 +434,7 @@ def run_extras(rank):
     ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
     ms = timed(ctl.tick, 10)
     out["mppi_tick_1024x32"] = {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
+    out["proposal_mlp_49x256x1024"] = mlp_throughput()
     return out
 
 
@@ -424,6 +467,9 @@ def cpu_baseline(nbody, rank, budget_s=20.0, reference=False):
 
 def main():
     args = parse()
+    if args.mlp_only:
+        print(json.dumps({"proposal_mlp_49x256x1024": mlp_throughput()}), flush=True)
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:

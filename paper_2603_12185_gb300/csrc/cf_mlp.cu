@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -263,11 +264,13 @@ __global__ void transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloa
 // Gaussian negative log-likelihood of targets a under mean mu = y[:, :D] and log-std
 // s = clamp(y[:, D:], lo, hi):  l = sum_d ((a - mu)^2 / (2 e^{2s}) + s) / (B D).
 // Writes dL/dy as bf16 into dy [Bp x 2D] (zero rows past B) and accumulates the loss.
-__global__ void nll_grad(const float* y, const float* a, int B, int Bp, int D, float lo, float hi, __nv_bfloat16* dy,
-                         float* loss) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Grid-stride over the Bp x D elements; the loss is reduced per CTA (shuffles, then shared
+// memory) and added with one atomic per CTA.
+__global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, int B, int Bp, int D, float lo, float hi,
+                                                __nv_bfloat16* dy, float* loss) {
   float l = 0.f;
-  if (i < Bp * D) {
+  const float inv_n = 1.f / ((float)B * (float)D);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Bp * D; i += gridDim.x * blockDim.x) {
     int r = i / D, d = i % D;
     float gmu = 0.f, gs = 0.f;
     if (r < B) {
@@ -275,24 +278,56 @@ __global__ void nll_grad(const float* y, const float* a, int B, int Bp, int D, f
       float s = fminf(fmaxf(sr, lo), hi);
       float e = a[(size_t)r * D + d] - mu;
       float iv = expf(-2.f * s);
-      float inv_n = 1.f / ((float)B * (float)D);
-      l = (0.5f * e * e * iv + s) * inv_n;
+      l += (0.5f * e * e * iv + s) * inv_n;
       gmu = -e * iv * inv_n;
       gs = (sr > lo && sr < hi) ? (1.f - e * e * iv) * inv_n : 0.f;
     }
     dy[(size_t)r * 2 * D + d] = __float2bfloat16_rn(gmu);
     dy[(size_t)r * 2 * D + D + d] = __float2bfloat16_rn(gs);
   }
+  __shared__ float red[8];
   for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (t != 0.f) atomicAdd(loss, t);
+  }
 }
 
-// db[n] = sum_r g[r][n] (fp32 accumulation of bf16 gradients), one thread per column
-__global__ void bias_grad(const __nv_bfloat16* g, int R, int N, float* db) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+// Column sums db[n] = sum_r g[r][n] of a bf16 gradient [R x N] (N a multiple of 64, R a multiple
+// of kColSlices) in two deterministic passes: CTA (c, s) sums rows of slice s for 64 columns
+// (each lane two adjacent columns, the 8 warps interleaved over the rows, combined in warp order)
+// into part[s][n]; then one thread per column adds the slices in order.
+constexpr int kColSlices = 32;
+__global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16* g, int R, int N, float* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * 64 + 2 * lane;
+  const int rows = R / kColSlices, r0 = blockIdx.y * rows;
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+  for (int r = r0 + warp; r < r0 + rows; r += 8) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(g + (size_t)r * N + c0);
+    s0 += __low2float(v);
+    s1 += __high2float(v);
+  }
+  __shared__ float2 red[8][32];
+  red[warp][lane] = make_float2(s0, s1);
+  __syncthreads();
+  if (warp == 0) {
+    float t0 = 0.f, t1 = 0.f;
+    for (int w = 0; w < 8; ++w) { t0 += red[w][lane].x; t1 += red[w][lane].y; }
+    part[(size_t)blockIdx.y * N + c0] = t0;
+    part[(size_t)blockIdx.y * N + c0 + 1] = t1;
+  }
+}
+
+__global__ void bias_grad_final(const float* part, int N, float* db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   float s = 0.f;
-  for (int r = 0; r < R; ++r) s += __bfloat162float(g[(size_t)r * N + n]);
+  for (int k = 0; k < kColSlices; ++k) s += part[(size_t)k * N + n];
   db[n] = s;
 }
 
@@ -402,7 +437,7 @@ struct cf_mlp {
   size_t oW1, ob1, oW2, ob2, oW3, ob3;
   __nv_bfloat16 *W1b, *W2b, *W3b, *W2t, *W3t;
   __nv_bfloat16 *X0, *Z1, *H1, *Z2, *H2, *dY, *dA2, *dA1, *dYt, *H2t, *dA2t, *H1t, *dA1t, *X0t;
-  float *Y, *loss;
+  float *Y, *loss, *colpart;
   int* err;
   long step;
 };
@@ -422,6 +457,7 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
   size_t o_H2t = take((size_t)Bp * H * 2), o_dA2t = take((size_t)Bp * H * 2), o_H1t = take((size_t)Bp * H * 2);
   size_t o_dA1t = take((size_t)Bp * H * 2), o_X0t = take((size_t)Bp * kin * 2);
   size_t o_Y = take((size_t)Bp * O * 4), o_loss = take(16), o_err = take(16);
+  size_t o_colpart = take((size_t)kColSlices * (O > H ? O : H) * 4);
   if (m) {
     char* b = m->ws;
     m->fin = fin; m->kin = kin; m->H = H; m->O = O; m->maxB = maxB; m->Bp_max = Bp;
@@ -437,6 +473,7 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
     m->H2t = (__nv_bfloat16*)(b + o_H2t); m->dA2t = (__nv_bfloat16*)(b + o_dA2t); m->H1t = (__nv_bfloat16*)(b + o_H1t);
     m->dA1t = (__nv_bfloat16*)(b + o_dA1t); m->X0t = (__nv_bfloat16*)(b + o_X0t);
     m->Y = (float*)(b + o_Y); m->loss = (float*)(b + o_loss); m->err = (int*)(b + o_err);
+    m->colpart = (float*)(b + o_colpart);
   }
   return off;
 }
@@ -531,7 +568,11 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   const int Bp = (B + 127) / 128 * 128, H = m->H, O = m->O, D = O / 2;
   cudaMemsetAsync(m->loss, 0, 4, s);
   int n = Bp * D;
-  nll_grad<<<(n + 255) / 256, 256, 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->loss);
+  nll_grad<<<std::min((n + 255) / 256, 1216), 256, 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->loss);
+  auto colsum = [&](const __nv_bfloat16* gm, int N, float* db) {
+    bias_grad_part<<<dim3(N / 64, kColSlices), 256, 0, s>>>(gm, Bp, N, m->colpart);
+    bias_grad_final<<<(N + 127) / 128, 128, 0, s>>>(m->colpart, N, db);
+  };
   dim3 tb(32, 8);
   auto T = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
     transpose_bf16<<<dim3((C + 31) / 32, (R + 31) / 32), tb, 0, s>>>(in, R, C, out);
@@ -543,7 +584,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   EpiArgs ew{};
   ew.out_f32 = m->g + m->oW3; ew.ldo = H; ew.m_valid = O; ew.err = m->err;
   e = gemm<EPI_F32>(m->dYt, O, m->H2t, H, Bp, ew, s);
-  bias_grad<<<(O + 127) / 128, 128, 0, s>>>(m->dY, Bp, O, m->g + m->ob3);
+  colsum(m->dY, O, m->g + m->ob3);
   EpiArgs eb{};
   eb.out_bf16 = m->dA2; eb.z = m->Z2; eb.ldo = H; eb.m_valid = Bp; eb.err = m->err;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dY, Bp, m->W3t, H, O, eb, s);
@@ -552,7 +593,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   T(m->H1, Bp, H, m->H1t);
   ew.out_f32 = m->g + m->oW2; ew.ldo = H; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA2t, H, m->H1t, H, Bp, ew, s);
-  bias_grad<<<(H + 127) / 128, 128, 0, s>>>(m->dA2, Bp, H, m->g + m->ob2);
+  colsum(m->dA2, H, m->g + m->ob2);
   eb.out_bf16 = m->dA1; eb.z = m->Z1;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dA2, Bp, m->W2t, H, H, eb, s);
   // layer 1
@@ -560,7 +601,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   T(m->X0, Bp, m->kin, m->X0t);
   ew.out_f32 = m->g + m->oW1; ew.ldo = m->kin; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA1t, H, m->X0t, m->kin, Bp, ew, s);
-  bias_grad<<<(H + 127) / 128, 128, 0, s>>>(m->dA1, Bp, H, m->g + m->ob1);
+  colsum(m->dA1, H, m->g + m->ob1);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
   return CF_OK;
