@@ -198,36 +198,52 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
   tc_fence_after();
   if (!ok && lane == 0) atomicOr(ep.err, CF_FLAG_TIMEOUT);
   if (ok && s_ok) {
-    const int row = m0 + warp * 32 + lane;
+    // tcgen05.ld hands each lane one row; a 32-row x 16-column slice is staged in shared memory
+    // (the operand ring is idle once `done` has fired) and written back four columns per lane,
+    // four lanes per row and eight rows per instruction, so that global stores (and the loads
+    // of z) are 16- or 8-byte vectors on contiguous 64- or 32-byte row segments.  Row stride 20
+    // floats keeps the staging writes of a quarter-warp on distinct banks.
+    float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 20);
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    const int quad = lane & 3, ro = lane >> 2;
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tmem_ld16(tbase + c, v);
-      if (row < ep.m_valid) {
-        const int n = n0 + c;
-        const size_t o = (size_t)row * ep.ldo + n;
-        if (EPI == EPI_BIAS_GELU) {
 #pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            float z0 = v[i] + ep.bias[n + i], z1 = v[i + 1] + ep.bias[n + i + 1];
-            *reinterpret_cast<__nv_bfloat162*>(ep.out_z + o + i) = __floats2bfloat162_rn(z0, z1);
-            *reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o + i) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-          }
-        } else if (EPI == EPI_BIAS_F32) {
+      for (int i = 0; i < 16; i += 4)
+        *reinterpret_cast<float4*>(stage + lane * 20 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      __syncwarp();
+      const int n = n0 + c + 4 * quad;
+      float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (EPI == EPI_BIAS_GELU || EPI == EPI_BIAS_F32) b = *reinterpret_cast<const float4*>(ep.bias + n);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) ep.out_f32[o + i] = v[i] + ep.bias[n + i];
-        } else if (EPI == EPI_F32) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) ep.out_f32[o + i] = v[i];
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            float g0 = v[i] * gelu_grad(__bfloat162float(ep.z[o + i]));
-            float g1 = v[i + 1] * gelu_grad(__bfloat162float(ep.z[o + i + 1]));
-            *reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o + i) = __floats2bfloat162_rn(g0, g1);
+      for (int rr = 0; rr < 4; ++rr) {
+        const int r = 8 * rr + ro;
+        const int row = m0 + warp * 32 + r;
+        if (row < ep.m_valid) {
+          const float4 a = *reinterpret_cast<const float4*>(stage + r * 20 + 4 * quad);
+          const size_t o = (size_t)row * ep.ldo + n;
+          if (EPI == EPI_BIAS_GELU) {
+            const float z0 = a.x + b.x, z1 = a.y + b.y, z2 = a.z + b.z, z3 = a.w + b.w;
+            __nv_bfloat162 zz[2] = {__floats2bfloat162_rn(z0, z1), __floats2bfloat162_rn(z2, z3)};
+            __nv_bfloat162 hh[2] = {__floats2bfloat162_rn(gelu(z0), gelu(z1)), __floats2bfloat162_rn(gelu(z2), gelu(z3))};
+            *reinterpret_cast<uint2*>(ep.out_z + o) = *reinterpret_cast<const uint2*>(zz);
+            *reinterpret_cast<uint2*>(ep.out_bf16 + o) = *reinterpret_cast<const uint2*>(hh);
+          } else if (EPI == EPI_BIAS_F32) {
+            *reinterpret_cast<float4*>(ep.out_f32 + o) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+          } else if (EPI == EPI_F32) {
+            *reinterpret_cast<float4*>(ep.out_f32 + o) = a;
+          } else {
+            const uint2 zr = *reinterpret_cast<const uint2*>(ep.z + o);
+            const __nv_bfloat162* zp = reinterpret_cast<const __nv_bfloat162*>(&zr);
+            __nv_bfloat162 gg[2] = {
+                __floats2bfloat162_rn(a.x * gelu_grad(__low2float(zp[0])), a.y * gelu_grad(__high2float(zp[0]))),
+                __floats2bfloat162_rn(a.z * gelu_grad(__low2float(zp[1])), a.w * gelu_grad(__high2float(zp[1])))};
+            *reinterpret_cast<uint2*>(ep.out_bf16 + o) = *reinterpret_cast<const uint2*>(gg);
           }
         }
       }
+      __syncwarp();
     }
   }
   tc_fence_before();
