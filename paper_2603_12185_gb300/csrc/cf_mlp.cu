@@ -35,6 +35,7 @@ struct EpiArgs {
   __nv_bfloat16* out_z;     // [M x ldo] pre-activation (EPI_BIAS_GELU)
   const __nv_bfloat16* z;   // [M x ldo] pre-activation read by EPI_GELU_BWD
   float* out_f32;           // [M x ldo] (EPI_BIAS_F32, EPI_F32)
+  size_t slice_stride;      // split-K: CTA z stores its partial tile at out_f32 + z * slice_stride
   int ldo;
   int m_valid;              // rows >= m_valid are not stored
   int* err;
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
   uint8_t* sB = smem + STAGES * A_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = K / BK;
+  const int nk = K / BK;              // K: this CTA's share of the reduction (split-K: blockIdx.z)
+  const int kz = blockIdx.z * K;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     mbar_init(&done, 1);
@@ -164,8 +166,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     const int pre = nk < STAGES ? nk : STAGES;
     for (int s = 0; s < pre; ++s) {
       mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-      tma_load_2d(sA + s * A_BYTES, &tmA, s * BK, m0, &full[s]);
-      tma_load_2d(sB + s * B_BYTES, &tmB, s * BK, n0, &full[s]);
+      tma_load_2d(sA + s * A_BYTES, &tmA, kz + s * BK, m0, &full[s]);
+      tma_load_2d(sB + s * B_BYTES, &tmB, kz + s * BK, n0, &full[s]);
     }
     for (int k = 0; k < nk && ok; ++k) {
       const int s = k % STAGES;
@@ -181,8 +183,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
       if (k + STAGES < nk) {
         if (!mbar_wait(&empty[s], par)) { ok = false; break; }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        tma_load_2d(sA + s * A_BYTES, &tmA, (k + STAGES) * BK, m0, &full[s]);
-        tma_load_2d(sB + s * B_BYTES, &tmB, (k + STAGES) * BK, n0, &full[s]);
+        tma_load_2d(sA + s * A_BYTES, &tmA, kz + (k + STAGES) * BK, m0, &full[s]);
+        tma_load_2d(sB + s * B_BYTES, &tmB, kz + (k + STAGES) * BK, n0, &full[s]);
       }
     }
     if (ok) {
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 20);
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
     const int quad = lane & 3, ro = lane >> 2;
+    float* out_f32 = ep.out_f32 + (size_t)blockIdx.z * ep.slice_stride;
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tmem_ld16(tbase + c, v);
@@ -230,9 +233,9 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
             *reinterpret_cast<uint2*>(ep.out_z + o) = *reinterpret_cast<const uint2*>(zz);
             *reinterpret_cast<uint2*>(ep.out_bf16 + o) = *reinterpret_cast<const uint2*>(hh);
           } else if (EPI == EPI_BIAS_F32) {
-            *reinterpret_cast<float4*>(ep.out_f32 + o) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+            *reinterpret_cast<float4*>(out_f32 + o) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
           } else if (EPI == EPI_F32) {
-            *reinterpret_cast<float4*>(ep.out_f32 + o) = a;
+            *reinterpret_cast<float4*>(out_f32 + o) = a;
           } else {
             const uint2 zr = *reinterpret_cast<const uint2*>(ep.z + o);
             const __nv_bfloat162* zp = reinterpret_cast<const __nv_bfloat162*>(&zr);
@@ -419,7 +422,8 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows)
 size_t gemm_smem(int BN) { return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024; }
 
 template <int BN, int EPI>
-cudaError_t gemm_launch(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s) {
+cudaError_t gemm_launch(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s,
+                        int split = 1) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN)) return cudaErrorInvalidValue;
   static bool attr = false;
@@ -429,8 +433,8 @@ cudaError_t gemm_launch(const void* A, int M, const void* B, int N, int K, const
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(N / BN, M / BM);
-  gemm_kernel<BN, EPI><<<grid, 128, gemm_smem(BN), s>>>(ta, tb, ep, K);
+  dim3 grid(N / BN, M / BM, split);
+  gemm_kernel<BN, EPI><<<grid, 128, gemm_smem(BN), s>>>(ta, tb, ep, K / split);
   return cudaGetLastError();
 }
 
@@ -439,6 +443,42 @@ cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const EpiArg
   if (M % BM || K % BK || N % 64) return cudaErrorInvalidValue;
   if (N % 128 == 0) return gemm_launch<128, EPI>(A, M, B, N, K, ep, s);
   return gemm_launch<64, EPI>(A, M, B, N, K, ep, s);
+}
+
+// out[i] = sum_z part[z * n + i], the split-K partial tiles added in order
+__global__ void splitk_reduce(const float* part, int split, size_t n, float* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float t = 0.f;
+    for (int z = 0; z < split; ++z) t += part[(size_t)z * n + i];
+    out[i] = t;
+  }
+}
+
+constexpr int kMaxSplit = 64;     // slices of one split-K product
+constexpr int kSplitScratch = 16; // scratch: this many copies of the largest weight matrix
+
+// FP32 GEMM with a long reduction (the weight gradients, K = the batch): the K range is cut
+// into `split` slices, so that the few output tiles still give every SM work; each slice's
+// partial tile goes to `scratch` and a second pass adds them in order (deterministic).
+cudaError_t gemm_f32_splitk(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, float* scratch,
+                            size_t scratch_floats, int num_sms, cudaStream_t s) {
+  if (M % BM || K % BK || N % 64) return cudaErrorInvalidValue;
+  const int BN = N % 128 == 0 ? 128 : 64;
+  const int tiles = (N / BN) * (M / BM);
+  int split = 1;
+  for (int c = 2; c <= kMaxSplit; ++c)
+    if ((K / BK) % c == 0 && tiles * c <= 2 * num_sms && (size_t)c * M * N <= scratch_floats) split = c;
+  if (split == 1) return gemm<EPI_F32>(A, M, B, N, K, ep, s);
+  EpiArgs ps = ep;
+  ps.out_f32 = scratch;
+  ps.ldo = N;
+  ps.slice_stride = (size_t)M * N;
+  cudaError_t e = BN == 128 ? gemm_launch<128, EPI_F32>(A, M, B, N, K, ps, s, split)
+                            : gemm_launch<64, EPI_F32>(A, M, B, N, K, ps, s, split);
+  if (e != cudaSuccess) return e;
+  const size_t n = (size_t)M * N;
+  splitk_reduce<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, s>>>(scratch, split, n, ep.out_f32);
+  return cudaGetLastError();
 }
 
 inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -453,7 +493,9 @@ struct cf_mlp {
   size_t oW1, ob1, oW2, ob2, oW3, ob3;
   __nv_bfloat16 *W1b, *W2b, *W3b, *W2t, *W3t;
   __nv_bfloat16 *X0, *Z1, *H1, *Z2, *H2, *dY, *dA2, *dA1, *dYt, *H2t, *dA2t, *H1t, *dA1t, *X0t;
-  float *Y, *loss, *colpart;
+  float *Y, *loss, *colpart, *splitk;
+  size_t splitk_floats;
+  int num_sms;
   int* err;
   long step;
 };
@@ -474,6 +516,8 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
   size_t o_dA1t = take((size_t)Bp * H * 2), o_X0t = take((size_t)Bp * kin * 2);
   size_t o_Y = take((size_t)Bp * O * 4), o_loss = take(16), o_err = take(16);
   size_t o_colpart = take((size_t)kColSlices * (O > H ? O : H) * 4);
+  const size_t wmax = std::max((size_t)O * H, std::max((size_t)H * H, (size_t)H * kin));
+  size_t o_splitk = take((size_t)kSplitScratch * wmax * 4);
   if (m) {
     char* b = m->ws;
     m->fin = fin; m->kin = kin; m->H = H; m->O = O; m->maxB = maxB; m->Bp_max = Bp;
@@ -490,6 +534,8 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
     m->dA1t = (__nv_bfloat16*)(b + o_dA1t); m->X0t = (__nv_bfloat16*)(b + o_X0t);
     m->Y = (float*)(b + o_Y); m->loss = (float*)(b + o_loss); m->err = (int*)(b + o_err);
     m->colpart = (float*)(b + o_colpart);
+    m->splitk = (float*)(b + o_splitk);
+    m->splitk_floats = (size_t)kSplitScratch * wmax;
   }
   return off;
 }
@@ -528,6 +574,11 @@ extern "C" cf_status cf_mlp_create(int32_t fin, int32_t hidden, int32_t fout, in
   if (!m) return mfail(CF_ERR_OUT_OF_MEMORY, "mlp allocation");
   m->ws = static_cast<char*>(device_workspace);
   mlp_layout(fin, hidden, fout, max_batch, m);
+  {
+    int dev = 0;
+    m->num_sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(m->ws, 0, need, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->w, params, m->nparam * 4, cudaMemcpyDeviceToDevice, s);
@@ -599,7 +650,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   T(m->H2, Bp, H, m->H2t);
   EpiArgs ew{};
   ew.out_f32 = m->g + m->oW3; ew.ldo = H; ew.m_valid = O; ew.err = m->err;
-  e = gemm<EPI_F32>(m->dYt, O, m->H2t, H, Bp, ew, s);
+  e = gemm_f32_splitk(m->dYt, O, m->H2t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
   colsum(m->dY, O, m->g + m->ob3);
   EpiArgs eb{};
   eb.out_bf16 = m->dA2; eb.z = m->Z2; eb.ldo = H; eb.m_valid = Bp; eb.err = m->err;
@@ -608,7 +659,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   T(m->dA2, Bp, H, m->dA2t);
   T(m->H1, Bp, H, m->H1t);
   ew.out_f32 = m->g + m->oW2; ew.ldo = H; ew.m_valid = H;
-  if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA2t, H, m->H1t, H, Bp, ew, s);
+  if (e == cudaSuccess) e = gemm_f32_splitk(m->dA2t, H, m->H1t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
   colsum(m->dA2, H, m->g + m->ob2);
   eb.out_bf16 = m->dA1; eb.z = m->Z1;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dA2, Bp, m->W2t, H, H, eb, s);
@@ -616,7 +667,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   T(m->dA1, Bp, H, m->dA1t);
   T(m->X0, Bp, m->kin, m->X0t);
   ew.out_f32 = m->g + m->oW1; ew.ldo = m->kin; ew.m_valid = H;
-  if (e == cudaSuccess) e = gemm<EPI_F32>(m->dA1t, H, m->X0t, m->kin, Bp, ew, s);
+  if (e == cudaSuccess) e = gemm_f32_splitk(m->dA1t, H, m->X0t, m->kin, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
   colsum(m->dA1, H, m->g + m->ob1);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
