@@ -560,7 +560,8 @@ static void sphere_box(const V3<S>& c, S r, const V3<S>& bc, const M3<S>& R, con
   out.push_back(k);
 }
 
-/* Box-box contacts (reading 16): the separating-axis test over the six face axes (A's three,
+/* Box-box contacts (the paper delegates collision detection to MJWarp and names no method;
+ * this is the reading taken here): the separating-axis test over the six face axes (A's three,
  * then B's) picks the axis of least overlap, whose box is the reference and whose face toward
  * the other (incident) box is the reference face.  The incident box's face most anti-parallel
  * to it is clipped by the reference face's four side planes (Sutherland-Hodgman: incident
@@ -632,7 +633,7 @@ static void box_box(const V3<S>& ca, const M3<S>& Ra, const V3<S>& ha, const V3<
 }
 
 /* Ellipsoid (centre c, rotation R, semi-axes e along the body axes) against a plane (point o,
- * unit normal n), reading 17: the ellipsoid's support point against n,
+ * unit normal n); the paper names no method, and the reading taken is the support point against n,
  * p = c - R D^2 R^T n / |D R^T n| with D = diag(e), is the lowest point; gap = its height. */
 template <class S>
 static void ellipsoid_plane(const V3<S>& c, const M3<S>& R, const V3<S>& e, const V3<S>& o, const V3<S>& n,
@@ -651,7 +652,7 @@ static void ellipsoid_plane(const V3<S>& c, const M3<S>& R, const V3<S>& e, cons
 }
 
 /* Cylinder (centre c, rotation R, radius r, half length h along the body z axis) against a
- * plane, reading 17: each end cap contributes three rim points 120 degrees apart, starting from
+ * plane; the paper names no method, and in the reading taken each end cap contributes three rim points 120 degrees apart, starting from
  * the rim's lowest direction w = -(n - (n.u) u)/|.| (the body x axis when the cap is parallel
  * to the plane): a tilted cylinder touches with its lowest rim point, a lying one along a line,
  * a standing one on a tripod.  Subs 3 cap + k (cap 0 at -h). */
@@ -679,7 +680,7 @@ static void cylinder_plane(const V3<S>& c, const M3<S>& R, S r, S h, const V3<S>
 }
 
 /* Sphere (centre s, radius rs) against a solid cylinder (centre c, axis u, radius r, half
- * length h), reading 17: with t = u.(s - c) and the radial offset d = (s - c) - t u, a centre
+ * length h); the paper names no method, and the reading taken is: with t = u.(s - c) and the radial offset d = (s - c) - t u, a centre
  * outside the cylinder is pushed from the closest point c + clamp(t) u + min(|d|, r) d/|d|; a
  * centre inside leaves through the nearer of the side (depth r - |d|) and the cap (depth
  * h - |t|).  The normal points from the cylinder toward the sphere. */
@@ -1405,6 +1406,60 @@ double ow_impnet_loss_grad(const double* theta, const double* x, const double* y
     }
   }
   return loss / n;
+}
+
+/* The MPC costs of one state (Sec. V, Eq. mpc and its running and terminal cost terms).
+ * The object is the free body `cost_body`; goal[7] = its target position and quaternion (wxyz);
+ * qref[nq] = the home pose, of which only hinge coordinates count; wts[8] = w_quat, w_pos,
+ * w_contact, w_joint, w_fallen (the paper's Omega), fall_radius, term_pos (phi_1), term_quat
+ * (phi_2).  Running cost:
+ *   w_quat (1 - (q*^T q)^2) + w_pos (|p_x - p*_x| + |p_y - p*_y| + |p_z - p*_z|)
+ *   + w_contact sum_tips |p - tip|^2 + w_joint sum_hinges (q_k - qref_k)^2 + w_fallen [fallen],
+ * where a fingertip is the far end (centre + half length along the geom's z axis) of every
+ * capsule carried by a hinge body that has no child body, and "fallen" means the object's
+ * horizontal distance from the target exceeds fall_radius (the synthetic palm is the floor, so
+ * the paper's height test cannot tell a dropped object).  Terminal cost:
+ *   term_pos |p - p*|^2 + term_quat (1 - (q*^T q)^2). */
+int ow_mpc_cost(const ow_world* w, int cost_body, const double* q, const double* goal, const double* qref,
+                const double* wts, double* running, double* terminal) {
+  Structure st;
+  if (!build_structure(w, st)) return -1;
+  if (cost_body < 0 || cost_body >= w->nbody || w->body_jnt[cost_body] != FREE) return -1;
+  std::vector<Pose<double>> P;
+  forward_kinematics(w, st, q, P);
+  const double* qo = q + st.qadr[cost_body];
+  const double align = goal[3] * qo[3] + goal[4] * qo[4] + goal[5] * qo[5] + goal[6] * qo[6];
+  const double c_quat = 1.0 - align * align;
+  double c = wts[0] * c_quat;
+  c += wts[1] * (std::fabs(qo[0] - goal[0]) + std::fabs(qo[1] - goal[1]) + std::fabs(qo[2] - goal[2]));
+  double tips = 0.0;
+  for (int g = 0; g < w->ngeom; ++g) {
+    const int b = w->geom_body[g];
+    if (b < 0 || w->geom_type[g] != CAPSULE || w->body_jnt[b] != HINGE) continue;
+    bool leaf = true;
+    for (int k = 0; k < w->nbody; ++k)
+      if (w->body_parent[k] == b) leaf = false;
+    if (!leaf) continue;
+    const double gq[4] = {w->geom_quat[4 * g], w->geom_quat[4 * g + 1], w->geom_quat[4 * g + 2], w->geom_quat[4 * g + 3]};
+    const M3<double> Rg = mul(P[b].R, quat_to_mat(gq));
+    const V3<double> centre = P[b].x + mul(P[b].R, vload<double>(w->geom_pos + 3 * g));
+    const V3<double> tip = centre + w->geom_size[3 * g + 1] * Rg.col(2);
+    const V3<double> d = V3<double>(qo[0], qo[1], qo[2]) - tip;
+    tips += dot(d, d);
+  }
+  c += wts[2] * tips;
+  double cj = 0.0;
+  for (int b = 0; b < w->nbody; ++b)
+    if (w->body_jnt[b] == HINGE) {
+      const double e = q[st.qadr[b]] - qref[st.qadr[b]];
+      cj += e * e;
+    }
+  c += wts[3] * cj;
+  if (std::hypot(qo[0] - goal[0], qo[1] - goal[1]) > wts[5]) c += wts[4];
+  *running = c;
+  const double dx = qo[0] - goal[0], dy = qo[1] - goal[1], dz = qo[2] - goal[2];
+  *terminal = wts[6] * (dx * dx + dy * dy + dz * dz) + wts[7] * c_quat;
+  return 0;
 }
 
 /* Rollout loss of body `body` after T steps, L = |x_T - x*|^2 + (1 - (quat*^T quat_T)^2), and

@@ -86,6 +86,7 @@ def lib():
             L.ow_impnet_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
             L.ow_impnet_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
             L.ow_impnet_loss_grad.restype = C.c_double
+            L.ow_mpc_cost.argtypes = [P(OWorld), C.c_int] + [C.c_void_p] * 4 + [P(C.c_double), P(C.c_double)]
             _lib = L
     return _lib
 
@@ -230,6 +231,24 @@ def rollout_loss_dir(desc, params, dt, q0, v0, tau, dq0, dv0, dtau, body, target
     if rc:
         raise RuntimeError("oracle rollout failed")
     return L.value, dL.value
+
+
+MPC_WEIGHTS = ("w_quat", "w_pos", "w_contact", "w_joint", "w_fallen", "fall_radius", "term_pos", "term_quat")
+
+
+def mpc_cost(desc, q, goal, qref, weights, cost_body=0):
+    """(running, terminal) MPC cost of state q (Sec. V, Eq. mpc): goal = target position and
+    quaternion of the free body `cost_body`, qref = home pose (hinge entries), weights = any
+    object with the attributes in MPC_WEIGHTS."""
+    w = desc if isinstance(desc, World) else World(desc)
+    q = np.ascontiguousarray(q, np.float64)
+    g = np.ascontiguousarray(goal, np.float64)
+    r = np.ascontiguousarray(qref, np.float64)
+    wt = np.array([float(getattr(weights, k)) for k in MPC_WEIGHTS], np.float64)
+    run, term = C.c_double(), C.c_double()
+    if lib().ow_mpc_cost(C.byref(w.s), cost_body, _p(q), _p(g), _p(r), _p(wt), C.byref(run), C.byref(term)):
+        raise RuntimeError("oracle mpc cost failed")
+    return run.value, term.value
 
 
 class BatchRunner:

@@ -132,6 +132,186 @@ def test_worked_single_contact_step(oracle, v0x):
         assert sum(lam) == pytest.approx(4 * Mphi * 0.000223544, rel=1e-9)  # printed digits of the hand sum
 
 
+# ------------------------------------------------------------------------------------------
+# the 6D cone's torsional and rolling rows (Sec. III-A, Eqs. primal_cone, dual_cone,
+# dual_polyhedral, tilde_defs), by hand on a sphere 2 mm into the plane z = 0 with the C2
+# cone (8 tangential, 2 torsional, 8 rolling facets; mu = 0.8, 0.005, 0.005)
+# ------------------------------------------------------------------------------------------
+MU6 = (0.8, 0.005, 0.005)
+LEVER = 0.049                            # centre to the contact midpoint (r + phi/2)
+
+
+def _lam_6d(s):
+    """Facet impulse of Eq. cf_wrench at the worked contact: lambda dt = (-k M (s dt + phi) - d M s)+
+    with M(phi) = r_max/(1 - r_max) / trace, trace = 3/m + 2 l^2 / I (unit mass, I = 1e-3)."""
+    trace = 3.0 + 2.0 * LEVER ** 2 / 1e-3
+    M = 19.0 / trace
+    return max(0.0, -0.1 * M * (s * DT - 0.002) - 0.001 * M * s)
+
+
+@pytest.mark.parametrize("omega", [20.0, 60.0])
+def test_torsional_facets_by_hand(oracle, omega):
+    """A sphere spinning at omega about the normal: J_tor v = n . omega = omega while the contact
+    point does not slide (omega is parallel to the lever) and no rolling row sees the spin.  The
+    two torsional facets J~ = J_n -+ mu_tor J_tor have s = v_n -+ mu_tor omega; the other 16
+    facets have s = v_n.  The wrench's torsion -mu_tor (lambda_+ - lambda_-) is the only angular
+    impulse, so omega+ = omega + torsion / I.  At 60 rad/s the retarding facet is inactive.
+    A linear row in place of J_tor (s = v_n (1 -+ mu_tor)), a dropped mu_tor or a flipped sign
+    each change v+ or omega+ far beyond the tolerance."""
+    d = Wd.sphere_on_plane(mu=MU6)
+    q, v = Wd.free_state((0, 0, 0.048), ang=(0, 0, omega))
+    rec = oracle.step_record(d, Wd.params(n_t=8, n_tor=2, n_rol=8), DT, q, v)
+    vz = -G * DT
+    lp, lm = _lam_6d(vz - MU6[1] * omega), _lam_6d(vz + MU6[1] * omega)
+    N = 16 * _lam_6d(vz) + lp + lm
+    torsion = -MU6[1] * (lp - lm)
+    c = rec["contacts"][0]
+    assert len(rec["contacts"]) == 1 and c["nfacet"] == 18
+    assert c["nactive"] == (18 if lm > 0 else 17)
+    assert (lm > 0) == (omega == 20.0)
+    assert c["wrench"][0] == pytest.approx(N, rel=1e-12)
+    assert c["wrench"][3] == pytest.approx(torsion, rel=1e-12)
+    np.testing.assert_allclose(c["wrench"][[1, 2, 4, 5]], 0.0, atol=1e-18)
+    np.testing.assert_allclose(rec["v"][:3], [0.0, 0.0, vz + N], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][3:], [0.0, 0.0, omega + torsion / 1e-3], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("omega_y", [10.0, 40.0])
+def test_rolling_facets_by_hand(oracle, omega_y):
+    """A sphere rolling without slip along +x: omega = (0, w, 0) and v_x = l w, so the contact
+    point is at rest (every tangential facet has s = v_n) and J_tor v = 0, while the rolling rows
+    see (t1 . omega, t2 . omega) = (0, w).  Rolling facet j (direction (cos, sin)(2 pi j / 8))
+    has s_j = v_n - mu_rol sin_j w.  The rolling moment (R1, R2) = -mu_rol sum_j (cos_j, sin_j)
+    lambda_j is the only angular impulse (the normal force passes through the centre), so
+    omega+ = (R1, w + R2, 0) / I.  Rows built from the linear point velocity (zero here) would
+    leave omega unchanged; a dropped mu_rol or sign flips R2."""
+    d = Wd.sphere_on_plane(mu=MU6)
+    q, v = Wd.free_state((0, 0, 0.048), lin=(LEVER * omega_y, 0, 0), ang=(0, omega_y, 0))
+    rec = oracle.step_record(d, Wd.params(n_t=8, n_tor=2, n_rol=8), DT, q, v)
+    vz = -G * DT
+    th = 2 * np.pi * np.arange(8) / 8
+    lam_r = np.array([_lam_6d(vz - MU6[2] * np.sin(t) * omega_y) for t in th])
+    N = 10 * _lam_6d(vz) + lam_r.sum()
+    R1 = -MU6[2] * np.sum(np.cos(th) * lam_r)
+    R2 = -MU6[2] * np.sum(np.sin(th) * lam_r)
+    assert R2 < 0.0                       # resists the rolling
+    assert (lam_r.min() > 0) == (omega_y == 10.0)
+    c = rec["contacts"][0]
+    assert c["wrench"][0] == pytest.approx(N, rel=1e-12)
+    assert c["wrench"][5] == pytest.approx(R2, rel=1e-12)
+    assert abs(c["wrench"][4] - R1) < 1e-15 * N
+    np.testing.assert_allclose(rec["v"][:3], [LEVER * omega_y, 0.0, vz + N], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][3:], [R1 / 1e-3, omega_y + R2 / 1e-3, 0.0], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# the tangent frame of non-plane contacts (the paper fixes none): t1 = normalize(e_z x n) when
+# |n_z| < 0.5, else normalize(e_x x n); t2 = n x t1
+# ------------------------------------------------------------------------------------------
+def _two_spheres(n, u=(0.0, 0.0, 0.0), overlap=0.002):
+    """Sphere A (geom 0, 1 kg, I 1e-3) touching sphere B (geom 1, 2 kg, I 3e-3) along unit n
+    from B to A, both r = 0.05, A moving at u; no gravity."""
+    n = np.asarray(n, float)
+    d = Wd.world([dict(mass=1.0, inertia=(1e-3,) * 3), dict(mass=2.0, inertia=(3e-3,) * 3)],
+                 [dict(type=S.SPHERE, body=0, size=(0.05, 0, 0), mu=(0.5, 0, 0)),
+                  dict(type=S.SPHERE, body=1, size=(0.05, 0, 0), mu=(0.5, 0, 0))])
+    qa, va = Wd.free_state(tuple((0.1 - overlap) * n + np.array([0, 0, 1.0])), lin=tuple(u))
+    qb, vb = Wd.free_state((0, 0, 1.0))
+    return d, np.concatenate([qa, qb]), np.concatenate([va, vb])
+
+
+# (n, expected t1): the four cases worked by hand from the rule
+FRAMES = [
+    ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0)),                                   # e_z x e_x = e_y
+    ((0.0, 0.0, 1.0), (0.0, -1.0, 0.0)),                                  # e_x x e_z = -e_y
+    ((0.8, 0.36, 0.48), (-0.36 / np.hypot(0.36, 0.8), 0.8 / np.hypot(0.36, 0.8), 0.0)),   # |n_z| < 0.5
+    ((0.48, 0.36, 0.8), (0.0, -0.8 / np.hypot(0.8, 0.36), 0.36 / np.hypot(0.8, 0.36))),   # |n_z| >= 0.5
+]
+
+
+@pytest.mark.parametrize("n,t1", FRAMES)
+def test_tangent_frame_rule(oracle, n, t1):
+    d, q, v = _two_spheres(n)
+    rec = oracle.step_record(d, Wd.params(n_t=4, gravity=(0.0, 0.0, 0.0)), DT, q, v)
+    c = rec["contacts"][0]
+    np.testing.assert_allclose(c["normal"], n, atol=1e-12)
+    np.testing.assert_allclose(c["t1"], t1, atol=1e-12)
+    np.testing.assert_allclose(c["t2"], np.cross(n, t1), atol=1e-12)
+
+
+def test_tangent_frame_decides_the_pyramid_friction(oracle):
+    """A sliding sphere-sphere contact through the anisotropic 4-facet pyramid, by hand in the
+    frame the rule gives for n = (0.48, 0.36, 0.8).  The other branch's frame is turned by 137
+    degrees about n (not a symmetry of the pyramid), so taking it changes the friction impulse
+    and both bodies' velocities.  At 1 m/s the facet leaning along the slide is inactive
+    (with all four active the soft law gives friction exactly against the slide, in any frame),
+    so the friction is not anti-parallel to the slide."""
+    n, t1 = np.array(FRAMES[3][0]), np.array(FRAMES[3][1])
+    t2 = np.cross(n, t1)
+    slide = 1.0 * (np.cos(0.4) * t1 + np.sin(0.4) * t2)     # tangential, 0.4 rad from t1
+    d, q, v = _two_spheres(n, u=slide)
+    rec = oracle.step_record(d, Wd.params(n_t=4, gravity=(0.0, 0.0, 0.0)), DT, q, v)
+    la, lb = -0.049 * n, 0.049 * n                           # levers to the contact midpoint
+    trace = (3.0 + 2 * 0.049 ** 2 / 1e-3) + (1.5 + 2 * 0.049 ** 2 / 3e-3)
+    M = 19.0 / trace
+    dirs = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    vt = (slide @ t1, slide @ t2)
+    lam = [max(0.0, -0.1 * M * (s * DT - 0.002) - 0.001 * M * s)
+           for s in (-0.5 * (dc * vt[0] + ds * vt[1]) for dc, ds in dirs)]
+    f = sum(lam) * n - 0.5 * sum(l * dc for l, (dc, ds) in zip(lam, dirs)) * t1 \
+        - 0.5 * sum(l * ds for l, (dc, ds) in zip(lam, dirs)) * t2
+    np.testing.assert_allclose(rec["v"][:3], slide + f, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][3:6], np.cross(la, f) / 1e-3, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(rec["v"][6:9], -f / 2.0, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rec["v"][9:], -np.cross(lb, f) / 3e-3, rtol=1e-12, atol=1e-13)
+    assert min(lam) == 0.0 and max(lam) > 0.0
+    assert abs(np.cross(f - (f @ n) * n, slide) @ n) > 1e-2 * np.linalg.norm(f)  # friction not along -slide
+
+
+# ------------------------------------------------------------------------------------------
+# the MPC costs (Sec. V, Eq. mpc) on a hand-built state
+# ------------------------------------------------------------------------------------------
+class _W:
+    w_quat, w_pos, w_contact, w_joint, w_fallen, fall_radius, term_pos, term_quat = 2.0, 3.0, 10.0, 0.05, 5.0, 0.08, 50.0, 20.0
+
+
+def _cost_world():
+    """A free cube (body 0); a one-link finger hinged at (0.1, 0, 0) about y (body 1, capsule
+    half length 0.02 at (0, 0, 0.02): a fingertip); a two-link finger hinged at (-0.1, 0, 0)
+    about x (body 2 with a capsule: not a tip; its child body 3 at (0, 0, 0.04), capsule half
+    length 0.015 at (0, 0, 0.015): a tip)."""
+    cap = lambda b, h: dict(type=S.CAPSULE, body=b, pos=(0, 0, h), size=(0.01, h, 0))
+    return Wd.world([dict(mass=0.1, inertia=(6e-5,) * 3),
+                     dict(parent=-1, jnt=S.HINGE, pos=(0.1, 0, 0), axis=(0, 1, 0)),
+                     dict(parent=-1, jnt=S.HINGE, pos=(-0.1, 0, 0), axis=(1, 0, 0)),
+                     dict(parent=2, jnt=S.HINGE, pos=(0, 0, 0.04), axis=(1, 0, 0))],
+                    [dict(type=S.PLANE, body=-1), dict(type=S.BOX, body=0, size=(0.03,) * 3),
+                     cap(1, 0.02), cap(2, 0.02), cap(3, 0.015)])
+
+
+@pytest.mark.parametrize("fall_radius", [0.08, 0.02])
+def test_mpc_cost_by_hand(oracle, fall_radius):
+    """Cube at p = (0.01, 0.02, 0.03) turned 0.5 rad about z, target (0, 0, 0.05) turned 1 rad:
+    q*^T q = cos 0.25.  Hinges (pi/2, 0, pi/2), home pose 0.1 each.  Tips: finger 1 turned by
+    pi/2 about y points along +x, tip (0.14, 0, 0); finger 2's second link turned by pi/2 about
+    x points along -y, tip (-0.1, -0.03, 0.04).  The cube is 0.0224 m from the target
+    horizontally: fallen only for the 0.02 m radius."""
+    d = _cost_world()
+    p = np.array([0.01, 0.02, 0.03])
+    q = np.concatenate([p, [np.cos(0.25), 0, 0, np.sin(0.25)], [np.pi / 2, 0.0, np.pi / 2]])
+    goal = np.array([0.0, 0.0, 0.05, np.cos(0.5), 0, 0, np.sin(0.5)])
+    qref = np.concatenate([np.zeros(7), [0.1, 0.1, 0.1]])
+    w = _W()
+    w.fall_radius = fall_radius
+    run, term = oracle.mpc_cost(d, q, goal, qref, w)
+    cq = np.sin(0.25) ** 2
+    tips = np.sum((p - [0.14, 0, 0]) ** 2) + np.sum((p - [-0.1, -0.03, 0.04]) ** 2)
+    joint = 2 * (np.pi / 2 - 0.1) ** 2 + 0.1 ** 2
+    exp = 2.0 * cq + 3.0 * (0.01 + 0.02 + 0.02) + 10.0 * tips + 0.05 * joint + (5.0 if fall_radius == 0.02 else 0.0)
+    assert run == pytest.approx(exp, rel=1e-13)
+    assert term == pytest.approx(50.0 * (0.01 ** 2 + 0.02 ** 2 + 0.02 ** 2) + 20.0 * cq, rel=1e-13)
+
+
 def test_exact_impedance_worked_step(oracle):
     """The exact diagonal impedance of Sec. III-B (trace_mode 2), by hand: a 1 kg sphere
     (r = 0.05, I = 1e-3) at rest 2 mm into the plane, 4 facets, mu = 0.5.  Facet j's row is
@@ -174,7 +354,8 @@ def _hinge(axis, ipos, rng=(0.0, 0.0), fl=0.0, inertia=(1e-3, 1e-3, 2e-3)):
 
 @pytest.mark.parametrize("q0,v_exp", [(-0.51, 0.019), (0.51, -0.019), (0.2, 0.0)])
 def test_joint_limit_closed_form(oracle, q0, v_exp):
-    """A limit is a one-row constraint with the contact impulse law (reading 15).  A vertical
+    """A limit is a one-row constraint with the contact impulse law (the paper names joint limits
+    in its system model without a formula; this is the reading taken).  A vertical
     hinge (no gravity torque) at rest, 1 cm past its limit [-0.5, 0.5]: r(|gap|) = r_max = 0.95,
     M = r/(1-r) / (M~^-1)_kk, lambda dt = k M |gap|, so v+ = (M~^-1)_kk lambda dt =
     k r/(1-r) |gap| = 0.1 * 19 * 0.01 = 0.019 rad/s whatever the inertia; inside the range
@@ -187,7 +368,7 @@ def test_joint_limit_closed_form(oracle, q0, v_exp):
 
 @pytest.mark.parametrize("fl", [2.0, 0.5])
 def test_dry_joint_friction_closed_form(oracle, fl):
-    """Dry joint friction (reading 15): a horizontal hinge (axis y) with its 1 kg centre of mass
+    """Dry joint friction (the stopping impulse -v_s / (M~^-1)_kk clamped to +-f dt): a horizontal hinge (axis y) with its 1 kg centre of mass
     10 cm out along x carries the gravity torque 0.981 N m about M = 1e-3 + 1 * 0.1^2 = 0.011.
     The stopping impulse -v_s M = -0.981 dt fits inside +-fl dt for fl = 2 (the joint holds:
     v+ = 0); for fl = 0.5 it saturates: v+ = (0.981 - 0.5) dt / 0.011."""
