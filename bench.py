@@ -40,6 +40,10 @@ METRIC = "world-steps/s & contacts resolved/s vs contacts/world at 1 GB300; % of
 # whose digest is given; reported as null once the sources differ from the ones measured.
 STEP_SOURCES = ("cf_step.cu", "cf_device_math.cuh", "cf_internal.cuh")
 TRAFFIC = {"digest": "0b1c8021b8903d67", "bytes": 92.41e6}
+# warp instructions executed (smsp__inst_executed.sum) by one such launch, same capture rules:
+# the step's issue-rate bound is this count over the issue ceiling (SMs x 4 schedulers x 1
+# warp instruction per cycle x the SM clock sampled during the timed region)
+INSTRUCTIONS = {"digest": None, "warp_instructions": None}
 
 
 def step_digest():
@@ -61,7 +65,7 @@ def parse():
     ap.add_argument("--bodies", type=int, default=BODIES)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10, help="end-to-end steps (0: skip, for profiles)")
+    ap.add_argument("--e2e-steps", type=int, default=100, help="end-to-end steps (0: skip, for profiles)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--episode", type=int, default=EPISODE, help="episode length (the timed steps are its last)")
     ap.add_argument("--warps", type=int, default=0,
@@ -70,6 +74,8 @@ def parse():
                     help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
     ap.add_argument("--mlp-only", action="store_true",
                     help="time only the proposal MLP's tensor-core training step and forward pass (for profiles)")
+    ap.add_argument("--only", default=None, choices=sorted(ONLY),
+                    help="run one of the other workloads alone and print its JSON (for profiles)")
     ap.add_argument("--impedance", default="heuristic", choices=sorted(IMPEDANCE_MODES),
                     help="impedance mode of the headline workload (the exact and learned forms of Sec. III-B; "
                          "for profiles)")
@@ -330,59 +336,63 @@ def mlp_throughput(batch=16384, reps=20):
             "peak_source": src}
 
 
-def run_extras(rank):
-    """The other workloads, each timed with CUDA events after warm-up (reported beside the headline):
-    mixed batches of uneven worlds in one persistent launch, the hand adjoint, an MPPI tick."""
+def _timed(fn, reps):
     import torch
-    from paper_2603_12185_gb300 import autograd as AG
-    from paper_2603_12185_gb300 import comfree as CF
-    from paper_2603_12185_gb300 import mppi as MP
-    from paper_2603_12185_gb300 import scenes as S
-    out = {}
-
-    def timed(fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
         fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
-    # small case: 64 worlds x 8 spheres on a plane, 500 steps, one launch per step and one
-    # launch for all 500 steps (the kernel keeps the worlds in shared memory across steps)
+
+def extra_spheres(rank):
+    """Small case: 64 worlds x 8 spheres on a plane, 500 steps, one launch per step, one launch
+    for all 500 steps (the kernel keeps the worlds in shared memory across steps), and 100
+    one-step launches replayed from one CUDA graph."""
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import scenes as S
     sb = S.make_spheres_on_plane(64, seed=R.rank_seed(1900, rank))
     _, b = CF.from_scenes(sb)
-    ms1 = timed(lambda: b.step(sb.dt, 1), 500)
-    ms500 = timed(lambda: b.step(sb.dt, 500), 3)
-    g = b.graph(sb.dt, 1, repeat=100)         # 100 one-step launches in one CUDA graph
-    ms_graph = timed(g.replay, 5) / 100
-    out["spheres_64x8"] = {"world_steps_per_s": 64 / (ms1 / 1e3), "ms_per_step": ms1,
-                           "world_steps_per_s_graph": 64 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
-                           "world_steps_per_s_500_steps_per_launch": 64 * 500 / (ms500 / 1e3)}
-    del g
-    del b
-    # uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step
+    ms1 = _timed(lambda: b.step(sb.dt, 1), 500)
+    ms500 = _timed(lambda: b.step(sb.dt, 500), 3)
+    g = b.graph(sb.dt, 1, repeat=100)
+    ms_graph = _timed(g.replay, 5) / 100
+    return {"world_steps_per_s": 64 / (ms1 / 1e3), "ms_per_step": ms1,
+            "world_steps_per_s_graph": 64 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
+            "world_steps_per_s_500_steps_per_launch": 64 * 500 / (ms500 / 1e3)}
+
+
+def extra_mixed(rank):
+    """Uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step,
+    eager and from a CUDA graph of ten launches."""
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import scenes as S
     sb = S.make_mixed(8192, seed=R.rank_seed(2000, rank))
     _, b = CF.from_scenes(sb)
     chosen = b.autotune(sb.dt)
     for _ in range(300):
         b.step(sb.dt, 1)
-    ms = timed(lambda: b.step(sb.dt, 1), 20)
+    ms = _timed(lambda: b.step(sb.dt, 1), 20)
     c = b.contact_counts()
-    g = b.graph(sb.dt, 1, repeat=10)          # ten one-step launches captured in one CUDA graph
-    ms_graph = timed(g.replay, 5) / 10
-    out["mixed_8192"] = {"world_steps_per_s": 8192 / (ms / 1e3), "ms_per_step": ms,
-                         "world_steps_per_s_graph": 8192 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
-                         "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
-    del g
-    del b
-    # exact diagonal impedance (trace_mode 2) and the learned impedance (trace_mode 3, fitted
-    # here to exact-mode contacts of other piles) against the heuristic: one step of the jammed
-    # 4096 x 256 pile from the same state (events around the step only)
+    g = b.graph(sb.dt, 1, repeat=10)
+    ms_graph = _timed(g.replay, 5) / 10
+    return {"world_steps_per_s": 8192 / (ms / 1e3), "ms_per_step": ms,
+            "world_steps_per_s_graph": 8192 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
+            "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
+
+
+def extra_impedance(rank):
+    """The exact diagonal impedance (trace_mode 2) and the learned impedance (trace_mode 3,
+    fitted here to exact-mode contacts of other piles) against the heuristic: one step of the
+    jammed 4096 x 256 pile from the same state (events around the step only)."""
     import dataclasses
+    import torch
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import scenes as S
     net, fit = learned_impedance(rank, evaluate=True)
     sbj = S.make_pile(4096, 256, seed=R.rank_seed(1950, rank), jammed=True)
     res = {"learned_fit": fit}
@@ -407,8 +417,17 @@ def run_extras(rank):
         res[{0: "heuristic", 2: "exact", 3: "learned"}[mode]] = {
             "ms_per_step": float(np.mean(ts)), "contacts_per_world": float(bj.contact_counts().mean())}
         del bj
-    out["impedance_modes_jammed_pile_4096x256"] = res
-    # adjoint: 1024 hand worlds, 100 steps, checkpoints every 10
+    return res
+
+
+HAND_BYTES = (23 + 22) * 4 * 2 + 16 * 4   # q, v read + written, 16 torques read, per world-step
+
+
+def extra_adjoint(rank, reps=3):
+    """The hand adjoint: 1024 worlds, 100 steps, checkpoints every 10 (forward + reverse)."""
+    import torch
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import scenes as S
     T = 100
     sb = S.make_hand(1024, seed=R.rank_seed(2100, rank))
     _, b = CF.from_scenes(sb, max_ctrl_steps=T, grad_steps=T, grad_ckpt=10)
@@ -423,46 +442,111 @@ def run_extras(rank):
         b.set_ctrl(tau.reshape(-1))
         b.step_grad(T, sb.dt, gq, gv)
 
-    ms = timed(grad_once, 3)
-    out["adjoint_hand_1024x100"] = {"ms": ms, "world_steps_per_s": 1024 * T / (ms / 1e3)}
-    del b
-    # one MPPI control tick: 1024 rollouts x 32 steps of 5 ms with the fused cost
+    ms = _timed(grad_once, reps)
+    return {"ms": ms, "world_steps_per_s": 1024 * T / (ms / 1e3)}
+
+
+def extra_hand_rollout(rank, reps=10):
+    """Forward hand rollouts alone (the MPPI tick's simulation): 1024 hand worlds x 32 steps of
+    5 ms in one launch with the fused cost, 2 warps per world; world-steps/s and the fraction of
+    HBM bandwidth at (23 + 22) floats of state read and written plus 16 torques per world-step."""
+    import torch
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
     t = S.hand_template(0)
     params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
     ctl = MP.HandMPPI(t, params, N=1024)
     sbh = S.make_hand(1, seed=R.rank_seed(2200, rank))
     ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
-    ms = timed(ctl.tick, 10)
-    out["mppi_tick_1024x32"] = {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
-    out["proposal_mlp_49x256x1024"] = mlp_throughput()
-    return out
+    ctl.tick()
+    ctl.rollouts.set_ctrl(torch.randn(32 * 1024 * 16, device="cuda") * 0.3)
+    q, v = ctl.rollouts.get_state()
+    q, v = q.clone(), v.clone()
+
+    def roll():
+        ctl.rollouts.set_state(q, v)
+        ctl.rollouts.step(0.005, 32)
+
+    ms = _timed(roll, reps)
+    ws = 1024 * 32 / (ms / 1e3)
+    pk, src = peaks()
+    gbs = ws * HAND_BYTES / 1e9
+    return {"ms_per_launch": ms, "world_steps_per_s": ws, "bytes_per_world_step": HAND_BYTES,
+            "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "peak_source": src}
 
 
-def cpu_baseline(nbody, rank, budget_s=20.0, reference=False):
-    """The FP64 oracle as it stands, OpenMP over the host cores, on a bounded sample: the first
-    worlds of the same seeded workload, from their initial state."""
+def extra_mppi(rank, reps=10):
+    """One MPPI control tick: 1024 rollouts x 32 steps of 5 ms with the fused cost and the update."""
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    t = S.hand_template(0)
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    ctl = MP.HandMPPI(t, params, N=1024)
+    sbh = S.make_hand(1, seed=R.rank_seed(2200, rank))
+    ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
+    ms = _timed(ctl.tick, reps)
+    return {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
+
+
+EXTRAS = {"spheres_64x8": extra_spheres, "mixed_8192": extra_mixed,
+          "impedance_modes_jammed_pile_4096x256": extra_impedance, "adjoint_hand_1024x100": extra_adjoint,
+          "hand_rollout_1024x32": extra_hand_rollout, "mppi_tick_1024x32": extra_mppi,
+          "proposal_mlp_49x256x1024": lambda rank: mlp_throughput()}
+ONLY = {"spheres": "spheres_64x8", "mixed": "mixed_8192", "impedance": "impedance_modes_jammed_pile_4096x256",
+        "adjoint": "adjoint_hand_1024x100", "hand": "hand_rollout_1024x32", "mppi": "mppi_tick_1024x32",
+        "mlp": "proposal_mlp_49x256x1024"}
+
+
+def run_extras(rank):
+    """The other workloads, each timed with CUDA events after warm-up (reported beside the headline):
+    the small case, mixed batches of uneven worlds in one persistent launch, the impedance modes,
+    the hand adjoint, hand rollouts, an MPPI tick and the proposal MLP."""
+    return {k: fn(rank) for k, fn in EXTRAS.items()}
+
+
+def cpu_baseline(nbody, rank, budget_s=40.0, min_steps=100):
+    """The FP64 oracle as it stands, OpenMP over the host cores, on a bounded sample of the timed
+    workload.  For the 256-body headline: the 16 sampled worlds (0, 256, ..., 3840) of the same
+    seeded 4096-world batch at step 800 of the episode, where the GPU's timed window starts
+    (advanced there by the oracle alone, oracle/late_states.py), stepped from there for at least
+    min_steps steps or until the budget is spent.  Other body counts: the same batch's first
+    worlds from their initial state (the sample says so)."""
     from oracle import oracle as O
     from paper_2603_12185_gb300 import scenes as S
-    nw = 16
-    sb = S.make_pile(nw, nbody, seed=R.rank_seed(1000, rank))
+    late = None
+    if nbody == 256 and rank == 0:
+        from oracle import late_states as LS
+        if os.path.exists(LS.PATH):
+            late = LS
+    if late is not None:
+        sb, _ = late.load()
+        start = late.STEPS
+        where = (f"worlds {late.WORLDS[0]}, {late.WORLDS[1]}, ..., {late.WORLDS[-1]} of the seeded 4096 x {nbody} "
+                 f"batch from their step-{start} state (the start of the GPU's timed window; oracle-advanced)")
+    else:
+        sb = S.make_pile(16, nbody, seed=R.rank_seed(1000, rank))
+        start = 0
+        where = f"16 worlds x {nbody} bodies of the same seeded workload from the initial state"
+    nw = sb.nworld
     runner = O.BatchRunner([sb.world(w) for w in range(nw)], sb.params)
-    q = np.concatenate([np.asarray(x, np.float64) for x in sb.q0])
-    v = np.concatenate([np.asarray(x, np.float64) for x in sb.v0])
+    q = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.q0])
+    v = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.v0])
     cores = O.max_threads()
-    steps, done, t_total, contacts = 2, 0, 0.0, 0
-    while t_total < budget_s:
+    chunk, done, t_total, contacts = 5, 0, 0.0, 0
+    while done < min_steps or t_total < budget_s / 4:
         t0 = time.perf_counter()
-        c = runner.run(q, v, sb.dt, steps)
+        c = runner.run(q, v, sb.dt, chunk)
         t_total += time.perf_counter() - t0
-        done += steps
+        done += chunk
         contacts += int(c.sum())
-        if t_total < budget_s / 4:
-            steps *= 2
+        if t_total > budget_s:
+            break
     ws = nw * done / t_total
     return dict(value=ws, unit="world-steps/s", cores=cores, kind="oracle",
-                sample=f"{nw} worlds x {nbody} bodies of the same seeded workload, steps 1..{done} of the episode "
-                       f"from the initial state (FP64, {cores} OpenMP threads, {t_total:.1f} s)",
-                contacts_per_s=contacts / t_total, seconds=t_total, steps=done)
+                sample=f"{where}, steps {start + 1}..{start + done} (FP64, {cores} OpenMP threads, {t_total:.1f} s)",
+                contacts_per_s=contacts / t_total, contacts_per_world=contacts / (nw * done), seconds=t_total,
+                steps=done)
 
 
 def main():
@@ -470,18 +554,26 @@ def main():
     if args.mlp_only:
         print(json.dumps({"proposal_mlp_49x256x1024": mlp_throughput()}), flush=True)
         return
+    if args.only:
+        import torch
+        from paper_2603_12185_gb300 import build
+        build.build()
+        torch.cuda.set_device(0)
+        name = ONLY[args.only]
+        print(json.dumps({name: EXTRAS[name](0)}), flush=True)
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:
             return
-        cb = cpu_baseline(args.bodies, 0, budget_s=max(10.0, min(60.0, 3.0 * (args.steps + args.warmup))),
-                          reference=True)
+        cb = cpu_baseline(args.bodies, 0, budget_s=max(10.0, min(60.0, 3.0 * (args.steps + args.warmup))))
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "world-steps/s",
                 "n_gpus": args.gpus, "steps": cb["steps"], "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / cb["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"pile_{args.worlds}x{args.bodies}", "worlds_sampled": 16,
                            "bodies_per_world": args.bodies},
-                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "contacts_per_s": cb["contacts_per_s"], "contacts_per_world": cb["contacts_per_world"],
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "contacts_per_s")},
                 "e2e": {"value": cb["value"], "unit": "world-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -531,8 +623,16 @@ def main():
     launch_s = res["per_launch_ms"] / 1e3
     alg_bytes = res["worlds"] * res["bodies"] * BYTES_PER_BODY
     achieved = alg_bytes / launch_s / 1e9
+    issue = None
+    if INSTRUCTIONS["digest"] == step_digest() and args.impedance == "heuristic":
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
+        ceiling = sms * 4 * mhz * 1e6
+        issue = {"warp_instructions_per_launch": INSTRUCTIONS["warp_instructions"],
+                 "ceiling_warp_instructions_per_s": ceiling, "sm_mhz": mhz,
+                 "frac": INSTRUCTIONS["warp_instructions"] / (ceiling * launch_s)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"],
+                "frac": achieved / pk["hbm_gbs"], "issue": issue,
                 "traffic": (TRAFFIC["bytes"] if TRAFFIC["digest"] == step_digest() and args.impedance == "heuristic"
                             else None),
                 "kernel_digest": step_digest(), "peak_source": src,
@@ -561,7 +661,8 @@ def main():
         line["other_workloads"] = run_extras(rank)
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(args.bodies, rank)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "contacts_per_s",
+                                                    "contacts_per_world")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

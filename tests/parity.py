@@ -99,3 +99,30 @@ def geom_offsets(sb):
         off.append(acc)
         acc += t.ngeom
     return off
+
+
+def oracle_fp32_state(sb, nsteps, snapshots):
+    """The FP64 oracle stepped one step at a time with its state rounded to FP32 after every step
+    (as the GPU stores it in HBM between steps), worlds spread over the host cores.  Returns
+    {step: (qs, vs)} at the requested snapshot steps, plus the same for the plain FP64 oracle:
+    (fp32_state, fp64).  Where the two part by more than the comparison's tolerance, the
+    dynamics themselves amplify FP32 rounding of the state past it, and no FP32 implementation
+    can be held to that tolerance there."""
+    runner = O.BatchRunner([sb.world(w) for w in range(sb.nworld)], sb.params)
+    nq, nv = len(sb.q0[0]), len(sb.v0[0])
+    q32 = np.concatenate([f32(x) for x in sb.q0])
+    v32 = np.concatenate([f32(x) for x in sb.v0])
+    q64, v64 = q32.copy(), v32.copy()
+    out32, out64 = {}, {}
+    done = 0
+    for s in sorted(snapshots):
+        runner.run(q64, v64, sb.dt, s - done)
+        for _ in range(s - done):
+            runner.run(q32, v32, sb.dt, 1)
+            q32[:] = q32.astype(np.float32)
+            v32[:] = v32.astype(np.float32)
+        done = s
+        split = lambda a, n: [a[i * n:(i + 1) * n].copy() for i in range(sb.nworld)]
+        out32[s] = (split(q32, nq), split(v32, nv))
+        out64[s] = (split(q64, nq), split(v64, nv))
+    return out32, out64

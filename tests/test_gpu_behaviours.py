@@ -43,7 +43,7 @@ def run(d, params, q0, v0, dt, steps, every):
 def test_torsional_friction_decays_spin_monotonically():
     """A sphere on a vertical hinge, pressed 2 mm into the floor, spinning about the normal.
     The contact point lies on the hinge axis, so no DoF moves it translationally and the
-    trace of reading 3 is zero; the test uses the per-body 1/m impedance (trace_mode 1)."""
+    translational point-Jacobian trace tr(J M~^-1 J^T) that M(phi) divides by is zero; the test uses the per-body 1/m impedance (trace_mode 1)."""
     finals = {}
     for mu_tor in (0.002, 0.01):
         d = Wd.world([dict(parent=-1, jnt=S.HINGE, pos=(0, 0, 0.048), axis=(0, 0, 1), mass=1.0,

@@ -1,5 +1,5 @@
 """MPPI on the batched step: the kernels' update against its closed form, the fused cost against
-a host recomputation, and an end-to-end control run that lowers the task cost."""
+the oracle's MPC cost, and an end-to-end control run that lowers the task cost."""
 import numpy as np
 import pytest
 import torch
@@ -56,9 +56,9 @@ def test_sampling_clips_and_mixes_the_proposal():
     np.testing.assert_array_equal(c.transpose(1, 0, 2), s)
 
 
-def test_fused_cost_matches_host_recomputation():
+def test_fused_cost_matches_the_oracle():
     """One-step rollouts: the running cost of the initial state plus the terminal cost of the final
-    state, recomputed on the host from the oracle's kinematics."""
+    state (Sec. V, Eq. mpc), against the oracle's cost of the same states."""
     from oracle import oracle as O
     from paper_2603_12185_gb300 import comfree as CF
     from paper_2603_12185_gb300 import mppi as MP
@@ -76,27 +76,54 @@ def test_fused_cost_matches_host_recomputation():
     qT, _ = b.get_state()
     gpu = costs.cpu().numpy()
     qT = qT.cpu().numpy().reshape(W, 23)
-    t = sb.templates[0]
     g = goals[0].cpu().numpy().astype(np.float64)
+    qr = qref.cpu().numpy().astype(np.float64).reshape(W, 23)
     for w in range(W):
         q = np.asarray(q0[w * 23:(w + 1) * 23], np.float64)
-        _, _, poses = O.dynamics(sb.world(w), (0, 0, -9.81), q, np.zeros(22))
-        dq = g[3:] @ q[3:7]
-        c = cd.w_quat * (1 - dq * dq) + cd.w_pos * np.abs(q[:3] - g[:3]).sum()
-        tips = 0.0
-        for f in range(4):
-            b_ = 1 + 4 * f + 3
-            R = poses[b_, 3:12].reshape(3, 3)
-            L = 2 * t.geom_size[2 + 4 * f + 3][1]
-            tip = poses[b_, :3] + R @ np.array([0, 0, L])
-            tips += np.sum((q[:3] - tip) ** 2)
-        c += cd.w_contact * tips + cd.w_joint * np.sum((q[7:] - (q[7:] + 0.05)) ** 2)
-        if np.hypot(*(q[:2] - g[:2])) > cd.fall_radius:
-            c += cd.w_fallen
-        qt = qT[w]
-        dqt = g[3:] @ qt[3:7]
-        c += cd.term_pos * np.sum((qt[:3] - g[:3]) ** 2) + cd.term_quat * (1 - dqt * dqt)
-        assert gpu[w] == pytest.approx(c, rel=2e-4, abs=1e-5)
+        run, _ = O.mpc_cost(sb.world(w), q, g, qr[w], cd, cost_body=cd.body)
+        _, term = O.mpc_cost(sb.world(w), qT[w].astype(np.float64), g, qr[w], cd, cost_body=cd.body)
+        assert gpu[w] == pytest.approx(run + term, rel=2e-4, abs=1e-5)
+
+
+def test_fused_cost_over_a_horizon_matches_the_oracle():
+    """An 8-step controlled rollout: J = sum_t c(x_t) + V(x_8) on the GPU against the oracle's
+    cost along the oracle's own trajectory (the states agree to the 1e-3 horizon tolerance, so
+    the cost is compared at 1e-3)."""
+    from oracle import oracle as O
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    import parity as PT
+    H = 8
+    sb = S.make_hand(4, seed=9)
+    rng = np.random.default_rng(3)
+    nu = sb.templates[0].nu
+    ctrl = [rng.normal(0.0, 0.05, (H, nu)).astype(np.float32) for _ in range(sb.nworld)]
+    _, b = CF.from_scenes(sb, max_ctrl_steps=H)
+    seq = np.concatenate([c for c in ctrl], axis=1)
+    b.set_ctrl(torch.from_numpy(np.ascontiguousarray(seq)).cuda().reshape(-1))
+    W = sb.nworld
+    goal = np.array([0.0, 0.01, 0.04, 0.9238795, 0.0, 0.0, 0.3826834])
+    goals = torch.from_numpy(np.tile(goal.astype(np.float32), (W, 1))).cuda()
+    q0, _ = CF.flatten_state(sb)
+    qref = torch.from_numpy(q0.copy()).cuda()
+    costs = torch.zeros(W, device="cuda")
+    cd = MP.default_cost()
+    b.set_cost(cd, goals, qref, costs)
+    b.step(sb.dt, H)
+    gpu = costs.cpu().numpy()
+    g = goals[0].cpu().numpy().astype(np.float64)
+    for w in range(W):
+        d = sb.world(w)
+        q, v = PT.f32(sb.q0[w]), PT.f32(sb.v0[w])
+        qr = PT.f32(q0[w * 23:(w + 1) * 23])
+        J = 0.0
+        for t in range(H):
+            J += O.mpc_cost(d, q, g, qr, cd, cost_body=cd.body)[0]
+            tau = PT.tau_full(sb, w, ctrl[w][t])[None]
+            q, v, _ = O.step(d, sb.params, sb.dt, 1, q, v, tau)
+        J += O.mpc_cost(d, q, g, qr, cd, cost_body=cd.body)[1]
+        assert gpu[w] == pytest.approx(J, rel=1e-3)
 
 
 def test_mppi_lowers_the_task_cost():

@@ -1,4 +1,5 @@
-"""Cylinders and ellipsoids (reading 17) on the GPU against the FP64 oracle: piles where they
+"""Cylinders and ellipsoids (ellipsoid-plane by the support point, cylinder-plane by three rim
+points per cap, sphere-cylinder by the closest point of the solid) on the GPU against the FP64 oracle: piles where they
 replace part of the spheres and capsules (plane and sphere-cylinder contacts), and an
 articulated scene with a free cylinder, a free ellipsoid and a hinged sphere."""
 import numpy as np
