@@ -61,8 +61,8 @@ typedef enum {
 #define CF_GEOM_CAPSULE 2 /* size[0] = radius, size[1] = half length along local z      */
 #define CF_GEOM_BOX 3     /* size = half extents                                        */
 #define CF_GEOM_CYLINDER 4  /* size[0] = radius, size[1] = half length along local z; touches
-                               planes and spheres only (reading 17)                         */
-#define CF_GEOM_ELLIPSOID 5 /* size = semi-axes; touches planes only (reading 17)          */
+                               planes and spheres only                                      */
+#define CF_GEOM_ELLIPSOID 5 /* size = semi-axes; touches planes only                        */
 #define CF_JOINT_FREE 0
 #define CF_JOINT_HINGE 1
 
@@ -220,8 +220,12 @@ cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
  * cotangents of the final state dL_dqT[total_nq], dL_dvT[total_nv] (device), writes
  * dL_dq0[total_nq], dL_dv0[total_nv] and dL_dtau[T][total_nu] (device).  The forward state is
  * recomputed from checkpoints every grad_ckpt steps.  The batch state is left at the rollout's
- * final state.  Errors: CF_ERR_UNSUPPORTED for scenes outside the differentiable set (hinge
- * trees and free bodies with sphere/capsule/box/plane geoms), CF_ERR_INVALID_ARGUMENT. */
+ * final state.  The differentiable set: hinge trees (with joint limits and dry joint friction)
+ * and free bodies with sphere/capsule/box/plane geoms, the heuristic impedance (trace_mode 0
+ * or 1); at a kink (a facet or a limit turning on, friction saturating, a narrowphase branch)
+ * the derivative is that of the branch the state selects.  Errors: CF_ERR_UNSUPPORTED for
+ * scenes outside that set (piles, box-box pairs, cylinders, ellipsoids, trace_mode 2 or 3),
+ * CF_ERR_INVALID_ARGUMENT. */
 cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                        float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);
 
@@ -258,6 +262,9 @@ cf_status cf_mppi_update(int32_t N, int32_t H, int32_t nu, const float* costs, c
                          float* mean, float* stats, void* stream);
 /* receding horizon: mean[h] <- mean[h + 1] for h < H - 1 */
 cf_status cf_mppi_shift(int32_t H, int32_t nu, float* mean, void* stream);
+/* out[n] = base[n] + scale * delta[n] (device; out may alias base): a plan corrected by the
+ * learned proposal's output (the learned warm start).  n = 0 does nothing. */
+cf_status cf_mppi_blend(int32_t n, const float* base, const float* delta, float scale, float* out, void* stream);
 /* copy one world's state into W back-to-back worlds */
 cf_status cf_broadcast_state(const float* q0, const float* v0, int32_t nq, int32_t nv, int32_t W, float* q, float* v,
                              void* stream);
@@ -300,17 +307,30 @@ cf_status cf_mlp_status(cf_mlp* mlp, void* stream);
  * memory pool, a real-time loop that must not touch the allocator).  The paper has no
  * counterpart: this is a deployment convenience around the same step kernel.
  *   q[n_worlds * nq], v[n_worlds * nv]  device, the worlds' states back to back (in/out);
- *   world_params                        device, nullable; pile scenes only: one 8-float block
- *                                       per body per world, as in cf_batch_create;
+ *   world_params                        device, nullable, 16-byte aligned (the kernel reads it
+ *                                       as float4; a misaligned pointer is refused with
+ *                                       CF_ERR_INVALID_ARGUMENT before any launch); pile scenes
+ *                                       only: one 8-float block per body per world, as in
+ *                                       cf_batch_create.  The blocks are not validated (a zero
+ *                                       mass or an unknown geom type gives undefined results).
+ *                                       A pile call with world_params always runs the kernel
+ *                                       instantiation with every optional feature compiled in
+ *                                       (the blocks may hold boxes), which is slower than the
+ *                                       batch path's pile kernel; without world_params the
+ *                                       scene's own bodies and geoms are used;
  *   contacts                            device, nullable; per-world contact counts (out).
  * Controls are zero.  All scratch (scene templates, world records, work units, work-queue
  * counters, flags) lives in a file-scope 2 MiB device array that every GPU loading the library
  * holds until the process exits; at most 16384 worlds per call, and the model plus the worlds'
  * records must fit the array (CF_ERR_INVALID_ARGUMENT otherwise).  The first call on a device
- * looks up the array's device address (make that first call before any stream capture).  Each
- * call clears the counters it needs; every call shares the one array, so calls that overlap on
- * the GPU (other streams, other host threads) race and must be serialised by the caller.
- * Device-side flags (non-finite state) are not reported by this entry point. */
+ * looks up the array's device address (make that first call before any stream capture).
+ * CF_ERR_UNSUPPORTED while `stream` is being captured: each call uploads its records from host
+ * memory that lives only for the call.  Each call clears the counters it needs; every call
+ * shares the one array, so calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Device-side flags are not reported by this entry
+ * point: neither CF_FLAG_NONFINITE (a non-finite state) nor CF_FLAG_RANGE (a velocity change
+ * beyond the scatter's fixed-point range, after which the velocities are wrong); a caller that
+ * needs them uses the batch path (cf_batch_status). */
 cf_status cf_step_noalloc(const cf_model* model, int32_t scene, int32_t n_worlds, float* q, float* v,
                           const float* world_params, float dt, int32_t nsteps, int32_t* contacts, void* stream);
 

@@ -1,9 +1,11 @@
 // Host runtime of libcomfree: model validation, batch layout inside the caller's device
 // workspace, work-unit scheduling, autotuning, and the C entry points of comfree.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -232,6 +234,15 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
     }
     sc.boxbox = (nbox >= 2 || nextra > 0) ? 1 : 0;
   }
+  {
+    // one friction triple for every geom: the pair friction (the larger of two equal values)
+    // is that triple, and the kernels need not look the geoms up per contact
+    sc.mu_uniform = d.ngeom > 0 ? 1 : 0;
+    for (int g = 0; g < d.ngeom; ++g)
+      for (int k = 0; k < 3; ++k)
+        if (G[g].mu[k] != G[0].mu[k]) sc.mu_uniform = 0;
+    for (int k = 0; k < 3; ++k) sc.mu[k] = d.ngeom > 0 ? G[0].mu[k] : 0.f;
+  }
   sc.npair = (int)m->pairs.size() - sc.pair0;
   sc.nq = nq;
   sc.nv = nv;
@@ -311,6 +322,8 @@ struct cf_batch {
   std::vector<int> warps;      // per scene
   std::vector<DUnit> units;    // all worlds
   int nunits = 0;
+  int group_warps = 0;         // warps per world when every unit shares it and grouping is on, else 0
+  bool allow_group = false;    // warp groups pull worlds by themselves (cf_batch_autotune decides)
   size_t smem_all = 0;
   bool artic_all = false;
   bool ext = false;  // needs the extended kernel: possible box-box contacts, cylinders or ellipsoids
@@ -435,8 +448,34 @@ static void build_units(const cf_batch* b, const std::vector<int>& list, std::ve
     }
   }
   std::stable_sort(tmp.begin(), tmp.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+  // lay the worlds out in the units' (cost) order, so that order[] itself is that order
+  std::vector<int> sorted;
+  sorted.reserve(order.size());
   units.clear();
-  for (auto& t : tmp) units.push_back(t.second);
+  for (auto& t : tmp) {
+    DUnit u = t.second;
+    const int first = (int)sorted.size();
+    for (int k = 0; k < u.count; ++k) sorted.push_back(order[u.first + k]);
+    u.first = first;
+    units.push_back(u);
+  }
+  order.swap(sorted);
+}
+
+// warps per world shared by every unit (the launch can then let each warp group pull worlds
+// by itself), else 0
+static int uniform_warps(const std::vector<DUnit>& units) {
+  if (units.empty()) return 0;
+  for (const DUnit& u : units)
+    if (u.warps != units[0].warps) return 0;
+  return units[0].warps;
+}
+
+// the work list of a launch: units for CTAs, or (uniform warps, grouping on) the worlds for
+// warp groups
+static void set_work(StepParams& p, const std::vector<DUnit>& units, size_t nworld, bool allow_group) {
+  p.group_warps = allow_group ? uniform_warps(units) : 0;
+  p.nunits = p.group_warps > 0 ? (int)nworld : (int)units.size();
 }
 
 static cf_status upload_units(cf_batch* b, cudaStream_t st) {
@@ -444,6 +483,7 @@ static cf_status upload_units(cf_batch* b, cudaStream_t st) {
   for (int w = 0; w < b->W; ++w) all[w] = w;
   build_units(b, all, order, b->units, b->smem_all, b->artic_all);
   b->nunits = (int)b->units.size();
+  b->group_warps = b->allow_group ? uniform_warps(b->units) : 0;
   if (b->smem_all > step_max_dynamic_smem())
     return fail(CF_ERR_UNSUPPORTED, "a work unit needs %zu bytes of shared memory", b->smem_all);
   CF_CUDA(cudaMemcpyAsync(b->ws + b->L.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st),
@@ -660,7 +700,8 @@ static StepParams make_params(const cf_batch* b, float dt, int nsteps) {
   p.worlds = b->at<DWorld>(b->L.worlds);
   p.units = b->at<DUnit>(b->L.units);
   p.order = b->at<int>(b->L.order);
-  p.nunits = b->nunits;
+  p.group_warps = b->group_warps;
+  p.nunits = b->group_warps > 0 ? b->W : b->nunits;
   p.q = b->at<float>(b->L.q);
   p.v = b->at<float>(b->L.v);
   p.wparam = b->at<float>(b->L.wparam);
@@ -710,7 +751,8 @@ static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t sme
     return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode 3 needs an impedance network (cf_batch_set_impedance_net)");
   const int var = b->ext ? kExtVariant : (b->imp ? kImpVariant : b->variant);
   int per_sm = step_max_blocks_per_sm(artic, var, smem);
-  int grid = std::min(p.nunits, std::max(1, b->num_sms * per_sm));
+  const int per_block = p.group_warps > 0 ? kWarps / p.group_warps : 1;
+  int grid = std::min((p.nunits + per_block - 1) / per_block, std::max(1, b->num_sms * per_sm));
   cudaError_t e = launch_step(p, artic, var, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "step launch");
   return CF_OK;
@@ -741,7 +783,7 @@ extern "C" cf_status cf_step(cf_batch* b, const int32_t* worlds, int32_t n, floa
           "upload subset");
   p.order = b->at<int>(b->L.sub_order);
   p.units = b->at<DUnit>(b->L.sub_units);
-  p.nunits = (int)units.size();
+  set_work(p, units, order.size(), b->allow_group);
   cf_status st = launch(b, p, artic, smem, s);
   // the host lists above are pageable: the copies completed before cudaMemcpyAsync returned
   return st;
@@ -836,7 +878,7 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
       StepParams p = make_params(b, dt, 1);
       p.order = b->at<int>(b->L.sub_order);
       p.units = b->at<DUnit>(b->L.sub_units);
-      p.nunits = (int)units.size();
+      set_work(p, units, order.size(), b->allow_group);
       cf_status st = launch(b, p, artic, smem, s);  // warm-up
       if (st != CF_OK) return st;
       cudaEventRecord(e0, s);
@@ -879,6 +921,28 @@ extern "C" cf_status cf_batch_autotune(cf_batch* b, float dt, void* stream, int3
         if (ms < best) { best = ms; best_v = var; }
       }
       b->variant = best_v;
+    }
+    // CTAs pulling units of worlds, or (every world of the batch with the same warps) warp
+    // groups pulling worlds by themselves: timed on the whole batch
+    if (uniform_warps(b->units) > 0) {
+      float best = 3e38f;
+      bool best_g = false;
+      for (int g = 0; g < 2; ++g) {
+        b->allow_group = g == 1;
+        st = upload_units(b, s);
+        if (st != CF_OK) return st;
+        StepParams p = make_params(b, dt, 1);
+        st = launch(b, p, b->artic_all, b->smem_all, s);
+        if (st != CF_OK) return st;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch(b, p, b->artic_all, b->smem_all, s);
+        cudaEventRecord(e1, s);
+        CF_CUDA(cudaEventSynchronize(e1), "autotune timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_g = g == 1; }
+      }
+      b->allow_group = best_g;
     }
   }
   cudaEventDestroy(e0);
@@ -985,9 +1049,9 @@ extern "C" const char* cf_last_error(void) { return g_err.c_str(); }
 // ---------------------------------------------------------------------------------------
 // Stepping without any device allocation.
 //
-// Some callers cannot allocate device memory at all: code running inside a memory pool or a
-// graph whose allocations are fixed up front, plugins of hosts that own the CUDA context and
-// forbid cudaMalloc, or real-time loops that must not touch the allocator.  cf_step_noalloc
+// Some callers cannot allocate device memory at all: code running inside a memory pool whose
+// allocations are fixed up front, plugins of hosts that own the CUDA context and forbid
+// cudaMalloc, or real-time loops that must not touch the allocator.  cf_step_noalloc
 // serves them: the caller passes its state and parameters, and every piece of scratch the
 // step needs (scene templates, world records, work units, the work-queue counters, flags)
 // lives in one file-scope device array of fixed size that each GPU loading the library keeps
@@ -998,7 +1062,7 @@ constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;  // 2 MiB per device
 constexpr int kNoAllocMaxWorlds = 16384;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 constexpr int kNoAllocMaxDevices = 64;
-char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::atomic<char*> g_noalloc_ptr[kNoAllocMaxDevices];  // static storage: starts as null
 }  // namespace
 
 extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n_worlds, float* q, float* v,
@@ -1014,6 +1078,17 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
   const DScene& sc = m->scenes[scene];
   if (!sc.pile && world_params) return fail(CF_ERR_INVALID_ARGUMENT, "per-world parameters need a pile scene");
   if (m->trace_mode == 3) return fail(CF_ERR_UNSUPPORTED, "cf_step_noalloc has no impedance network (trace_mode 3)");
+  // the pile kernel reads the parameter blocks as float4
+  if (reinterpret_cast<uintptr_t>(world_params) & 15)
+    return fail(CF_ERR_INVALID_ARGUMENT, "world_params must be 16-byte aligned");
+  // the uploads below come from host memory local to this call: a graph could not replay them
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(CF_ERR_UNSUPPORTED, "cf_step_noalloc does not run while its stream is being captured");
+  }
 
   // layout of the static scratch for this call
   size_t off = 0;
@@ -1042,13 +1117,14 @@ extern "C" cf_status cf_step_noalloc(const cf_model* m, int32_t scene, int32_t n
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CF_ERR_UNSUPPORTED, "device ordinal %d", dev);
-  if (!g_noalloc_ptr[dev]) {
+  char* base = g_noalloc_ptr[dev].load();
+  if (!base) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
-    g_noalloc_ptr[dev] = static_cast<char*>(ptr);
+    base = static_cast<char*>(ptr);
+    g_noalloc_ptr[dev].store(base);  // every thread that looks it up finds the same address
   }
-  char* base = g_noalloc_ptr[dev];
 
   // host-side records: worlds of one scene packed back to back, units of kWarps / warps worlds
   const int warps = default_warps(sc);

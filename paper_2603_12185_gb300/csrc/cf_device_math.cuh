@@ -656,11 +656,12 @@ __device__ __forceinline__ float from_fix(unsigned long long a) {
 // to an unsigned one, by native 32-bit shared atomics.  Integer sums do not depend on the
 // order, so the result is deterministic; the quantum is 2^-36 and the sum is exact while
 // |sum| < 2^15 and a word receives fewer than 4096 contributions.
-__device__ __forceinline__ void fix2_add(int* hi, unsigned* lo, float x, bool& range) {
-  range |= !(fabsf(x) <= kFix2Range);
-  x = fminf(fmaxf(x, -kFix2Range), kFix2Range) * kFix2Hi;
+__device__ __forceinline__ void fix2_add(int* hi, unsigned* lo, float x) {
+  // the caller has checked |x| <= kFix2Range (else it raises CF_FLAG_RANGE and the result is
+  // void); the float-to-integer conversions saturate, so no value faults here
+  x *= kFix2Hi;
   const float h = floorf(x);
-  atomicAdd(hi, (int)h);
+  atomicAdd(hi, __float2int_rz(h));
   atomicAdd(lo, __float2uint_rn((x - h) * kFix2Lo));
 }
 __device__ __forceinline__ float fix2_get(int hi, unsigned lo) {

@@ -36,6 +36,8 @@ struct alignas(16) DScene {
   int body0, geom0, tree0, pair0;
   int npair, plane0, maxdepth, joints;  // joints: some hinge is limited or has dry friction
   int boxbox, pad1, pad2, pad3;         // boxbox: needs the extended kernel (two boxes, cylinders, ellipsoids)
+  float mu[3];                          // every geom's friction coefficients, when they are all equal:
+  int mu_uniform;                       // then every pair's friction is mu (else 0)
 };
 
 struct alignas(16) DBody {
@@ -77,7 +79,9 @@ struct StepParams {
   const DWorld* worlds;
   const DUnit* units;
   const int* order;
-  int nunits;
+  int nunits;                // units (group_warps 0) or worlds in order (group_warps > 0)
+  int group_warps;           // > 0: every world takes this many warps and each warp group
+                             // pulls worlds from order[] by itself; 0: CTAs pull units
   float* q;
   float* v;
   const float* wparam;

@@ -8,6 +8,7 @@
 //      (articulated worlds) or of M^-1 J~^T lambda (free bodies) into fixed-point shared
 //      accumulators                                    (Eqs. tilde_defs, cf_wrench; Kernels II-III)
 //   C. v+ = v_s + M~^-1 p, semi-implicit Euler                      (Eq. vel_correction; Kernel IV)
+#include <atomic>
 #include <cstdio>
 
 #include "cf_device_math.cuh"
@@ -68,7 +69,7 @@ struct PileView {
   float4* rec;              // [N][7] body records, see kRec*
   const DGeom* geoms;       // the scene's geoms: body i carries geom i (friction coefficients)
   float* planes;            // [NP][12]
-  int* queue;               // [warps][kQueue] broadphase candidates
+  int* queue;               // [warps][kCandQueue] broadphase candidates
   float* cq;                // [warps][8][kQueue] contacts: p.xyz, n.xyz, phi, code
   int* count;               // [0] contacts, [1] captured
 };
@@ -82,6 +83,7 @@ constexpr int kBodyMask = 0xfff;
 
 __device__ __forceinline__ int code_with_sub(int code, int sub) { return code | (sub << 12); }
 constexpr int kCqWords = 8;
+constexpr int kCandQueue = 128;  // per-warp broadphase candidate queue of a pile world (entries)
 
 // Body record of a pile body, 7 float4 (one vector load each):
 //   0: linear velocity (v, then v_s, then v+), 1/m      1: body-frame angular velocity, 1/I_0
@@ -91,7 +93,7 @@ constexpr int kRec = 7;
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
   // accumulators (12 words/body) + position (4) + record (28) + planes + both queues + counters
-  size_t words = (size_t)N * 12 + (size_t)N * 32 + (size_t)NP * 12 + (size_t)warps * kQueue * (1 + kCqWords) + 4;
+  size_t words = (size_t)N * 12 + (size_t)N * 32 + (size_t)NP * 12 + (size_t)warps * (kQueue * kCqWords + kCandQueue) + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -105,7 +107,7 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   s.rec = reinterpret_cast<float4*>(f); f += 4 * (size_t)kRec * N;
   s.planes = f; f += (size_t)NP * 12;
   s.cq = f; f += (size_t)warps * kQueue * kCqWords;
-  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
+  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kCandQueue;
   s.count = reinterpret_cast<int*>(f);
   return s;
 }
@@ -140,12 +142,17 @@ __device__ __forceinline__ void pile_apply(PileView& s, int i, float im, f3 ii, 
   const f3 ang = mulT(R, cross(r, f) + m);
   const float sm = sign * im;
   const int N = s.N;
-  fix2_add(s.acch + i, s.accl + i, sm * f.x, range);
-  fix2_add(s.acch + N + i, s.accl + N + i, sm * f.y, range);
-  fix2_add(s.acch + 2 * N + i, s.accl + 2 * N + i, sm * f.z, range);
-  fix2_add(s.acch + 3 * N + i, s.accl + 3 * N + i, sign * ii.x * ang.x, range);
-  fix2_add(s.acch + 4 * N + i, s.accl + 4 * N + i, sign * ii.y * ang.y, range);
-  fix2_add(s.acch + 5 * N + i, s.accl + 5 * N + i, sign * ii.z * ang.z, range);
+  const float d0 = sm * f.x, d1 = sm * f.y, d2 = sm * f.z;
+  const float d3 = sign * ii.x * ang.x, d4 = sign * ii.y * ang.y, d5 = sign * ii.z * ang.z;
+  // a contribution beyond the fixed-point range (or NaN) voids the step: CF_FLAG_RANGE
+  range |= !(fabsf(d0) <= kFix2Range) || !(fabsf(d1) <= kFix2Range) || !(fabsf(d2) <= kFix2Range) ||
+           !(fabsf(d3) <= kFix2Range) || !(fabsf(d4) <= kFix2Range) || !(fabsf(d5) <= kFix2Range);
+  fix2_add(s.acch + i, s.accl + i, d0);
+  fix2_add(s.acch + N + i, s.accl + N + i, d1);
+  fix2_add(s.acch + 2 * N + i, s.accl + 2 * N + i, d2);
+  fix2_add(s.acch + 3 * N + i, s.accl + 3 * N + i, d3);
+  fix2_add(s.acch + 4 * N + i, s.accl + 4 * N + i, d4);
+  fix2_add(s.acch + 5 * N + i, s.accl + 5 * N + i, d5);
 }
 
 // Solve one queued contact: frame, M(phi), facet impulses, scatter onto both bodies
@@ -164,17 +171,21 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   const int b = plane ? -1 : (bc & kBodyMask);
   const int sub = (bc >> 12) & 7;
   f3 px = mk3(0.f, 0.f, 0.f);
-  float mub0, mub1, mub2;
+  // pair friction: the larger of the two geoms' coefficients (one triple for uniform scenes)
+  float mu_t = sc.mu[0], mu_tor = sc.mu[1], mu_rol = sc.mu[2];
   int gb;
   if (plane) {
     const float* pl = s.planes + 12 * (bc & kPlaneMask);
     px = mk3(pl[6], pl[7], pl[8]);
-    mub0 = pl[9]; mub1 = pl[10]; mub2 = pl[11];
+    if (!sc.mu_uniform) { mu_t = pl[9]; mu_tor = pl[10]; mu_rol = pl[11]; }
     gb = sc.geom0 + sc.plane0 + (bc & kPlaneMask);
   } else {
-    const float* mb = s.geoms[b].mu;
-    mub0 = mb[0]; mub1 = mb[1]; mub2 = mb[2];
+    if (!sc.mu_uniform) { const float* mb = s.geoms[b].mu; mu_t = mb[0]; mu_tor = mb[1]; mu_rol = mb[2]; }
     gb = sc.geom0 + b;
+  }
+  if (!sc.mu_uniform) {
+    const float* ma = s.geoms[a].mu;
+    mu_t = fmaxf(ma[0], mu_t); mu_tor = fmaxf(ma[1], mu_tor); mu_rol = fmaxf(ma[2], mu_rol);
   }
   f3 t1, t2;
   contact_frame(k.n, plane, px, t1, t2);
@@ -203,9 +214,6 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
     iib = mk3(wb4.w, s.rec[kRec * b + 2].w, s.rec[kRec * b + 3].w);
     tr += pile_trace(P, imb, iib, Rb, rb);
   }
-  // pair friction: the larger of the two geoms' coefficients
-  const float* ma = s.geoms[a].mu;
-  const float mu_t = fmaxf(ma[0], mub0), mu_tor = fmaxf(ma[1], mub1), mu_rol = fmaxf(ma[2], mub2);
   float mphi = 0.f, target = 0.f;
   float w[6];
   ImpFeat feat;
@@ -237,7 +245,6 @@ __device__ __forceinline__ void pile_solve(const StepParams& P, PileView& s, con
   f3 m = w[3] * k.n + w[4] * t1 + w[5] * t2;
   pile_apply(s, a, ima, iia, Ra, ra, f, m, 1.f, range);
   if (b >= 0) pile_apply(s, b, imb, iib, Rb, rb, f, m, -1.f, range);
-  atomicAdd(s.count, 1);
   if (P.capture_cap > 0)
     capture_contact(P, world, s.count, sc.geom0 + a, gb, sub, k.phi, k.p, k.n, w[0], mphi, imp ? feat.x[1] : 0.f,
                     imp ? feat.x[2] : 0.f, target, b < 0);
@@ -253,6 +260,10 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
   const f3 cb = mk3(pb4.x, pb4.y, pb4.z);
   Raw k;
   k.phi = 3.0e38f;
+  // sphere and capsule pairs reduce to two spheres at the closest points of their axes
+  // (a sphere's axis is its centre), met by one sphere-sphere test after the branches
+  f3 sa = ca, sb = cb;
+  bool spheres = false;
   if ((kExt & kExtGeo) && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
     if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER)
       k = nf_sphere_cylinder(ca, pile_rad(s, a), cb, pile_R(s, b), pile_rad(s, b), pile_hl(s, b), true);
@@ -263,7 +274,9 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
     f3 p1 = ca - pile_hl(s, a) * ua, q1 = ca + pile_hl(s, a) * ua, p2 = cb - pile_hl(s, b) * ub, q2 = cb + pile_hl(s, b) * ub;
     float ss, tt;
     nf_segments(p1, q1, p2, q2, ss, tt);
-    k = nf_sphere_sphere(p1 + ss * (q1 - p1), pile_rad(s, a), p2 + tt * (q2 - p2), pile_rad(s, b));
+    sa = p1 + ss * (q1 - p1);
+    sb = p2 + tt * (q2 - p2);
+    spheres = true;
   } else if (ta != CF_GEOM_BOX && tb != CF_GEOM_BOX) {  // sphere-sphere, capsule-sphere, sphere-capsule
     const bool capA = ta == CF_GEOM_CAPSULE;
     const int ic = capA ? a : b;
@@ -272,7 +285,9 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
     const f3 u = pile_axis(s, ic);
     const float t = fminf(fmaxf(dot(cs - cc, u), -h), h);
     const f3 pc = cc + t * u;
-    k = nf_sphere_sphere(capA ? pc : ca, pile_rad(s, a), capA ? cb : pc, pile_rad(s, b));
+    if (capA) sa = pc;
+    else sb = pc;
+    spheres = true;
   } else if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertex `sub`
     if (kExt & kExtGeo)
       k = nf_box_box(ca, pile_R(s, a), mk3(pile_rad(s, a), pile_hl(s, a), pile_s2(s, a)), cb, pile_R(s, b), mk3(pile_rad(s, b), pile_hl(s, b), pile_s2(s, b)),
@@ -291,6 +306,7 @@ __device__ __forceinline__ Raw pile_narrow_pair(const PileView& s, int a, int b,
       k = nf_sphere_box(co + t * u, pile_rad(s, io), cbx, Rbx, hs, !boxA);
     }
   }
+  if (spheres) k = nf_sphere_sphere(sa, pile_rad(s, a), sb, pile_rad(s, b));
   return k;
 }
 
@@ -337,6 +353,23 @@ __device__ __forceinline__ bool pile_narrow(const StepParams& P, const PileView&
     k = pile_narrow_pair<kExt>(s, a, bc, ca, sub);
   }
   return k.phi < P.margin;
+}
+
+// cos(th) and sin(th) / |w| for th = |w| dt / 2, from w2 = |w|^2: for th^2 <= 0.25 the Taylor
+// series of cos and of sin(th) / th to the th^8 term (truncation below th^10 / 10! < 3e-10),
+// with no square root or division; beyond it, sincosf of th
+__device__ __forceinline__ void exp_half_angle(float w2, float dt, float& c, float& s_over_w) {
+  const float h = 0.5f * dt;
+  const float x = h * h * w2;  // th^2
+  if (x <= 0.25f) {
+    c = 1.f + x * (-1.f / 2.f + x * (1.f / 24.f + x * (-1.f / 720.f + x * (1.f / 40320.f))));
+    s_over_w = h * (1.f + x * (-1.f / 6.f + x * (1.f / 120.f + x * (-1.f / 5040.f + x * (1.f / 362880.f)))));
+  } else {
+    const float wn = sqrtf(w2);
+    float sn;
+    sincosf(h * wn, &sn, &c);
+    s_over_w = sn / wn;
+  }
 }
 
 template <int kExt>
@@ -392,7 +425,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     o[6] = pl.x.x; o[7] = pl.x.y; o[8] = pl.x.z; o[9] = pl.mu[0]; o[10] = pl.mu[1]; o[11] = pl.mu[2];
   }
   const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
-  int* queue = s.queue + wig * kQueue;
+  int* queue = s.queue + wig * kCandQueue;
   bool range = false;  // some velocity change left the scatter's range
 
   for (int step = 0; step < P.nsteps; ++step) {
@@ -407,7 +440,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       rc[3] = make_float4(R.m[3], R.m[4], R.m[5], ii2);
       rc[4] = make_float4(R.m[6], R.m[7], R.m[8], rc[4].w);
       float w0 = r1.x, w1 = r1.y, w2 = r1.z;
-      f3 gy = cross(mk3(w0, w1, w2), mk3(w0 / ii0, w1 / ii1, w2 / ii2));
+      f3 gy = cross(mk3(w0, w1, w2), mk3(__fdividef(w0, ii0), __fdividef(w1, ii1), __fdividef(w2, ii2)));
       rc[0] = make_float4(r0.x + g.x * dt, r0.y + g.y * dt, r0.z + g.z * dt, r0.w);
       rc[1] = make_float4(w0 - dt * gy.x * ii0, w1 - dt * gy.y * ii1, w2 - dt * gy.z * ii2, ii0);
 #pragma unroll
@@ -419,9 +452,10 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     // ---- B. broadphase -> candidate queue -> narrowphase -> contact queue -> solve ----
     // Body pairs are tested in 32 x 32 tiles (i-chunk <= j-chunk) dealt round-robin to the
     // warps: each lane holds body i in registers, the j loop is warp-uniform (broadcast loads)
-    // and the bounding-sphere hits of a tile are kept as a 32-bit mask per lane, then drained
-    // one candidate per lane per pass; after the tiles, every body is tested against each
-    // plane.  Candidates are compacted into the candidate queue; every 32 of them run the
+    // and the bounding-sphere hits of a tile are kept as a 32-bit mask per lane.  All hits of a
+    // tile are then compacted into the candidate queue at once (a warp prefix sum of the masks'
+    // popcounts gives each lane its slots); after the tiles, every body is tested against the
+    // planes, 32 planes per mask, and compacted the same way.  Every 32 queued candidates run the
     // narrowphase one per lane, whose hits are compacted into the contact queue; every 32
     // contacts are solved one per lane.  So the solve, the costly part, runs on full warps
     // although only a fraction of the candidates touch.
@@ -432,96 +466,111 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       const int nchunk = (N + 31) >> 5;
       const int ntile = nchunk * (nchunk + 1) / 2;
       int qn = 0, cn = 0;
-      int phase = 0;  // 0: body-pair tiles, 1: planes, 2: done
-      int t = wig - gwarps, j0 = 0, i0 = 0;  // the first pass of the loop advances to tile wig
-      unsigned hits = 0;  // this lane's remaining bounding-sphere hits in the current tile (bit k: body j0 + k)
-      int pl_i = 0, base = wig * 32;
-      // advance to this warp's next tile (from t) with any hit; test it one j per step (broadcast
-      // loads), keeping the hits as a bit mask per lane
-      auto next_tile = [&]() {
-        while (true) {
-          if (t >= ntile) { phase = NP > 0 ? 1 : 2; return; }
-          int rem = t, ci = 0;
-          while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
-          const int cj = ci + rem;
-          i0 = ci << 5;
-          const int i = i0 + lane;
-          float4 pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
-          if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
-          j0 = cj << 5;
-          const int kmax = min(32, N - j0);
-          unsigned m = 0;
-#pragma unroll 8
-          for (int k = 0; k < kmax; ++k) {
-            const float4 pj = s.pb[j0 + k];
-            const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
-            const float rr = pi4.w + pj.w;
-            if (dx * dx + dy * dy + dz * dz < rr * rr) m |= 1u << k;
-          }
-          hits = ci != cj ? m : (m & (0xfffffffeu << lane));  // diagonal tile: j > i only
-          if (__any_sync(0xffffffffu, hits != 0)) return;
-          t += gwarps;
-        }
-      };
+      int phase = 0;                        // 0: body-pair tiles, 1: planes, 2: all masks made
+      int t = wig, a0 = wig * 32, p0 = 0;   // next tile; next (32 bodies, 32 planes) plane block
+      unsigned m = 0;                       // this lane's hits not yet queued (bit k: j0 + k)
+      int code_hi = 0, j0 = 0, total = 0, excl = 0;
       while (true) {
-        int code = -1;
-        if (phase == 0) {
-          if (hits) {
-            code = ((i0 + lane) << 16) | (j0 + __ffs(hits) - 1);
-            hits &= hits - 1;
+        if (qn < 32) {
+          // make the next mask with any hit: a tile's bounding-sphere hits, or a block of planes
+          while (total == 0 && phase < 2) {
+            if (phase == 0) {
+              if (t >= ntile) { phase = NP > 0 ? 1 : 2; continue; }
+              int rem = t, ci = 0;
+              while (rem >= nchunk - ci) { rem -= nchunk - ci; ++ci; }
+              const int cj = ci + rem;
+              const int i = (ci << 5) + lane;
+              float4 pi4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.f);
+              if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
+              j0 = cj << 5;
+              const int kmax = min(32, N - j0);
+              m = 0;
+#pragma unroll 8
+              for (int k = 0; k < kmax; ++k) {
+                const float4 pj = s.pb[j0 + k];
+                const float dx = pi4.x - pj.x, dy = pi4.y - pj.y, dz = pi4.z - pj.z;
+                const float rr = pi4.w + pj.w;
+                if (dx * dx + dy * dy + dz * dz < rr * rr) m |= 1u << k;
+              }
+              if (ci == cj) m &= 0xfffffffeu << lane;  // diagonal tile: j > i only
+              code_hi = i << 16;
+              t += gwarps;
+            } else {
+              if (a0 >= N) { phase = 2; break; }
+              const int a = a0 + lane;
+              m = 0;
+              if (a < N) {
+                const float4 a4 = s.pb[a];
+                const int pn = min(32, NP - p0);
+                for (int k = 0; k < pn; ++k) {
+                  const float* pl = s.planes + 12 * (p0 + k);
+                  const float d = (a4.x - pl[0]) * pl[3] + (a4.y - pl[1]) * pl[4] + (a4.z - pl[2]) * pl[5];
+                  if (d < a4.w + margin) m |= 1u << k;
+                }
+              }
+              code_hi = (a << 16) | kPlaneBit;
+              j0 = p0;
+              p0 += 32;
+              if (p0 >= NP) { p0 = 0; a0 += T; }
+            }
+            const int cnt = __popc(m);
+            total = __reduce_add_sync(0xffffffffu, cnt);
+            int incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, incl, d);
+              if (lane >= d) incl += y;
+            }
+            excl = incl - cnt;
           }
-          if (!__any_sync(0xffffffffu, hits != 0)) {
-            t += gwarps;
-            next_tile();
-          }
-        } else if (phase == 1) {
-          const int a = base + lane;
-          if (a < N) {
-            const float* pl = s.planes + 12 * pl_i;
-            const float4 a4 = s.pb[a];
-            const float d = (a4.x - pl[0]) * pl[3] + (a4.y - pl[1]) * pl[4] + (a4.z - pl[2]) * pl[5];
-            if (d < a4.w + margin) code = (a << 16) | kPlaneBit | pl_i;
-          }
-          base += T;
-          if (base >= N) {
-            base = wig * 32;
-            if (++pl_i == NP) phase = 2;
+          // queue as many of the mask's hits as fit (each lane from its prefix-sum slot)
+          if (total > 0) {
+            const int room = kCandQueue - qn;
+            __syncwarp();
+            for (int k = excl; m && k < room; ++k) {
+              queue[qn + k] = code_hi | (j0 + __ffs(m) - 1);
+              m &= m - 1;
+            }
+            const int put = min(total, room);
+            qn += put;
+            total -= put;
+            excl = max(excl - room, 0);
           }
         }
-        const bool flush = phase == 2;
-        const unsigned m = __ballot_sync(0xffffffffu, code >= 0);
-        if (code >= 0) queue[qn + __popc(m & lt)] = code;
-        qn += __popc(m);
-        while (qn >= 32 || (flush && (qn > 0 || cn > 0))) {
-          __syncwarp();
-          const int nb = min(qn, 32);
-          const int mine = lane < nb ? queue[qn - nb + lane] : -1;
-          qn -= nb;
-          const int my_nsub = pile_nsub<kExt>(s, mine);
-          const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
-          for (int sub = 0; sub < nsub; ++sub) {
-            Raw kc;
-            const bool hit = sub < my_nsub && pile_narrow<kExt>(P, s, mine, sub, kc);
-            const unsigned hm = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-              const int slot = cn + __popc(hm & lt);
-              cq[slot] = kc.p.x; cq[kQueue + slot] = kc.p.y; cq[2 * kQueue + slot] = kc.p.z;
-              cq[3 * kQueue + slot] = kc.n.x; cq[4 * kQueue + slot] = kc.n.y; cq[5 * kQueue + slot] = kc.n.z;
-              cq[6 * kQueue + slot] = kc.phi;
-              cq[7 * kQueue + slot] = __int_as_float(code_with_sub(mine, sub));
-            }
-            cn += __popc(hm);
-            const bool last = flush && qn == 0 && sub + 1 == nsub;
-            while (cn >= 32 || (last && cn > 0)) {
-              __syncwarp();
-              const int ns = min(cn, 32);
-              if (lane < ns) pile_solve<kExt>(P, s, sc, world, cq, cn - ns + lane, range);
-              cn -= ns;
-              __syncwarp();
-            }
+        const bool fin = phase == 2 && total == 0;   // every candidate is queued
+        if (qn < 32 && !fin) continue;
+        // narrowphase of the top nb candidates, one per lane; contacts to the contact queue;
+        // every 32 contacts (at the end: all of them) solved one per lane
+        const int nb = min(qn, 32);
+        const bool last = fin && qn <= 32;
+        __syncwarp();
+        const int mine = lane < nb ? queue[qn - nb + lane] : -1;
+        qn -= nb;
+        const int my_nsub = pile_nsub<kExt>(s, mine);
+        const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
+        for (int sub = 0; sub < nsub; ++sub) {
+          Raw kc;
+          const bool hit = sub < my_nsub && pile_narrow<kExt>(P, s, mine, sub, kc);
+          const unsigned hm = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const int slot = cn + __popc(hm & lt);
+            cq[slot] = kc.p.x; cq[kQueue + slot] = kc.p.y; cq[2 * kQueue + slot] = kc.p.z;
+            cq[3 * kQueue + slot] = kc.n.x; cq[4 * kQueue + slot] = kc.n.y; cq[5 * kQueue + slot] = kc.n.z;
+            cq[6 * kQueue + slot] = kc.phi;
+            cq[7 * kQueue + slot] = __int_as_float(code_with_sub(mine, sub));
+          }
+          cn += __popc(hm);
+          const bool flush = last && sub + 1 == nsub;
+          while (cn >= 32 || (flush && cn > 0)) {
+            __syncwarp();
+            const int ns = min(cn, 32);
+            if (lane < ns) pile_solve<kExt>(P, s, sc, world, cq, cn - ns + lane, range);
+            if (lane == 0) atomicAdd(s.count, ns);  // contacts of the world
+            cn -= ns;
+            __syncwarp();
           }
         }
-        if (flush) break;
+        if (last) break;
       }
     }
     group_sync(gid, T);
@@ -539,14 +588,9 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
       rc[0] = make_float4(v0, v1, v2, r0.w);
       rc[1] = make_float4(w0, w1, w2, r1.w);
       s.pb[i].x += v0 * dt; s.pb[i].y += v1 * dt; s.pb[i].z += v2 * dt;
-      float wn = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
-      float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
-      if (wn > 0.f) {
-        float sn, cs;
-        sincosf(0.5f * wn * dt, &sn, &cs);
-        float sc_ = sn / wn;
-        dq0 = cs; dq1 = sc_ * w0; dq2 = sc_ * w1; dq3 = sc_ * w2;
-      }
+      float dq0, sh;  // the rotation by w dt: (cos th, sin th w / |w|), th = |w| dt / 2
+      exp_half_angle(w0 * w0 + w1 * w1 + w2 * w2, dt, dq0, sh);
+      const float dq1 = sh * w0, dq2 = sh * w1, dq3 = sh * w2;
       const float4 qq = rc[6];
       float a0 = qq.x, a1 = qq.y, a2 = qq.z, a3 = qq.w;
       float n0 = a0 * dq0 - a1 * dq1 - a2 * dq2 - a3 * dq3;
@@ -1369,25 +1413,45 @@ template <bool kArtic, int kMinBlocks, int kExt>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) step_kernel(StepParams P) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_unit;
+  __shared__ int s_world[kWarps];
   const int warp = threadIdx.x >> 5;
+  // group_warps > 0: every world takes that many warps, and each warp group pulls its next
+  // world as soon as it is done (worlds of one CTA do not wait for each other); otherwise the
+  // CTA pulls a unit of worlds and its warp groups take one world each
+  const bool grouped = P.group_warps > 0;
   for (;;) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(P.queue, 1);
-    __syncthreads();
-    const int u = s_unit;
-    if (u >= P.nunits) break;
-    const DUnit U = P.units[u];
-    const int gid = warp / U.warps;
-    if (gid < U.count) {
-      const int world = P.order[U.first + gid];
-      const DScene& sc = P.scenes[P.worlds[world].scene];
-      size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, U.warps)
-                           : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, U.warps);
-      float* base = smem + per * gid;
-      if (!kArtic || sc.pile) pile_world<kExt>(P, base, world, gid, U.warps);
-      else artic_world<kExt>(P, base, world, gid, U.warps);
+    int world = -1, gid = 0, warps = 0;
+    if (grouped) {
+      warps = P.group_warps;
+      gid = warp / warps;
+      const int tid = threadIdx.x - gid * 32 * warps;
+      if (tid == 0) s_world[gid] = atomicAdd(P.queue, 1);
+      group_sync(gid, 32 * warps);
+      const int k = s_world[gid];
+      group_sync(gid, 32 * warps);
+      if (k >= P.nunits) break;
+      world = P.order[k];
+    } else {
+      if (threadIdx.x == 0) s_unit = atomicAdd(P.queue, 1);
+      __syncthreads();
+      const int u = s_unit;
+      if (u >= P.nunits) break;
+      const DUnit U = P.units[u];
+      warps = U.warps;
+      gid = warp / warps;
+      if (gid < U.count) world = P.order[U.first + gid];
     }
-    __syncthreads();
+    if (world >= 0) {
+      const DScene& sc = P.scenes[P.worlds[world].scene];
+      size_t per = sc.pile ? pile_floats(sc.nbody, sc.nplane, warps)
+                           : artic_floats(sc.nbody, sc.ngeom, sc.nq, sc.nv, sc.ntree, warps);
+      float* base = smem + per * gid;
+      if (!kArtic || sc.pile) pile_world<kExt>(P, base, world, gid, warps);
+      else artic_world<kExt>(P, base, world, gid, warps);
+    }
+    if (!grouped) __syncthreads();
   }
+  __syncthreads();
   // the last CTA to finish resets the work counters for the next launch
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1415,7 +1479,10 @@ static const StepFn kVariants[kStepVariants] = {step_kernel<false, 2, 0>,
                                                 step_kernel<true, 2, 0>,
                                                 step_kernel<true, 2, kExtImp | kExtGeo>,
                                                 step_kernel<false, 2, kExtImp>};
-static size_t g_max_dyn[kStepVariants] = {0, 0, 0, 0, 0, 0};
+// the opted-in dynamic shared memory of each variant, per device (the attribute is set on the
+// current device; 0 = not yet set there)
+constexpr int kAttrDevices = 64;
+static std::atomic<size_t> g_max_dyn[kAttrDevices][kStepVariants];
 
 static int variant_index(bool artic, int variant) {
   if (variant == kExtVariant) return 4;
@@ -1423,11 +1490,17 @@ static int variant_index(bool artic, int variant) {
   return artic ? 3 : (variant < 0 ? 0 : (variant > 2 ? 2 : variant));
 }
 
-static cudaError_t ensure_attr(int vi) {
-  if (g_max_dyn[vi]) return cudaSuccess;
+static cudaError_t ensure_attr(int vi, size_t* out) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+  const size_t cached = g_max_dyn[dev][vi].load();
+  if (cached) {
+    *out = cached;
+    return cudaSuccess;
+  }
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kVariants[vi]);
   if (e != cudaSuccess) return e;
@@ -1435,31 +1508,36 @@ static cudaError_t ensure_attr(int vi) {
   e = cudaFuncSetAttribute(kVariants[vi], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   // prefer the largest shared-memory carveout so several CTAs fit per SM
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kVariants[vi], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess) g_max_dyn[vi] = dyn;
-  return e;
+  if (e != cudaSuccess) return e;
+  g_max_dyn[dev][vi].store(dyn);
+  *out = dyn;
+  return cudaSuccess;
 }
 
 size_t step_max_dynamic_smem() {
   size_t m = 0;
   for (int i = 0; i < kStepVariants; ++i) {
-    if (ensure_attr(i) != cudaSuccess) return 0;
-    m = (m == 0 || g_max_dyn[i] < m) ? g_max_dyn[i] : m;
+    size_t d = 0;
+    if (ensure_attr(i, &d) != cudaSuccess) return 0;
+    m = (m == 0 || d < m) ? d : m;
   }
   return m;
 }
 
 cudaError_t launch_step(const StepParams& p, bool artic, int variant, int grid, size_t smem, cudaStream_t stream) {
   int vi = variant_index(artic, variant);
-  cudaError_t e = ensure_attr(vi);
+  size_t dyn = 0;
+  cudaError_t e = ensure_attr(vi, &dyn);
   if (e != cudaSuccess) return e;
-  if (smem > g_max_dyn[vi]) return cudaErrorInvalidValue;
+  if (smem > dyn) return cudaErrorInvalidValue;
   kVariants[vi]<<<grid, kBlock, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
 int step_max_blocks_per_sm(bool artic, int variant, size_t smem) {
   int vi = variant_index(artic, variant);
-  if (ensure_attr(vi) != cudaSuccess) return 1;
+  size_t dyn = 0;
+  if (ensure_attr(vi, &dyn) != cudaSuccess) return 1;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kVariants[vi], kBlock, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
