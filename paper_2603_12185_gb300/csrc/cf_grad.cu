@@ -720,6 +720,44 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, S* q, S* v, const
     }
     if (cand) w1_pair(P, sc, w, ga, gb);
   }
+  // joint limits and dry joint friction, the step kernel's per-hinge impulses on the smooth
+  // prediction: a limit below the margin is a one-row constraint +-e_k with the facet law and
+  // M = r(|gap|) / (1 - r(|gap|)) / (M~^-1)_kk; friction applies the stopping impulse
+  // -v_s,k / (M~^-1)_kk clamped to +-frictionloss dt.  Derivatives follow the primal branch:
+  // an inactive limit or a saturated friction impulse passes none.
+  if (sc.joints) {
+    for (int t = 0; t < sc.ntree; ++t) {
+      const DTree& tr = P.trees[sc.tree0 + t];
+      if (tr.free) continue;
+      const S* mi = w.minv[t];
+      for (int j = 0; j < tr.nbody; ++j) {
+        const DBody& bd = B[tr.body0 + j];
+        if (!bd.limited && !(bd.frictionloss > 0.f)) continue;
+        const int k = bd.voff - tr.voff;
+        const S wkk = mi[k * kMaxTreeDof + k];
+        const S vsk = w.vs[bd.voff];
+        S pk(0.f);
+        if (bd.limited) {
+          const S qk = q[bd.qoff];
+          for (int side = 0; side < 2; ++side) {
+            const S gap = side ? S(bd.range[1]) - qk : qk - S(bd.range[0]);
+            if (!(val(gap) < P.margin)) continue;
+            const S sg(side ? -1.f : 1.f);
+            const S sv = sg * vsk;
+            const S r = w1_solimp(P, sabs(gap));
+            const S Mk = r / ((S(1.f) - r) * wkk);
+            const S lam = -S(P.k_user) * Mk * (sv * S(P.dt) + gap) - S(P.d_user) * Mk * sv;
+            if (val(lam) > 0.f) pk += sg * lam;
+          }
+        }
+        if (bd.frictionloss > 0.f) {
+          const S cap(bd.frictionloss * P.dt);
+          pk += sclamp(-vsk / wkk, -cap, cap);
+        }
+        w.p[bd.voff] += pk;
+      }
+    }
+  }
   const S dt(P.dt);
   for (int t = 0; t < sc.ntree; ++t) {
     const DTree& tr = P.trees[sc.tree0 + t];
@@ -794,7 +832,6 @@ __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float
 
 bool grad_scene_supported(const DScene& s, const char** why) {
   if (s.pile) { *why = "pile scenes are not differentiable here"; return false; }
-  if (s.joints) { *why = "the adjoint does not cover joint limits or dry joint friction"; return false; }
   if (s.boxbox) { *why = "the adjoint does not cover box-box pairs, cylinders or ellipsoids"; return false; }
   if (s.nbody > kG1Body || s.ngeom > kG1Geom || s.nq > kG1Q || s.nv > kG1V || s.ntree > kG1Tree) {
     *why = "scene exceeds the adjoint's per-world limits (24 bodies, 32 geoms, 48 q, 48 v, 8 trees)";

@@ -28,8 +28,13 @@ def _built():
     O.build()
 
 
-def _case(nworld, T, seed):
+def _case(nworld, T, seed, limited=False):
     sb = S.make_hand(nworld, seed=seed)
+    if limited:
+        # tight limits (abduction +-0.03 rad, flexion [0, 0.3] rad) and dry friction 0.005 N m on
+        # every hinge: limits and friction are active from the first steps
+        sb.templates[0] = S.with_joint_limits(sb.templates[0], abduction=(-0.03, 0.03), flexion=(0.0, 0.3),
+                                              frictionloss=0.005)
     rng = np.random.default_rng(seed + 100)
     tau = rng.normal(0, 0.05, (T, nworld, 16)).astype(np.float32)
     tp = np.array([0.0, 0.0, 0.05])
@@ -73,6 +78,21 @@ def _oracle(sb, w, tau_w, tp, tq, dv, dt_dir, h=1e-6):
     return L, dL, (Lp - Lm) / (2 * h)
 
 
+def _dual(sb, w, tau_w, tp, tq, coord):
+    """The oracle's forward-mode derivative of the loss along one unit direction: ("v", k) the
+    k-th hinge rate of v0, ("tau", s, k) the k-th torque at step s."""
+    T = tau_w.shape[0]
+    tau_full = np.zeros((T, 22))
+    tau_full[:, 6:] = tau_w
+    dv0, dtau = np.zeros(22), np.zeros((T, 22))
+    if coord[0] == "v":
+        dv0[6 + coord[1]] = 1.0
+    else:
+        dtau[coord[1], 6 + coord[2]] = 1.0
+    return O.rollout_loss_dir(sb.world(w), sb.params, sb.dt, PR.f32(sb.q0[w]), PR.f32(sb.v0[w]), tau_full,
+                              np.zeros(23), dv0, dtau, 0, tp, tq)[1]
+
+
 @pytest.mark.parametrize("T,ckpt,rtol", [(20, 5, 2e-3), (100, 10, 2e-2)])
 def test_adjoint_matches_oracle_and_fd(T, ckpt, rtol):
     nworld = 16
@@ -89,6 +109,75 @@ def test_adjoint_matches_oracle_and_fd(T, ckpt, rtol):
         assert g == pytest.approx(dLo, rel=rtol, abs=1e-6 * max(1.0, abs(dLo))), f"world {w}"
         checked += 1
     assert checked >= nworld // 2, f"only {checked} worlds checked ({excluded} excluded)"
+
+
+def test_adjoint_element_by_element():
+    """Every coordinate of dL/dv0 (the 16 hinge rates) and of dL/dtau at steps 0, 5 and 19 (16
+    torques each) at T = 20, each against the oracle's forward-mode dual along that unit
+    direction: 64 derivatives per world.  A coordinate passes within 1e-3 of its own size, with
+    an absolute floor of 1e-3 of the world's largest derivative (coordinates of fingers that do
+    not touch the cube are ~0 and carry only FP32 round-off).  A world is used only where the
+    oracle's dual agrees with its FP64 central difference along a random direction (the active
+    set does not change within +-h)."""
+    T, nworld, steps = 20, 10, (0, 5, 19)
+    sb, tau, tp, tq, dirs_v, dirs_t = _case(nworld, T, seed=13)
+    _, gv, gt = _gpu_grad(sb, tau, tp, tq, T, 5)
+    checked = uncoupled = 0
+    for w in range(nworld):
+        tw = tau[:, w].astype(np.float64)
+        _, dLo, fd = _oracle(sb, w, tw, tp, tq, dirs_v[w], dirs_t[:, w])
+        if abs(dLo - fd) > 1e-4 * max(abs(fd), 1e-6):
+            continue
+        ref, gpu = [], []
+        for k in range(16):
+            ref.append(_dual(sb, w, tw, tp, tq, ("v", k)))
+            gpu.append(gv[w, 6 + k])
+        for s_ in steps:
+            for k in range(16):
+                ref.append(_dual(sb, w, tw, tp, tq, ("tau", s_, k)))
+                gpu.append(gt[s_, w, k])
+        ref, gpu = np.array(ref), np.array(gpu)
+        scale = np.abs(ref).max()
+        if scale == 0.0:
+            # no finger reaches the cube within T steps: the loss does not depend on the hand
+            assert np.abs(gpu).max() == 0.0, f"world {w}: uncoupled, gpu {np.abs(gpu).max():.3e}"
+            uncoupled += 1
+            continue
+        bad = np.abs(gpu - ref) > 1e-3 * (np.abs(ref) + 1e-3 * scale)
+        assert not bad.any(), f"world {w}: coordinates {np.flatnonzero(bad)} gpu {gpu[bad]} oracle {ref[bad]}"
+        checked += 1
+    assert checked >= 4, f"only {checked} of {nworld} worlds checked ({uncoupled} uncoupled)"
+
+
+def test_adjoint_with_joint_limits_and_dry_friction():
+    """Hands whose hinges are limited and carry dry friction (the per-hinge constraint impulses
+    of the step): every coordinate of dL/dv0 and of dL/dtau at steps 0 and 9 at T = 10 against
+    the oracle's duals (1e-3 of the coordinate, floor 1e-3 of the world's largest), and the
+    random-direction derivative against FP64 central differences (worlds whose active set
+    changes within +-h excluded and counted)."""
+    T, nworld = 10, 8
+    sb, tau, tp, tq, dirs_v, dirs_t = _case(nworld, T, seed=17, limited=True)
+    assert sb.templates[0].body_frictionloss.max() > 0
+    _, gv, gt = _gpu_grad(sb, tau, tp, tq, T, 5)
+    checked = 0
+    for w in range(nworld):
+        tw = tau[:, w].astype(np.float64)
+        _, dLo, fd = _oracle(sb, w, tw, tp, tq, dirs_v[w], dirs_t[:, w])
+        if abs(dLo - fd) > 1e-4 * max(abs(fd), 1e-6):
+            continue
+        g = float(gv[w, 6:] @ dirs_v[w] + np.sum(gt[:, w] * dirs_t[:, w]))
+        assert g == pytest.approx(dLo, rel=2e-3, abs=1e-6 * max(1.0, abs(dLo))), f"world {w}"
+        ref = [_dual(sb, w, tw, tp, tq, ("v", k)) for k in range(16)]
+        gpu = list(gv[w, 6:])
+        for s_ in (0, T - 1):
+            ref += [_dual(sb, w, tw, tp, tq, ("tau", s_, k)) for k in range(16)]
+            gpu += list(gt[s_, w])
+        ref, gpu = np.array(ref), np.array(gpu)
+        scale = np.abs(ref).max()
+        bad = np.abs(gpu - ref) > 1e-3 * (np.abs(ref) + 1e-3 * scale)
+        assert not bad.any(), f"world {w}: coordinates {np.flatnonzero(bad)} gpu {gpu[bad]} oracle {ref[bad]}"
+        checked += 1
+    assert checked >= nworld // 2, f"only {checked} of {nworld} worlds checked"
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():

@@ -107,10 +107,12 @@ def test_limits_hold_the_fingers_back():
     assert e_free > 0.01 and e_lim < 0.5 * e_free, (e_lim, e_free)
 
 
-def test_adjoint_rejects_joint_constraints():
+def test_adjoint_runs_on_joint_constraints():
+    """The adjoint covers limited hinges and dry friction (gradients are checked against the
+    oracle in test_gpu_adjoint.py); here: it runs on limited hands and returns finite values."""
     sb = _limited_hand(2, seed=1)
     _, b = CF.from_scenes(sb, max_ctrl_steps=4, grad_steps=4, grad_ckpt=2)
-    gq = torch.zeros(b.total_nq, device="cuda")
+    gq = torch.ones(b.total_nq, device="cuda")
     gv = torch.zeros(b.total_nv, device="cuda")
-    with pytest.raises(CF.CfError, match="joint"):
-        b.step_grad(4, sb.dt, gq, gv)
+    dq0, dv0, dtau = b.step_grad(4, sb.dt, gq, gv)
+    assert torch.isfinite(dq0).all() and torch.isfinite(dv0).all() and torch.isfinite(dtau).all()
