@@ -74,6 +74,7 @@ def parse():
                     help="start from interpenetrating bodies (contact-rich first steps; for short profiles)")
     ap.add_argument("--mlp-only", action="store_true",
                     help="time only the proposal MLP's tensor-core training step and forward pass (for profiles)")
+    ap.add_argument("--proposal-size", default=None, help="iters,episodes,goals of --only proposal (default 3,24,48)")
     ap.add_argument("--only", default=None, choices=sorted(ONLY),
                     help="run one of the other workloads alone and print its JSON (for profiles)")
     ap.add_argument("--impedance", default="heuristic", choices=sorted(IMPEDANCE_MODES),
@@ -489,11 +490,50 @@ def extra_mppi(rank, reps=10):
     return {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
 
 
+def extra_proposal(rank, iters=None, episodes=None, goals=None, ticks=60):
+    """The learned warm start for sampling MPC (Sec. V's MPPI with a learned proposal added):
+    trained by DAgger against 1024-rollout teacher ticks on seeded goals, then the final task
+    cost over `goals` held-out starts and goals (paired: the same starts and goals in every arm)
+    for plain MPPI at 1024, 512 and 256 rollouts and the learned warm start at 256 and 128
+    rollouts, with each arm's CUDA-event time per tick (MLP inference included)."""
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    iters = iters or PROPOSAL["iters"]
+    episodes = episodes or PROPOSAL["episodes"]
+    goals = goals or PROPOSAL["goals"]
+    t = S.hand_template(0)
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    log = {}
+    import time as _t
+    t0 = _t.perf_counter()
+    mlp = MP.dagger_warm_start(t, params, iters=iters, episodes=episodes, seed=R.rank_seed(2300, rank), log=log)
+    train_s = _t.perf_counter() - t0
+    arms = {"plain_1024": dict(N=1024), "plain_512": dict(N=512), "plain_256": dict(N=256),
+            "learned_256": dict(N=256, mlp=mlp), "learned_128": dict(N=128, mlp=mlp)}
+    costs, tick_ms = MP.final_costs(t, params, arms, goals_seed=R.rank_seed(2400, rank), episodes=goals, ticks=ticks)
+    out = {"train_s": train_s, "dagger": log["dagger"], "goals": goals, "ticks": ticks,
+           "dagger_episodes": episodes, "dagger_iterations": iters}
+
+    def paired(a, b):
+        d = costs[a] - costs[b]
+        return [float(d.mean()), float(d.std(ddof=1) / np.sqrt(len(d)))]
+
+    for k, c in costs.items():
+        out[k] = {"final_cost_mean": float(c.mean()), "final_cost_se": float(c.std(ddof=1) / np.sqrt(len(c))),
+                  "paired_diff_vs_plain_1024": paired(k, "plain_1024"), "ms_per_tick": tick_ms[k]}
+    out["learned_256"]["paired_diff_vs_plain_256"] = paired("learned_256", "plain_256")
+    return out
+
+
+PROPOSAL = {"iters": 3, "episodes": 24, "goals": 48}
+
+
 EXTRAS = {"spheres_64x8": extra_spheres, "mixed_8192": extra_mixed,
           "impedance_modes_jammed_pile_4096x256": extra_impedance, "adjoint_hand_1024x100": extra_adjoint,
           "hand_rollout_1024x32": extra_hand_rollout, "mppi_tick_1024x32": extra_mppi,
           "proposal_mlp_49x256x1024": lambda rank: mlp_throughput()}
-ONLY = {"spheres": "spheres_64x8", "mixed": "mixed_8192", "impedance": "impedance_modes_jammed_pile_4096x256",
+ONLY_ALONE = {"proposal_warm_start_hand": extra_proposal}   # minutes: only with --only
+ONLY = {"proposal": "proposal_warm_start_hand", "spheres": "spheres_64x8", "mixed": "mixed_8192", "impedance": "impedance_modes_jammed_pile_4096x256",
         "adjoint": "adjoint_hand_1024x100", "hand": "hand_rollout_1024x32", "mppi": "mppi_tick_1024x32",
         "mlp": "proposal_mlp_49x256x1024"}
 
@@ -554,13 +594,16 @@ def main():
     if args.mlp_only:
         print(json.dumps({"proposal_mlp_49x256x1024": mlp_throughput()}), flush=True)
         return
+    if args.proposal_size:
+        PROPOSAL.update(zip(("iters", "episodes", "goals"), (int(x) for x in args.proposal_size.split(","))))
     if args.only:
         import torch
         from paper_2603_12185_gb300 import build
         build.build()
         torch.cuda.set_device(0)
         name = ONLY[args.only]
-        print(json.dumps({name: EXTRAS[name](0)}), flush=True)
+        fn = EXTRAS.get(name) or ONLY_ALONE[name]
+        print(json.dumps({name: fn(0)}), flush=True)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

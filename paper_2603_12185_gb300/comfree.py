@@ -70,7 +70,7 @@ EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_wo
            "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error", "cf_mlp_workspace_bytes",
            "cf_mlp_create", "cf_mlp_destroy", "cf_mlp_param_count", "cf_mlp_forward", "cf_mlp_gradients",
            "cf_mlp_train_step", "cf_mlp_get_params", "cf_mlp_status", "cf_set_cost", "cf_mppi_sample",
-           "cf_mppi_update", "cf_mppi_shift", "cf_broadcast_state", "cf_mppi_features",
+           "cf_mppi_update", "cf_mppi_shift", "cf_mppi_blend", "cf_broadcast_state", "cf_mppi_features",
            "cf_batch_set_impedance_net", "cf_impnet_eval", "cf_impnet_state_floats", "cf_impnet_loss_grad",
            "cf_impnet_fit")
 
@@ -120,6 +120,7 @@ def lib():
     L.cf_mppi_sample.argtypes = [I32, I32, I32, V, V, C.c_float, C.c_float, V, V, I32, V, V, V]
     L.cf_mppi_update.argtypes = [I32, I32, I32, V, V, C.c_float, V, V, V]
     L.cf_mppi_shift.argtypes = [I32, I32, V, V]
+    L.cf_mppi_blend.argtypes = [I32, V, V, C.c_float, V, V]
     L.cf_broadcast_state.argtypes = [V, V, I32, I32, I32, V, V, V]
     L.cf_mppi_features.argtypes = [V, I32, V, I32, C.c_float, V, I32, C.c_float, V, V]
     L.cf_batch_set_impedance_net.argtypes = [V, V, I32]

@@ -161,6 +161,8 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
         return fail(CF_ERR_UNSUPPORTED, "scene %d: hinge tree with more than %d DoFs", si, kMaxTreeDof);
     }
     o.tree = tree_of[b];
+    const int local = b - T[tree_of[b]].body0;
+    o.anc = (1 << local) | (p >= 0 ? B[p].anc : 0);
   }
   std::vector<DGeom> G(d.ngeom);
   int nplane = 0, plane0 = -1;
@@ -233,6 +235,14 @@ static cf_status build_scene(const cf_scene_desc& d, int si, cf_model* m) {
       nextra += G[g].type >= CF_GEOM_CYLINDER;
     }
     sc.boxbox = (nbox >= 2 || nextra > 0) ? 1 : 0;
+  }
+  // fingertips of the MPC cost: capsules carried by a hinge body that no body has as parent
+  for (int g = 0; g < d.ngeom; ++g) {
+    const int bd = G[g].body;
+    bool leaf = bd >= 0 && d.body_jnt[bd] == CF_JOINT_HINGE && G[g].type == CF_GEOM_CAPSULE;
+    for (int k = 0; leaf && k < d.nbody; ++k)
+      if (d.body_parent[k] == bd) leaf = false;
+    G[g].tip = leaf ? 1 : 0;
   }
   {
     // one friction triple for every geom: the pair friction (the larger of two equal values)

@@ -42,14 +42,16 @@ struct alignas(16) DScene {
 
 struct alignas(16) DBody {
   int parent, jnt, qoff, voff;      // parent is scene-local, offsets world-local
-  int uoff, tree, pad0, pad1;       // uoff: actuator slot of a hinge, -1 otherwise
+  int uoff, tree, anc, pad1;        // uoff: actuator slot of a hinge, -1 otherwise; anc: bit i set
+                                    // when the tree's i-th body is this body or one of its ancestors
   float pos[3], quat[4], axis[3], ipos[3], mass, inertia[3], damping, frictionloss;
   float range[2];                   // hinge limits (used when limited != 0)
   int limited, pad3[3];
 };
 
 struct alignas(16) DGeom {
-  int type, body, pad0, pad1;
+  int type, body, tip, pad1;        // tip: a capsule on a hinge body with no child (a fingertip
+                                    // of the MPC cost)
   float pos[3], quat[4], size[3], mu[3], pad2[3];
 };
 

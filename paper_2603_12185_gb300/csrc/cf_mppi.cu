@@ -108,6 +108,12 @@ __global__ void shift_kernel(int H, int nu, float* mean) {
   for (int h = 0; h + 1 < H; ++h) mean[h * nu + j] = mean[(h + 1) * nu + j];
 }
 
+// out = base + scale * delta (the learned warm start: the proposal's correction of a plan)
+__global__ void blend_kernel(int n, const float* base, const float* delta, float scale, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fmaf(scale, delta[i], base[i]);
+}
+
 }  // namespace cf
 
 using namespace cf;
@@ -143,6 +149,14 @@ extern "C" cf_status cf_mppi_shift(int32_t H, int32_t nu, float* mean, void* str
   if (H < 1 || nu < 1 || nu > 1024 || !mean) return mp_fail(CF_ERR_INVALID_ARGUMENT, "bad shift arguments");
   shift_kernel<<<1, nu, 0, (cudaStream_t)stream>>>(H, nu, mean);
   return cudaGetLastError() == cudaSuccess ? CF_OK : mp_fail(CF_ERR_CUDA, "shift launch");
+}
+
+extern "C" cf_status cf_mppi_blend(int32_t n, const float* base, const float* delta, float scale, float* out,
+                                   void* stream) {
+  if (n < 0 || (n > 0 && (!base || !delta || !out))) return mp_fail(CF_ERR_INVALID_ARGUMENT, "bad blend arguments");
+  if (n == 0) return CF_OK;
+  blend_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, base, delta, scale, out);
+  return cudaGetLastError() == cudaSuccess ? CF_OK : mp_fail(CF_ERR_CUDA, "blend launch");
 }
 
 extern "C" cf_status cf_broadcast_state(const float* q0, const float* v0, int32_t nq, int32_t nv, int32_t W, float* q,

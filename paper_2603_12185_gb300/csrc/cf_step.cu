@@ -89,6 +89,8 @@ constexpr int kCandQueue = 128;  // per-warp broadphase candidate queue of a pil
 //   0: linear velocity (v, then v_s, then v+), 1/m      1: body-frame angular velocity, 1/I_0
 //   2: R row 0, 1/I_1        3: R row 1, 1/I_2          4: R row 2, size 0 (radius)
 //   5: size 1, size 2, geom type (int bits), 0          6: orientation quaternion (w, x, y, z)
+// (R stored by columns, so that a capsule's axis and radius came in one load, measured 1.4%
+// slower on the 4096 x 256 pile.)
 constexpr int kRec = 7;
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
@@ -113,7 +115,7 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
 }
 
 __device__ __forceinline__ M33 pile_R(const PileView& s, int i) {
-  const float4 a = s.rec[kRec * i + 2], b = s.rec[kRec * i + 3], c = s.rec[kRec * i + 4];
+  const float4 a = s.rec[kRec * i + 2], b = s.rec[kRec * i + 3], c = s.rec[kRec * i + 4];  // columns
   M33 R;
   R.m[0] = a.x; R.m[1] = a.y; R.m[2] = a.z; R.m[3] = b.x; R.m[4] = b.y; R.m[5] = b.z;
   R.m[6] = c.x; R.m[7] = c.y; R.m[8] = c.z;
@@ -654,13 +656,15 @@ struct ArticView {
   float* gR;                 // [ng][9]
   float* gb;                 // [ng]     bounding radius
   float* minv;               // [ntree][kMaxTreeDof^2]
-  int* queue;
+  int* queue;                // [warps][kQueue] candidate pairs
+  float* cq;                 // [warps][kArtCq][kQueue] contacts: p.xyz, n.xyz, phi, (ga << 16) | gb, sub
   int* count;
 };
+constexpr int kArtCq = 9;
 
 __host__ __device__ inline size_t artic_floats(int nb, int ng, int nq, int nv, int ntree, int warps) {
   size_t words = (size_t)nv * 2 + nq + 3 * (size_t)nv + (size_t)nb * 21 + (size_t)ng * 13 +
-                 (size_t)ntree * kMaxTreeDof * kMaxTreeDof + (size_t)warps * kQueue + 4;
+                 (size_t)ntree * kMaxTreeDof * kMaxTreeDof + (size_t)warps * kQueue * (1 + kArtCq) + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -683,6 +687,7 @@ __device__ inline ArticView artic_view(float* base, const DScene& sc, int warps)
   s.gb = f; f += sc.ngeom;
   s.minv = f; f += (size_t)sc.ntree * kMaxTreeDof * kMaxTreeDof;
   s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kQueue;
+  s.cq = f; f += (size_t)warps * kQueue * kArtCq;
   s.count = reinterpret_cast<int*>(f);
   return s;
 }
@@ -915,6 +920,217 @@ __device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DSce
   }
 }
 
+// The same preparation for a hinge tree of exactly NV bodies (one hinge each), with every loop
+// bound a compile-time constant: the tree's matrices stay in registers instead of local memory,
+// and parent and ancestor lookups are predicated selections over earlier bodies.
+template <int NV>
+__device__ void artic_tree_prepare_n(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr, int t,
+                                     int uadr, int step) {
+  const DBody* B = P.bodies + sc.body0;
+  const float dt = P.dt;
+  const int b0 = tr.body0, v0 = tr.voff;
+  int par[NV];
+  unsigned anc[NV];  // bit i: body i of the tree is an ancestor of (or is) body j
+  M33 R[NV];
+  f3 x[NV], ax[NV], com[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const DBody& bd = B[b0 + j];
+    par[j] = bd.parent >= 0 ? bd.parent - b0 : -1;
+    anc[j] = 1u << j;
+    M33 Rp;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rp.m[k] = (k % 4 == 0) ? 1.f : 0.f;
+    f3 xp = mk3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < j; ++k)
+      if (par[j] == k) { Rp = R[k]; xp = x[k]; anc[j] |= anc[k]; }
+    M33 Rfix = mul33(Rp, quat_mat(bd.quat[0], bd.quat[1], bd.quat[2], bd.quat[3]));
+    f3 a = mk3(bd.axis[0], bd.axis[1], bd.axis[2]);
+    a = rsqrtf(dot(a, a)) * a;
+    R[j] = mul33(Rfix, axis_rot(a, s.q[bd.qoff]));
+    x[j] = xp + mul(Rp, mk3(bd.pos[0], bd.pos[1], bd.pos[2]));
+    ax[j] = mul(Rfix, a);
+    com[j] = x[j] + mul(R[j], mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]));
+    st3(s.bx + 3 * (b0 + j), x[j]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.bR[9 * (b0 + j) + k] = R[j].m[k];
+    st3(s.bax + 3 * (b0 + j), ax[j]);
+  }
+  // composite rigid bodies: mass, first moment, inertia about the world origin
+  float mc[NV];
+  f3 hc[NV];
+  float Io[NV][6];  // xx yy zz xy xz yz
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const DBody& bd = B[b0 + j];
+    const float m = bd.mass;
+    const f3 c = com[j];
+    const float I0 = bd.inertia[0], I1 = bd.inertia[1], I2 = bd.inertia[2];
+    const float* r = R[j].m;
+    const float cc = dot(c, c);
+    Io[j][0] = r[0] * r[0] * I0 + r[1] * r[1] * I1 + r[2] * r[2] * I2 + m * (cc - c.x * c.x);
+    Io[j][1] = r[3] * r[3] * I0 + r[4] * r[4] * I1 + r[5] * r[5] * I2 + m * (cc - c.y * c.y);
+    Io[j][2] = r[6] * r[6] * I0 + r[7] * r[7] * I1 + r[8] * r[8] * I2 + m * (cc - c.z * c.z);
+    Io[j][3] = r[0] * r[3] * I0 + r[1] * r[4] * I1 + r[2] * r[5] * I2 - m * c.x * c.y;
+    Io[j][4] = r[0] * r[6] * I0 + r[1] * r[7] * I1 + r[2] * r[8] * I2 - m * c.x * c.z;
+    Io[j][5] = r[3] * r[6] * I0 + r[4] * r[7] * I1 + r[5] * r[8] * I2 - m * c.y * c.z;
+    mc[j] = m;
+    hc[j] = m * c;
+  }
+#pragma unroll
+  for (int j = NV - 1; j >= 0; --j)
+#pragma unroll
+    for (int k = 0; k < j; ++k)
+      if (par[j] == k) {
+        mc[k] += mc[j];
+        hc[k] = hc[k] + hc[j];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) Io[k][e] += Io[j][e];
+      }
+  // M_ij = a_i . L_{o_i}(composite of subtree j moving with unit rate of joint j), ancestors only
+  float M[NV][NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const f3 cC = (1.f / mc[j]) * hc[j];
+    const float cc = dot(cC, cC);
+    const float I6[6] = {Io[j][0] - mc[j] * (cc - cC.x * cC.x), Io[j][1] - mc[j] * (cc - cC.y * cC.y),
+                         Io[j][2] - mc[j] * (cc - cC.z * cC.z), Io[j][3] + mc[j] * cC.x * cC.y,
+                         Io[j][4] + mc[j] * cC.x * cC.z, Io[j][5] + mc[j] * cC.y * cC.z};
+    const f3 aj = ax[j];
+    const f3 Ia = mk3(I6[0] * aj.x + I6[3] * aj.y + I6[4] * aj.z, I6[3] * aj.x + I6[1] * aj.y + I6[5] * aj.z,
+                      I6[4] * aj.x + I6[5] * aj.y + I6[2] * aj.z);
+    const f3 lin = mc[j] * cross(aj, cC - x[j]);
+#pragma unroll
+    for (int i = 0; i <= j; ++i) {
+      const float mij = ((anc[j] >> i) & 1u) ? dot(ax[i], Ia + cross(cC - x[i], lin)) : 0.f;
+      M[i][j] = mij;
+      M[j][i] = mij;
+    }
+  }
+  // Newton-Euler bias with zero joint acceleration, the world accelerating at -g
+  f3 om[NV], omd[NV], ac[NV], F[NV], Nn[NV];
+  const f3 gv = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const DBody& bd = B[b0 + j];
+    const float qd = s.v[v0 + j];
+    f3 omp = mk3(0.f, 0.f, 0.f), omdp = omp, acp = omp, comp = omp;
+    bool root = true;
+#pragma unroll
+    for (int k = 0; k < j; ++k)
+      if (par[j] == k) { omp = om[k]; omdp = omd[k]; acp = ac[k]; comp = com[k]; root = false; }
+    om[j] = omp + qd * ax[j];
+    omd[j] = omdp + cross(omp, qd * ax[j]);
+    f3 aanc;
+    if (!root) {
+      const f3 ro = x[j] - comp;
+      aanc = acp + cross(omdp, ro) + cross(omp, cross(omp, ro));
+    } else {
+      aanc = -gv;
+    }
+    const f3 rc = com[j] - x[j];
+    ac[j] = aanc + cross(omd[j], rc) + cross(om[j], cross(om[j], rc));
+    F[j] = bd.mass * ac[j];
+    Nn[j] = iw_mul(R[j], bd.inertia, omd[j]) + cross(om[j], iw_mul(R[j], bd.inertia, om[j]));
+  }
+  f3 ft[NV], nt[NV];
+  float rhs[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) { ft[j] = F[j]; nt[j] = Nn[j] + cross(com[j], F[j]); }
+#pragma unroll
+  for (int j = NV - 1; j >= 0; --j) {
+    const DBody& bd = B[b0 + j];
+    const float c = dot(ax[j], nt[j] - cross(x[j], ft[j]));
+    rhs[j] = ctrl_at(P, step, uadr, bd.uoff) - c - bd.damping * s.v[v0 + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k)
+      if (par[j] == k) { ft[k] = ft[k] + ft[j]; nt[k] = nt[k] + nt[j]; }
+    M[j][j] += dt * bd.damping;
+  }
+  // Cholesky M~ = L L^T, the inverse L^-1 and M~^-1 = L^-T L^-1
+  float L[NV][NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float d = M[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    d = sqrtf(fmaxf(d, 1e-30f));
+    L[j][j] = d;
+#pragma unroll
+    for (int i = j + 1; i < NV; ++i) {
+      float tt = M[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) tt -= L[i][k] * L[j][k];
+      L[i][j] = tt / d;
+    }
+  }
+  float Li[NV][NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Li[i][j] = 0.f;
+    Li[j][j] = 1.f / L[j][j];
+#pragma unroll
+    for (int i = j + 1; i < NV; ++i) {
+      float tt = 0.f;
+#pragma unroll
+      for (int k = j; k < i; ++k) tt += L[i][k] * Li[k][j];
+      Li[i][j] = -tt / L[i][i];
+    }
+  }
+  float* mi = s.minv + (size_t)t * kMaxTreeDof * kMaxTreeDof;
+  float mv[NV][NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      float tt = 0.f;
+#pragma unroll
+      for (int k = (i > j ? i : j); k < NV; ++k) tt += Li[k][i] * Li[k][j];
+      mv[i][j] = tt;
+      mi[i * kMaxTreeDof + j] = tt;
+    }
+  // smooth velocity and body twists
+  float vs[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float tt = 0.f;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tt += mv[i][j] * rhs[j];
+    vs[i] = s.v[v0 + i] + dt * tt;
+    s.vs[v0 + i] = vs[i];
+  }
+  f3 bom[NV], bvo[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    f3 omp = mk3(0.f, 0.f, 0.f), vop = omp, xp = omp;
+#pragma unroll
+    for (int k = 0; k < j; ++k)
+      if (par[j] == k) { omp = bom[k]; vop = bvo[k]; xp = x[k]; }
+    bom[j] = omp + vs[j] * ax[j];
+    bvo[j] = vop + cross(omp, x[j] - xp);
+    st3(s.bom + 3 * (b0 + j), bom[j]);
+    st3(s.bvo + 3 * (b0 + j), bvo[j]);
+  }
+}
+
+// one tree's preparation: the fixed-size versions for hinge trees of up to four bodies
+__device__ void artic_tree_prepare_any(const StepParams& P, ArticView& s, const DScene& sc, int t, int uadr,
+                                       int step) {
+  const DTree& tr = P.trees[sc.tree0 + t];
+  if (!tr.free) {
+    switch (tr.nv) {
+      case 1: artic_tree_prepare_n<1>(P, s, sc, tr, t, uadr, step); return;
+      case 2: artic_tree_prepare_n<2>(P, s, sc, tr, t, uadr, step); return;
+      case 3: artic_tree_prepare_n<3>(P, s, sc, tr, t, uadr, step); return;
+      case 4: artic_tree_prepare_n<4>(P, s, sc, tr, t, uadr, step); return;
+      default: break;
+    }
+  }
+  artic_tree_prepare(P, s, sc, tr, uadr, step);
+}
+
 // trace of the translational point Jacobian of body b at world point p through M~^-1
 __device__ float artic_trace(const StepParams& P, const ArticView& s, const DScene& sc, int b, f3 p) {
   const DBody* B = P.bodies + sc.body0;
@@ -928,18 +1144,20 @@ __device__ float artic_trace(const StepParams& P, const ArticView& s, const DSce
     float i0 = 1.f / bd.inertia[0], i1 = 1.f / bd.inertia[1], i2 = 1.f / bd.inertia[2];
     return 3.f / bd.mass + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
   }
+  // hinge chain: sum over the chain's joints i, j of (M~^-1)_ij (a_i x (p - o_i)) . (a_j x (p - o_j)),
+  // the chain read from the body's ancestor mask (no local arrays, no parent-pointer chasing)
   const float* mi = s.minv + (size_t)bd.tree * kMaxTreeDof * kMaxTreeDof;
-  int idx[kMaxTreeDof];
-  f3 cc[kMaxTreeDof];
-  int n = 0;
-  for (int a = b; a >= 0; a = B[a].parent) {
-    idx[n] = B[a].voff - tr.voff;
-    cc[n] = cross(ld3(s.bax + 3 * a), p - ld3(s.bx + 3 * a));
-    ++n;
-  }
   float t = 0.f;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) t += mi[idx[i] * kMaxTreeDof + idx[j]] * dot(cc[i], cc[j]);
+  for (unsigned mi_ = (unsigned)bd.anc; mi_; mi_ &= mi_ - 1) {
+    const int i = __ffs(mi_) - 1, bi = tr.body0 + i;
+    const f3 ci = cross(ld3(s.bax + 3 * bi), p - ld3(s.bx + 3 * bi));
+    f3 acc = mk3(0.f, 0.f, 0.f);
+    for (unsigned mj = (unsigned)bd.anc; mj; mj &= mj - 1) {
+      const int j = __ffs(mj) - 1, bj = tr.body0 + j;
+      acc = acc + mi[i * kMaxTreeDof + j] * cross(ld3(s.bax + 3 * bj), p - ld3(s.bx + 3 * bj));
+    }
+    t += dot(ci, acc);
+  }
   return t;
 }
 
@@ -955,10 +1173,10 @@ __device__ void artic_apply(const StepParams& P, ArticView& s, const DScene& sc,
     atomicAdd(a + 3, to_fix(ang.x)); atomicAdd(a + 4, to_fix(ang.y)); atomicAdd(a + 5, to_fix(ang.z));
     return;
   }
-  for (int a = b; a >= 0; a = B[a].parent) {
-    f3 ax = ld3(s.bax + 3 * a);
-    float gen = dot(ax, cross(p - ld3(s.bx + 3 * a), f) + m);
-    atomicAdd(s.acc + B[a].voff, to_fix(gen));
+  for (unsigned mk = (unsigned)bd.anc; mk; mk &= mk - 1) {  // the chain's joints
+    const int i = __ffs(mk) - 1, a = tr.body0 + i;
+    const float gen = dot(ld3(s.bax + 3 * a), cross(p - ld3(s.bx + 3 * a), f) + m);
+    atomicAdd(s.acc + tr.voff + i, to_fix(gen));
   }
 }
 
@@ -1020,10 +1238,18 @@ __device__ __noinline__ void artic_gram(const StepParams& P, const ArticView& s,
 }
 
 template <int kExt>
-__device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world, int ga,
-                                           int gb, int sub, const Raw& k, bool plane, f3 px) {
+__device__ __noinline__ void artic_contact(const StepParams& P, ArticView& s, const DScene& sc, int world,
+                                           const float* cq, int slot) {
+  Raw k;
+  k.p = mk3(cq[slot], cq[kQueue + slot], cq[2 * kQueue + slot]);
+  k.n = mk3(cq[3 * kQueue + slot], cq[4 * kQueue + slot], cq[5 * kQueue + slot]);
+  k.phi = cq[6 * kQueue + slot];
+  const int code = __float_as_int(cq[7 * kQueue + slot]), sub = __float_as_int(cq[8 * kQueue + slot]);
+  const int ga = code >> 16, gb = code & 0xffff;
   const DGeom& GA = P.geoms[sc.geom0 + ga];
   const DGeom& GB = P.geoms[sc.geom0 + gb];
+  const bool plane = GB.type == CF_GEOM_PLANE;
+  const f3 px = plane ? mk3(s.gR[9 * gb], s.gR[9 * gb + 3], s.gR[9 * gb + 6]) : mk3(0.f, 0.f, 0.f);
   const int ba = GA.body, bb = GB.body;
   f3 t1, t2;
   contact_frame(k.n, plane, px, t1, t2);
@@ -1123,10 +1349,29 @@ __device__ void artic_joint_constraints(const StepParams& P, ArticView& s, const
   }
 }
 
-// narrowphase of one scene pair (ga, gb), oriented so that a plane is always B
+// number of sub-contacts a candidate pair can produce: a plane against a capsule's end spheres,
+// a box's corners or a cylinder's rim points; box-box clipped vertices; otherwise one
 template <int kExt>
-__device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene& sc, int world, int code) {
-  int ga = code >> 16, gb = code & 0xffff;
+__device__ __forceinline__ int artic_nsub(const DGeom* G, int code) {
+  if (code < 0) return 0;
+  int ta = G[code >> 16].type, tb = G[code & 0xffff].type;
+  if (ta == CF_GEOM_PLANE) { const int t = ta; ta = tb; tb = t; }
+  if (tb == CF_GEOM_PLANE) {
+    if (ta == CF_GEOM_CAPSULE) return 2;
+    if (ta == CF_GEOM_BOX) return 8;
+    if ((kExt & kExtGeo) && ta == CF_GEOM_CYLINDER) return 6;
+    return 1;
+  }
+  return (kExt & kExtGeo) && ta == CF_GEOM_BOX && tb == CF_GEOM_BOX ? 8 : 1;
+}
+
+// narrowphase of sub-contact `sub` of one scene pair, oriented so that a plane is always B;
+// (ga, gb) receive the oriented pair.  True when it is a contact.
+template <int kExt>
+__device__ bool artic_narrow(const StepParams& P, const ArticView& s, const DScene& sc, int code, int sub, Raw& k,
+                             int& ga, int& gb) {
+  ga = code >> 16;
+  gb = code & 0xffff;
   const DGeom* G = P.geoms + sc.geom0;
   int ta = G[ga].type, tb = G[gb].type;
   if (ta == CF_GEOM_PLANE) { int t = ga; ga = gb; gb = t; t = ta; ta = tb; tb = t; }
@@ -1134,36 +1379,23 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
   M33 Ra = ld33(s.gR + 9 * ga), Rb = ld33(s.gR + 9 * gb);
   const float* sa = G[ga].size;
   const float* sb = G[gb].size;
-  if (tb == CF_GEOM_PLANE) {
-    f3 nz = col(Rb, 2), px = col(Rb, 0);
-    if (ta == CF_GEOM_SPHERE) {
-      Raw k = nf_sphere_plane(ca, sa[0], cb, nz);
-      if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, true, px);
-    } else if (ta == CF_GEOM_CAPSULE) {
-      f3 ax = col(Ra, 2);
-      for (int e = 0; e < 2; ++e) {
-        Raw k = nf_sphere_plane(ca + (e ? sa[1] : -sa[1]) * ax, sa[0], cb, nz);
-        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, e, k, true, px);
-      }
-    } else if ((kExt & kExtGeo) && ta == CF_GEOM_CYLINDER) {
-      for (int sub = 0; sub < 6; ++sub) {
-        Raw k = nf_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
-        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, k, true, px);
-      }
-    } else if ((kExt & kExtGeo) && ta == CF_GEOM_ELLIPSOID) {
-      Raw k = nf_ellipsoid_plane(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, nz);
-      if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, true, px);
-    } else if (ta == CF_GEOM_BOX) {
-      for (int ci = 0; ci < 8; ++ci) {
-        f3 corner = ca + mul(Ra, mk3((ci & 4) ? sa[0] : -sa[0], (ci & 2) ? sa[1] : -sa[1], (ci & 1) ? sa[2] : -sa[2]));
-        Raw k = nf_sphere_plane(corner, 0.f, cb, nz);
-        if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, ci, k, true, px);
-      }
-    }
-    return;
-  }
-  Raw k;
   k.phi = 3.0e38f;
+  if (tb == CF_GEOM_PLANE) {
+    f3 nz = col(Rb, 2);
+    if (ta == CF_GEOM_SPHERE) {
+      k = nf_sphere_plane(ca, sa[0], cb, nz);
+    } else if (ta == CF_GEOM_CAPSULE) {
+      k = nf_sphere_plane(ca + (sub ? sa[1] : -sa[1]) * col(Ra, 2), sa[0], cb, nz);
+    } else if ((kExt & kExtGeo) && ta == CF_GEOM_CYLINDER) {
+      k = nf_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
+    } else if ((kExt & kExtGeo) && ta == CF_GEOM_ELLIPSOID) {
+      k = nf_ellipsoid_plane(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, nz);
+    } else if (ta == CF_GEOM_BOX) {
+      f3 corner = ca + mul(Ra, mk3((sub & 4) ? sa[0] : -sa[0], (sub & 2) ? sa[1] : -sa[1], (sub & 1) ? sa[2] : -sa[2]));
+      k = nf_sphere_plane(corner, 0.f, cb, nz);
+    }
+    return k.phi < P.margin;
+  }
   if ((kExt & kExtGeo) && (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER)) {  // cylinders touch spheres only
     if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER) k = nf_sphere_cylinder(ca, sa[0], cb, Rb, sb[0], sb[1], true);
     else if (ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE) k = nf_sphere_cylinder(cb, sb[0], ca, Ra, sa[0], sa[1], false);
@@ -1184,12 +1416,9 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
     float t = fminf(fmaxf(dot(ca - cb, u), -sb[1]), sb[1]);
     k = nf_sphere_sphere(ca, sa[0], cb + t * u, sb[0]);
   } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
-    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertices, subs 0..7
-      for (int sub = 0; (kExt & kExtGeo) && sub < 8; ++sub) {
-        const Raw kb = nf_box_box(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, Rb, mk3(sb[0], sb[1], sb[2]), sub);
-        if (kb.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, sub, kb, false, mk3(0.f, 0.f, 0.f));
-      }
-      return;
+    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // clipped face vertex `sub`
+      if (kExt & kExtGeo) k = nf_box_box(ca, Ra, mk3(sa[0], sa[1], sa[2]), cb, Rb, mk3(sb[0], sb[1], sb[2]), sub);
+      return k.phi < P.margin;
     }
     bool boxA = ta == CF_GEOM_BOX;
     const M33& Rbx = boxA ? Ra : Rb;
@@ -1206,7 +1435,7 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
       k = nf_sphere_box(co + t * u, os[0], cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < P.margin) artic_contact<kExt>(P, s, sc, world, ga, gb, 0, k, false, mk3(0.f, 0.f, 0.f));
+  return k.phi < P.margin;
 }
 
 // MPC running cost of the state at the start of a step (Sec. V, Eq. mpc cost terms): object
@@ -1214,35 +1443,32 @@ __device__ void artic_candidate(const StepParams& P, ArticView& s, const DScene&
 // to the fingertips (the +z ends of the capsules of leaf bodies), squared deviation of the
 // hinges from the home pose, and a penalty once the object leaves the fall radius.
 __device__ float artic_running_cost(const StepParams& P, const ArticView& s, const DScene& sc, const DWorld& W,
-                                    int world) {
+                                    int world, int lane) {
+  // one warp: lanes take the fingertip geoms and the hinges, then a butterfly sum
   const DBody* B = P.bodies + sc.body0;
   const DGeom* G = P.geoms + sc.geom0;
   const float* gl = P.goal + 7 * world;
   const float* qo = s.q + B[P.cost_body].qoff;
-  float dq = gl[3] * qo[3] + gl[4] * qo[4] + gl[5] * qo[5] + gl[6] * qo[6];
+  const f3 po = mk3(qo[0], qo[1], qo[2]);
+  float part = 0.f;
+  for (int g = lane; g < sc.ngeom; g += 32) {
+    if (!G[g].tip) continue;
+    const f3 tip = ld3(s.gc + 3 * g) + G[g].size[1] * mk3(s.gR[9 * g + 2], s.gR[9 * g + 5], s.gR[9 * g + 8]);
+    const f3 d = po - tip;
+    part += P.cw[2] * dot(d, d);
+  }
+  for (int b = lane; b < sc.nbody; b += 32)
+    if (B[b].jnt == CF_JOINT_HINGE) {
+      const float e = s.q[B[b].qoff] - P.qref[W.qadr + B[b].qoff];
+      part += P.cw[3] * e * e;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  const float dq = gl[3] * qo[3] + gl[4] * qo[4] + gl[5] * qo[5] + gl[6] * qo[6];
   float c = P.cw[0] * (1.f - dq * dq);
   c += P.cw[1] * (fabsf(qo[0] - gl[0]) + fabsf(qo[1] - gl[1]) + fabsf(qo[2] - gl[2]));
-  float tips = 0.f;
-  for (int g = 0; g < sc.ngeom; ++g) {
-    int b = G[g].body;
-    if (b < 0 || G[g].type != CF_GEOM_CAPSULE || B[b].jnt != CF_JOINT_HINGE) continue;
-    bool leaf = true;
-    for (int k = 0; k < sc.nbody; ++k)
-      if (B[k].parent == b) leaf = false;
-    if (!leaf) continue;
-    f3 tip = ld3(s.gc + 3 * g) + G[g].size[1] * mk3(s.gR[9 * g + 2], s.gR[9 * g + 5], s.gR[9 * g + 8]);
-    f3 d = mk3(qo[0], qo[1], qo[2]) - tip;
-    tips += dot(d, d);
-  }
-  c += P.cw[2] * tips;
-  float dj = 0.f;
-  for (int b = 0; b < sc.nbody; ++b)
-    if (B[b].jnt == CF_JOINT_HINGE) {
-      float e = s.q[B[b].qoff] - P.qref[W.qadr + B[b].qoff];
-      dj += e * e;
-    }
-  c += P.cw[3] * dj;
-  float rx = qo[0] - gl[0], ry = qo[1] - gl[1];
+  c += part;
+  const float rx = qo[0] - gl[0], ry = qo[1] - gl[1];
   if (rx * rx + ry * ry > P.cw[5] * P.cw[5]) c += P.cw[4];
   return c;
 }
@@ -1265,7 +1491,7 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
-    for (int t = tid; t < sc.ntree; t += T) artic_tree_prepare(P, s, sc, P.trees[sc.tree0 + t], W.uadr, step);
+    for (int t = tid; t < sc.ntree; t += T) artic_tree_prepare_any(P, s, sc, t, W.uadr, step);
     for (int i = tid; i < sc.nv; i += T) s.acc[i] = 0ull;
     if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
     group_sync(gid, T);
@@ -1292,38 +1518,78 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
                 : sqrtf(gd.size[0] * gd.size[0] + gd.size[1] * gd.size[1] + gd.size[2] * gd.size[2]);
     }
     group_sync(gid, T);
-    if (P.cost && tid == 0) cost_acc += artic_running_cost(P, s, sc, W, world);
-    // ---- B. pair loop with per-warp compaction ----
-    int qn = 0;
-    for (int base = wig * 32; base < sc.npair; base += T) {
-      int k = base + lane;
-      int code = -1;
-      if (k < sc.npair) {
-        uint32_t pr = P.pairs[sc.pair0 + k];
-        int ga = pr >> 16, gb = pr & 0xffff;
-        bool pa = G[ga].type == CF_GEOM_PLANE, pb = G[gb].type == CF_GEOM_PLANE;
-        if (pa || pb) {
-          int gp = pa ? ga : gb, go = pa ? gb : ga;
-          f3 nz = mk3(s.gR[9 * gp + 2], s.gR[9 * gp + 5], s.gR[9 * gp + 8]);
-          float d = dot(nz, ld3(s.gc + 3 * go) - ld3(s.gc + 3 * gp));
-          if (d < s.gb[go] + P.margin) code = (int)pr;
-        } else {
-          f3 d = ld3(s.gc + 3 * ga) - ld3(s.gc + 3 * gb);
-          float rr = s.gb[ga] + s.gb[gb] + P.margin;
-          if (dot(d, d) < rr * rr) code = (int)pr;
+    if (P.cost && wig == 0) {
+      const float c = artic_running_cost(P, s, sc, W, world, lane);
+      if (lane == 0) cost_acc += c;
+    }
+    // ---- B. pair loop: bounding-sphere tests compacted into the candidate queue; every 32
+    // candidates run the narrowphase one per lane and sub-contact by sub-contact, whose hits
+    // are compacted into the contact queue; every 32 contacts are solved one per lane ----
+    {
+      const unsigned lt = (1u << lane) - 1u;
+      float* cq = s.cq + wig * kQueue * kArtCq;
+      int qn = 0, cn = 0;
+      int base = wig * 32;
+      while (true) {
+        if (qn < 32 && base < sc.npair) {
+          const int k = base + lane;
+          int code = -1;
+          if (k < sc.npair) {
+            uint32_t pr = P.pairs[sc.pair0 + k];
+            int ga = pr >> 16, gb = pr & 0xffff;
+            bool pa = G[ga].type == CF_GEOM_PLANE, pb = G[gb].type == CF_GEOM_PLANE;
+            if (pa || pb) {
+              int gp = pa ? ga : gb, go = pa ? gb : ga;
+              f3 nz = mk3(s.gR[9 * gp + 2], s.gR[9 * gp + 5], s.gR[9 * gp + 8]);
+              float d = dot(nz, ld3(s.gc + 3 * go) - ld3(s.gc + 3 * gp));
+              if (d < s.gb[go] + P.margin) code = (int)pr;
+            } else {
+              f3 d = ld3(s.gc + 3 * ga) - ld3(s.gc + 3 * gb);
+              float rr = s.gb[ga] + s.gb[gb] + P.margin;
+              if (dot(d, d) < rr * rr) code = (int)pr;
+            }
+          }
+          __syncwarp();
+          const unsigned m = __ballot_sync(0xffffffffu, code >= 0);
+          if (code >= 0) queue[qn + __popc(m & lt)] = code;
+          qn += __popc(m);
+          base += T;
         }
-      }
-      unsigned m = __ballot_sync(0xffffffffu, code >= 0);
-      if (code >= 0) queue[qn + __popc(m & ((1u << lane) - 1u))] = code;
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {
-        artic_candidate<kExt>(P, s, sc, world, queue[qn - 32 + lane]);
-        qn -= 32;
+        const bool done = base >= sc.npair;
+        if (qn < 32 && !done) continue;
+        const int nb = min(qn, 32);
+        const bool last = done && qn <= 32;
         __syncwarp();
+        const int mine = lane < nb ? queue[qn - nb + lane] : -1;
+        qn -= nb;
+        const int my_nsub = artic_nsub<kExt>(G, mine);
+        const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);
+        for (int sub = 0; sub < nsub; ++sub) {
+          Raw kc;
+          int ga = 0, gb = 0;
+          const bool hit = sub < my_nsub && artic_narrow<kExt>(P, s, sc, mine, sub, kc, ga, gb);
+          const unsigned hm = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const int slot = cn + __popc(hm & lt);
+            cq[slot] = kc.p.x; cq[kQueue + slot] = kc.p.y; cq[2 * kQueue + slot] = kc.p.z;
+            cq[3 * kQueue + slot] = kc.n.x; cq[4 * kQueue + slot] = kc.n.y; cq[5 * kQueue + slot] = kc.n.z;
+            cq[6 * kQueue + slot] = kc.phi;
+            cq[7 * kQueue + slot] = __int_as_float((ga << 16) | gb);
+            cq[8 * kQueue + slot] = __int_as_float(sub);
+          }
+          cn += __popc(hm);
+          const bool flush = last && sub + 1 == nsub;
+          while (cn >= 32 || (flush && cn > 0)) {
+            __syncwarp();
+            const int ns = min(cn, 32);
+            if (lane < ns) artic_contact<kExt>(P, s, sc, world, cq, cn - ns + lane);
+            cn -= ns;
+            __syncwarp();
+          }
+        }
+        if (last) break;
       }
     }
-    if (lane < qn) artic_candidate<kExt>(P, s, sc, world, queue[lane]);
     if (sc.joints)
       for (int t = tid; t < sc.ntree; t += T) artic_joint_constraints(P, s, sc, P.trees[sc.tree0 + t], t);
     group_sync(gid, T);

@@ -44,3 +44,46 @@ def test_proposal_finds_better_cold_start_plans_with_fewer_rollouts(trained):
           % (plain64.mean(), learned64.mean(), plain256.mean()))
     assert learned64.mean() < plain64.mean()
     assert learned64.mean() < plain256.mean()
+
+
+def test_learned_warm_start_with_zero_output_is_plain_mppi():
+    """The learned warm start samples around m + D, D the network's correction of the plan: a
+    network whose output is exactly zero (all parameters zero: GELU(0) = 0) must reproduce plain
+    MPPI bit for bit, plans and plant states alike."""
+    from paper_2603_12185_gb300 import build
+    build.build()
+    from paper_2603_12185_gb300 import comfree as CF
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    tpl = S.hand_template(0)
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    fin = MP.NQ + MP.NV + 4 + MP.PLAN_IN
+    probe = CF.Mlp(fin, 256, 2 * 32 * MP.NU, max_batch=4, seed=0)
+    zero = CF.Mlp(fin, 256, 2 * 32 * MP.NU, max_batch=4, params=np.zeros(probe.nparam, np.float32))
+    sb = S.make_hand(1, seed=31)
+    goal = MP.random_goal(sb.q0[0], np.random.default_rng(3))
+    plans = []
+    for mlp in (None, zero):
+        ctl = MP.HandMPPI(tpl, params, N=128, seed=5, mlp=mlp, mode="warm")
+        ctl.reset(sb.q0[0], sb.v0[0], goal)
+        plans.append([ctl.tick().cpu().numpy() for _ in range(5)] + [ctl.plant_state()[0]])
+    for a, b in zip(*plans):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_dagger_training_lowers_the_nll():
+    """Two DAgger iterations of the learned warm start on a few episodes: the labels (1024-rollout
+    teacher plans minus the warm start) are finite and each iteration's training lowers the NLL."""
+    from paper_2603_12185_gb300 import build
+    build.build()
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    tpl = S.hand_template(0)
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    log = {}
+    MP.dagger_warm_start(tpl, params, iters=2, episodes=4, ticks=20, N=128, N_teacher=512, epochs=200, seed=1,
+                         log=log)
+    st = log["dagger"]
+    assert [s["samples"] for s in st] == [80, 160]
+    for s in st:
+        assert np.isfinite(s["nll_last"]) and s["nll_last"] < s["nll_first"]
