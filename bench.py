@@ -494,8 +494,9 @@ def extra_proposal(rank, iters=None, episodes=None, goals=None, ticks=60):
     """The learned warm start for sampling MPC (Sec. V's MPPI with a learned proposal added):
     trained by DAgger against 1024-rollout teacher ticks on seeded goals, then the final task
     cost over `goals` held-out starts and goals (paired: the same starts and goals in every arm)
-    for plain MPPI at 1024, 512 and 256 rollouts and the learned warm start at 256 and 128
-    rollouts, with each arm's CUDA-event time per tick (MLP inference included)."""
+    for plain MPPI at 1024, 512 and 256 rollouts and the learned warm start at 512, 256 and 128
+    rollouts (and at 256 with half the rollouts around the uncorrected warm start), with each
+    arm's CUDA-event time per tick (MLP inference included)."""
     from paper_2603_12185_gb300 import mppi as MP
     from paper_2603_12185_gb300 import scenes as S
     iters = iters or PROPOSAL["iters"]
@@ -509,7 +510,8 @@ def extra_proposal(rank, iters=None, episodes=None, goals=None, ticks=60):
     mlp = MP.dagger_warm_start(t, params, iters=iters, episodes=episodes, seed=R.rank_seed(2300, rank), log=log)
     train_s = _t.perf_counter() - t0
     arms = {"plain_1024": dict(N=1024), "plain_512": dict(N=512), "plain_256": dict(N=256),
-            "learned_256": dict(N=256, mlp=mlp), "learned_128": dict(N=128, mlp=mlp)}
+            "learned_512": dict(N=512, mlp=mlp), "learned_256": dict(N=256, mlp=mlp),
+            "hedged_256": dict(N=256, mlp=mlp, n_prop=128), "learned_128": dict(N=128, mlp=mlp)}
     costs, tick_ms = MP.final_costs(t, params, arms, goals_seed=R.rank_seed(2400, rank), episodes=goals, ticks=ticks)
     out = {"train_s": train_s, "dagger": log["dagger"], "goals": goals, "ticks": ticks,
            "dagger_episodes": episodes, "dagger_iterations": iters}
@@ -522,6 +524,8 @@ def extra_proposal(rank, iters=None, episodes=None, goals=None, ticks=60):
         out[k] = {"final_cost_mean": float(c.mean()), "final_cost_se": float(c.std(ddof=1) / np.sqrt(len(c))),
                   "paired_diff_vs_plain_1024": paired(k, "plain_1024"), "ms_per_tick": tick_ms[k]}
     out["learned_256"]["paired_diff_vs_plain_256"] = paired("learned_256", "plain_256")
+    out["hedged_256"]["paired_diff_vs_plain_256"] = paired("hedged_256", "plain_256")
+    out["learned_512"]["paired_diff_vs_plain_512"] = paired("learned_512", "plain_512")
     return out
 
 

@@ -69,7 +69,7 @@ struct PileView {
   float4* rec;              // [N][7] body records, see kRec*
   const DGeom* geoms;       // the scene's geoms: body i carries geom i (friction coefficients)
   float* planes;            // [NP][12]
-  int* queue;               // [warps][kCandQueue] broadphase candidates
+  int* queue;               // [warps][2][kCandQueue] broadphase candidates: capsule-capsule pairs, the rest
   float* cq;                // [warps][8][kQueue] contacts: p.xyz, n.xyz, phi, code
   int* count;               // [0] contacts, [1] captured
 };
@@ -95,7 +95,7 @@ constexpr int kRec = 7;
 
 __host__ __device__ inline size_t pile_floats(int N, int NP, int warps) {
   // accumulators (12 words/body) + position (4) + record (28) + planes + both queues + counters
-  size_t words = (size_t)N * 12 + (size_t)N * 32 + (size_t)NP * 12 + (size_t)warps * (kQueue * kCqWords + kCandQueue) + 4;
+  size_t words = (size_t)N * 12 + (size_t)N * 32 + (size_t)NP * 12 + (size_t)warps * (kQueue * kCqWords + 2 * kCandQueue) + 4;
   return (words + 3) & ~(size_t)3;
 }
 
@@ -109,7 +109,7 @@ __device__ inline PileView pile_view(float* base, int N, int NP, int warps) {
   s.rec = reinterpret_cast<float4*>(f); f += 4 * (size_t)kRec * N;
   s.planes = f; f += (size_t)NP * 12;
   s.cq = f; f += (size_t)warps * kQueue * kCqWords;
-  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * kCandQueue;
+  s.queue = reinterpret_cast<int*>(f); f += (size_t)warps * 2 * kCandQueue;
   s.count = reinterpret_cast<int*>(f);
   return s;
 }
@@ -427,7 +427,7 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     o[6] = pl.x.x; o[7] = pl.x.y; o[8] = pl.x.z; o[9] = pl.mu[0]; o[10] = pl.mu[1]; o[11] = pl.mu[2];
   }
   const f3 g = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
-  int* queue = s.queue + wig * kCandQueue;
+  int* queue = s.queue + wig * 2 * kCandQueue;   // [0]: capsule-capsule pairs, [kCandQueue]: the rest
   bool range = false;  // some velocity change left the scatter's range
 
   for (int step = 0; step < P.nsteps; ++step) {
@@ -454,28 +454,30 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
     // ---- B. broadphase -> candidate queue -> narrowphase -> contact queue -> solve ----
     // Body pairs are tested in 32 x 32 tiles (i-chunk <= j-chunk) dealt round-robin to the
     // warps: each lane holds body i in registers, the j loop is warp-uniform (broadcast loads)
-    // and the bounding-sphere hits of a tile are kept as a 32-bit mask per lane.  All hits of a
-    // tile are then compacted into the candidate queue at once (a warp prefix sum of the masks'
-    // popcounts gives each lane its slots); after the tiles, every body is tested against the
-    // planes, 32 planes per mask, and compacted the same way.  Every 32 queued candidates run the
-    // narrowphase one per lane, whose hits are compacted into the contact queue; every 32
-    // contacts are solved one per lane.  So the solve, the costly part, runs on full warps
-    // although only a fraction of the candidates touch.
+    // and the bounding-sphere hits of a tile are kept as a 32-bit mask per lane, split into
+    // capsule-capsule pairs and the rest (a ballot of the j-chunk's capsules).  All hits of a
+    // tile are then compacted into the two candidate queues at once (a warp prefix sum of the
+    // masks' popcounts gives each lane its slots); after the tiles, every body is tested against
+    // the planes, 32 planes per mask, and compacted the same way.  Every 32 candidates of one
+    // queue run the narrowphase one per lane, so a batch takes one narrowphase branch (the
+    // segment-segment one or the cheap ones), and its hits are compacted into the contact
+    // queue; every 32 contacts are solved one per lane.  So the solve, the costly part, runs on
+    // full warps although only a fraction of the candidates touch.
     {
       const float margin = P.margin;
       const unsigned lt = (1u << lane) - 1u;
       float* cq = s.cq + wig * kQueue * kCqWords;
       const int nchunk = (N + 31) >> 5;
       const int ntile = nchunk * (nchunk + 1) / 2;
-      int qn = 0, cn = 0;
+      int qa = 0, qb = 0, cn = 0;           // queued capsule-capsule pairs, queued other candidates
       int phase = 0;                        // 0: body-pair tiles, 1: planes, 2: all masks made
       int t = wig, a0 = wig * 32, p0 = 0;   // next tile; next (32 bodies, 32 planes) plane block
-      unsigned m = 0;                       // this lane's hits not yet queued (bit k: j0 + k)
-      int code_hi = 0, j0 = 0, total = 0, excl = 0;
+      unsigned ma = 0, mb = 0;              // this lane's hits not yet queued, by class (bit k: j0 + k)
+      int code_hi = 0, j0 = 0, totala = 0, totalb = 0, excla = 0, exclb = 0;
       while (true) {
-        if (qn < 32) {
-          // make the next mask with any hit: a tile's bounding-sphere hits, or a block of planes
-          while (total == 0 && phase < 2) {
+        if (qa < 32 && qb < 32) {
+          while (totala == 0 && totalb == 0 && phase < 2) {
+            unsigned m = 0;
             if (phase == 0) {
               if (t >= ntile) { phase = NP > 0 ? 1 : 2; continue; }
               int rem = t, ci = 0;
@@ -486,7 +488,6 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
               if (i < N) { pi4 = s.pb[i]; pi4.w += margin; }
               j0 = cj << 5;
               const int kmax = min(32, N - j0);
-              m = 0;
 #pragma unroll 8
               for (int k = 0; k < kmax; ++k) {
                 const float4 pj = s.pb[j0 + k];
@@ -494,13 +495,16 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
                 const float rr = pi4.w + pj.w;
                 if (dx * dx + dy * dy + dz * dz < rr * rr) m |= 1u << k;
               }
-              if (ci == cj) m &= 0xfffffffeu << lane;  // diagonal tile: j > i only
+              if (ci == cj) m &= 0xfffffffeu << lane;
+              const unsigned capj = __ballot_sync(0xffffffffu, j0 + lane < N && pile_type(s, j0 + lane) == CF_GEOM_CAPSULE);
+              const bool cc = i < N && pile_type(s, i) == CF_GEOM_CAPSULE;
               code_hi = i << 16;
               t += gwarps;
+              ma = cc ? (m & capj) : 0u;
+              mb = m & ~ma;
             } else {
               if (a0 >= N) { phase = 2; break; }
               const int a = a0 + lane;
-              m = 0;
               if (a < N) {
                 const float4 a4 = s.pb[a];
                 const int pn = min(32, NP - p0);
@@ -514,39 +518,54 @@ __device__ void pile_world(const StepParams& P, float* smem, int world, int gid,
               j0 = p0;
               p0 += 32;
               if (p0 >= NP) { p0 = 0; a0 += T; }
+              ma = 0u;
+              mb = m;
             }
-            const int cnt = __popc(m);
-            total = __reduce_add_sync(0xffffffffu, cnt);
-            int incl = cnt;
+            const int ca_ = __popc(ma), cb_ = __popc(mb);
+            totala = __reduce_add_sync(0xffffffffu, ca_);
+            totalb = __reduce_add_sync(0xffffffffu, cb_);
+            int ia = ca_, ib = cb_;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, incl, d);
-              if (lane >= d) incl += y;
+              const int ya = __shfl_up_sync(0xffffffffu, ia, d), yb = __shfl_up_sync(0xffffffffu, ib, d);
+              if (lane >= d) { ia += ya; ib += yb; }
             }
-            excl = incl - cnt;
+            excla = ia - ca_;
+            exclb = ib - cb_;
           }
-          // queue as many of the mask's hits as fit (each lane from its prefix-sum slot)
-          if (total > 0) {
-            const int room = kCandQueue - qn;
-            __syncwarp();
-            for (int k = excl; m && k < room; ++k) {
-              queue[qn + k] = code_hi | (j0 + __ffs(m) - 1);
-              m &= m - 1;
+          __syncwarp();
+          if (totala > 0) {
+            const int room = kCandQueue - qa;
+            for (int k = excla; ma && k < room; ++k) {
+              queue[qa + k] = code_hi | (j0 + __ffs(ma) - 1);
+              ma &= ma - 1;
             }
-            const int put = min(total, room);
-            qn += put;
-            total -= put;
-            excl = max(excl - room, 0);
+            const int put = min(totala, room);
+            qa += put;
+            totala -= put;
+            excla = max(excla - room, 0);
+          }
+          if (totalb > 0) {
+            const int room = kCandQueue - qb;
+            for (int k = exclb; mb && k < room; ++k) {
+              queue[kCandQueue + qb + k] = code_hi | (j0 + __ffs(mb) - 1);
+              mb &= mb - 1;
+            }
+            const int put = min(totalb, room);
+            qb += put;
+            totalb -= put;
+            exclb = max(exclb - room, 0);
           }
         }
-        const bool fin = phase == 2 && total == 0;   // every candidate is queued
-        if (qn < 32 && !fin) continue;
-        // narrowphase of the top nb candidates, one per lane; contacts to the contact queue;
-        // every 32 contacts (at the end: all of them) solved one per lane
+        const bool fin = phase == 2 && totala == 0 && totalb == 0;
+        if (qa < 32 && qb < 32 && !fin) continue;
+        const bool from_a = qa >= 32 || (qb < 32 && qa > 0);
+        int& qn = from_a ? qa : qb;
+        int* qsrc = from_a ? queue : queue + kCandQueue;
         const int nb = min(qn, 32);
-        const bool last = fin && qn <= 32;
+        const bool last = fin && qa + qb == nb;
         __syncwarp();
-        const int mine = lane < nb ? queue[qn - nb + lane] : -1;
+        const int mine = lane < nb ? qsrc[qn - nb + lane] : -1;
         qn -= nb;
         const int my_nsub = pile_nsub<kExt>(s, mine);
         const int nsub = max(__reduce_max_sync(0xffffffffu, my_nsub), 1);

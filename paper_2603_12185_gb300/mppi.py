@@ -8,8 +8,9 @@ Per control tick (all on the GPU, one rollout launch):
      - "mix": features = (q, v, goal quaternion) -> MLP -> Gaussian over the H x nu plan, and
        n_prop of the N samples are drawn from it;
      - "warm" (the learned warm start): features = (q, v, goal quaternion, the first steps of the
-       warm-start plan m) -> MLP -> a correction D of the plan, and all N samples are drawn around
-       m + D with MPPI's own sigma (D = 0 is plain MPPI);
+       warm-start plan m) -> MLP -> a correction D of the plan, and the samples are drawn around
+       m + D with MPPI's own sigma (all N, or n_prop of them with the rest around m; D = 0 is
+       plain MPPI);
   4. sample N control sequences (cf_mppi_sample), clipped to the torque limit;
   5. roll all N worlds H steps with the fused running/terminal cost (cf_set_cost, cf_step);
   6. MPPI update of the mean (cf_mppi_update); apply its first action to the plant; shift.
@@ -54,7 +55,9 @@ class HandMPPI:
         self.N, self.H, self.dt, self.sigma, self.lam, self.limit = N, H, dt, sigma, lam, limit
         self.mode = mode
         self.mlp = mlp
-        self.n_prop = (n_prop if mlp is not None else 0) if mode == "mix" else (N if mlp is not None else 0)
+        # "warm": n_prop of the N samples (all when n_prop = 0) around the corrected plan, the
+        # rest around the warm start itself
+        self.n_prop = (n_prop if mlp is not None else 0) if mode == "mix" else ((n_prop or N) if mlp is not None else 0)
         self.model = CF.Model([template], params)
         self.rollouts = CF.Batch(self.model, np.zeros(N, np.int32), max_ctrl_steps=H)
         self.rollouts.set_warps(0, warps)  # warps per rollout world (2: the fastest for 1024 hands)
