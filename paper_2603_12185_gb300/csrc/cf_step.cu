@@ -883,7 +883,7 @@ __device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DSce
     nt[j] = nt[j] + Nn[j] + cross(com[j], F[j]);
     f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
     float c = dot(a, nt[j] - cross(x, ft[j]));
-    float tau = ctrl_at(P, step, uadr, bd.uoff);
+    float tau = bd.uoff >= 0 ? s.tau[bd.uoff] : 0.f;  // this step's torques, staged by the world
     rhs[j] = tau - c - bd.damping * s.v[v0 + j];
     int p = bd.parent >= 0 ? bd.parent - b0 : -1;
     if (p >= 0) { ft[p] = ft[p] + ft[j]; nt[p] = nt[p] + nt[j]; }
@@ -1061,7 +1061,7 @@ __device__ void artic_tree_prepare_n(const StepParams& P, ArticView& s, const DS
   for (int j = NV - 1; j >= 0; --j) {
     const DBody& bd = B[b0 + j];
     const float c = dot(ax[j], nt[j] - cross(x[j], ft[j]));
-    rhs[j] = ctrl_at(P, step, uadr, bd.uoff) - c - bd.damping * s.v[v0 + j];
+    rhs[j] = (bd.uoff >= 0 ? s.tau[bd.uoff] : 0.f) - c - bd.damping * s.v[v0 + j];
 #pragma unroll
     for (int k = 0; k < j; ++k)
       if (par[j] == k) { ft[k] = ft[k] + ft[j]; nt[k] = nt[k] + nt[j]; }
@@ -1507,6 +1507,9 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
   int* queue = s.queue + wig * kQueue;
   const float dt = P.dt;
   float cost_acc = 0.f;
+  // the first step's actuator torques in shared memory (each later step's are staged at the end
+  // of the step before), so that the trees' serial chains read no global memory for them
+  for (int k = tid; k < sc.nu; k += T) s.tau[k] = ctrl_at(P, 0, W.uadr, k);
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
@@ -1655,6 +1658,8 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
         }
       }
     }
+    if (step + 1 < P.nsteps)
+      for (int k = tid; k < sc.nu; k += T) s.tau[k] = ctrl_at(P, step + 1, W.uadr, k);
   }
   group_sync(gid, T);
   bool bad = false;
