@@ -726,13 +726,12 @@ __device__ __forceinline__ f3 iw_mul(const M33& R, const float* I, f3 u) {
   return mul(R, mk3(I[0] * l.x, I[1] * l.y, I[2] * l.z));
 }
 
-// One hinge tree (thread per tree): kinematics, composite-rigid-body inertia, Newton-Euler
-// bias, implicit damping, Cholesky inverse, smooth velocity and body twists.
-__device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr, int uadr,
-                                   int step) {
+// A free body's preparation (hinge trees: artic_tree_prepare_group): pose from q, the smooth
+// velocity with the gyroscopic bias w x I w, and its twist.
+__device__ void artic_free_prepare(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr) {
   const DBody* B = P.bodies + sc.body0;
   const float dt = P.dt;
-  if (tr.free) {
+  {
     const int b = tr.body0;
     const DBody& bd = B[b];
     const float* qb = s.q + bd.qoff;
@@ -753,401 +752,248 @@ __device__ void artic_tree_prepare(const StepParams& P, ArticView& s, const DSce
     st3(s.bom + 3 * b, mul(R, mk3(vsb[3], vsb[4], vsb[5])));
     st3(s.bvo + 3 * b, mk3(vsb[0], vsb[1], vsb[2]));
     st3(s.bax + 3 * b, mk3(0.f, 0.f, 0.f));
-    return;
   }
-  const int n = tr.nv, b0 = tr.body0, v0 = tr.voff;
-  // -- forward kinematics (bodies of the tree are contiguous, parents first) --
-  f3 com[kMaxTreeDof];
-  for (int j = 0; j < n; ++j) {
-    const int b = b0 + j;
+}
+
+// ---- lane-parallel preparation of hinge trees: an 8-lane group per tree, lane r = body r ----
+__device__ __forceinline__ float gshf(float v, int k) { return __shfl_sync(0xffffffffu, v, k, 8); }
+__device__ __forceinline__ int gshi(int v, int k) { return __shfl_sync(0xffffffffu, v, k, 8); }
+__device__ __forceinline__ f3 gsh3(f3 v, int k) { return mk3(gshf(v.x, k), gshf(v.y, k), gshf(v.z, k)); }
+// sum over the group's lanes k with bit k of `sel` set of v_k
+__device__ __forceinline__ f3 gsum3(f3 v, unsigned sel) {
+  f3 acc = mk3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const f3 vk = gsh3(v, k);
+    if ((sel >> k) & 1u) acc = acc + vk;
+  }
+  return acc;
+}
+
+// One hinge tree of n <= 8 bodies (one hinge each, parents first) prepared by an 8-lane group:
+// the same quantities as artic_tree_prepare -- kinematics, composite inertia, bias, implicit
+// damping, the explicit M~^-1, the smooth velocity and the body twists -- with the chains
+// replaced by log-depth and masked-sum forms:
+//   - world poses by pointer jumping: (R, t) <- (R, t) of the pointer's frame o (R, t), three
+//     rounds covering depth 8;
+//   - sums over a body's ancestors (angular velocities and their rates, the acceleration of the
+//     joint origin, the twists) and over its subtree (composite inertia, the backward forces)
+//     as masked sums over the group, the masks being the per-body ancestor bitmasks;
+//   - M~ assembled column by column (lane j: the ancestors i of j), factorised by one lane
+//     (n <= 8), and M~^-1 solved column by column (lane j: M~ x = e_j).
+// Every lane of the warp calls it in step (`active` false: no tree for this group), so that
+// the shuffles see the whole warp.
+__device__ void artic_tree_prepare_group(const StepParams& P, ArticView& s, const DScene& sc, int t, bool active,
+                                         int r) {
+  const DBody* B = P.bodies + sc.body0;
+  const float dt = P.dt;
+  int body0 = 0, n = 0;
+  if (active) {
+    const DTree& tr = P.trees[sc.tree0 + t];
+    body0 = tr.body0;
+    n = tr.nv;
+  }
+  const bool me = r < n;
+  const int b = body0 + r;
+  // this lane's body
+  int par = -1, uoff = -1, qoff = 0, voff = 0;
+  unsigned anc = 0u;
+  float mass = 1.f, damp = 0.f, q = 0.f, qd = 0.f;
+  f3 a = mk3(0.f, 0.f, 1.f), pos = mk3(0.f, 0.f, 0.f), ipos = pos, inert = mk3(1.f, 1.f, 1.f);
+  M33 Rq;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Rq.m[k] = (k % 4 == 0) ? 1.f : 0.f;
+  if (me) {
     const DBody& bd = B[b];
-    M33 Rp;
-    f3 xp = mk3(0.f, 0.f, 0.f);
-    if (bd.parent >= 0) {
-      Rp = ld33(s.bR + 9 * bd.parent);
-      xp = ld3(s.bx + 3 * bd.parent);
-    } else {
-      for (int k = 0; k < 9; ++k) Rp.m[k] = (k % 4 == 0) ? 1.f : 0.f;
+    par = bd.parent >= 0 ? bd.parent - body0 : -1;
+    anc = (unsigned)bd.anc;
+    uoff = bd.uoff;
+    qoff = bd.qoff;
+    voff = bd.voff;
+    mass = bd.mass;
+    damp = bd.damping;
+    inert = mk3(bd.inertia[0], bd.inertia[1], bd.inertia[2]);
+    pos = mk3(bd.pos[0], bd.pos[1], bd.pos[2]);
+    ipos = mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]);
+    a = mk3(bd.axis[0], bd.axis[1], bd.axis[2]);
+    a = rsqrtf(dot(a, a)) * a;
+    Rq = quat_mat(bd.quat[0], bd.quat[1], bd.quat[2], bd.quat[3]);
+    q = s.q[qoff];
+    qd = s.v[voff];
+  }
+  // world pose by pointer jumping over the parent chain
+  M33 R = mul33(Rq, axis_rot(a, q));
+  f3 x = pos;
+  int up = par;
+#pragma unroll
+  for (int round = 0; round < 3; ++round) {
+    const int src = up >= 0 ? up : r;
+    M33 Ru;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ru.m[k] = gshf(R.m[k], src);
+    const f3 xu = gsh3(x, src);
+    const int uu = gshi(up, src);
+    if (up >= 0) {
+      x = xu + mul(Ru, x);
+      R = mul33(Ru, R);
+      up = uu;
     }
-    M33 Rfix = mul33(Rp, quat_mat(bd.quat[0], bd.quat[1], bd.quat[2], bd.quat[3]));
-    f3 ax = mk3(bd.axis[0], bd.axis[1], bd.axis[2]);
-    ax = rsqrtf(dot(ax, ax)) * ax;
-    M33 R = mul33(Rfix, axis_rot(ax, s.q[bd.qoff]));
-    f3 x = xp + mul(Rp, mk3(bd.pos[0], bd.pos[1], bd.pos[2]));
+  }
+  const f3 ax = mul(R, a);  // the hinge axis is fixed by its own rotation
+  const f3 com = x + mul(R, ipos);
+  if (me) {
     st3(s.bx + 3 * b, x);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.bR[9 * b + k] = R.m[k];
-    st3(s.bax + 3 * b, mul(Rfix, ax));
-    com[j] = x + mul(R, mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]));
+    st3(s.bax + 3 * b, ax);
   }
-  // -- composite rigid bodies: mass, first moment, inertia about the world origin --
-  float mc[kMaxTreeDof];
-  f3 hc[kMaxTreeDof];
-  float Io[kMaxTreeDof][6];  // xx yy zz xy xz yz
-  for (int j = 0; j < n; ++j) {
-    const DBody& bd = B[b0 + j];
-    M33 R = ld33(s.bR + 9 * (b0 + j));
-    float m = bd.mass;
-    f3 c = com[j];
-    // R diag(I) R^T + m (|c|^2 1 - c c^T)
-    float Iw[6];
-    {
-      float I0 = bd.inertia[0], I1 = bd.inertia[1], I2 = bd.inertia[2];
-      const float* r = R.m;
-      Iw[0] = r[0] * r[0] * I0 + r[1] * r[1] * I1 + r[2] * r[2] * I2;
-      Iw[1] = r[3] * r[3] * I0 + r[4] * r[4] * I1 + r[5] * r[5] * I2;
-      Iw[2] = r[6] * r[6] * I0 + r[7] * r[7] * I1 + r[8] * r[8] * I2;
-      Iw[3] = r[0] * r[3] * I0 + r[1] * r[4] * I1 + r[2] * r[5] * I2;
-      Iw[4] = r[0] * r[6] * I0 + r[1] * r[7] * I1 + r[2] * r[8] * I2;
-      Iw[5] = r[3] * r[6] * I0 + r[4] * r[7] * I1 + r[5] * r[8] * I2;
-    }
-    float cc = dot(c, c);
-    Io[j][0] = Iw[0] + m * (cc - c.x * c.x);
-    Io[j][1] = Iw[1] + m * (cc - c.y * c.y);
-    Io[j][2] = Iw[2] + m * (cc - c.z * c.z);
-    Io[j][3] = Iw[3] - m * c.x * c.y;
-    Io[j][4] = Iw[4] - m * c.x * c.z;
-    Io[j][5] = Iw[5] - m * c.y * c.z;
-    mc[j] = m;
-    hc[j] = m * c;
+  // parent's origin (the world's for a root)
+  const int psrc = par >= 0 ? par : r;
+  const f3 xps = gsh3(x, psrc);  // every lane shuffles; roots then take the world's origin
+  const f3 xp = par >= 0 ? xps : mk3(0.f, 0.f, 0.f);
+  // composite rigid bodies over the subtree: mass, first moment, inertia about the world origin
+  float Iw[6];
+  {
+    const float* rr = R.m;
+    const float cc = dot(com, com);
+    Iw[0] = rr[0] * rr[0] * inert.x + rr[1] * rr[1] * inert.y + rr[2] * rr[2] * inert.z + mass * (cc - com.x * com.x);
+    Iw[1] = rr[3] * rr[3] * inert.x + rr[4] * rr[4] * inert.y + rr[5] * rr[5] * inert.z + mass * (cc - com.y * com.y);
+    Iw[2] = rr[6] * rr[6] * inert.x + rr[7] * rr[7] * inert.y + rr[8] * rr[8] * inert.z + mass * (cc - com.z * com.z);
+    Iw[3] = rr[0] * rr[3] * inert.x + rr[1] * rr[4] * inert.y + rr[2] * rr[5] * inert.z - mass * com.x * com.y;
+    Iw[4] = rr[0] * rr[6] * inert.x + rr[1] * rr[7] * inert.y + rr[2] * rr[8] * inert.z - mass * com.x * com.z;
+    Iw[5] = rr[3] * rr[6] * inert.x + rr[4] * rr[7] * inert.y + rr[5] * rr[8] * inert.z - mass * com.y * com.z;
   }
-  for (int j = n - 1; j >= 0; --j) {
-    int p = B[b0 + j].parent;
-    if (p >= 0) {
-      int jp = p - b0;
-      mc[jp] += mc[j];
-      hc[jp] = hc[jp] + hc[j];
-      for (int k = 0; k < 6; ++k) Io[jp][k] += Io[j][k];
-    }
-  }
-  // -- M_ij = a_i . L_{o_i}(composite of subtree j moving with unit rate of joint j) --
-  float M[kMaxTreeDof][kMaxTreeDof];
-  for (int j = 0; j < n; ++j) {
-    f3 aj = ld3(s.bax + 3 * (b0 + j)), oj = ld3(s.bx + 3 * (b0 + j));
-    f3 cC = (1.f / mc[j]) * hc[j];
-    float cc = dot(cC, cC);
-    // inertia about the composite COM: I_O - m (|c|^2 1 - c c^T)
-    float I6[6] = {Io[j][0] - mc[j] * (cc - cC.x * cC.x), Io[j][1] - mc[j] * (cc - cC.y * cC.y),
-                   Io[j][2] - mc[j] * (cc - cC.z * cC.z), Io[j][3] + mc[j] * cC.x * cC.y,
-                   Io[j][4] + mc[j] * cC.x * cC.z, Io[j][5] + mc[j] * cC.y * cC.z};
-    f3 Ia = mk3(I6[0] * aj.x + I6[3] * aj.y + I6[4] * aj.z, I6[3] * aj.x + I6[1] * aj.y + I6[5] * aj.z,
-                I6[4] * aj.x + I6[5] * aj.y + I6[2] * aj.z);
-    f3 lin = mc[j] * cross(aj, cC - oj);
-    for (int i = j; i >= 0; i = (B[b0 + i].parent >= 0 ? B[b0 + i].parent - b0 : -1)) {
-      f3 ai = ld3(s.bax + 3 * (b0 + i)), oi = ld3(s.bx + 3 * (b0 + i));
-      float mij = dot(ai, Ia + cross(cC - oi, lin));
-      M[i][j] = mij;
-      M[j][i] = mij;
-    }
-  }
-  // zero entries of non-ancestor pairs
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      bool rel = false;
-      for (int a = j; a >= 0; a = (B[b0 + a].parent >= 0 ? B[b0 + a].parent - b0 : -1))
-        if (a == i) rel = true;
-      for (int a = i; a >= 0; a = (B[b0 + a].parent >= 0 ? B[b0 + a].parent - b0 : -1))
-        if (a == j) rel = true;
-      if (!rel) M[i][j] = 0.f;
-    }
-  // -- Newton-Euler bias with zero joint acceleration, world accelerating at -g --
-  f3 om[kMaxTreeDof], omd[kMaxTreeDof], ac[kMaxTreeDof], F[kMaxTreeDof], Nn[kMaxTreeDof];
-  const f3 gv = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
-  for (int j = 0; j < n; ++j) {
-    const DBody& bd = B[b0 + j];
-    int p = bd.parent >= 0 ? bd.parent - b0 : -1;
-    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
-    float qd = s.v[v0 + j];
-    f3 omp = p >= 0 ? om[p] : mk3(0.f, 0.f, 0.f), omdp = p >= 0 ? omd[p] : mk3(0.f, 0.f, 0.f);
-    om[j] = omp + qd * a;
-    omd[j] = omdp + cross(omp, qd * a);
-    f3 aanc;
-    if (p >= 0) {
-      f3 ro = x - com[p];
-      aanc = ac[p] + cross(omdp, ro) + cross(omp, cross(omp, ro));
-    } else {
-      aanc = -gv;
-    }
-    f3 rc = com[j] - x;
-    ac[j] = aanc + cross(omd[j], rc) + cross(om[j], cross(om[j], rc));
-    M33 R = ld33(s.bR + 9 * (b0 + j));
-    F[j] = bd.mass * ac[j];
-    Nn[j] = iw_mul(R, bd.inertia, omd[j]) + cross(om[j], iw_mul(R, bd.inertia, om[j]));
-  }
-  f3 ft[kMaxTreeDof], nt[kMaxTreeDof];
-  for (int j = 0; j < n; ++j) { ft[j] = mk3(0.f, 0.f, 0.f); nt[j] = mk3(0.f, 0.f, 0.f); }
-  float rhs[kMaxTreeDof];
-  for (int j = n - 1; j >= 0; --j) {
-    const DBody& bd = B[b0 + j];
-    ft[j] = ft[j] + F[j];
-    nt[j] = nt[j] + Nn[j] + cross(com[j], F[j]);
-    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
-    float c = dot(a, nt[j] - cross(x, ft[j]));
-    float tau = bd.uoff >= 0 ? s.tau[bd.uoff] : 0.f;  // this step's torques, staged by the world
-    rhs[j] = tau - c - bd.damping * s.v[v0 + j];
-    int p = bd.parent >= 0 ? bd.parent - b0 : -1;
-    if (p >= 0) { ft[p] = ft[p] + ft[j]; nt[p] = nt[p] + nt[j]; }
-    M[j][j] += dt * bd.damping;
-  }
-  // -- Cholesky M~ = L L^T, then the explicit inverse L^-T L^-1 --
-  float L[kMaxTreeDof][kMaxTreeDof];
-  for (int j = 0; j < n; ++j) {
-    float d = M[j][j];
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    d = sqrtf(fmaxf(d, 1e-30f));
-    L[j][j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      float t = M[i][j];
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / d;
-    }
-  }
-  float Li[kMaxTreeDof][kMaxTreeDof];  // L^-1 (lower)
-  for (int j = 0; j < n; ++j) {
-    for (int i = 0; i < n; ++i) Li[i][j] = 0.f;
-    Li[j][j] = 1.f / L[j][j];
-    for (int i = j + 1; i < n; ++i) {
-      float t = 0.f;
-      for (int k = j; k < i; ++k) t += L[i][k] * Li[k][j];
-      Li[i][j] = -t / L[i][i];
-    }
-  }
-  float* mi = s.minv + (size_t)(&tr - (P.trees + sc.tree0)) * kMaxTreeDof * kMaxTreeDof;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      float t = 0.f;
-      for (int k = max(i, j); k < n; ++k) t += Li[k][i] * Li[k][j];
-      mi[i * kMaxTreeDof + j] = t;
-    }
-  // -- smooth velocity and body twists --
-  for (int i = 0; i < n; ++i) {
-    float t = 0.f;
-    for (int j = 0; j < n; ++j) t += mi[i * kMaxTreeDof + j] * rhs[j];
-    s.vs[v0 + i] = s.v[v0 + i] + dt * t;
-  }
-  for (int j = 0; j < n; ++j) {
-    const DBody& bd = B[b0 + j];
-    f3 a = ld3(s.bax + 3 * (b0 + j)), x = ld3(s.bx + 3 * (b0 + j));
-    f3 omp = mk3(0.f, 0.f, 0.f), vop = mk3(0.f, 0.f, 0.f), xp = mk3(0.f, 0.f, 0.f);
-    if (bd.parent >= 0) {
-      omp = ld3(s.bom + 3 * bd.parent);
-      vop = ld3(s.bvo + 3 * bd.parent);
-      xp = ld3(s.bx + 3 * bd.parent);
-    }
-    st3(s.bom + 3 * (b0 + j), omp + s.vs[v0 + j] * a);
-    st3(s.bvo + 3 * (b0 + j), vop + cross(omp, x - xp));
-  }
-}
-
-// The same preparation for a hinge tree of exactly NV bodies (one hinge each), with every loop
-// bound a compile-time constant: the tree's matrices stay in registers instead of local memory,
-// and parent and ancestor lookups are predicated selections over earlier bodies.
-template <int NV>
-__device__ void artic_tree_prepare_n(const StepParams& P, ArticView& s, const DScene& sc, const DTree& tr, int t,
-                                     int uadr, int step) {
-  const DBody* B = P.bodies + sc.body0;
-  const float dt = P.dt;
-  const int b0 = tr.body0, v0 = tr.voff;
-  int par[NV];
-  unsigned anc[NV];  // bit i: body i of the tree is an ancestor of (or is) body j
-  M33 R[NV];
-  f3 x[NV], ax[NV], com[NV];
+  float mc = 0.f, Io[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  f3 hc = mk3(0.f, 0.f, 0.f);
+  {
+    const float mine = me ? mass : 0.f;
+    const f3 hm = mine * com;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const DBody& bd = B[b0 + j];
-    par[j] = bd.parent >= 0 ? bd.parent - b0 : -1;
-    anc[j] = 1u << j;
-    M33 Rp;
+    for (int k = 0; k < 8; ++k) {
+      const bool in = (gshi((int)anc, k) >> r) & 1;  // this lane's body is an ancestor of body k
+      const float mk = gshf(mine, k);
+      const f3 hk = gsh3(hm, k);
+      float ik[6];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Rp.m[k] = (k % 4 == 0) ? 1.f : 0.f;
-    f3 xp = mk3(0.f, 0.f, 0.f);
+      for (int e = 0; e < 6; ++e) ik[e] = gshf(me ? Iw[e] : 0.f, k);
+      if (in) {
+        mc += mk;
+        hc = hc + hk;
 #pragma unroll
-    for (int k = 0; k < j; ++k)
-      if (par[j] == k) { Rp = R[k]; xp = x[k]; anc[j] |= anc[k]; }
-    M33 Rfix = mul33(Rp, quat_mat(bd.quat[0], bd.quat[1], bd.quat[2], bd.quat[3]));
-    f3 a = mk3(bd.axis[0], bd.axis[1], bd.axis[2]);
-    a = rsqrtf(dot(a, a)) * a;
-    R[j] = mul33(Rfix, axis_rot(a, s.q[bd.qoff]));
-    x[j] = xp + mul(Rp, mk3(bd.pos[0], bd.pos[1], bd.pos[2]));
-    ax[j] = mul(Rfix, a);
-    com[j] = x[j] + mul(R[j], mk3(bd.ipos[0], bd.ipos[1], bd.ipos[2]));
-    st3(s.bx + 3 * (b0 + j), x[j]);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s.bR[9 * (b0 + j) + k] = R[j].m[k];
-    st3(s.bax + 3 * (b0 + j), ax[j]);
-  }
-  // composite rigid bodies: mass, first moment, inertia about the world origin
-  float mc[NV];
-  f3 hc[NV];
-  float Io[NV][6];  // xx yy zz xy xz yz
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const DBody& bd = B[b0 + j];
-    const float m = bd.mass;
-    const f3 c = com[j];
-    const float I0 = bd.inertia[0], I1 = bd.inertia[1], I2 = bd.inertia[2];
-    const float* r = R[j].m;
-    const float cc = dot(c, c);
-    Io[j][0] = r[0] * r[0] * I0 + r[1] * r[1] * I1 + r[2] * r[2] * I2 + m * (cc - c.x * c.x);
-    Io[j][1] = r[3] * r[3] * I0 + r[4] * r[4] * I1 + r[5] * r[5] * I2 + m * (cc - c.y * c.y);
-    Io[j][2] = r[6] * r[6] * I0 + r[7] * r[7] * I1 + r[8] * r[8] * I2 + m * (cc - c.z * c.z);
-    Io[j][3] = r[0] * r[3] * I0 + r[1] * r[4] * I1 + r[2] * r[5] * I2 - m * c.x * c.y;
-    Io[j][4] = r[0] * r[6] * I0 + r[1] * r[7] * I1 + r[2] * r[8] * I2 - m * c.x * c.z;
-    Io[j][5] = r[3] * r[6] * I0 + r[4] * r[7] * I1 + r[5] * r[8] * I2 - m * c.y * c.z;
-    mc[j] = m;
-    hc[j] = m * c;
-  }
-#pragma unroll
-  for (int j = NV - 1; j >= 0; --j)
-#pragma unroll
-    for (int k = 0; k < j; ++k)
-      if (par[j] == k) {
-        mc[k] += mc[j];
-        hc[k] = hc[k] + hc[j];
-#pragma unroll
-        for (int e = 0; e < 6; ++e) Io[k][e] += Io[j][e];
+        for (int e = 0; e < 6; ++e) Io[e] += ik[e];
       }
-  // M_ij = a_i . L_{o_i}(composite of subtree j moving with unit rate of joint j), ancestors only
-  float M[NV][NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const f3 cC = (1.f / mc[j]) * hc[j];
+    }
+  }
+// M~ column by column: lane j writes M_ij = M_ji for the ancestors i of j (zero otherwise),
+  // with the implicit damping on the diagonal, into the tree's M~^-1 slot used as scratch
+  float* mt = s.minv + (size_t)t * kMaxTreeDof * kMaxTreeDof;
+  {
+    const f3 cC = (mc > 0.f ? 1.f / mc : 0.f) * hc;
     const float cc = dot(cC, cC);
-    const float I6[6] = {Io[j][0] - mc[j] * (cc - cC.x * cC.x), Io[j][1] - mc[j] * (cc - cC.y * cC.y),
-                         Io[j][2] - mc[j] * (cc - cC.z * cC.z), Io[j][3] + mc[j] * cC.x * cC.y,
-                         Io[j][4] + mc[j] * cC.x * cC.z, Io[j][5] + mc[j] * cC.y * cC.z};
-    const f3 aj = ax[j];
-    const f3 Ia = mk3(I6[0] * aj.x + I6[3] * aj.y + I6[4] * aj.z, I6[3] * aj.x + I6[1] * aj.y + I6[5] * aj.z,
-                      I6[4] * aj.x + I6[5] * aj.y + I6[2] * aj.z);
-    const f3 lin = mc[j] * cross(aj, cC - x[j]);
+    const float I6[6] = {Io[0] - mc * (cc - cC.x * cC.x), Io[1] - mc * (cc - cC.y * cC.y),
+                         Io[2] - mc * (cc - cC.z * cC.z), Io[3] + mc * cC.x * cC.y,
+                         Io[4] + mc * cC.x * cC.z, Io[5] + mc * cC.y * cC.z};
+    const f3 Ia = mk3(I6[0] * ax.x + I6[3] * ax.y + I6[4] * ax.z, I6[3] * ax.x + I6[1] * ax.y + I6[5] * ax.z,
+                      I6[4] * ax.x + I6[5] * ax.y + I6[2] * ax.z);
+    const f3 lin = mc * cross(ax, cC - x);
 #pragma unroll
-    for (int i = 0; i <= j; ++i) {
-      const float mij = ((anc[j] >> i) & 1u) ? dot(ax[i], Ia + cross(cC - x[i], lin)) : 0.f;
-      M[i][j] = mij;
-      M[j][i] = mij;
+    for (int i = 0; i < 8; ++i) {
+      const f3 axi = gsh3(ax, i), xi = gsh3(x, i);
+      if (me && i <= r) {
+        float mij = ((anc >> i) & 1u) ? dot(axi, Ia + cross(cC - xi, lin)) : 0.f;
+        if (i == r) mij += dt * damp;
+        mt[i * kMaxTreeDof + r] = mij;
+        mt[r * kMaxTreeDof + i] = mij;
+      }
     }
   }
   // Newton-Euler bias with zero joint acceleration, the world accelerating at -g
-  f3 om[NV], omd[NV], ac[NV], F[NV], Nn[NV];
-  const f3 gv = mk3(P.gravity[0], P.gravity[1], P.gravity[2]);
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const DBody& bd = B[b0 + j];
-    const float qd = s.v[v0 + j];
-    f3 omp = mk3(0.f, 0.f, 0.f), omdp = omp, acp = omp, comp = omp;
-    bool root = true;
-#pragma unroll
-    for (int k = 0; k < j; ++k)
-      if (par[j] == k) { omp = om[k]; omdp = omd[k]; acp = ac[k]; comp = com[k]; root = false; }
-    om[j] = omp + qd * ax[j];
-    omd[j] = omdp + cross(omp, qd * ax[j]);
-    f3 aanc;
-    if (!root) {
-      const f3 ro = x[j] - comp;
-      aanc = acp + cross(omdp, ro) + cross(omp, cross(omp, ro));
-    } else {
-      aanc = -gv;
-    }
-    const f3 rc = com[j] - x[j];
-    ac[j] = aanc + cross(omd[j], rc) + cross(om[j], cross(om[j], rc));
-    F[j] = bd.mass * ac[j];
-    Nn[j] = iw_mul(R[j], bd.inertia, omd[j]) + cross(om[j], iw_mul(R[j], bd.inertia, om[j]));
+  const f3 w = qd * ax;                      // this joint's twist
+  const f3 om = gsum3(w, anc);               // over the ancestors and the body itself
+  const f3 omd = gsum3(cross(om, w), anc);   // om_parent x w = om x w
+  const f3 omp = gsh3(om, psrc), omdp = gsh3(omd, psrc);
+  const f3 ro = x - xp;
+  const f3 term = par >= 0 ? cross(omdp, ro) + cross(omp, cross(omp, ro)) : mk3(0.f, 0.f, 0.f);
+  const f3 ao = gsum3(term, anc) - mk3(P.gravity[0], P.gravity[1], P.gravity[2]);  // joint origin
+  const f3 rc = com - x;
+  const f3 ac = ao + cross(omd, rc) + cross(om, cross(om, rc));
+  const f3 F = me ? mass * ac : mk3(0.f, 0.f, 0.f);
+  f3 Nn;
+  {
+    const f3 l1 = mulT(R, omd), l2 = mulT(R, om);
+    Nn = mul(R, mk3(inert.x * l1.x, inert.y * l1.y, inert.z * l1.z)) +
+         cross(om, mul(R, mk3(inert.x * l2.x, inert.y * l2.y, inert.z * l2.z)));
   }
-  f3 ft[NV], nt[NV];
-  float rhs[NV];
+  const f3 T = me ? Nn + cross(com, F) : mk3(0.f, 0.f, 0.f);
+  f3 ft = mk3(0.f, 0.f, 0.f), nt = ft;  // over the subtree
 #pragma unroll
-  for (int j = 0; j < NV; ++j) { ft[j] = F[j]; nt[j] = Nn[j] + cross(com[j], F[j]); }
-#pragma unroll
-  for (int j = NV - 1; j >= 0; --j) {
-    const DBody& bd = B[b0 + j];
-    const float c = dot(ax[j], nt[j] - cross(x[j], ft[j]));
-    rhs[j] = (bd.uoff >= 0 ? s.tau[bd.uoff] : 0.f) - c - bd.damping * s.v[v0 + j];
-#pragma unroll
-    for (int k = 0; k < j; ++k)
-      if (par[j] == k) { ft[k] = ft[k] + ft[j]; nt[k] = nt[k] + nt[j]; }
-    M[j][j] += dt * bd.damping;
+  for (int k = 0; k < 8; ++k) {
+    const bool in = (gshi((int)anc, k) >> r) & 1;
+    const f3 fk = gsh3(F, k), tk = gsh3(T, k);
+    if (in) { ft = ft + fk; nt = nt + tk; }
   }
-  // Cholesky M~ = L L^T, the inverse L^-1 and M~^-1 = L^-T L^-1
-  float L[NV][NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    float d = M[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    d = sqrtf(fmaxf(d, 1e-30f));
-    L[j][j] = d;
-#pragma unroll
-    for (int i = j + 1; i < NV; ++i) {
-      float tt = M[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) tt -= L[i][k] * L[j][k];
-      L[i][j] = tt / d;
+  const float rhs = (uoff >= 0 ? s.tau[uoff] : 0.f) - dot(ax, nt - cross(x, ft)) - damp * qd;
+  __syncwarp();
+  // M~ = L L^T by one lane (n <= 8), in place in the lower triangle
+  if (me && r == 0) {
+    for (int j = 0; j < n; ++j) {
+      float d = mt[j * kMaxTreeDof + j];
+      for (int k = 0; k < j; ++k) d -= mt[j * kMaxTreeDof + k] * mt[j * kMaxTreeDof + k];
+      d = sqrtf(fmaxf(d, 1e-30f));
+      mt[j * kMaxTreeDof + j] = d;
+      for (int i = j + 1; i < n; ++i) {
+        float tt = mt[i * kMaxTreeDof + j];
+        for (int k = 0; k < j; ++k) tt -= mt[i * kMaxTreeDof + k] * mt[j * kMaxTreeDof + k];
+        mt[i * kMaxTreeDof + j] = tt / d;
+      }
     }
   }
-  float Li[NV][NV];
+  __syncwarp();
+  // column r of M~^-1: L y = e_r, then L^T x = y
+  float col[8];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
+  for (int i = 0; i < 8; ++i) {
+    float yi = 0.f;
+    if (me && i < n) {
+      yi = i == r ? 1.f : 0.f;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) Li[i][j] = 0.f;
-    Li[j][j] = 1.f / L[j][j];
+      for (int k = 0; k < i; ++k) yi -= mt[i * kMaxTreeDof + k] * col[k];
+      yi /= mt[i * kMaxTreeDof + i];
+    }
+    col[i] = yi;
+  }
 #pragma unroll
-    for (int i = j + 1; i < NV; ++i) {
-      float tt = 0.f;
+  for (int i = 7; i >= 0; --i) {
+    if (me && i < n) {
+      float xi = col[i];
 #pragma unroll
-      for (int k = j; k < i; ++k) tt += L[i][k] * Li[k][j];
-      Li[i][j] = -tt / L[i][i];
+      for (int k = i + 1; k < 8; ++k)
+        if (k < n) xi -= mt[k * kMaxTreeDof + i] * col[k];
+      col[i] = xi / mt[i * kMaxTreeDof + i];
     }
   }
-  float* mi = s.minv + (size_t)t * kMaxTreeDof * kMaxTreeDof;
-  float mv[NV][NV];
+  __syncwarp();
+  if (me)
 #pragma unroll
-  for (int i = 0; i < NV; ++i)
+    for (int i = 0; i < 8; ++i)
+      if (i < n) mt[i * kMaxTreeDof + r] = col[i];
+  __syncwarp();
+  // smooth velocity v_s = v + dt M~^-1 rhs (row r), then the body twists over the ancestors
+  float acc = 0.f;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      float tt = 0.f;
-#pragma unroll
-      for (int k = (i > j ? i : j); k < NV; ++k) tt += Li[k][i] * Li[k][j];
-      mv[i][j] = tt;
-      mi[i * kMaxTreeDof + j] = tt;
-    }
-  // smooth velocity and body twists
-  float vs[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float tt = 0.f;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) tt += mv[i][j] * rhs[j];
-    vs[i] = s.v[v0 + i] + dt * tt;
-    s.vs[v0 + i] = vs[i];
+  for (int k = 0; k < 8; ++k) {
+    const float rk = gshf(rhs, k);
+    if (me && k < n) acc += mt[r * kMaxTreeDof + k] * rk;
   }
-  f3 bom[NV], bvo[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    f3 omp = mk3(0.f, 0.f, 0.f), vop = omp, xp = omp;
-#pragma unroll
-    for (int k = 0; k < j; ++k)
-      if (par[j] == k) { omp = bom[k]; vop = bvo[k]; xp = x[k]; }
-    bom[j] = omp + vs[j] * ax[j];
-    bvo[j] = vop + cross(omp, x[j] - xp);
-    st3(s.bom + 3 * (b0 + j), bom[j]);
-    st3(s.bvo + 3 * (b0 + j), bvo[j]);
+  const float vs = qd + dt * acc;
+  if (me) s.vs[voff] = vs;
+  const f3 bom = gsum3(vs * ax, anc);
+  const f3 bomp = gsh3(bom, psrc);
+  const f3 bvo = gsum3(par >= 0 ? cross(bomp, ro) : mk3(0.f, 0.f, 0.f), anc);
+  if (me) {
+    st3(s.bom + 3 * b, bom);
+    st3(s.bvo + 3 * b, bvo);
   }
-}
-
-// one tree's preparation: the fixed-size versions for hinge trees of up to four bodies
-__device__ void artic_tree_prepare_any(const StepParams& P, ArticView& s, const DScene& sc, int t, int uadr,
-                                       int step) {
-  const DTree& tr = P.trees[sc.tree0 + t];
-  if (!tr.free) {
-    switch (tr.nv) {
-      case 1: artic_tree_prepare_n<1>(P, s, sc, tr, t, uadr, step); return;
-      case 2: artic_tree_prepare_n<2>(P, s, sc, tr, t, uadr, step); return;
-      case 3: artic_tree_prepare_n<3>(P, s, sc, tr, t, uadr, step); return;
-      case 4: artic_tree_prepare_n<4>(P, s, sc, tr, t, uadr, step); return;
-      default: break;
-    }
-  }
-  artic_tree_prepare(P, s, sc, tr, uadr, step);
 }
 
 // trace of the translational point Jacobian of body b at world point p through M~^-1
@@ -1513,7 +1359,14 @@ __device__ void artic_world(const StepParams& P, float* smem, int world, int gid
 
   for (int step = 0; step < P.nsteps; ++step) {
     group_sync(gid, T);
-    for (int t = tid; t < sc.ntree; t += T) artic_tree_prepare_any(P, s, sc, t, W.uadr, step);
+    // hinge trees by 8-lane groups (every thread of the world steps through the same loop, so
+    // that each warp's shuffles see all its lanes), then free bodies by their group's lane 0
+    for (int t0 = 0; t0 < sc.ntree; t0 += T / 8) {
+      const int t = t0 + tid / 8;
+      const bool hinge = t < sc.ntree && !P.trees[sc.tree0 + t].free;
+      artic_tree_prepare_group(P, s, sc, t, hinge, tid & 7);
+      if (t < sc.ntree && !hinge && (tid & 7) == 0) artic_free_prepare(P, s, sc, P.trees[sc.tree0 + t]);
+    }
     for (int i = tid; i < sc.nv; i += T) s.acc[i] = 0ull;
     if (tid == 0) { s.count[0] = 0; s.count[1] = 0; }
     group_sync(gid, T);
