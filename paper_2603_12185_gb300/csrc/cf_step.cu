@@ -770,10 +770,11 @@ __device__ __forceinline__ f3 gsum3(f3 v, unsigned sel) {
   return acc;
 }
 
-// One hinge tree of n <= 8 bodies (one hinge each, parents first) prepared by an 8-lane group:
-// the same quantities as artic_tree_prepare -- kinematics, composite inertia, bias, implicit
-// damping, the explicit M~^-1, the smooth velocity and the body twists -- with the chains
-// replaced by log-depth and masked-sum forms:
+// One hinge tree of n <= 8 bodies (one hinge each, parents first) prepared by an 8-lane group
+// (Sec. III-A's smooth prediction): body poses, the composite-rigid-body inertia M, the
+// Newton-Euler bias c, the implicitly damped M~ = M + dt diag(b), the explicit M~^-1, the
+// smooth velocity and the body twists.  Walks along a chain become log-depth or masked-sum
+// forms:
 //   - world poses by pointer jumping: (R, t) <- (R, t) of the pointer's frame o (R, t), three
 //     rounds covering depth 8;
 //   - sums over a body's ancestors (angular velocities and their rates, the acceleration of the
