@@ -112,11 +112,12 @@ typedef struct {
                               point Jacobian; 1: 1/m_i per body; 2: the exact diagonal
                               impedance of Sec. III-B instead of M(phi): per facet j,
                               M_j = 1 / ((k_user dt + d_user) J~_j M~^-1 J~_j^T) (solimp
-                              unused; cf_step_grad answers CF_ERR_UNSUPPORTED); 3: the
-                              learned impedance of Sec. III-B's learning-based K(q), D(q):
-                              mode 0's M(phi) times exp(clamp(g(x), -8, 8)), g the network
-                              of cf_batch_set_impedance_net (joint limits keep mode 0;
-                              cf_step_grad and cf_step_noalloc answer CF_ERR_UNSUPPORTED) */
+                              unused); 3: the learned impedance of Sec. III-B's
+                              learning-based K(q), D(q): mode 0's M(phi) times
+                              exp(clamp(g(x), -8, 8)), g the network of
+                              cf_batch_set_impedance_net (joint limits keep mode 0;
+                              cf_step_noalloc answers CF_ERR_UNSUPPORTED).  cf_step_grad
+                              differentiates all four modes */
 } cf_model_desc;
 
 /* Validate a description and build the host model.  Errors: CF_ERR_INVALID_ARGUMENT for a
@@ -221,11 +222,13 @@ cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
  * dL_dq0[total_nq], dL_dv0[total_nv] and dL_dtau[T][total_nu] (device).  The forward state is
  * recomputed from checkpoints every grad_ckpt steps.  The batch state is left at the rollout's
  * final state.  The differentiable set: hinge trees (with joint limits and dry joint friction)
- * and free bodies with sphere/capsule/box/plane geoms, the heuristic impedance (trace_mode 0
- * or 1); at a kink (a facet or a limit turning on, friction saturating, a narrowphase branch)
- * the derivative is that of the branch the state selects.  Errors: CF_ERR_UNSUPPORTED for
- * scenes outside that set (piles, box-box pairs, cylinders, ellipsoids, trace_mode 2 or 3),
- * CF_ERR_INVALID_ARGUMENT. */
+ * and free bodies with sphere/capsule/box/plane geoms, under every impedance mode (the
+ * heuristic ones, trace_mode 0 and 1; the exact, 2, through each facet's J~_j M~^-1 J~_j^T;
+ * the learned, 3, through the network's inputs); at a kink (a facet or a limit turning on,
+ * friction saturating, a narrowphase branch, a clamp of the network's inputs or output) the
+ * derivative is that of the branch the state selects.  Errors: CF_ERR_UNSUPPORTED for scenes
+ * outside that set (piles, box-box pairs, cylinders, ellipsoids), CF_ERR_INVALID_ARGUMENT
+ * (also trace_mode 3 without an impedance network). */
 cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                        float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);
 

@@ -218,13 +218,14 @@ def solimp_r(aphi, solimp):
     return lib().ow_solimp_r(float(aphi), _p(s))
 
 
-def rollout_loss_dir(desc, params, dt, q0, v0, tau, dq0, dv0, dtau, body, target_pos, target_quat):
-    """(L, dL/d(direction)) for the free body `body` after len(tau) steps (forward-mode duals)."""
+def rollout_loss_dir(desc, params, dt, q0, v0, tau, dq0, dv0, dtau, body, target_pos, target_quat, impnet=None):
+    """(L, dL/d(direction)) for the free body `body` after len(tau) steps (forward-mode duals);
+    impnet: the learned impedance's parameters when params.trace_mode == 3."""
     w = desc if isinstance(desc, World) else World(desc)
     T = len(tau)
     arr = [np.ascontiguousarray(a, np.float64) for a in (q0, v0, tau, dq0, dv0, dtau, target_pos, target_quat)]
     L, dL = C.c_double(), C.c_double()
-    ps = params_struct(params)
+    ps = params_struct(params, impnet)
     rc = lib().ow_rollout_loss_dir(C.byref(w.s), C.byref(ps), dt, T, _p(arr[0]), _p(arr[1]), _p(arr[2]),
                                    _p(arr[3]), _p(arr[4]), _p(arr[5]), body, _p(arr[6]), _p(arr[7]), C.byref(L),
                                    C.byref(dL))

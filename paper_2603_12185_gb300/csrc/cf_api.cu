@@ -1008,7 +1008,8 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
                                   float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream) {
   if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
   if (b->opts.grad_steps <= 0) return fail(CF_ERR_UNSUPPORTED, "batch created without an adjoint tape (grad_steps = 0)");
-  if (b->model.trace_mode >= 2) return fail(CF_ERR_UNSUPPORTED, "the adjoint covers the heuristic impedance only");
+  if (b->model.trace_mode == 3 && !b->impnet)
+    return fail(CF_ERR_INVALID_ARGUMENT, "trace_mode 3 needs an impedance network (cf_batch_set_impedance_net)");
   if (T < 1 || T > b->opts.grad_steps || T > b->opts.max_ctrl_steps)
     return fail(CF_ERR_INVALID_ARGUMENT, "T = %d outside [1, min(grad_steps, max_ctrl_steps)]", T);
   if (!(dt > 0.f)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
@@ -1035,6 +1036,7 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
   g.dtau = b->total_nu > 0 ? dL_dtau : nullptr;
   g.num_sms = b->num_sms;
   g.smem = b->smem_all;
+  g.variant = b->imp ? kExtVariant : 0;  // the impedance modes live in the extended kernel
   cudaError_t e = run_grad(p, g, b->nctrl, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return CF_OK;

@@ -58,6 +58,16 @@ __device__ __forceinline__ DF spow(DF a, float p) {
   return DF(r, a.v != 0.f ? p * r / a.v * a.d : 0.f);
 }
 __device__ __forceinline__ float spow(float a, float p) { return powf(a, p); }
+__device__ __forceinline__ DF sexp(DF a) {
+  const float e = expf(a.v);
+  return DF(e, e * a.d);
+}
+__device__ __forceinline__ float sexp(float a) { return expf(a); }
+__device__ __forceinline__ DF stanh(DF a) {
+  const float t = tanhf(a.v);
+  return DF(t, (1.f - t * t) * a.d);
+}
+__device__ __forceinline__ float stanh(float a) { return tanhf(a); }
 template <class S> __device__ __forceinline__ S sabs(S a) { return a < S(0.f) ? -a : a; }
 template <class S> __device__ __forceinline__ S smax(S a, S b) { return a > b ? a : b; }
 template <class S> __device__ __forceinline__ S smin(S a, S b) { return a < b ? a : b; }
@@ -505,7 +515,7 @@ template <class S>
 __device__ S w1_trace(const StepParams& P, const DScene& sc, const W1<S>& w, int b, V3<S> p) {
   const DBody* B = P.bodies + sc.body0;
   const DBody& bd = B[b];
-  if (P.trace_mode) return S(1.f / bd.mass);
+  if (P.trace_mode == 1) return S(1.f / bd.mass);
   const DTree& tr = P.trees[sc.tree0 + bd.tree];
   if (tr.free) {
     V3<S> r = p - w.bx[b];
@@ -552,9 +562,160 @@ __device__ S w1_solimp(const StepParams& P, S aphi) {
   return S(P.solimp[0]) + (S(P.solimp[1]) - S(P.solimp[0])) * g;
 }
 
+// Gram blocks of a contact's six basis rows (n, t1, t2 linear; n, t1, t2 angular) through
+// M~^-1, as the exact diagonal impedance of Sec. III-B needs them
+template <class S> struct GramS {
+  S nn, n1, n2, t11, t12, t22;  // translational block
+  S n3, r33;                    // torsional
+  S n4, n5, r44, r45, r55;      // rolling
+};
+
+// free body: inverse mass im, inverse principal inertia ii, rotation R, lever r
 template <class S>
-__device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int ga, int gb, const RawS<S>& k,
-                           bool plane, V3<S> px) {
+__device__ void w1_gram_free(GramS<S>& g, S im, V3<S> ii, const M3<S>& R, V3<S> r, V3<S> n, V3<S> t1, V3<S> t2) {
+  const V3<S> a0 = mulT(R, cross(r, n)), a1 = mulT(R, cross(r, t1)), a2 = mulT(R, cross(r, t2));
+  const V3<S> e0 = mulT(R, n), e1 = mulT(R, t1), e2 = mulT(R, t2);
+  auto q = [&](V3<S> x, V3<S> y) { return x.x * y.x * ii.x + x.y * y.y * ii.y + x.z * y.z * ii.z; };
+  g.nn += im + q(a0, a0); g.n1 += q(a0, a1); g.n2 += q(a0, a2);
+  g.t11 += im + q(a1, a1); g.t12 += q(a1, a2); g.t22 += im + q(a2, a2);
+  g.n3 += q(a0, e0); g.r33 += q(e0, e0);
+  g.n4 += q(a0, e1); g.n5 += q(a0, e2); g.r44 += q(e1, e1); g.r45 += q(e1, e2); g.r55 += q(e2, e2);
+}
+
+// Gram of the contact between bodies ba and bb (bb < 0: static): free bodies in closed form,
+// hinge chains through their joint-space rows and the tree's M~^-1, the rows of two bodies of
+// one tree combined first (J = J_A - J_B)
+template <class S>
+__device__ void w1_gram(const StepParams& P, const DScene& sc, const W1<S>& w, int ba, int bb, V3<S> p, V3<S> n,
+                        V3<S> t1, V3<S> t2, GramS<S>& g) {
+  const DBody* B = P.bodies + sc.body0;
+  S G[2][6][kMaxTreeDof];
+  int gtree[2] = {-1, -1}, gnv[2] = {0, 0};
+  int ng = 0;
+  g.nn = g.n1 = g.n2 = g.t11 = g.t12 = g.t22 = g.n3 = g.r33 = g.n4 = g.n5 = g.r44 = g.r45 = g.r55 = S(0.f);
+  for (int side = 0; side < 2; ++side) {
+    const int b = side ? bb : ba;
+    if (b < 0) continue;
+    const S sg(side ? -1.f : 1.f);
+    const DBody& bd = B[b];
+    const DTree& tr = P.trees[sc.tree0 + bd.tree];
+    if (tr.free) {
+      w1_gram_free(g, S(1.f / bd.mass), v3(S(1.f / bd.inertia[0]), S(1.f / bd.inertia[1]), S(1.f / bd.inertia[2])),
+                   w.bR[b], p - w.bx[b], n, t1, t2);
+      continue;
+    }
+    const int slot = (ng > 0 && gtree[0] == bd.tree) ? 0 : ng;
+    if (slot == ng) {
+      gtree[slot] = bd.tree;
+      gnv[slot] = tr.nv;
+      for (int x = 0; x < 6; ++x)
+        for (int i = 0; i < kMaxTreeDof; ++i) G[slot][x][i] = S(0.f);
+      ++ng;
+    }
+    for (int a = b; a >= 0; a = B[a].parent) {
+      const int k = B[a].voff - tr.voff;
+      const V3<S> ax = w.bax[a];
+      const V3<S> lin = cross(ax, p - w.bx[a]);  // point velocity per unit joint rate
+      G[slot][0][k] += sg * dot(n, lin); G[slot][1][k] += sg * dot(t1, lin); G[slot][2][k] += sg * dot(t2, lin);
+      G[slot][3][k] += sg * dot(n, ax); G[slot][4][k] += sg * dot(t1, ax); G[slot][5][k] += sg * dot(t2, ax);
+    }
+  }
+  for (int slot = 0; slot < ng; ++slot) {
+    const S* mi = w.minv[gtree[slot]];
+    const int nv = gnv[slot];
+    auto q = [&](int x, int y) {  // G_x^T M~^-1 G_y
+      S acc(0.f);
+      for (int i = 0; i < nv; ++i) {
+        S h(0.f);
+        for (int j = 0; j < nv; ++j) h += mi[i * kMaxTreeDof + j] * G[slot][y][j];
+        acc += G[slot][x][i] * h;
+      }
+      return acc;
+    };
+    g.nn += q(0, 0); g.n1 += q(0, 1); g.n2 += q(0, 2); g.t11 += q(1, 1); g.t12 += q(1, 2); g.t22 += q(2, 2);
+    g.n3 += q(0, 3); g.r33 += q(3, 3);
+    g.n4 += q(0, 4); g.n5 += q(0, 5); g.r44 += q(4, 4); g.r45 += q(4, 5); g.r55 += q(5, 5);
+  }
+}
+
+// J~_j M~^-1 J~_j^T of a facet row n_row - mu (c x + s y) from the Gram entries of its rows
+template <class S>
+__device__ S w1_gram_facet(S nn, S nx, S ny, S xx, S xy, S yy, S mu, float c, float s) {
+  return nn - S(2.f) * mu * (S(c) * nx + S(s) * ny) +
+         mu * mu * (S(c * c) * xx + S(2.f * c * s) * xy + S(s * s) * yy);
+}
+
+// Facet impulses with the exact diagonal impedance of Sec. III-B: M(phi) replaced per facet j
+// by M_j = 1 / ((k dt + d) J~_j M~^-1 J~_j^T); outputs the resultant (normal, t1, t2, torsion,
+// rolling t1, rolling t2) on A
+template <class S>
+__device__ void w1_facets_exact(const StepParams& P, S vn, S vt1, S vt2, S wn, S wr1, S wr2, S phi, S mu_t, S mu_tor,
+                                S mu_rol, const GramS<S>& g, S& N, S& F1, S& F2, S& Tq, S& R1, S& R2) {
+  const S kd(fmaf(P.k_user, P.dt, P.d_user));
+  const S a = -S(P.k_user) * phi - kd * vn;
+  S f1(0.f), f2(0.f), t(0.f), r1(0.f), r2(0.f);
+  for (int j = 0; j < P.n_t; ++j) {
+    const float c = P.tcos[j], s = P.tsin[j];
+    const S gj = a + kd * mu_t * (S(c) * vt1 + S(s) * vt2);
+    if (val(gj) > 0.f) {
+      const S lam = gj / (kd * w1_gram_facet(g.nn, g.n1, g.n2, g.t11, g.t12, g.t22, mu_t, c, s));
+      N += lam; f1 += S(c) * lam; f2 += S(s) * lam;
+    }
+  }
+  for (int j = 0; j < P.n_tor; ++j) {
+    const S sg((j & 1) ? -1.f : 1.f);
+    const S gj = a + kd * mu_tor * sg * wn;
+    if (val(gj) > 0.f) {
+      const S lam = gj / (kd * (g.nn - S(2.f) * mu_tor * sg * g.n3 + mu_tor * mu_tor * g.r33));
+      N += lam; t += sg * lam;
+    }
+  }
+  for (int j = 0; j < P.n_rol; ++j) {
+    const float c = P.rcos[j], s = P.rsin[j];
+    const S gj = a + kd * mu_rol * (S(c) * wr1 + S(s) * wr2);
+    if (val(gj) > 0.f) {
+      const S lam = gj / (kd * w1_gram_facet(g.nn, g.n4, g.n5, g.r44, g.r45, g.r55, mu_rol, c, s));
+      N += lam; r1 += S(c) * lam; r2 += S(s) * lam;
+    }
+  }
+  F1 = -mu_t * f1; F2 = -mu_t * f2; Tq = -mu_tor * t; R1 = -mu_rol * r1; R2 = -mu_rol * r2;
+}
+
+// The learned impedance's factor exp(clamp(g(x), -8, 8)) on M(phi) (Sec. III-B's learned
+// K(q), D(q)): inputs x = (phi / width, 1 - 3 sum(1/m) / tr, w_n / tr, b static), with w_n the
+// normal row's inverse mass of both links taken as free bodies about their centres of mass;
+// g = b2 + sum_h w2_h tanh(b1_h + sum_i W1_hi x_i) with parameters th [W1 (8 x 4), b1, w2, b2]
+template <class S>
+__device__ S w1_impnet_scale(const StepParams& P, const DScene& sc, const W1<S>& w, const float* th, int ba, int bb,
+                             V3<S> p, V3<S> n, S phi, S tr) {
+  const DBody* B = P.bodies + sc.body0;
+  auto side = [&](int b) {
+    const DBody& bd = B[b];
+    const M3<S>& R = w.bR[b];
+    const V3<S> com = w.bx[b] + mul(R, v3f<S>(bd.ipos));
+    const V3<S> u = mulT(R, cross(p - com, n));
+    return S(1.f / bd.mass) + u.x * u.x * S(1.f / bd.inertia[0]) + u.y * u.y * S(1.f / bd.inertia[1]) +
+           u.z * u.z * S(1.f / bd.inertia[2]);
+  };
+  const S im_sum(1.f / B[ba].mass + (bb >= 0 ? 1.f / B[bb].mass : 0.f));
+  const S w_n = bb >= 0 ? side(ba) + side(bb) : side(ba);
+  S x[kImpIn];
+  x[0] = sclamp(phi / S(P.solimp[2]), S(-1.f), S(1.f));
+  x[1] = sclamp(S(1.f) - S(3.f) * im_sum / tr, S(-1.f), S(1.f));
+  x[2] = sclamp(w_n / tr, S(0.f), S(4.f));
+  x[3] = S(bb < 0 ? 1.f : 0.f);
+  S gsum(th[kImpParams - 1]);
+  for (int h = 0; h < kImpHidden; ++h) {
+    S a(th[kImpHidden * kImpIn + h]);
+    for (int i = 0; i < kImpIn; ++i) a += S(th[h * kImpIn + i]) * x[i];
+    gsum += S(th[kImpHidden * kImpIn + kImpHidden + h]) * stanh(a);
+  }
+  return sexp(sclamp(gsum, S(-kImpClamp), S(kImpClamp)));
+}
+
+template <class S, bool kImp>
+__device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int world, int ga, int gb,
+                           const RawS<S>& k, bool plane, V3<S> px) {
   const DGeom& GA = P.geoms[sc.geom0 + ga];
   const DGeom& GB = P.geoms[sc.geom0 + gb];
   const int ba = GA.body, bb = GB.body;
@@ -574,14 +735,26 @@ __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int 
     wc = wc - w.om[bb];
     tr += w1_trace(P, sc, w, bb, k.p);
   }
-  S r = w1_solimp(P, sabs(k.phi));
-  S mphi = r / (S(1.f) - r) / tr;
-  S kM = S(P.k_user) * mphi, dM = S(P.d_user) * mphi;
-  S A = -kM * k.phi, Bc = kM * S(P.dt) + dM;
   S vn = dot(k.n, vc), vt1 = dot(t1, vc), vt2 = dot(t2, vc);
   S wn = dot(k.n, wc), wr1 = dot(t1, wc), wr2 = dot(t2, wc);
   S mut(fmaxf(GA.mu[0], GB.mu[0])), mutor(fmaxf(GA.mu[1], GB.mu[1])), murol(fmaxf(GA.mu[2], GB.mu[2]));
   S N(0.f), F1(0.f), F2(0.f), Tq(0.f), R1(0.f), R2(0.f);
+  if (kImp && P.trace_mode == 2) {
+    GramS<S> g;
+    w1_gram(P, sc, w, ba, bb, k.p, k.n, t1, t2, g);
+    w1_facets_exact(P, vn, vt1, vt2, wn, wr1, wr2, k.phi, mut, mutor, murol, g, N, F1, F2, Tq, R1, R2);
+    V3<S> f = N * k.n + F1 * t1 + F2 * t2;
+    V3<S> m = Tq * k.n + R1 * t1 + R2 * t2;
+    w1_apply(P, sc, w, ba, k.p, f, m);
+    if (bb >= 0) w1_apply(P, sc, w, bb, k.p, -f, -m);
+    return;
+  }
+  S r = w1_solimp(P, sabs(k.phi));
+  S mphi = r / (S(1.f) - r) / tr;
+  if (kImp && P.trace_mode == 3)
+    mphi = mphi * w1_impnet_scale(P, sc, w, P.impnet + (size_t)world * P.impnet_stride, ba, bb, k.p, k.n, k.phi, tr);
+  S kM = S(P.k_user) * mphi, dM = S(P.d_user) * mphi;
+  S A = -kM * k.phi, Bc = kM * S(P.dt) + dM;
   for (int j = 0; j < P.n_t; ++j) {
     S c(P.tcos[j]), s(P.tsin[j]);
     S lam = smax(A - Bc * (vn - mut * (c * vt1 + s * vt2)), S(0.f));
@@ -608,8 +781,8 @@ __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int 
   if (bb >= 0) w1_apply(P, sc, w, bb, k.p, -f, -m);
 }
 
-template <class S>
-__device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int ga, int gb) {
+template <class S, bool kImp>
+__device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int world, int ga, int gb) {
   const DGeom* G = P.geoms + sc.geom0;
   int ta = G[ga].type, tb = G[gb].type;
   if (ta == CF_GEOM_PLANE) { int t = ga; ga = gb; gb = t; t = ta; ta = tb; tb = t; }
@@ -623,19 +796,19 @@ __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int ga,
     V3<S> nz = colv(Rb, 2), px = colv(Rb, 0);
     if (ta == CF_GEOM_SPHERE) {
       RawS<S> k = g_sphere_plane(ca, S(sa[0]), cb, nz);
-      if (k.phi < margin) w1_contact(P, sc, w, ga, gb, k, true, px);
+      if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
     } else if (ta == CF_GEOM_CAPSULE) {
       V3<S> ax = colv(Ra, 2);
       for (int e = 0; e < 2; ++e) {
         RawS<S> k = g_sphere_plane(ca + S(e ? sa[1] : -sa[1]) * ax, S(sa[0]), cb, nz);
-        if (k.phi < margin) w1_contact(P, sc, w, ga, gb, k, true, px);
+        if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
       }
     } else if (ta == CF_GEOM_BOX) {
       for (int ci = 0; ci < 8; ++ci) {
         V3<S> corner = ca + mul(Ra, v3(S((ci & 4) ? sa[0] : -sa[0]), S((ci & 2) ? sa[1] : -sa[1]),
                                        S((ci & 1) ? sa[2] : -sa[2])));
         RawS<S> k = g_sphere_plane(corner, S(0.f), cb, nz);
-        if (k.phi < margin) w1_contact(P, sc, w, ga, gb, k, true, px);
+        if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
       }
     }
     return;
@@ -675,13 +848,13 @@ __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int ga,
       k = g_sphere_box(co + t * u, S(os[0]), cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < margin) w1_contact(P, sc, w, ga, gb, k, false, v3(S(0.f), S(0.f), S(0.f)));
+  if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, false, v3(S(0.f), S(0.f), S(0.f)));
 }
 
 // one step of an articulated world in scalar type S: q[nq], v[nv] updated in place, tau per
 // actuated hinge (scene order)
-template <class S>
-__device__ void w1_step(const StepParams& P, const DScene& sc, S* q, S* v, const S* tau, W1<S>& w) {
+template <class S, bool kImp>
+__device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, S* v, const S* tau, W1<S>& w) {
   const DBody* B = P.bodies + sc.body0;
   const DGeom* G = P.geoms + sc.geom0;
   for (int t = 0; t < sc.ntree; ++t) w1_tree(P, sc, t, q, v, tau, w);
@@ -718,7 +891,7 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, S* q, S* v, const
       float rr = bound(ga) + bound(gb) + P.margin;
       cand = val(dot(d, d)) < rr * rr;
     }
-    if (cand) w1_pair(P, sc, w, ga, gb);
+    if (cand) w1_pair<S, kImp>(P, sc, w, world, ga, gb);
   }
   // joint limits and dry joint friction, the step kernel's per-hinge impulses on the smooth
   // prediction: a limit below the margin is a one-row constraint +-e_k with the facet law and
@@ -744,8 +917,13 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, S* q, S* v, const
             if (!(val(gap) < P.margin)) continue;
             const S sg(side ? -1.f : 1.f);
             const S sv = sg * vsk;
-            const S r = w1_solimp(P, sabs(gap));
-            const S Mk = r / ((S(1.f) - r) * wkk);
+            S Mk;
+            if (kImp && P.trace_mode == 2) {  // the exact impedance of the one-row constraint
+              Mk = S(1.f) / (S(fmaf(P.k_user, P.dt, P.d_user)) * wkk);
+            } else {
+              const S r = w1_solimp(P, sabs(gap));
+              Mk = r / ((S(1.f) - r) * wkk);
+            }
             const S lam = -S(P.k_user) * Mk * (sv * S(P.dt) + gap) - S(P.d_user) * Mk * sv;
             if (val(lam) > 0.f) pk += sg * lam;
           }
@@ -805,6 +983,8 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, S* q, S* v, const
 // vector-Jacobian product of one step: CTA per world, lane j = input coordinate j
 // (q, then v, then actuated tau); a_in = adjoint of the step's output state
 // ---------------------------------------------------------------------------------------
+// kImp: the exact and learned impedances (trace_mode 2, 3) compiled in
+template <bool kImp>
 __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float* q, const float* v, int step,
                                                        const float* aq_in, const float* av_in, float* aq_out,
                                                        float* av_out, float* dtau, int64_t total_nu) {
@@ -820,7 +1000,7 @@ __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float
     int slice = P.nctrl > 0 ? (step < P.nctrl ? step : P.nctrl - 1) : -1;
     for (int i = 0; i < sc.nu; ++i)
       tau[i] = DF(slice >= 0 ? P.ctrl[(size_t)slice * P.total_nu + Wd.uadr + i] : 0.f, j == sc.nq + sc.nv + i ? 1.f : 0.f);
-    w1_step(P, sc, qs, vs, tau, w);
+    w1_step<DF, kImp>(P, sc, world, qs, vs, tau, w);
     float acc = 0.f;
     for (int i = 0; i < sc.nq; ++i) acc = fmaf(qs[i].d, aq_in[Wd.qadr + i], acc);
     for (int i = 0; i < sc.nv; ++i) acc = fmaf(vs[i].d, av_in[Wd.vadr + i], acc);
@@ -872,9 +1052,9 @@ cudaError_t run_grad(const StepParams& p0, const GradArgs& g, int nctrl, cudaStr
     ps.nsteps = n;
     ps.capture = nullptr;
     ps.capture_cap = 0;
-    int per = step_max_blocks_per_sm(true, 0, g.smem);
+    int per = step_max_blocks_per_sm(true, g.variant, g.smem);
     int grid = ps.nunits < g.num_sms * per ? ps.nunits : g.num_sms * per;
-    return launch_step(ps, true, 0, grid, g.smem, s);
+    return launch_step(ps, true, g.variant, grid, g.smem, s);
   };
   // forward pass with checkpoints (the batch state advances to step T)
   e = cudaMemcpyAsync(qptr(ckpt(0)), p.q, nq * sizeof(float), cudaMemcpyDeviceToDevice, s);
@@ -905,8 +1085,12 @@ cudaError_t run_grad(const StepParams& p0, const GradArgs& g, int nctrl, cudaStr
     for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
       StepParams pv = p;
       pv.ctrl_offset = 0;
-      vjp_kernel<<<g.W, kG1Lanes, 0, s>>>(pv, qptr(seg(i)), vptr(seg(i)), first + i, qptr(ain), vptr(ain), qptr(aout),
-                                          vptr(aout), g.dtau, g.total_nu);
+      if (p.trace_mode >= 2)
+        vjp_kernel<true><<<g.W, kG1Lanes, 0, s>>>(pv, qptr(seg(i)), vptr(seg(i)), first + i, qptr(ain), vptr(ain),
+                                                  qptr(aout), vptr(aout), g.dtau, g.total_nu);
+      else
+        vjp_kernel<false><<<g.W, kG1Lanes, 0, s>>>(pv, qptr(seg(i)), vptr(seg(i)), first + i, qptr(ain), vptr(ain),
+                                                   qptr(aout), vptr(aout), g.dtau, g.total_nu);
       e = cudaGetLastError();
       char* t = ain;
       ain = aout;

@@ -23,6 +23,7 @@ struct GradArgs {
   float *dq0, *dv0, *dtau;
   int num_sms;
   size_t smem;               // dynamic shared memory of the step launch over all worlds
+  int variant;               // step-kernel variant of the forward recomputation (launch_step)
 };
 
 size_t grad_workspace_bytes(int W, int64_t total_nq, int64_t total_nv, const cf_batch_opts& o);

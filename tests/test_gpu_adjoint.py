@@ -6,6 +6,8 @@ checked along a seeded random direction in (initial joint velocities, per-step j
 A world whose active set changes within +-h (oracle duals and oracle differences disagree) is
 excluded and counted.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -44,8 +46,10 @@ def _case(nworld, T, seed, limited=False):
     return sb, tau, tp, tq, dirs_v, dirs_t
 
 
-def _gpu_grad(sb, tau, tp, tq, T, ckpt):
+def _gpu_grad(sb, tau, tp, tq, T, ckpt, net=None):
     _, b = CF.from_scenes(sb, max_ctrl_steps=T, grad_steps=T, grad_ckpt=ckpt)
+    if net is not None:
+        b.set_impedance_net(torch.tensor(net, dtype=torch.float32, device="cuda").view(1, -1), 1)
     q0, v0 = CF.flatten_state(sb)
     q0 = torch.from_numpy(q0).cuda().requires_grad_(True)
     v0 = torch.from_numpy(v0).cuda().requires_grad_(True)
@@ -59,7 +63,7 @@ def _gpu_grad(sb, tau, tp, tq, T, ckpt):
     return L.detach().cpu().numpy(), v0.grad.view(W, 22).cpu().numpy(), tt.grad.view(T, W, 16).cpu().numpy()
 
 
-def _oracle(sb, w, tau_w, tp, tq, dv, dt_dir, h=1e-6):
+def _oracle(sb, w, tau_w, tp, tq, dv, dt_dir, h=1e-6, net=None):
     d = sb.world(w)
     T = tau_w.shape[0]
     tau_full = np.zeros((T, 22))
@@ -70,15 +74,15 @@ def _oracle(sb, w, tau_w, tp, tq, dv, dt_dir, h=1e-6):
     dv0[6:] = dv
     q0 = PR.f32(sb.q0[w])
     v0 = PR.f32(sb.v0[w])
-    L, dL = O.rollout_loss_dir(d, sb.params, sb.dt, q0, v0, tau_full, np.zeros(23), dv0, dtau, 0, tp, tq)
+    L, dL = O.rollout_loss_dir(d, sb.params, sb.dt, q0, v0, tau_full, np.zeros(23), dv0, dtau, 0, tp, tq, impnet=net)
     Lp, _ = O.rollout_loss_dir(d, sb.params, sb.dt, q0, v0 + h * dv0, tau_full + h * dtau, np.zeros(23), dv0, dtau, 0,
-                               tp, tq)
+                               tp, tq, impnet=net)
     Lm, _ = O.rollout_loss_dir(d, sb.params, sb.dt, q0, v0 - h * dv0, tau_full - h * dtau, np.zeros(23), dv0, dtau, 0,
-                               tp, tq)
+                               tp, tq, impnet=net)
     return L, dL, (Lp - Lm) / (2 * h)
 
 
-def _dual(sb, w, tau_w, tp, tq, coord):
+def _dual(sb, w, tau_w, tp, tq, coord, net=None):
     """The oracle's forward-mode derivative of the loss along one unit direction: ("v", k) the
     k-th hinge rate of v0, ("tau", s, k) the k-th torque at step s."""
     T = tau_w.shape[0]
@@ -90,7 +94,7 @@ def _dual(sb, w, tau_w, tp, tq, coord):
     else:
         dtau[coord[1], 6 + coord[2]] = 1.0
     return O.rollout_loss_dir(sb.world(w), sb.params, sb.dt, PR.f32(sb.q0[w]), PR.f32(sb.v0[w]), tau_full,
-                              np.zeros(23), dv0, dtau, 0, tp, tq)[1]
+                              np.zeros(23), dv0, dtau, 0, tp, tq, impnet=net)[1]
 
 
 @pytest.mark.parametrize("T,ckpt,rtol", [(20, 5, 2e-3), (100, 10, 2e-2)])
@@ -171,6 +175,44 @@ def test_adjoint_with_joint_limits_and_dry_friction():
         gpu = list(gv[w, 6:])
         for s_ in (0, T - 1):
             ref += [_dual(sb, w, tw, tp, tq, ("tau", s_, k)) for k in range(16)]
+            gpu += list(gt[s_, w])
+        ref, gpu = np.array(ref), np.array(gpu)
+        scale = np.abs(ref).max()
+        bad = np.abs(gpu - ref) > 1e-3 * (np.abs(ref) + 1e-3 * scale)
+        assert not bad.any(), f"world {w}: coordinates {np.flatnonzero(bad)} gpu {gpu[bad]} oracle {ref[bad]}"
+        checked += 1
+    assert checked >= nworld // 2, f"only {checked} of {nworld} worlds checked"
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_adjoint_in_the_exact_and_learned_impedance_modes(mode):
+    """The impedance modes of Sec. III-B through the adjoint.
+    - trace_mode 2: the exact diagonal impedance, M_j = 1 / ((k dt + d) J~_j M~^-1 J~_j^T) per
+      facet from the contact's Gram blocks, and its one-row form at joint limits.
+    - trace_mode 3: the learned one, M(phi) times exp(clamp(g(x))) of a seeded network (FP32
+      values, as the GPU holds them).
+    As with joint limits, every coordinate of dL/dv0 and of dL/dtau at steps 0 and 9 at
+    T = 10 is checked against the oracle's duals, and the random-direction derivative against
+    FP64 central differences."""
+    T, nworld = 10, 8
+    sb, tau, tp, tq, dirs_v, dirs_t = _case(nworld, T, seed=19, limited=True)
+    sb.params = dataclasses.replace(sb.params, trace_mode=mode)
+    net = None
+    if mode == 3:
+        net = np.random.default_rng(3).normal(0.0, 0.4, O.impnet_params()).astype(np.float32).astype(np.float64)
+    _, gv, gt = _gpu_grad(sb, tau, tp, tq, T, 5, net=net)
+    checked = 0
+    for w in range(nworld):
+        tw = tau[:, w].astype(np.float64)
+        _, dLo, fd = _oracle(sb, w, tw, tp, tq, dirs_v[w], dirs_t[:, w], net=net)
+        if abs(dLo - fd) > 1e-4 * max(abs(fd), 1e-6):
+            continue
+        g = float(gv[w, 6:] @ dirs_v[w] + np.sum(gt[:, w] * dirs_t[:, w]))
+        assert g == pytest.approx(dLo, rel=2e-3, abs=1e-6 * max(1.0, abs(dLo))), f"world {w}"
+        ref = [_dual(sb, w, tw, tp, tq, ("v", k), net=net) for k in range(16)]
+        gpu = list(gv[w, 6:])
+        for s_ in (0, T - 1):
+            ref += [_dual(sb, w, tw, tp, tq, ("tau", s_, k), net=net) for k in range(16)]
             gpu += list(gt[s_, w])
         ref, gpu = np.array(ref), np.array(gpu)
         scale = np.abs(ref).max()
