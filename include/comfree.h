@@ -222,12 +222,14 @@ cf_status cf_batch_set_warps(cf_batch* batch, int32_t scene, int32_t warps);
  * dL_dq0[total_nq], dL_dv0[total_nv] and dL_dtau[T][total_nu] (device).  The forward state is
  * recomputed from checkpoints every grad_ckpt steps.  The batch state is left at the rollout's
  * final state.  The differentiable set: hinge trees (with joint limits and dry joint friction)
- * and free bodies with sphere/capsule/box/plane geoms, under every impedance mode (the
+ * and free bodies with every geom type (sphere, capsule, box, cylinder, ellipsoid, plane;
+ * box-box pairs through their clipped face vertices), under every impedance mode (the
  * heuristic ones, trace_mode 0 and 1; the exact, 2, through each facet's J~_j M~^-1 J~_j^T;
  * the learned, 3, through the network's inputs); at a kink (a facet or a limit turning on,
  * friction saturating, a narrowphase branch, a clamp of the network's inputs or output) the
- * derivative is that of the branch the state selects.  Errors: CF_ERR_UNSUPPORTED for scenes
- * outside that set (piles, box-box pairs, cylinders, ellipsoids), CF_ERR_INVALID_ARGUMENT
+ * derivative is that of the branch the state selects (a separating axis, a reference face or
+ * a clipped vertex included).  Errors: CF_ERR_UNSUPPORTED for pile scenes and for worlds past
+ * the per-world limits (24 bodies, 32 geoms, 48 q, 48 v, 8 trees), CF_ERR_INVALID_ARGUMENT
  * (also trace_mode 3 without an impedance network). */
 cf_status cf_step_grad(cf_batch* batch, int32_t T, float dt, const float* dL_dqT, const float* dL_dvT,
                        float* dL_dq0, float* dL_dv0, float* dL_dtau, void* stream);

@@ -1036,7 +1036,8 @@ extern "C" cf_status cf_step_grad(cf_batch* b, int32_t T, float dt, const float*
   g.dtau = b->total_nu > 0 ? dL_dtau : nullptr;
   g.num_sms = b->num_sms;
   g.smem = b->smem_all;
-  g.variant = b->imp ? kExtVariant : 0;  // the impedance modes live in the extended kernel
+  // the impedance modes, box-box pairs, cylinders and ellipsoids live in the extended kernel
+  g.variant = (b->imp || b->ext) ? kExtVariant : 0;
   cudaError_t e = run_grad(p, g, b->nctrl, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return CF_OK;

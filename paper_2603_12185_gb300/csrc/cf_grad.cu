@@ -305,6 +305,152 @@ template <class S> __device__ S g_capsule_box_param(V3<S> x0v, V3<S> wv, S h, V3
   return best;
 }
 
+// Ellipsoid (centre c, rotation R, semi-axes e) against a plane (point o, normal n): the
+// support point against n, c - R D^2 R^T n / |D R^T n| (D = diag(e)), is the lowest point
+template <class S> __device__ RawS<S> g_ellipsoid_plane(V3<S> c, const M3<S>& R, V3<S> e, V3<S> o, V3<S> n) {
+  const V3<S> nl = mulT(R, n);
+  const V3<S> dn = v3(e.x * nl.x, e.y * nl.y, e.z * nl.z);
+  const S il = S(1.f) / ssqrt(dot(dn, dn));
+  const V3<S> p = c - mul(R, v3(e.x * dn.x * il, e.y * dn.y * il, e.z * dn.z * il));
+  RawS<S> k;
+  k.phi = dot(n, p - o);
+  k.p = p - (S(0.5f) * k.phi) * n;
+  k.n = n;
+  return k;
+}
+
+// Cylinder (centre c, rotation R, radius r, half length h along body z) against a plane: rim
+// point `sub` = 3 cap + j, cap 0 at -h and cap 1 at +h, at 120 j degrees from the rim's lowest
+// direction u x (u x n) normalised (the body x axis when the caps are parallel to the plane)
+template <class S>
+__device__ RawS<S> g_cylinder_plane(V3<S> c, const M3<S>& R, float r, float h, V3<S> o, V3<S> n, int sub) {
+  const V3<S> u = colv(R, 2);
+  V3<S> w = cross(u, cross(u, n));
+  const S wl2 = dot(w, w);
+  w = val(wl2) > 1e-12f ? (S(1.f) / ssqrt(wl2)) * w : colv(R, 0);
+  const V3<S> w2 = cross(u, w);
+  const int j = sub % 3;
+  const float cs = j == 0 ? 1.f : -0.5f, sn = j == 0 ? 0.f : (j == 1 ? 0.8660254f : -0.8660254f);
+  const V3<S> p = c + S(sub >= 3 ? h : -h) * u + S(r * cs) * w + S(r * sn) * w2;
+  RawS<S> k;
+  k.phi = dot(n, p - o);
+  k.p = p - (S(0.5f) * k.phi) * n;
+  k.n = n;
+  return k;
+}
+
+// Sphere (centre sc, radius rs) against a solid cylinder: a centre outside meets the closest
+// point of the cylinder, one inside leaves through the nearer of the side and the cap; the
+// normal points from B to A (sphere_is_a: the sphere is A)
+template <class S>
+__device__ RawS<S> g_sphere_cylinder(V3<S> sc, S rs, V3<S> c, const M3<S>& R, float r, float h, bool sphere_is_a) {
+  const V3<S> u = colv(R, 2);
+  const V3<S> rel = sc - c;
+  const S t = dot(u, rel);
+  const V3<S> d = rel - t * u;
+  const S rho = ssqrt(dot(d, d));
+  const V3<S> dr = val(rho) > 1e-12f ? (S(1.f) / rho) * d : colv(R, 0);
+  V3<S> nb, q;
+  S dist;
+  if (fabsf(val(t)) <= h && val(rho) <= r) {
+    const S side = S(r) - rho, cap = S(h) - sabs(t);
+    if (val(side) <= val(cap)) {
+      nb = dr;
+      dist = -side;
+      q = c + t * u + S(r) * dr;
+    } else {
+      const S sg(val(t) >= 0.f ? 1.f : -1.f);
+      nb = sg * u;
+      dist = -cap;
+      q = c + (sg * S(h)) * u + d;
+    }
+  } else {
+    const S tc = sclamp(t, S(-h), S(h)), rc = smin(rho, S(r));
+    q = c + tc * u + rc * dr;
+    const V3<S> g = sc - q;
+    dist = ssqrt(dot(g, g));
+    nb = (S(1.f) / dist) * g;
+  }
+  RawS<S> k;
+  k.phi = dist - rs;
+  k.p = S(0.5f) * ((sc - rs * nb) + q);
+  k.n = sphere_is_a ? nb : -nb;
+  return k;
+}
+
+// Box-box contact `sub` (0..7): the separating-axis test over the six face axes (A's first,
+// the least overlap wins) picks the reference face; the incident box's face most anti-parallel
+// to it is clipped by the reference face's four side planes; clipped vertex `sub` gives the
+// gap (its distance to the reference plane), the point (midway to its projection) and the
+// normal (the reference normal, from B to A).  phi = 3e38 when the polygon has fewer vertices.
+// Every choice (axis, face, side of a plane) is taken on the values.
+template <class S>
+__device__ RawS<S> g_box_box(V3<S> ca, const M3<S>& Ra, V3<S> ha, V3<S> cb, const M3<S>& Rb, V3<S> hb, int sub) {
+  RawS<S> o;
+  o.phi = S(3.0e38f);
+  o.p = ca;
+  o.n = v3(S(0.f), S(0.f), S(1.f));
+  const V3<S> d = cb - ca;
+  const S hav[3] = {ha.x, ha.y, ha.z}, hbv[3] = {hb.x, hb.y, hb.z};
+  int best = 0;
+  float best_sep = 0.f;
+  for (int k = 0; k < 6; ++k) {
+    const V3<S> u = k < 3 ? colv(Ra, k) : colv(Rb, k - 3);
+    S ra(0.f), rb(0.f);
+    for (int i = 0; i < 3; ++i) {
+      ra += hav[i] * sabs(dot(colv(Ra, i), u));
+      rb += hbv[i] * sabs(dot(colv(Rb, i), u));
+    }
+    const float sep = val(sabs(dot(d, u)) - ra - rb);
+    if (k == 0 || sep > best_sep) { best_sep = sep; best = k; }
+  }
+  const bool refA = best < 3;
+  const int jr = best % 3;
+  const V3<S> cR = refA ? ca : cb, cI = refA ? cb : ca;
+  const M3<S>& RR = refA ? Ra : Rb;
+  const M3<S>& RI = refA ? Rb : Ra;
+  const S* hR = refA ? hav : hbv;
+  const S* hI = refA ? hbv : hav;
+  const V3<S> nR = S(val(dot(cI - cR, colv(RR, jr))) >= 0.f ? 1.f : -1.f) * colv(RR, jr);
+  int ji = 0;
+  float most = 0.f;
+  for (int i = 0; i < 3; ++i) {
+    const float c = fabsf(val(dot(colv(RI, i), nR)));
+    if (i == 0 || c > most) { most = c; ji = i; }
+  }
+  const S si(val(dot(colv(RI, ji), nR)) > 0.f ? -1.f : 1.f);
+  const int i1 = (ji + 1) % 3, i2 = (ji + 2) % 3;
+  const V3<S> fc = cI + (si * hI[ji]) * colv(RI, ji);
+  const V3<S> e1 = hI[i1] * colv(RI, i1), e2 = hI[i2] * colv(RI, i2);
+  V3<S> poly[8], tmp[8];
+  poly[0] = fc + e1 + e2; poly[1] = fc - e1 + e2; poly[2] = fc - e1 - e2; poly[3] = fc + e1 - e2;
+  int n = 4;
+  const int k1 = (jr + 1) % 3, k2 = (jr + 2) % 3;
+  for (int pl = 0; pl < 4 && n > 0; ++pl) {
+    const int ax = pl < 2 ? k1 : k2;
+    const V3<S> u = S((pl & 1) ? -1.f : 1.f) * colv(RR, ax);
+    const S hh = hR[ax];
+    int m = 0;
+    for (int v = 0; v < n; ++v) {
+      const V3<S> Pv = poly[v], Qv = poly[v + 1 < n ? v + 1 : 0];
+      const S dP = dot(Pv - cR, u) - hh, dQ = dot(Qv - cR, u) - hh;
+      const bool inP = val(dP) <= 0.f, inQ = val(dQ) <= 0.f;
+      if (inP && m < 8) tmp[m++] = Pv;
+      if (inP != inQ && m < 8) tmp[m++] = Pv + (dP / (dP - dQ)) * (Qv - Pv);
+    }
+    for (int v = 0; v < m; ++v) poly[v] = tmp[v];
+    n = m;
+  }
+  if (sub < n) {
+    const V3<S> v = poly[sub];
+    const S dist = dot(v - cR, nR) - hR[jr];
+    o.phi = dist;
+    o.p = v - (S(0.5f) * dist) * nR;
+    o.n = refA ? -nR : nR;
+  }
+  return o;
+}
+
 // ---------------------------------------------------------------------------------------
 // one articulated world, one thread
 // ---------------------------------------------------------------------------------------
@@ -713,7 +859,7 @@ __device__ S w1_impnet_scale(const StepParams& P, const DScene& sc, const W1<S>&
   return sexp(sclamp(gsum, S(-kImpClamp), S(kImpClamp)));
 }
 
-template <class S, bool kImp>
+template <class S, bool kExt>
 __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int world, int ga, int gb,
                            const RawS<S>& k, bool plane, V3<S> px) {
   const DGeom& GA = P.geoms[sc.geom0 + ga];
@@ -739,7 +885,7 @@ __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int 
   S wn = dot(k.n, wc), wr1 = dot(t1, wc), wr2 = dot(t2, wc);
   S mut(fmaxf(GA.mu[0], GB.mu[0])), mutor(fmaxf(GA.mu[1], GB.mu[1])), murol(fmaxf(GA.mu[2], GB.mu[2]));
   S N(0.f), F1(0.f), F2(0.f), Tq(0.f), R1(0.f), R2(0.f);
-  if (kImp && P.trace_mode == 2) {
+  if (kExt && P.trace_mode == 2) {
     GramS<S> g;
     w1_gram(P, sc, w, ba, bb, k.p, k.n, t1, t2, g);
     w1_facets_exact(P, vn, vt1, vt2, wn, wr1, wr2, k.phi, mut, mutor, murol, g, N, F1, F2, Tq, R1, R2);
@@ -751,7 +897,7 @@ __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int 
   }
   S r = w1_solimp(P, sabs(k.phi));
   S mphi = r / (S(1.f) - r) / tr;
-  if (kImp && P.trace_mode == 3)
+  if (kExt && P.trace_mode == 3)
     mphi = mphi * w1_impnet_scale(P, sc, w, P.impnet + (size_t)world * P.impnet_stride, ba, bb, k.p, k.n, k.phi, tr);
   S kM = S(P.k_user) * mphi, dM = S(P.d_user) * mphi;
   S A = -kM * k.phi, Bc = kM * S(P.dt) + dM;
@@ -781,7 +927,7 @@ __device__ void w1_contact(const StepParams& P, const DScene& sc, W1<S>& w, int 
   if (bb >= 0) w1_apply(P, sc, w, bb, k.p, -f, -m);
 }
 
-template <class S, bool kImp>
+template <class S, bool kExt>
 __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int world, int ga, int gb) {
   const DGeom* G = P.geoms + sc.geom0;
   int ta = G[ga].type, tb = G[gb].type;
@@ -796,26 +942,39 @@ __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int wor
     V3<S> nz = colv(Rb, 2), px = colv(Rb, 0);
     if (ta == CF_GEOM_SPHERE) {
       RawS<S> k = g_sphere_plane(ca, S(sa[0]), cb, nz);
-      if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
+      if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, true, px);
     } else if (ta == CF_GEOM_CAPSULE) {
       V3<S> ax = colv(Ra, 2);
       for (int e = 0; e < 2; ++e) {
         RawS<S> k = g_sphere_plane(ca + S(e ? sa[1] : -sa[1]) * ax, S(sa[0]), cb, nz);
-        if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
+        if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, true, px);
       }
     } else if (ta == CF_GEOM_BOX) {
       for (int ci = 0; ci < 8; ++ci) {
         V3<S> corner = ca + mul(Ra, v3(S((ci & 4) ? sa[0] : -sa[0]), S((ci & 2) ? sa[1] : -sa[1]),
                                        S((ci & 1) ? sa[2] : -sa[2])));
         RawS<S> k = g_sphere_plane(corner, S(0.f), cb, nz);
-        if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, true, px);
+        if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, true, px);
       }
+    } else if (kExt && ta == CF_GEOM_CYLINDER) {
+      for (int sub = 0; sub < 6; ++sub) {
+        RawS<S> k = g_cylinder_plane(ca, Ra, sa[0], sa[1], cb, nz, sub);
+        if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, true, px);
+      }
+    } else if (kExt && ta == CF_GEOM_ELLIPSOID) {
+      RawS<S> k = g_ellipsoid_plane(ca, Ra, v3f<S>(sa), cb, nz);
+      if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, true, px);
     }
     return;
   }
   RawS<S> k;
   k.phi = S(3.0e38f);
-  if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
+  if (ta >= CF_GEOM_CYLINDER || tb >= CF_GEOM_CYLINDER) {  // cylinders touch spheres only
+    if (kExt && ta == CF_GEOM_SPHERE && tb == CF_GEOM_CYLINDER)
+      k = g_sphere_cylinder(ca, S(sa[0]), cb, Rb, sb[0], sb[1], true);
+    else if (kExt && ta == CF_GEOM_CYLINDER && tb == CF_GEOM_SPHERE)
+      k = g_sphere_cylinder(cb, S(sb[0]), ca, Ra, sa[0], sa[1], false);
+  } else if (ta == CF_GEOM_SPHERE && tb == CF_GEOM_SPHERE) {
     k = g_sphere_sphere(ca, S(sa[0]), cb, S(sb[0]));
   } else if (ta == CF_GEOM_CAPSULE && tb == CF_GEOM_CAPSULE) {
     V3<S> ua = colv(Ra, 2), ub = colv(Rb, 2);
@@ -832,7 +991,14 @@ __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int wor
     S t = sclamp(dot(ca - cb, u), S(-sb[1]), S(sb[1]));
     k = g_sphere_sphere(ca, S(sa[0]), cb + t * u, S(sb[0]));
   } else if (ta == CF_GEOM_BOX || tb == CF_GEOM_BOX) {
-    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) return;
+    if (ta == CF_GEOM_BOX && tb == CF_GEOM_BOX) {  // each clipped face vertex
+      if (kExt)
+        for (int sub = 0; sub < 8; ++sub) {
+          RawS<S> kb = g_box_box(ca, Ra, v3f<S>(sa), cb, Rb, v3f<S>(sb), sub);
+          if (kb.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, kb, false, v3(S(0.f), S(0.f), S(0.f)));
+        }
+      return;
+    }
     bool boxA = ta == CF_GEOM_BOX;
     const M3<S>& Rbx = boxA ? Ra : Rb;
     V3<S> cbx = boxA ? ca : cb, co = boxA ? cb : ca;
@@ -848,12 +1014,12 @@ __device__ void w1_pair(const StepParams& P, const DScene& sc, W1<S>& w, int wor
       k = g_sphere_box(co + t * u, S(os[0]), cbx, Rbx, hs, !boxA);
     }
   }
-  if (k.phi < margin) w1_contact<S, kImp>(P, sc, w, world, ga, gb, k, false, v3(S(0.f), S(0.f), S(0.f)));
+  if (k.phi < margin) w1_contact<S, kExt>(P, sc, w, world, ga, gb, k, false, v3(S(0.f), S(0.f), S(0.f)));
 }
 
 // one step of an articulated world in scalar type S: q[nq], v[nv] updated in place, tau per
 // actuated hinge (scene order)
-template <class S, bool kImp>
+template <class S, bool kExt>
 __device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, S* v, const S* tau, W1<S>& w) {
   const DBody* B = P.bodies + sc.body0;
   const DGeom* G = P.geoms + sc.geom0;
@@ -891,7 +1057,7 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, 
       float rr = bound(ga) + bound(gb) + P.margin;
       cand = val(dot(d, d)) < rr * rr;
     }
-    if (cand) w1_pair<S, kImp>(P, sc, w, world, ga, gb);
+    if (cand) w1_pair<S, kExt>(P, sc, w, world, ga, gb);
   }
   // joint limits and dry joint friction, the step kernel's per-hinge impulses on the smooth
   // prediction: a limit below the margin is a one-row constraint +-e_k with the facet law and
@@ -918,7 +1084,7 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, 
             const S sg(side ? -1.f : 1.f);
             const S sv = sg * vsk;
             S Mk;
-            if (kImp && P.trace_mode == 2) {  // the exact impedance of the one-row constraint
+            if (kExt && P.trace_mode == 2) {  // the exact impedance of the one-row constraint
               Mk = S(1.f) / (S(fmaf(P.k_user, P.dt, P.d_user)) * wkk);
             } else {
               const S r = w1_solimp(P, sabs(gap));
@@ -983,8 +1149,9 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, 
 // vector-Jacobian product of one step: CTA per world, lane j = input coordinate j
 // (q, then v, then actuated tau); a_in = adjoint of the step's output state
 // ---------------------------------------------------------------------------------------
-// kImp: the exact and learned impedances (trace_mode 2, 3) compiled in
-template <bool kImp>
+// kExt: the extended step compiled in: the exact and learned impedances (trace_mode 2, 3),
+// box-box pairs, cylinders and ellipsoids
+template <bool kExt>
 __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float* q, const float* v, int step,
                                                        const float* aq_in, const float* av_in, float* aq_out,
                                                        float* av_out, float* dtau, int64_t total_nu) {
@@ -1000,7 +1167,7 @@ __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float
     int slice = P.nctrl > 0 ? (step < P.nctrl ? step : P.nctrl - 1) : -1;
     for (int i = 0; i < sc.nu; ++i)
       tau[i] = DF(slice >= 0 ? P.ctrl[(size_t)slice * P.total_nu + Wd.uadr + i] : 0.f, j == sc.nq + sc.nv + i ? 1.f : 0.f);
-    w1_step<DF, kImp>(P, sc, world, qs, vs, tau, w);
+    w1_step<DF, kExt>(P, sc, world, qs, vs, tau, w);
     float acc = 0.f;
     for (int i = 0; i < sc.nq; ++i) acc = fmaf(qs[i].d, aq_in[Wd.qadr + i], acc);
     for (int i = 0; i < sc.nv; ++i) acc = fmaf(vs[i].d, av_in[Wd.vadr + i], acc);
@@ -1012,7 +1179,6 @@ __global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float
 
 bool grad_scene_supported(const DScene& s, const char** why) {
   if (s.pile) { *why = "pile scenes are not differentiable here"; return false; }
-  if (s.boxbox) { *why = "the adjoint does not cover box-box pairs, cylinders or ellipsoids"; return false; }
   if (s.nbody > kG1Body || s.ngeom > kG1Geom || s.nq > kG1Q || s.nv > kG1V || s.ntree > kG1Tree) {
     *why = "scene exceeds the adjoint's per-world limits (24 bodies, 32 geoms, 48 q, 48 v, 8 trees)";
     return false;
@@ -1085,7 +1251,7 @@ cudaError_t run_grad(const StepParams& p0, const GradArgs& g, int nctrl, cudaStr
     for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
       StepParams pv = p;
       pv.ctrl_offset = 0;
-      if (p.trace_mode >= 2)
+      if (g.variant == kExtVariant)
         vjp_kernel<true><<<g.W, kG1Lanes, 0, s>>>(pv, qptr(seg(i)), vptr(seg(i)), first + i, qptr(ain), vptr(ain),
                                                   qptr(aout), vptr(aout), g.dtau, g.total_nu);
       else

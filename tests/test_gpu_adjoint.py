@@ -229,3 +229,113 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     _, gv2, gt2 = _gpu_grad(sb, tau, tp, tq, T, 7)
     np.testing.assert_array_equal(gv1, gv2)
     np.testing.assert_array_equal(gt1, gt2)
+
+
+def _geo_scene(nworld, seed):
+    """Two stacked free boxes (box-box contacts), a free cylinder (standing or lying), a free
+    ellipsoid and a hinged sphere arm over the cylinder, on a plane; friction (0.8, 0.005, 0.005)
+    so that every facet subspace acts.  Returns the batch; q per world: 4 free bodies x 7, then
+    the hinge."""
+    import worlds as Wd
+    mu = (0.8, 0.005, 0.005)
+    cyl = S.cylinder_mass_inertia(0.03, 0.04, 1000.0)
+    ell = S.ellipsoid_mass_inertia((0.04, 0.03, 0.02), 1000.0)
+    d = Wd.world([dict(mass=0.2, inertia=S.box_mass_inertia((0.03, 0.03, 0.02), 0.2)[1]),
+                  dict(mass=0.3, inertia=S.box_mass_inertia((0.04, 0.04, 0.02), 0.3)[1]),
+                  dict(mass=cyl[0], inertia=cyl[1]), dict(mass=ell[0], inertia=ell[1]),
+                  dict(parent=-1, jnt=S.HINGE, pos=(0.15, 0.0, 0.1635), axis=(0, 1, 0), ipos=(0, 0, -0.06),
+                       mass=0.1, inertia=(1e-4, 1e-4, 1e-4), damping=0.02)],
+                 [dict(type=S.PLANE, body=-1, mu=mu),
+                  dict(type=S.BOX, body=0, size=(0.03, 0.03, 0.02), mu=mu),
+                  dict(type=S.BOX, body=1, size=(0.04, 0.04, 0.02), mu=mu),
+                  dict(type=S.CYLINDER, body=2, size=(0.03, 0.04, 0), mu=mu),
+                  dict(type=S.ELLIPSOID, body=3, size=(0.04, 0.03, 0.02), mu=mu),
+                  dict(type=S.SPHERE, body=4, pos=(0, 0, -0.06), size=(0.025, 0, 0), mu=mu)])
+    t = S.Template(name="geo", pile=False, **{k: np.asarray(v) for k, v in d.items()})
+    rng = np.random.default_rng(seed)
+    q0, v0 = [], []
+    for w in range(nworld):
+        qb = np.concatenate([[0.0, 0.0, 0.0195], S.quat_about((0, 0, 1), rng.uniform(-0.3, 0.3))])
+        qa = np.concatenate([rng.uniform(-0.005, 0.005, 2), [0.0595 - rng.uniform(0, 0.001)],
+                             S.quat_about((0, 0, 1), rng.uniform(-0.5, 0.5))])
+        if w % 2:   # the cylinder lying on its side
+            qc = np.concatenate([[0.15, 0.0, 0.0295], S.quat_about((1, 0, 0), np.pi / 2)])
+        else:
+            qc = np.concatenate([[0.15, 0.0, 0.0395], S.quat_about((0, 0, 1), rng.uniform(0, 1))])
+        qe = np.concatenate([[-0.15, 0.0, 0.0195], S.quat_about((0, 0, 1), rng.uniform(0, 1))])
+        q0.append(np.concatenate([qa, qb, qc, qe, [rng.uniform(-0.05, 0.05)]]))
+        v0.append(np.concatenate([rng.normal(0, 0.05, 24), [rng.normal(0, 0.3)]]))
+    return S.Batch([t], S.Params(**S.PILE_PARAMS), np.zeros(nworld, np.int32), [None] * nworld, q0, v0, 0.002, 100,
+                   {"workload": "geo"})
+
+
+def test_adjoint_through_box_box_cylinder_and_ellipsoid_contacts():
+    """Box-box (clipped face vertices), cylinder-plane (rim points), ellipsoid-plane (support
+    point) and sphere-cylinder contacts through the adjoint.  The pose loss of the top box, of
+    the cylinder and of the ellipsoid after T = 10 steps: every coordinate of dL/dv0 (25) and
+    dL/dtau of the hinge at steps 0 and 9 against the oracle's duals (1e-3 of the coordinate,
+    floor 1e-3 of the largest), the random-direction derivative against FP64 central
+    differences (worlds whose active set changes within +-h excluded and counted)."""
+    T, nworld = 10, 8
+    sb = _geo_scene(nworld, seed=23)
+    nq, nv = 29, 25
+    rng = np.random.default_rng(29)
+    tau = rng.normal(0, 0.005, (T, nworld, 1)).astype(np.float32)
+    tp = np.array([0.01, -0.01, 0.05])
+    tq = S.quat_about((0, 0, 1), 0.3)
+    checked = {}
+    for body in (0, 2, 3):
+        _, b = CF.from_scenes(sb, max_ctrl_steps=T, grad_steps=T, grad_ckpt=5)
+        q0, v0 = CF.flatten_state(sb)
+        q0 = torch.from_numpy(q0).cuda().requires_grad_(True)
+        v0 = torch.from_numpy(v0).cuda().requires_grad_(True)
+        tt = torch.from_numpy(tau.reshape(T, -1)).cuda().requires_grad_(True)
+        qT, vT = AG.rollout(b, sb.dt, q0, v0, tt)
+        qw = qT.view(nworld, nq)[:, 7 * body:7 * body + 7]
+        L = ((qw[:, :3] - torch.tensor(tp, device="cuda", dtype=torch.float32)) ** 2).sum(1) + \
+            1 - (qw[:, 3:7] @ torch.tensor(tq, device="cuda", dtype=torch.float32)) ** 2
+        L.sum().backward()
+        gv = v0.grad.view(nworld, nv).cpu().numpy()
+        gt = tt.grad.view(T, nworld).cpu().numpy()
+        checked[body] = 0
+        for w in range(nworld):
+            d = sb.world(w)
+            qw0, vw0 = PR.f32(sb.q0[w]), PR.f32(sb.v0[w])
+            tau_full = np.zeros((T, nv))
+            tau_full[:, nv - 1] = tau[:, w, 0]
+
+            def dual(dv, dtau):
+                return O.rollout_loss_dir(d, sb.params, sb.dt, qw0, vw0, tau_full, np.zeros(nq), dv, dtau, body, tp,
+                                          tq)
+
+            dv_r = rng.standard_normal(nv)
+            dt_r = np.zeros((T, nv))
+            dt_r[:, nv - 1] = rng.standard_normal(T)
+            _, dLo = dual(dv_r, dt_r)
+            h = 1e-6
+            Lp = O.rollout_loss_dir(d, sb.params, sb.dt, qw0, vw0 + h * dv_r, tau_full + h * dt_r, np.zeros(nq),
+                                    dv_r, dt_r, body, tp, tq)[0]
+            Lm = O.rollout_loss_dir(d, sb.params, sb.dt, qw0, vw0 - h * dv_r, tau_full - h * dt_r, np.zeros(nq),
+                                    dv_r, dt_r, body, tp, tq)[0]
+            fd = (Lp - Lm) / (2 * h)
+            if abs(dLo - fd) > 1e-4 * max(abs(fd), 1e-6):
+                continue
+            g = float(gv[w] @ dv_r + gt[:, w] @ dt_r[:, nv - 1])
+            assert g == pytest.approx(dLo, rel=2e-3, abs=1e-6 * max(1.0, abs(dLo))), f"body {body} world {w}"
+            ref, gpu = [], []
+            for k in range(nv):
+                e = np.zeros(nv)
+                e[k] = 1.0
+                ref.append(dual(e, np.zeros((T, nv)))[1])
+                gpu.append(gv[w, k])
+            for s_ in (0, T - 1):
+                e = np.zeros((T, nv))
+                e[s_, nv - 1] = 1.0
+                ref.append(dual(np.zeros(nv), e)[1])
+                gpu.append(gt[s_, w])
+            ref, gpu = np.array(ref), np.array(gpu)
+            scale = np.abs(ref).max()
+            bad = np.abs(gpu - ref) > 1e-3 * (np.abs(ref) + 1e-3 * scale)
+            assert not bad.any(), f"body {body} world {w}: {np.flatnonzero(bad)} gpu {gpu[bad]} oracle {ref[bad]}"
+            checked[body] += 1
+    assert all(c >= nworld // 2 for c in checked.values()), checked
