@@ -485,7 +485,8 @@ def extra_hand_rollout(rank, reps=10):
 
 
 def extra_mppi(rank, reps=10):
-    """One MPPI control tick: 1024 rollouts x 32 steps of 5 ms with the fused cost and the update."""
+    """One MPPI control tick: 1024 rollouts x 32 steps of 5 ms with the fused cost and the update,
+    eagerly and replayed from a CUDA graph of the tick."""
     from paper_2603_12185_gb300 import mppi as MP
     from paper_2603_12185_gb300 import scenes as S
     t = S.hand_template(0)
@@ -494,7 +495,10 @@ def extra_mppi(rank, reps=10):
     sbh = S.make_hand(1, seed=R.rank_seed(2200, rank))
     ctl.reset(sbh.q0[0], sbh.v0[0], MP.random_goal(sbh.q0[0], np.random.default_rng(rank)))
     ms = _timed(ctl.tick, reps)
-    return {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3)}
+    g = ctl.tick_graph()
+    ms_graph = _timed(g.replay, reps)
+    return {"ms": ms, "rollout_world_steps_per_s": 1024 * 32 / (ms / 1e3), "ms_graph": ms_graph,
+            "rollout_world_steps_per_s_graph": 1024 * 32 / (ms_graph / 1e3)}
 
 
 def extra_proposal(rank, iters=None, episodes=None, goals=None, ticks=60):

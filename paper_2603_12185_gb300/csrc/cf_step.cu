@@ -1019,18 +1019,19 @@ __device__ float artic_trace(const StepParams& P, const ArticView& s, const DSce
     return 3.f / bd.mass + dot(r, r) * (i0 + i1 + i2) - (l.x * l.x * i0 + l.y * l.y * i1 + l.z * l.z * i2);
   }
   // hinge chain: sum over the chain's joints i, j of (M~^-1)_ij (a_i x (p - o_i)) . (a_j x (p - o_j)),
-  // the chain read from the body's ancestor mask (no local arrays, no parent-pointer chasing)
+  // the chain read from the body's ancestor mask (no local arrays, no parent-pointer chasing);
+  // M~^-1 is symmetric, so the pairs j > i count twice and j < i are skipped
   const float* mi = s.minv + (size_t)bd.tree * kMaxTreeDof * kMaxTreeDof;
   float t = 0.f;
   for (unsigned mi_ = (unsigned)bd.anc; mi_; mi_ &= mi_ - 1) {
     const int i = __ffs(mi_) - 1, bi = tr.body0 + i;
     const f3 ci = cross(ld3(s.bax + 3 * bi), p - ld3(s.bx + 3 * bi));
-    f3 acc = mk3(0.f, 0.f, 0.f);
-    for (unsigned mj = (unsigned)bd.anc; mj; mj &= mj - 1) {
+    f3 acc = (0.5f * mi[i * kMaxTreeDof + i]) * ci;
+    for (unsigned mj = mi_ & (mi_ - 1); mj; mj &= mj - 1) {
       const int j = __ffs(mj) - 1, bj = tr.body0 + j;
       acc = acc + mi[i * kMaxTreeDof + j] * cross(ld3(s.bax + 3 * bj), p - ld3(s.bx + 3 * bj));
     }
-    t += dot(ci, acc);
+    t += 2.f * dot(ci, acc);
   }
   return t;
 }

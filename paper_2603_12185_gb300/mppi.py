@@ -142,6 +142,21 @@ class HandMPPI:
             CF.check(CF.lib().cf_mppi_shift(self.H, NU, CF._ptr(self.mean), s))
         return plan
 
+    def tick_graph(self):
+        """A CUDA graph of one control tick (apply=True): each replay() runs the next tick on the
+        current stream with the same buffers, its plan left in self.mean, and draws fresh noise
+        (the controller's generator is registered with the graph), so replays reproduce the
+        eager ticks bit for bit.  One eager tick runs first (kernel attributes), so the plant
+        advances by one tick here.  A tick is a dozen small launches around the rollout; the
+        graph removes their host launch overhead."""
+        self.tick()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        g.register_generator_state(self.gen)
+        with torch.cuda.graph(g):
+            self.tick()
+        return g
+
     def plan_from(self, qp, vp, mean):
         """The plan one tick computes from plant state (qp, vp) and warm start `mean` (device),
         without stepping this controller's plant."""

@@ -81,12 +81,19 @@ def test_hand_exact_single_step_and_contacts():
     assert GP._check_contact_sets(sb) > 5   # the oracle record step runs without controls
 
 
-def test_exact_mode_has_no_adjoint():
+def test_exact_mode_adjoint_runs_and_pile_adjoint_is_refused():
+    """cf_step_grad covers the exact impedance (its gradients are checked against the oracle's
+    duals in test_gpu_adjoint.py) and still refuses pile scenes."""
     import torch
     from paper_2603_12185_gb300 import comfree as CF
     sb = exact(S.make_hand(2, seed=4))
     _, b = CF.from_scenes(sb, max_ctrl_steps=4, grad_steps=4, grad_ckpt=2)
     gq = torch.zeros(b.total_nq, device="cuda")
     gv = torch.zeros(b.total_nv, device="cuda")
-    with pytest.raises(CF.CfError, match="heuristic"):
-        b.step_grad(4, sb.dt, gq, gv)
+    out = b.step_grad(4, sb.dt, gq, gv)
+    torch.cuda.synchronize()
+    assert all(torch.isfinite(t).all() for t in out if t is not None)
+    sp = exact(S.make_pile(2, 16))
+    _, bp = CF.from_scenes(sp, max_ctrl_steps=4, grad_steps=4, grad_ckpt=2)
+    with pytest.raises(CF.CfError, match="pile"):
+        bp.step_grad(4, sp.dt, torch.zeros(bp.total_nq, device="cuda"), torch.zeros(bp.total_nv, device="cuda"))

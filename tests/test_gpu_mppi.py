@@ -139,3 +139,38 @@ def test_mppi_lowers_the_task_cost():
     final = MP.run_episode(ctl, sb.q0[0], sb.v0[0], goal, 60)
     assert np.isfinite(final)
     assert final < start
+
+
+def test_tick_graph_replays_the_eager_ticks():
+    """A CUDA graph of one tick, replayed, gives the same plans and plant states as eager ticks
+    from the same start and seed, bit for bit (the noise generator advances with each replay)."""
+    from paper_2603_12185_gb300 import mppi as MP
+    from paper_2603_12185_gb300 import scenes as S
+    sb = S.make_hand(1, seed=8)
+    t = sb.templates[0]
+    params = S.Params(**dict(S.HAND_PARAMS, d_user=0.002))
+    goal = MP.random_goal(sb.q0[0], np.random.default_rng(4))
+    runs = []
+    for graphed in (False, True):
+        ctl = MP.HandMPPI(t, params, N=256, seed=3)
+        ctl.reset(sb.q0[0], sb.v0[0], goal)
+        plans, states = [], []
+        if graphed:
+            g = ctl.tick_graph()              # the first tick runs eagerly inside
+            plans.append(ctl.mean.clone())
+            states.append(torch.cat(ctl.plant.get_state()))
+            for _ in range(4):
+                g.replay()
+                plans.append(ctl.mean.clone())
+                states.append(torch.cat(ctl.plant.get_state()))
+        else:
+            for _ in range(5):
+                ctl.tick()
+                plans.append(ctl.mean.clone())
+                states.append(torch.cat(ctl.plant.get_state()))
+        torch.cuda.synchronize()
+        runs.append((torch.stack(plans).cpu().numpy(), torch.stack(states).cpu().numpy()))
+    (pe, se), (pg, sg) = runs
+    assert np.array_equal(pe.view(np.uint32), pg.view(np.uint32))
+    assert np.array_equal(se.view(np.uint32), sg.view(np.uint32))
+    assert np.abs(se[-1] - se[0]).max() > 0   # the plant moved
