@@ -249,9 +249,13 @@ def run_pile(nbody, nworld, steps, warmup, rank, flush=None, episode=EPISODE, ja
 
 def run_e2e(res, steps, blocks=8):
     """Same workload through the public API with the state in pinned host memory: every step
-    copies q, v host -> device, steps, and copies them device -> host.  Measured twice: serially
-    on one batch, and with comfree.Pipeline, which splits the worlds into `blocks` batches on
-    their own streams so that one block's copies overlap another's step."""
+    moves q, v host -> device, steps, and moves the new state device -> host, the host waiting
+    for it.  Measured three ways:
+    - serially on one batch (copy in, step, copy out);
+    - with comfree.Pipeline, which splits the worlds into `blocks` batches on their own streams
+      so that one block's copies overlap another's step;
+    - in place (Batch.step_host): the step kernel reads the host state and writes it back itself.
+    The reported value is the faster of the last two."""
     import torch
     from paper_2603_12185_gb300 import comfree as CF
     b = res["batch"]
@@ -301,7 +305,25 @@ def run_e2e(res, steps, blocks=8):
     for st, _ in pipe.status():
         if st != 0:
             raise RuntimeError(f"device status {st} in the pipelined run")
-    return dict(value=W * steps / sec, serial=serial, blocks=blocks, h2d=nbytes, d2h=nbytes)
+    pipelined = W * steps / sec
+    # in place: the step kernel reads the pinned host state and writes the new state back itself
+    # (cf_step_host; the transfers run over the host link while other worlds compute), and every
+    # step ends with the host synchronised on it, the new state in host memory
+    b.step_host(hq, hv, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.step_host(hq, hv, dt)
+        torch.cuda.synchronize()
+    in_place = W * steps / (time.perf_counter() - t0)
+    st, _ = b.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the in-place run")
+    best = "in_place" if in_place >= pipelined else "pipelined"
+    return dict(value=max(in_place, pipelined), serial=serial, pipelined=pipelined, in_place=in_place,
+                blocks=blocks, h2d=nbytes, d2h=nbytes,
+                api="Batch.step_host (cf_step_host) on pinned host state" if best == "in_place"
+                else f"comfree.Pipeline, {blocks} blocks")
 
 
 def mlp_throughput(batch=16384, reps=20):
@@ -711,8 +733,8 @@ def main():
             "roofline": roofline,
             "e2e": None if e2e is None else {
                 "value": e2e_v, "unit": "world-steps/s", "h2d_bytes_per_step": e2e["h2d"],
-                "d2h_bytes_per_step": e2e["d2h"], "api": f"comfree.Pipeline, {e2e['blocks']} blocks",
-                "serial_value": e2e["serial"]},
+                "d2h_bytes_per_step": e2e["d2h"], "api": e2e["api"], "serial_value": e2e["serial"],
+                "pipelined_value": e2e["pipelined"], "in_place_value": e2e["in_place"]},
             "gpu_launches": res["steps"],
             "clocks": clk}
     if not args.no_extras:

@@ -180,6 +180,16 @@ cf_status cf_set_ctrl(cf_batch* batch, const float* tau, int32_t T, int32_t on_d
  * its world list from pageable host memory and cannot be captured. */
 cf_status cf_step(cf_batch* batch, const int32_t* worlds, int32_t n, float dt, int32_t nsteps, void* stream);
 
+/* cf_step of every world with the state in the caller's host memory: q[total_nq] and
+ * v[total_nv] are page-locked host buffers (cudaHostAlloc, cudaHostRegister or a pinned torch
+ * tensor), 4-byte aligned, that the step kernel itself reads at the start of the launch and
+ * overwrites with the new state at its end, over the host-device link; the batch's device
+ * state is neither read nor changed.  No separate copy is enqueued: on a coherent host link
+ * (NVLink-C2C) the transfers overlap the other worlds' compute.  Asynchronous on `stream`; the
+ * buffers must stay valid until the stream reaches this point.  Errors: CF_ERR_INVALID_ARGUMENT
+ * (null batch, a buffer that is not page-locked host memory, bad dt or nsteps), CF_ERR_CUDA. */
+cf_status cf_step_host(cf_batch* batch, float* q, float* v, float dt, int32_t nsteps, void* stream);
+
 /* Per-world number of contacts (phi < margin) detected in the last step of the last cf_step,
  * counts[n_worlds] (device or host per on_device). */
 cf_status cf_get_contact_counts(const cf_batch* batch, int32_t* counts, int32_t on_device, void* stream);

@@ -65,7 +65,7 @@ class CostDesc(C.Structure):
 
 
 EXPORTS = ("cf_model_create", "cf_model_destroy", "cf_scene_sizes", "cf_batch_workspace_bytes", "cf_batch_create",
-           "cf_batch_destroy", "cf_batch_sizes", "cf_set_state", "cf_get_state", "cf_set_ctrl", "cf_step",
+           "cf_batch_destroy", "cf_batch_sizes", "cf_set_state", "cf_get_state", "cf_set_ctrl", "cf_step", "cf_step_host",
            "cf_get_contact_counts", "cf_get_contacts", "cf_batch_status", "cf_batch_autotune", "cf_batch_set_warps",
            "cf_step_grad", "cf_step_noalloc", "cf_status_string", "cf_last_error", "cf_mlp_workspace_bytes",
            "cf_mlp_create", "cf_mlp_destroy", "cf_mlp_param_count", "cf_mlp_forward", "cf_mlp_gradients",
@@ -99,6 +99,7 @@ def lib():
     L.cf_get_state.argtypes = [V, V, V, I32, V]
     L.cf_set_ctrl.argtypes = [V, V, I32, I32, V]
     L.cf_step.argtypes = [V, V, I32, C.c_float, I32, V]
+    L.cf_step_host.argtypes = [V, V, V, C.c_float, I32, V]
     L.cf_get_contact_counts.argtypes = [V, V, I32, V]
     L.cf_get_contacts.argtypes = [V, V, V, V]
     L.cf_batch_status.argtypes = [V, V, I32, V]
@@ -276,6 +277,14 @@ class Batch:
     def step(self, dt, nsteps=1, worlds=None, stream=None):
         wl = None if worlds is None else np.ascontiguousarray(worlds, dtype=np.int32)
         check(lib().cf_step(self.h, _ptr(wl), 0 if wl is None else len(wl), float(dt), int(nsteps), _stream(stream)))
+
+    def step_host(self, q, v, dt, nsteps=1, stream=None):
+        """Step every world with the state in pinned host tensors q[total_nq], v[total_nv]: the
+        step kernel reads them and writes the new state back in place (cf_step_host); the
+        batch's own device state is untouched.  Asynchronous on `stream`."""
+        assert q.is_pinned() and v.is_pinned() and q.dtype == torch.float32 and v.dtype == torch.float32
+        assert q.is_contiguous() and v.is_contiguous() and q.numel() == self.total_nq and v.numel() == self.total_nv
+        check(lib().cf_step_host(self.h, _ptr(q), _ptr(v), float(dt), int(nsteps), _stream(stream)))
 
     def graph(self, dt, nsteps=1, repeat=1):
         """A CUDA graph of `repeat` all-world cf_step launches (dt, nsteps each); replay() runs

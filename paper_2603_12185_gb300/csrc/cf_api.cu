@@ -768,6 +768,34 @@ static cf_status launch(const cf_batch* b, StepParams& p, bool artic, size_t sme
   return CF_OK;
 }
 
+// The device address of page-locked host memory `p` (nullptr when it is not page-locked host
+// memory)
+static void* host_device_ptr(void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
+}
+
+extern "C" cf_status cf_step_host(cf_batch* b, float* q, float* v, float dt, int32_t nsteps, void* stream) {
+  if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
+  if (!(dt > 0.f) || !std::isfinite(dt)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");
+  if (nsteps < 1) return fail(CF_ERR_INVALID_ARGUMENT, "nsteps must be >= 1");
+  if ((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(v)) & 3)
+    return fail(CF_ERR_INVALID_ARGUMENT, "q and v must be 4-byte aligned");
+  float* dq = static_cast<float*>(host_device_ptr(q));
+  float* dv = static_cast<float*>(host_device_ptr(v));
+  if (!dq || !dv) return fail(CF_ERR_INVALID_ARGUMENT, "q and v must be page-locked host memory");
+  StepParams p = make_params(b, dt, nsteps);
+  p.q = dq;
+  p.v = dv;
+  return launch(b, p, b->artic_all, b->smem_all, (cudaStream_t)stream);
+}
+
 extern "C" cf_status cf_step(cf_batch* b, const int32_t* worlds, int32_t n, float dt, int32_t nsteps, void* stream) {
   if (!b) return fail(CF_ERR_INVALID_ARGUMENT, "null batch");
   if (!(dt > 0.f) || !std::isfinite(dt)) return fail(CF_ERR_INVALID_ARGUMENT, "dt must be positive");

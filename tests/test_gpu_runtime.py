@@ -104,6 +104,34 @@ def test_pipeline_matches_one_batch():
     assert all(st == 0 for st, _ in pipe.status())
 
 
+@pytest.mark.parametrize("kind", ["pile", "mixed"])
+def test_step_host_matches_device_steps(kind):
+    """cf_step_host (the kernel reads and writes the state in pinned host memory) gives states
+    bit-identical to device steps of the same batch, leaves the batch's device state alone, and
+    refuses pageable host memory."""
+    sb = S.make_pile(8, 64, seed=23) if kind == "pile" else S.make_mixed(8, seed=23)
+    _, b = CF.from_scenes(sb)
+    b.step(sb.dt, 30)
+    q0, v0 = _state(b)
+    hq = torch.from_numpy(q0.copy()).pin_memory()
+    hv = torch.from_numpy(v0.copy()).pin_memory()
+    for _ in range(4):
+        b.step_host(hq, hv, sb.dt)
+    torch.cuda.synchronize()
+    qd, vd = _state(b)
+    assert np.array_equal(qd, q0) and np.array_equal(vd, v0)   # the device state untouched
+    for _ in range(4):
+        b.step(sb.dt, 1)
+    q1, v1 = _state(b)
+    assert np.array_equal(hq.numpy().view(np.uint32), q1.view(np.uint32))
+    assert np.array_equal(hv.numpy().view(np.uint32), v1.view(np.uint32))
+    assert b.status()[0] == 0
+    pq = torch.from_numpy(q0.copy())
+    pv = torch.from_numpy(v0.copy())
+    with pytest.raises(CF.CfError, match="page-locked"):
+        CF.check(CF.lib().cf_step_host(b.h, CF._ptr(pq), CF._ptr(pv), float(sb.dt), 1, CF._stream()))
+
+
 def test_state_round_trip_host_and_device():
     sb = S.make_mixed(8, seed=5)
     _, b = CF.from_scenes(sb)
