@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100, help="end-to-end steps (0: skip, for profiles)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--e2e-blocks", type=int, default=8, help="blocks of worlds of the end-to-end pipeline")
     ap.add_argument("--episode", type=int, default=EPISODE, help="episode length (the timed steps are its last)")
     ap.add_argument("--warps", type=int, default=0,
                     help="warps per world (0: autotune); a fixed shape makes profiles comparable")
@@ -695,7 +696,7 @@ def main():
     sec = barrier_max(res["ms"] / 1e3, world)
     total_contacts = barrier_sum(res["contacts"], world)
     value = world * res["worlds"] * res["steps"] / sec
-    e2e = run_e2e(res, args.e2e_steps) if args.e2e_steps > 0 else None
+    e2e = run_e2e(res, args.e2e_steps, blocks=args.e2e_blocks) if args.e2e_steps > 0 else None
     if e2e is not None:
         e2e_v = barrier_sum(e2e["value"], world) if world > 1 else e2e["value"]
 
