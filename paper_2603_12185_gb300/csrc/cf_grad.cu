@@ -1150,9 +1150,11 @@ __device__ void w1_step(const StepParams& P, const DScene& sc, int world, S* q, 
 // (q, then v, then actuated tau); a_in = adjoint of the step's output state
 // ---------------------------------------------------------------------------------------
 // kExt: the extended step compiled in: the exact and learned impedances (trace_mode 2, 3),
-// box-box pairs, cylinders and ellipsoids
+// box-box pairs, cylinders and ellipsoids.  At most 128 registers, so that 8 worlds of 64 lanes
+// are resident per SM (1216 on 152 SMs): a batch of 1024 worlds then runs in one wave instead
+// of a full wave and a tail (168 registers left room for 6 per SM).
 template <bool kExt>
-__global__ void __launch_bounds__(kG1Lanes) vjp_kernel(StepParams P, const float* q, const float* v, int step,
+__global__ void __launch_bounds__(kG1Lanes, 8) vjp_kernel(StepParams P, const float* q, const float* v, int step,
                                                        const float* aq_in, const float* av_in, float* aq_out,
                                                        float* av_out, float* dtau, int64_t total_nu) {
   const int world = blockIdx.x;
