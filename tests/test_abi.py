@@ -33,6 +33,15 @@ def test_header_symbols_exported(cf):
     assert set(names) <= set(cf.EXPORTS) | set(names)
 
 
+def test_host_state_step_rejects_bad_arguments_without_a_device(cf):
+    """cf_step_host validates its batch, dt and nsteps on the host before any CUDA call."""
+    import ctypes as C
+    L = cf.lib()
+    buf = (C.c_float * 8)()
+    assert cf.STATUS[L.cf_step_host(None, buf, buf, C.c_float(0.002), 1, None)] == "CF_ERR_INVALID_ARGUMENT"
+    assert "null batch" in L.cf_last_error().decode()
+
+
 def test_status_strings(cf):
     for k, v in cf.STATUS.items():
         assert cf.lib().cf_status_string(k).decode() == v
