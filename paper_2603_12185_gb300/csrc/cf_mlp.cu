@@ -24,7 +24,11 @@
 namespace cf {
 namespace mlp {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+// Two stages of the TMA ring: the products here run at most four BK steps per CTA (K = 64 or
+// 256, split-K slices of the batch), which two buffers already overlap, and 65 KB of shared
+// memory per 128-wide CTA lets three CTAs share an SM (a 4-stage ring of 129 KB allowed one:
+// the 256- to 1024-CTA grids then ran in several waves)
+constexpr int BM = 128, BK = 64, STAGES = 2;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 enum Epi { EPI_BIAS_GELU = 0, EPI_BIAS_F32 = 1, EPI_F32 = 2, EPI_GELU_BWD = 3 };
