@@ -270,17 +270,45 @@ __global__ void pack_input(const float* x, int B, int fin, int Bp, int kin, __nv
 }
 
 // out[c][r] = in[r][c] for a [R x C] bf16 matrix (32 x 32 tiles through shared memory)
+// out[C x R] = in[R x C]^T by 64 x 64 tiles of a (32, 8) block: each lane moves two adjacent
+// elements, so a warp reads and writes 128-byte row segments (bf16 pairs when the row length is
+// even, single elements at odd edges); rows of 65 elements in shared memory keep the column
+// reads of a warp on distinct banks
 __global__ void transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
-  __shared__ __nv_bfloat16 t[32][33];
-  int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int r = r0 + k, c = c0 + threadIdx.x;
-    t[k][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+  __shared__ __nv_bfloat16 t[64][65];
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64, x2 = 2 * threadIdx.x;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + x2;
+    __nv_bfloat16 a = zero, b = zero;
+    if (r < R) {
+      const __nv_bfloat16* src = in + (size_t)r * C + c;
+      if ((C & 1) == 0 && c + 1 < C) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(src);
+        a = v.x;
+        b = v.y;
+      } else {
+        if (c < C) a = src[0];
+        if (c + 1 < C) b = src[1];
+      }
+    }
+    t[k][x2] = a;
+    t[k][x2 + 1] = b;
   }
   __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int c = c0 + k, r = r0 + threadIdx.x;
-    if (c < C && r < R) out[(size_t)c * R + r] = t[threadIdx.x][k];
+  for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + x2;
+    if (c >= C) continue;
+    __nv_bfloat16* dst = out + (size_t)c * R + r;
+    if ((R & 1) == 0 && r + 1 < R) {
+      __nv_bfloat162 v;
+      v.x = t[x2][k];
+      v.y = t[x2 + 1][k];
+      *reinterpret_cast<__nv_bfloat162*>(dst) = v;
+    } else {
+      if (r < R) dst[0] = t[x2][k];
+      if (r + 1 < R) dst[1] = t[x2 + 1][k];
+    }
   }
 }
 
@@ -646,7 +674,7 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   };
   dim3 tb(32, 8);
   auto T = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
-    transpose_bf16<<<dim3((C + 31) / 32, (R + 31) / 32), tb, 0, s>>>(in, R, C, out);
+    transpose_bf16<<<dim3((C + 63) / 64, (R + 63) / 64), tb, 0, s>>>(in, R, C, out);
   };
   cudaError_t e = cudaSuccess;
   // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 (times gelu'(Z2))
