@@ -348,14 +348,16 @@ __global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, 
 }
 
 // Column sums db[n] = sum_r g[r][n] of a bf16 gradient [R x N] (N a multiple of 64, R a multiple
-// of kColSlices) in two deterministic passes: CTA (c, s) sums rows of slice s for 64 columns
+// of `slices`) in two deterministic passes: CTA (c, s) sums rows of slice s for 64 columns
 // (each lane two adjacent columns, the 8 warps interleaved over the rows, combined in warp order)
-// into part[s][n]; then one thread per column adds the slices in order.
+// into part[s][n]; then one thread per column adds the slices in order.  Narrow gradients take
+// more slices (the partial buffer holds kColSlices x the widest layer), so that they too give
+// every SM blocks.
 constexpr int kColSlices = 32;
-__global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16* g, int R, int N, float* part) {
+__global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16* g, int R, int N, int slices, float* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.x * 64 + 2 * lane;
-  const int rows = R / kColSlices, r0 = blockIdx.y * rows;
+  const int rows = R / slices, r0 = blockIdx.y * rows;
   float s0 = 0.f, s1 = 0.f;
 #pragma unroll 4
   for (int r = r0 + warp; r < r0 + rows; r += 8) {
@@ -374,11 +376,11 @@ __global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16* g, in
   }
 }
 
-__global__ void bias_grad_final(const float* part, int N, float* db) {
+__global__ void bias_grad_final(const float* part, int N, int slices, float* db) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   float s = 0.f;
-  for (int k = 0; k < kColSlices; ++k) s += part[(size_t)k * N + n];
+  for (int k = 0; k < slices; ++k) s += part[(size_t)k * N + n];
   db[n] = s;
 }
 
@@ -669,8 +671,11 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   int n = Bp * D;
   nll_grad<<<std::min((n + 255) / 256, 1216), 256, 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->loss);
   auto colsum = [&](const __nv_bfloat16* gm, int N, float* db) {
-    bias_grad_part<<<dim3(N / 64, kColSlices), 256, 0, s>>>(gm, Bp, N, m->colpart);
-    bias_grad_final<<<(N + 127) / 128, 128, 0, s>>>(m->colpart, N, db);
+    int slices = kColSlices;
+    while (2 * slices * N <= kColSlices * (O > H ? O : H) && Bp % (2 * slices) == 0 && Bp / (2 * slices) >= 8)
+      slices *= 2;
+    bias_grad_part<<<dim3(N / 64, slices), 256, 0, s>>>(gm, Bp, N, slices, m->colpart);
+    bias_grad_final<<<(N + 127) / 128, 128, 0, s>>>(m->colpart, N, slices, db);
   };
   dim3 tb(32, 8);
   auto T = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
