@@ -753,8 +753,10 @@ def _box_pair_contacts(oracle, ha, hb, qa, qb, margin=0.0):
 
 
 def test_box_box_is_symmetric_under_swapping_the_boxes(oracle):
-    """Reading 16 does not depend on which box is A (random overlapping pairs, no ties): the same
-    reference face and clipped polygon, so the same subs, gaps and points, normals negated."""
+    """The box-box contacts (the face of least penetration is the reference face, the other box's
+    incident face is clipped against it, and each clipped vertex below the margin is a contact)
+    do not depend on which box is A (random overlapping pairs, no ties): the same reference face
+    and clipped polygon, so the same subs, gaps and points, normals negated."""
     rng = np.random.default_rng(21)
     ha, hb = np.array([0.03, 0.04, 0.05]), np.array([0.045, 0.025, 0.035])
     seen = 0
@@ -833,7 +835,8 @@ def _plane_contacts(oracle, geom, q):
 
 
 def test_ellipsoid_plane_is_the_lowest_surface_point(oracle):
-    """Reading 17: the gap of an ellipsoid over the floor is its lowest surface point's height
+    """Ellipsoid on a plane, one contact at the surface point furthest along -n: the gap of an
+    ellipsoid over the floor is its lowest surface point's height
     (dense surface samples), at any orientation; unrotated it is z - c."""
     rng = np.random.default_rng(31)
     e = np.array([0.05, 0.03, 0.02])
@@ -850,7 +853,8 @@ def test_ellipsoid_plane_is_the_lowest_surface_point(oracle):
 
 
 def test_cylinder_plane_rim_points(oracle):
-    """Reading 17: standing, the bottom rim's three points carry the cylinder (gap z - h); lying,
+    """Cylinder on a plane, six candidate points (three rim points 120 degrees apart on each
+    cap, starting from the cap's lowest rim point): standing, the bottom rim's three points carry the cylinder (gap z - h); lying,
     each cap's lowest rim point (gap z - r); tilted, the lowest of the six is the lowest point of
     the solid (dense rim samples)."""
     r, h = 0.03, 0.05
@@ -873,7 +877,7 @@ def test_cylinder_plane_rim_points(oracle):
 
 
 def test_sphere_cylinder_distance_brute_force(oracle):
-    """Reading 17: separated sphere-cylinder pairs: the gap is the distance from the sphere centre
+    """Sphere against a solid cylinder: for separated pairs the gap is the distance from the sphere centre
     to the solid cylinder (dense surface samples) minus the radius; for centres inside, the
     smaller of the side and cap depths."""
     rng = np.random.default_rng(33)
