@@ -25,13 +25,19 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_source(src: str, out: str, opt: str = "-O2") -> str:
+    """Compile an oracle source file into the shared library `out` (g++ -fopenmp)."""
+    cmd = ["g++", opt, "-std=c++17", "-fopenmp", "-fPIC", "-shared", src, "-o", out + ".tmp"]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.cpp into oracle/_build/liboracle.so (g++ -O2 -fopenmp)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp"]
-        subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 
@@ -58,36 +64,40 @@ class OContact(C.Structure):
                 ("m_exact", C.c_double)]
 
 
+def load(path: str):
+    """The oracle library at `path` with its entry points' argument types declared."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.ow_sizes.argtypes = [P(OWorld), P(C.c_int), P(C.c_int)]
+    L.ow_step.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                          P(C.c_int)]
+    L.ow_step_batch.argtypes = [C.c_int, C.c_void_p, P(OParams), C.c_double, C.c_int, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.ow_step_record.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, P(OContact), C.c_int, P(C.c_int)]
+    L.ow_dynamics.argtypes = [P(OWorld), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p]
+    L.ow_cholesky.argtypes = [C.c_void_p, C.c_int]
+    L.ow_capsule_box_param.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
+    L.ow_capsule_box_param.restype = C.c_double
+    L.ow_solimp_r.argtypes = [C.c_double, C.c_void_p]
+    L.ow_solimp_r.restype = C.c_double
+    L.ow_rollout_loss_dir.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_int] + [C.c_void_p] * 6 + [
+        C.c_int, C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_double)]
+    L.ow_max_threads.restype = C.c_int
+    L.ow_impnet_params.restype = C.c_int
+    L.ow_impnet_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    L.ow_impnet_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    L.ow_impnet_loss_grad.restype = C.c_double
+    L.ow_mpc_cost.argtypes = [P(OWorld), C.c_int] + [C.c_void_p] * 4 + [P(C.c_double), P(C.c_double)]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
-            P = C.POINTER
-            L.ow_sizes.argtypes = [P(OWorld), P(C.c_int), P(C.c_int)]
-            L.ow_step.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                  P(C.c_int)]
-            L.ow_step_batch.argtypes = [C.c_int, C.c_void_p, P(OParams), C.c_double, C.c_int, C.c_void_p,
-                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
-            L.ow_step_record.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
-                                         C.c_void_p, C.c_void_p, C.c_void_p, P(OContact), C.c_int, P(C.c_int)]
-            L.ow_dynamics.argtypes = [P(OWorld), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                      C.c_void_p]
-            L.ow_cholesky.argtypes = [C.c_void_p, C.c_int]
-            L.ow_capsule_box_param.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
-            L.ow_capsule_box_param.restype = C.c_double
-            L.ow_solimp_r.argtypes = [C.c_double, C.c_void_p]
-            L.ow_solimp_r.restype = C.c_double
-            L.ow_rollout_loss_dir.argtypes = [P(OWorld), P(OParams), C.c_double, C.c_int] + [C.c_void_p] * 6 + [
-                C.c_int, C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_double)]
-            L.ow_max_threads.restype = C.c_int
-            L.ow_impnet_params.restype = C.c_int
-            L.ow_impnet_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
-            L.ow_impnet_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
-            L.ow_impnet_loss_grad.restype = C.c_double
-            L.ow_mpc_cost.argtypes = [P(OWorld), C.c_int] + [C.c_void_p] * 4 + [P(C.c_double), P(C.c_double)]
-            _lib = L
+            _lib = load(build())
     return _lib
 
 

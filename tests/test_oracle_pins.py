@@ -128,8 +128,71 @@ def test_worked_single_contact_step(oracle, v0x):
     np.testing.assert_allclose(rec["v"][:3], v_exp, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(rec["v"][3:], w_exp, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(rec["q"][:3], np.array([0, 0, 0.048]) + DT * v_exp, rtol=1e-12, atol=1e-15)
+    # the wrench record: normal impulse and the friction along t1 = x, t2 = y
+    dirs = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    f_t = [-0.5 * sum(l * dx for l, (dx, dy) in zip(lam, dirs)), -0.5 * sum(l * dy for l, (dx, dy) in zip(lam, dirs))]
+    np.testing.assert_allclose(c["wrench"][:3], [sum(lam)] + f_t, rtol=1e-12, atol=1e-18)
+    assert (c["wrench"][1] < 0.0) == (v0x > 0.0)          # friction opposes the slide
     if v0x == 0.0:
         assert sum(lam) == pytest.approx(4 * Mphi * 0.000223544, rel=1e-9)  # printed digits of the hand sum
+
+
+@pytest.mark.parametrize("mu_sphere,mu_plane", [(0.2, 0.5), (0.5, 0.2)])
+def test_pair_friction_is_the_larger_coefficient(oracle, mu_sphere, mu_plane):
+    """A contact takes the larger of its two geoms' friction coefficients, whichever geom holds
+    it: the sliding worked step with mu 0.5 on one geom and 0.2 on the other matches the by-hand
+    step at mu = 0.5 (at 0.2 every facet impulse and the friction change)."""
+    d = Wd.world([dict(mass=1.0, inertia=(1e-3,) * 3)],
+                 [dict(type=S.PLANE, body=-1, mu=(mu_plane, 0, 0)),
+                  dict(type=S.SPHERE, body=0, size=(0.05, 0, 0), mu=(mu_sphere, 0, 0))])
+    q, v = Wd.free_state((0, 0, 0.048), lin=(0.1, 0, 0))
+    rec = oracle.step_record(d, Wd.params(n_t=4), DT, q, v)
+    Mphi, lam, v_exp, w_exp = _sphere_plane_by_hand(0.1)
+    assert rec["contacts"][0]["lam_sum"] == pytest.approx(sum(lam), rel=1e-12)
+    np.testing.assert_allclose(rec["v"], np.concatenate([v_exp, w_exp]), rtol=1e-12, atol=1e-15)
+
+
+def test_hinge_link_contact_by_hand(oracle):
+    """A hinged link pressed into the floor, by hand.  The hinge sits at a = (0, 0, 0.1); its body
+    frame is the world frame turned 90 degrees about z, and its axis is body x, so the world axis
+    is e_y.  A capsule (r = 1 cm) runs 10 cm from the hinge along body -y: at angle q the link
+    points along (cos q, 0, -sin q) (a turn by q about +y), and at sin q = 0.92 its tip sphere
+    is 2 mm into the floor.  The centre of mass is on the axis, so gravity exerts no torque and
+    M = I_x.  The contact row of the hinge rate is e_y x l with l the lever from the hinge to the
+    contact midpoint; its trace is |e_y x l|^2 / M.  Four facets {+-x, +-y} with mu = 0.5 take
+    the impulse law of Eq. cf_wrench, and v+ = v + sum_j J~_j lambda_j / M."""
+    I = (2e-4, 3e-4, 4e-4)
+    rz = (np.cos(np.pi / 4), 0.0, 0.0, np.sin(np.pi / 4))      # body frame: 90 degrees about z
+    rx = (np.cos(np.pi / 4), np.sin(np.pi / 4), 0.0, 0.0)      # capsule axis z -> body -y
+    d = Wd.world([dict(parent=-1, jnt=S.HINGE, pos=(0, 0, 0.1), quat=rz, axis=(1, 0, 0), mass=0.5, inertia=I)],
+                 [dict(type=S.PLANE, body=-1),
+                  dict(type=S.CAPSULE, body=0, pos=(0, -0.05, 0), quat=rx, size=(0.01, 0.05, 0))])
+    q0, v0 = np.arcsin(0.92), 1.5
+    rec = oracle.step_record(d, Wd.params(n_t=4), DT, [q0], [v0])
+    assert len(rec["contacts"]) == 1
+    c = rec["contacts"][0]
+    tip = np.array([0.1 * np.cos(q0), 0.0, 0.1 - 0.1 * np.sin(q0)])
+    assert c["phi"] == pytest.approx(tip[2] - 0.01, abs=1e-15)
+    p = np.array([tip[0], 0.0, (tip[2] - 0.01) / 2])          # midpoint of the two surface points
+    np.testing.assert_allclose(c["pos"], p, atol=1e-15)
+    lever = p - np.array([0, 0, 0.1])
+    Jl = np.cross([0.0, 1.0, 0.0], lever)                      # point velocity per unit hinge rate
+    M = I[0]
+    trace = Jl @ Jl / M
+    assert c["trace_a"] == pytest.approx(trace, rel=1e-12) and c["trace_b"] == 0.0
+    Mphi = 0.95 / 0.05 / trace
+    assert c["mphi"] == pytest.approx(Mphi, rel=1e-12)
+    pgen, lam_sum = 0.0, 0.0
+    for dx, dy in [(1, 0), (0, 1), (-1, 0), (0, -1)]:
+        row = Jl[2] - 0.5 * (dx * Jl[0] + dy * Jl[1])          # J~ = J_n - mu d^T J_t
+        s_j = row * v0
+        lam = max(0.0, -0.1 * Mphi * (s_j * DT + c["phi"]) - 0.001 * Mphi * s_j)
+        pgen += row * lam
+        lam_sum += lam
+    assert c["lam_sum"] == pytest.approx(lam_sum, rel=1e-12)
+    assert rec["v"][0] == pytest.approx(v0 + pgen / M, rel=1e-12)
+    assert rec["q"][0] == pytest.approx(q0 + DT * rec["v"][0], rel=1e-14)
+    assert rec["v"][0] < v0                                    # the floor slows the link
 
 
 # ------------------------------------------------------------------------------------------
@@ -528,6 +591,19 @@ def _planar_arm(l1=0.3, l2=0.2):
     return Wd.world(bodies, [dict(type=S.CAPSULE, body=0, pos=(l1 / 2, 0, 0), size=(0.02, 0.1, 0))])
 
 
+def _spatial_arm():
+    """Three hinges with non-parallel axes: about z at the origin; about y at (0.25, 0, 0) in a
+    child frame turned 0.3 rad about x; about x at (0, 0.1, 0.15) in a grandchild frame turned
+    0.5 rad about z.  Off-axis centres of mass, anisotropic inertias, joint damping."""
+    bodies = [dict(parent=-1, jnt=S.HINGE, axis=(0, 0, 1), ipos=(0.1, 0.02, 0), mass=1.1,
+                   inertia=(1e-3, 6e-3, 7e-3), damping=0.2),
+              dict(parent=0, jnt=S.HINGE, pos=(0.25, 0, 0), quat=S.quat_about((1, 0, 0), 0.3), axis=(0, 1, 0),
+                   ipos=(0.03, 0.05, 0.06), mass=0.6, inertia=(2e-3, 1e-3, 2.5e-3), damping=0.1),
+              dict(parent=1, jnt=S.HINGE, pos=(0, 0.1, 0.15), quat=S.quat_about((0, 0, 1), 0.5), axis=(1, 0, 0),
+                   ipos=(0.02, -0.01, 0.04), mass=0.3, inertia=(4e-4, 5e-4, 2e-4), damping=0.05)]
+    return Wd.world(bodies, [dict(type=S.CAPSULE, body=2, pos=(0, 0, 0.04), size=(0.01, 0.03, 0))])
+
+
 def test_forward_kinematics_planar_arm(oracle):
     """Closed form of a planar two-link arm: a rotation by +a about +y takes x to (cos a, 0, -sin a)."""
     l1, l2 = 0.3, 0.2
@@ -567,7 +643,7 @@ def _kinetic_fd(oracle, d, q, h=1e-6):
 
 
 def test_mass_matrix_matches_kinetic_energy(oracle):
-    for d, q in [(_planar_arm(), np.array([0.4, -1.1])),
+    for d, q in [(_planar_arm(), np.array([0.4, -1.1])), (_spatial_arm(), np.array([0.7, -0.4, 1.2])),
                  (S.hand_template(seed=2).__dict__, None)]:
         if q is None:
             t = S.hand_template(seed=2)
@@ -585,21 +661,27 @@ def test_mass_matrix_matches_kinetic_energy(oracle):
         np.testing.assert_allclose(M, M.T, atol=1e-16)
 
 
-def test_bias_forces_match_euler_lagrange(oracle):
+@pytest.mark.parametrize("arm", ["planar", "spatial"])
+def test_bias_forces_match_euler_lagrange(oracle, arm):
     """c(q, v) = Mdot v - dT/dq + dV/dq (Euler-Lagrange with zero joint acceleration), each term
-    by central differences of the (separately pinned) inertia and of the potential sum m g z."""
-    d = _planar_arm()
-    q, v = np.array([0.4, -1.1]), np.array([1.7, -2.3])
+    by central differences of the (separately pinned) inertia and of the potential sum m g z.
+    The spatial arm's non-parallel axes make the velocity-product terms that a planar chain
+    cancels (a child axis turning with its parent) count."""
+    if arm == "planar":
+        d, q, v = _planar_arm(), np.array([0.4, -1.1]), np.array([1.7, -2.3])
+    else:
+        d, q, v = _spatial_arm(), np.array([0.7, -0.4, 1.2]), np.array([1.3, -2.1, 2.6])
+    n = len(q)
     h = 1e-6
     M = lambda qq: oracle.dynamics(d, (0, 0, -G), qq, v)[0]
     Mdot = (M(q + h * v) - M(q - h * v)) / (2 * h)
-    dT = np.array([(0.5 * v @ M(q + h * e) @ v - 0.5 * v @ M(q - h * e) @ v) / (2 * h) for e in np.eye(2)])
+    dT = np.array([(0.5 * v @ M(q + h * e) @ v - 0.5 * v @ M(q - h * e) @ v) / (2 * h) for e in np.eye(n)])
 
     def V(qq):
         _, _, p = oracle.dynamics(d, (0, 0, -G), qq, v)
-        return sum(d["body_mass"][b] * G * p[b, 14] for b in range(2))
+        return sum(d["body_mass"][b] * G * p[b, 14] for b in range(n))
 
-    dV = np.array([(V(q + h * e) - V(q - h * e)) / (2 * h) for e in np.eye(2)])
+    dV = np.array([(V(q + h * e) - V(q - h * e)) / (2 * h) for e in np.eye(n)])
     _, c, _ = oracle.dynamics(d, (0, 0, -G), q, v)
     np.testing.assert_allclose(c, Mdot @ v - dT + dV, rtol=1e-7, atol=1e-9)
 
@@ -619,6 +701,22 @@ def test_implicit_damping_smooth_velocity(oracle):
     q, v, _ = oracle.step(d, Wd.params(gravity=(0.0, 0.0, 0.0)), DT, 1, np.zeros(1), np.array([2.0]))
     assert v[0] == pytest.approx(2.0 * 2e-2 / (2e-2 + DT * 0.3), rel=1e-14)
     assert q[0] == pytest.approx(DT * v[0], rel=1e-14)
+
+
+def test_smooth_prediction_on_a_coupled_chain(oracle):
+    """Eq. smooth_vel on the spatial arm (no contacts): v+ = v + dt (M + dt B)^-1 (tau - c - B v),
+    with M and c from the separately pinned inertia and bias and the solve done by numpy; the
+    chain's M is dense, so each factor and substitution step of the oracle's solve counts."""
+    d = _spatial_arm()
+    q, v, tau = np.array([0.7, -0.4, 1.2]), np.array([1.3, -2.1, 2.6]), np.array([0.4, -0.3, 0.05])
+    M, c, _ = oracle.dynamics(d, (0, 0, -G), q, v)
+    assert np.abs(M[0, 1]) > 1e-3 and np.abs(M[1, 2]) > 1e-4 and np.abs(M[0, 2]) > 1e-4
+    B = np.diag(d["body_damping"])
+    v_exp = v + DT * np.linalg.solve(M + DT * B, tau - c - B @ v)
+    q1, v1, nc = oracle.step(d, Wd.params(), DT, 1, q, v, tau=tau[None])
+    assert nc == 0
+    np.testing.assert_allclose(v1, v_exp, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(q1, q + DT * v_exp, rtol=1e-13, atol=1e-15)
 
 
 # ------------------------------------------------------------------------------------------
@@ -728,6 +826,54 @@ def test_narrowphase_distance_brute_force(oracle, ta, tb):
         if done >= 6:
             break
     assert done >= 3
+
+
+@pytest.mark.parametrize("sphere_first", [True, False])
+def test_sphere_centre_inside_a_box_leaves_through_the_nearest_face(oracle, sphere_first):
+    """A sphere (r = 2 cm) whose centre lies inside a turned box at local (0.04, 0.01, -0.005),
+    half extents (0.05, 0.04, 0.03): the face depths are 0.01, 0.03, 0.025, so the +x face is
+    nearest.  The gap is -(0.01 + r), the normal is the box's +x axis from the box to the sphere
+    (negated when the box is A), and the point is the midpoint of the sphere's deepest point and
+    the centre's projection onto that face."""
+    half = np.array([0.05, 0.04, 0.03])
+    qbox = np.concatenate([[0.1, -0.2, 0.3], S.quat_about((1, 2, -1), 0.8)])
+    R = _quat_mat(qbox[3:])
+    local = np.array([0.04, 0.01, -0.005])
+    centre = qbox[:3] + R @ local
+    qs = np.concatenate([centre, [1.0, 0, 0, 0]])
+    gs, gbx = dict(type=S.SPHERE, size=(0.02, 0, 0)), dict(type=S.BOX, size=tuple(half))
+    cs = (_two_body_contact(oracle, gs, gbx, qs, qbox) if sphere_first
+          else _two_body_contact(oracle, gbx, gs, qbox, qs))
+    assert len(cs) == 1
+    c = cs[0]
+    nb = R[:, 0]                                       # out of the +x face
+    assert c["phi"] == pytest.approx(-(0.01 + 0.02), abs=1e-15)
+    np.testing.assert_allclose(c["normal"], nb if sphere_first else -nb, atol=1e-15)
+    face = qbox[:3] + R @ np.array([0.05, 0.01, -0.005])
+    np.testing.assert_allclose(c["pos"], 0.5 * ((centre - 0.02 * nb) + face), atol=1e-15)
+
+
+@pytest.mark.parametrize("offset_x", [0.02, 0.08])
+def test_crossed_capsules_closed_form(oracle, offset_x):
+    """Capsule A along x (r = 1 cm, half length 5 cm) at the origin; capsule B along y
+    (r = 1.5 cm, half length 5 cm) centred at (offset_x, 0.03, 0.05).  At offset 0.02 the
+    closest axis points are (0.02, 0, 0) and (0.02, 0, 0.05), both inside their segments: gap
+    0.05 - 0.025, normal -z.  At 0.08 A's closest point clamps to its end (0.05, 0, 0), and B's
+    closest point to that is (0.08, 0, 0.05): gap |(-0.03, 0, -0.05)| - 0.025 along that
+    direction.  The contact point is the midpoint of the two surface points."""
+    qa = np.concatenate([[0.0, 0.0, 0.0], S.quat_about((0, 1, 0), np.pi / 2)])    # z -> x
+    qb = np.concatenate([[offset_x, 0.03, 0.05], S.quat_about((1, 0, 0), -np.pi / 2)])   # z -> y
+    cs = _two_body_contact(oracle, dict(type=S.CAPSULE, size=(0.01, 0.05, 0)),
+                           dict(type=S.CAPSULE, size=(0.015, 0.05, 0)), qa, qb)
+    assert len(cs) == 1
+    c = cs[0]
+    pa = np.array([min(offset_x, 0.05), 0.0, 0.0])
+    pb = np.array([offset_x, 0.0, 0.05])
+    dist = np.linalg.norm(pa - pb)
+    n = (pa - pb) / dist
+    assert c["phi"] == pytest.approx(dist - 0.025, abs=1e-15)
+    np.testing.assert_allclose(c["normal"], n, atol=1e-15)
+    np.testing.assert_allclose(c["pos"], 0.5 * ((pa - 0.01 * n) + (pb + 0.015 * n)), atol=1e-15)
 
 
 def _quat_mat(q):
@@ -874,6 +1020,32 @@ def test_cylinder_plane_rim_points(oracle):
         rim = np.concatenate([np.stack([r * np.cos(th), r * np.sin(th), np.full_like(th, z)], 1) for z in (-h, h)])
         low = (rim @ R.T)[:, 2].min() + 0.2
         assert min(c["phi"] for c in cs.values()) == pytest.approx(low, abs=1e-8)
+
+
+@pytest.mark.parametrize("sphere_first", [True, False])
+def test_sphere_centre_inside_a_cylinder_leaves_through_the_nearer_surface(oracle, sphere_first):
+    """A sphere (r = 1 cm) whose centre lies inside a turned solid cylinder (r = 3 cm, half
+    length 5 cm).  At local (0.025, 0, 0.01) the side is 0.005 deep and the cap 0.04: it leaves
+    through the side, normal along the radial direction, contact point on the mantle.  At local
+    (0.01, 0, 0.045) the cap (0.005) is nearer than the side (0.02): normal along the axis, point
+    on the cap.  The normal points from the cylinder to the sphere (negated when the cylinder is A)
+    and the contact point is the midpoint of the sphere's deepest point and the exit point."""
+    qc = np.concatenate([[0.1, 0.05, -0.2], S.quat_about((2, -1, 1), 1.1)])
+    R = _quat_mat(qc[3:])
+    gc, gs = dict(type=S.CYLINDER, size=(0.03, 0.05, 0)), dict(type=S.SPHERE, size=(0.01, 0, 0))
+    for local, n_local, depth, exit_local in [((0.025, 0, 0.01), (1, 0, 0), 0.005, (0.03, 0, 0.01)),
+                                               ((0.01, 0, 0.045), (0, 0, 1), 0.005, (0.01, 0, 0.05))]:
+        centre = qc[:3] + R @ np.array(local)
+        qs = np.concatenate([centre, [1.0, 0, 0, 0]])
+        cs = (_two_body_contact(oracle, gs, gc, qs, qc) if sphere_first
+              else _two_body_contact(oracle, gc, gs, qc, qs))
+        assert len(cs) == 1
+        c = cs[0]
+        nb = R @ np.array(n_local, float)
+        assert c["phi"] == pytest.approx(-(depth + 0.01), abs=1e-15)
+        np.testing.assert_allclose(c["normal"], nb if sphere_first else -nb, atol=1e-15)
+        exit_point = qc[:3] + R @ np.array(exit_local)
+        np.testing.assert_allclose(c["pos"], 0.5 * ((centre - 0.01 * nb) + exit_point), atol=1e-15)
 
 
 def test_sphere_cylinder_distance_brute_force(oracle):
