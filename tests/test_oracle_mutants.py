@@ -312,3 +312,122 @@ def test_a_pin_catches_the_mutant(i, libraries, pins, monkeypatch):
     fast, slow = pins
     caught = _first_failure(fast) or _first_failure(slow)
     assert caught, f"no pin fails with the oracle mutated: {MUTANTS[i][0]}"
+
+
+# ------------------------------------------------------------------------------------------
+# the MLP oracle (oracle/mlp.py) against the pins of test_mlp_oracle.py.  Its BF16 rounding
+# points mirror what the tensor-core kernels store and have no CPU pin: only the GPU
+# comparison fixes them, so no mutant moves one.
+# ------------------------------------------------------------------------------------------
+MLP_SOURCE = os.path.join(os.path.dirname(HERE), "oracle", "mlp.py")
+
+MLP_MUTANTS = [
+    ("BF16 rounding ties away from zero",
+     "u = (u + 0x7FFF + lsb) & 0xFFFF0000",
+     "u = (u + 0x8000) & 0xFFFF0000"),
+    ("BF16 rounding by truncation",
+     "u = (u + 0x7FFF + lsb) & 0xFFFF0000",
+     "u = u & 0xFFFF0000"),
+    ("GELU with erf(z / 2)",
+     "return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))",
+     "return 0.5 * z * (1.0 + _erf(z / 2.0))"),
+    ("GELU derivative without the density term",
+     "return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)",
+     "return 0.5 * (1.0 + _erf(z / math.sqrt(2.0)))"),
+    ("first layer without its bias",
+     'Z1 = X0 @ W1.T + P["b1"]',
+     "Z1 = X0 @ W1.T"),
+    ("second layer without its bias",
+     'Z2 = H1 @ W2.T + P["b2"]',
+     "Z2 = H1 @ W2.T"),
+    ("second layer fed the first layer's pre-activation",
+     'Z2 = H1 @ W2.T + P["b2"]',
+     'Z2 = Z1 @ W2.T + P["b2"]'),
+    ("a GELU on the output layer",
+     'Y = H2 @ W3.T + P["b3"]',
+     'Y = gelu(H2 @ W3.T + P["b3"])'),
+    ("log-std not clamped",
+     "s = np.clip(sr, lo, hi)",
+     "s = sr"),
+    ("NLL with exp(-s) for the inverse variance",
+     "iv = np.exp(-2.0 * s)",
+     "iv = np.exp(-s)"),
+    ("NLL averaged over samples only",
+     "n = a.shape[0] * D",
+     "n = a.shape[0]"),
+    ("NLL mean gradient with the wrong sign",
+     "dY[:, :D] = -e * iv / n",
+     "dY[:, :D] = e * iv / n"),
+    ("gradient flows through the clamped log-std",
+     "dY[:, D:] = np.where((sr > lo) & (sr < hi), (1.0 - e * e * iv) / n, 0.0)",
+     "dY[:, D:] = (1.0 - e * e * iv) / n"),
+    ("output weights' gradient from the first hidden layer",
+     'g = {"W3": dY.T @ c["H2"], "b3": dY.sum(0)}',
+     'g = {"W3": dY.T @ c["H1"], "b3": dY.sum(0)}'),
+    ("second layer's GELU derivative at the first layer's pre-activation",
+     'dA2 = r((dY @ c["W3"]) * gelu_grad(c["Z2"]))',
+     'dA2 = r((dY @ c["W3"]) * gelu_grad(c["Z1"]))'),
+    ("back-propagation through W2 transposed",
+     'dA1 = r((dA2 @ c["W2"]) * gelu_grad(c["Z1"]))',
+     'dA1 = r((dA2 @ c["W2"].T) * gelu_grad(c["Z1"]))'),
+    ("first bias gradient averaged instead of summed",
+     'g["W1"], g["b1"] = dA1.T @ c["X0"], dA1.sum(0)',
+     'g["W1"], g["b1"] = dA1.T @ c["X0"], dA1.mean(0)'),
+]
+
+MLP_IDS = ["-".join(re.findall(r"[a-z0-9]+", name.lower())[:9]) for name, _, _ in MLP_MUTANTS]
+
+
+def _mlp_module(text, name):
+    spec = importlib.util.spec_from_loader(name, loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    exec(compile(text, MLP_SOURCE, "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def mlp_pins():
+    spec = importlib.util.spec_from_file_location("mutation_test_mlp_oracle", os.path.join(HERE, "test_mlp_oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    cases = []
+    for name, fn in inspect.getmembers(mod, inspect.isfunction):
+        if not name.startswith("test_") or fn.__module__ != mod.__name__:
+            continue
+        marks = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+        assert len(marks) <= 1 and (not marks or isinstance(marks[0].args[0], str) and "," not in marks[0].args[0])
+        for val in (marks[0].args[1] if marks else [None]):
+            cases.append((name, fn, {} if val is None else {marks[0].args[0]: val}))
+    return mod, cases
+
+
+def _mlp_first_failure(mod, cases, mlp, monkeypatch):
+    monkeypatch.setattr(mod, "M", mlp)
+    for name, fn, kw in cases:
+        try:
+            fn(**kw)
+        except FAILURES as e:
+            return f"{name}{kw or ''}: {type(e).__name__}"
+    return None
+
+
+def test_every_mlp_mutant_changes_exactly_one_place():
+    src = open(MLP_SOURCE).read()
+    for name, old, new in MLP_MUTANTS:
+        assert old != new, name
+        assert src.count(old) == 1, f"{name}: the replaced text occurs {src.count(old)} times"
+    assert len(set(MLP_IDS)) == len(MLP_IDS)
+
+
+def test_the_mlp_pins_pass_on_an_unmutated_copy(mlp_pins, monkeypatch):
+    mod, cases = mlp_pins
+    assert _mlp_first_failure(mod, cases, _mlp_module(open(MLP_SOURCE).read(), "mlp_copy"), monkeypatch) is None
+
+
+@pytest.mark.parametrize("i", range(len(MLP_MUTANTS)), ids=MLP_IDS)
+def test_a_pin_catches_the_mlp_mutant(i, mlp_pins, monkeypatch):
+    name, old, new = MLP_MUTANTS[i]
+    mod, cases = mlp_pins
+    mutant = _mlp_module(open(MLP_SOURCE).read().replace(old, new), f"mlp_mutant{i}")
+    caught = _mlp_first_failure(mod, cases, mutant, monkeypatch)
+    assert caught, f"no pin fails with the MLP oracle mutated: {name}"
