@@ -167,16 +167,22 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
 
   if (threadIdx.x == 0) {
     bool ok = true;
+    // bit s of `pending`: stage s has a load in flight (a stage holds at most one); bit s of
+    // `phase`: the parity of the loads consumed from stage s, i.e. of the phase to wait on next
+    unsigned pending = 0, phase = 0;
     const int pre = nk < STAGES ? nk : STAGES;
     for (int s = 0; s < pre; ++s) {
       mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
       tma_load_2d(sA + s * A_BYTES, &tmA, kz + s * BK, m0, &full[s]);
       tma_load_2d(sB + s * B_BYTES, &tmB, kz + s * BK, n0, &full[s]);
+      pending |= 1u << s;
     }
     for (int k = 0; k < nk && ok; ++k) {
       const int s = k % STAGES;
       const uint32_t par = (k / STAGES) & 1;
       if (!mbar_wait(&full[s], par)) { ok = false; break; }
+      pending &= ~(1u << s);
+      phase ^= 1u << s;
       tc_fence_after();
       const uint64_t da = smem_desc(smem_u32(sA + s * A_BYTES));
       const uint64_t db = smem_desc(smem_u32(sB + s * B_BYTES));
@@ -189,15 +195,19 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
         tma_load_2d(sA + s * A_BYTES, &tmA, kz + (k + STAGES) * BK, m0, &full[s]);
         tma_load_2d(sB + s * B_BYTES, &tmB, kz + (k + STAGES) * BK, n0, &full[s]);
+        pending |= 1u << s;
       }
     }
-    if (ok) {
-      umma_commit(&done);
-    } else {
+    if (!ok) {
+      // a wait gave up: flag it, then let this CTA's own loads in flight land (each wait again
+      // bounded) before the shared memory they write is released
       s_ok = 0;
       atomicOr(ep.err, CF_FLAG_TIMEOUT);
-      mbar_arrive(&done);
+      for (int s = 0; s < STAGES; ++s)
+        if ((pending >> s) & 1u) mbar_wait(&full[s], (phase >> s) & 1u);
     }
+    // `done` fires once every MMA issued here has completed, so TMEM is freed only after them
+    umma_commit(&done);
   }
   __syncwarp();
   bool ok = mbar_wait(&done, 0);
