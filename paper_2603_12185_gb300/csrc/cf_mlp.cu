@@ -7,6 +7,7 @@
 // accumulator, and four warps run the fused epilogue from tcgen05.ld (bias, GELU or its
 // derivative, BF16/FP32 stores).  Every mbarrier wait is bounded: a wait that gives up sets the
 // error word, the CTA skips its remaining work, frees its TMEM and returns.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -43,6 +44,8 @@ struct EpiArgs {
   int ldo;
   int m_valid;              // rows >= m_valid are not stored
   int* err;
+  __nv_bfloat16* out_t;     // optional [N x ldt] transposed copy of out_bf16 (EPI_BIAS_GELU, EPI_GELU_BWD)
+  int ldt;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -132,7 +135,9 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-template <int BN, int EPI>
+// TR: also write the transposed copy ep.out_t (EPI_BIAS_GELU, EPI_GELU_BWD); a template
+// parameter, so that the instantiations without it keep the plain epilogue's code
+template <int BN, int EPI, bool TR = false>
 __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB, EpiArgs ep, int K) {
   extern __shared__ uint8_t smem_raw[];
@@ -220,6 +225,12 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     // of z) are 16- or 8-byte vectors on contiguous 64- or 32-byte row segments.  Row stride 20
     // floats keeps the staging writes of a quarter-warp on distinct banks.
     float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 20);
+    // the slice's bf16 outputs again, for the optional transposed copy: rows of kTB = 18
+    // elements (4-byte aligned; the two half-columns a lane pair reads fall on different banks)
+    constexpr bool trans = TR && (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD);
+    constexpr int kTB = 18;
+    __nv_bfloat16* tstage = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<float*>(smem) + 4 * 32 * 20) +
+                            warp * (32 * kTB);
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
     const int quad = lane & 3, ro = lane >> 2;
     float* out_f32 = ep.out_f32 + (size_t)blockIdx.z * ep.slice_stride;
@@ -246,6 +257,11 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
             __nv_bfloat162 hh[2] = {__floats2bfloat162_rn(gelu(z0), gelu(z1)), __floats2bfloat162_rn(gelu(z2), gelu(z3))};
             *reinterpret_cast<uint2*>(ep.out_z + o) = *reinterpret_cast<const uint2*>(zz);
             *reinterpret_cast<uint2*>(ep.out_bf16 + o) = *reinterpret_cast<const uint2*>(hh);
+            if (trans) {
+              __nv_bfloat162* t2 = reinterpret_cast<__nv_bfloat162*>(tstage + r * kTB + 4 * quad);
+              t2[0] = hh[0];
+              t2[1] = hh[1];
+            }
           } else if (EPI == EPI_BIAS_F32) {
             *reinterpret_cast<float4*>(out_f32 + o) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
           } else if (EPI == EPI_F32) {
@@ -257,10 +273,36 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
                 __floats2bfloat162_rn(a.x * gelu_grad(__low2float(zp[0])), a.y * gelu_grad(__high2float(zp[0]))),
                 __floats2bfloat162_rn(a.z * gelu_grad(__low2float(zp[1])), a.w * gelu_grad(__high2float(zp[1])))};
             *reinterpret_cast<uint2*>(ep.out_bf16 + o) = *reinterpret_cast<const uint2*>(gg);
+            if (trans) {
+              __nv_bfloat162* t2 = reinterpret_cast<__nv_bfloat162*>(tstage + r * kTB + 4 * quad);
+              t2[0] = gg[0];
+              t2[1] = gg[1];
+            }
           }
         }
       }
       __syncwarp();
+      if (trans) {
+        // transposed copy: lane pair (2j, 2j + 1) writes column n0 + c + j, rows 16h .. 16h + 15 of
+        // this warp's 32 as two 16-byte vectors (ldt is a multiple of 16 elements)
+        const int j = lane >> 1, h = lane & 1;
+        const int row0 = m0 + warp * 32 + 16 * h;
+        __nv_bfloat16* dst = ep.out_t + (size_t)(n0 + c + j) * ep.ldt + row0;
+        const __nv_bfloat16* src = tstage + 16 * h * kTB + j;
+        if (row0 + 16 <= ep.m_valid) {
+          uint32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            w[k] = (uint32_t)__bfloat16_as_ushort(src[(2 * k) * kTB]) |
+                   ((uint32_t)__bfloat16_as_ushort(src[(2 * k + 1) * kTB]) << 16);
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+          for (int t = 0; t < 16; ++t)
+            if (row0 + t < ep.m_valid) dst[t] = src[t * kTB];
+        }
+        __syncwarp();
+      }
     }
   }
   tc_fence_before();
@@ -324,35 +366,64 @@ __global__ void transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloa
 
 // Gaussian negative log-likelihood of targets a under mean mu = y[:, :D] and log-std
 // s = clamp(y[:, D:], lo, hi):  l = sum_d ((a - mu)^2 / (2 e^{2s}) + s) / (B D).
-// Writes dL/dy as bf16 into dy [Bp x 2D] (zero rows past B) and accumulates the loss.
-// Grid-stride over the Bp x D elements; the loss is reduced per CTA (shuffles, then shared
-// memory) and added with one atomic per CTA.
+// Writes dL/dy as bf16 twice: dy [Bp x 2D] (zero rows past B) for the backward product through
+// W3, and its transpose dyt [2D x Bp] for the weight gradient, both with coalesced stores.  A
+// (32, 8) block takes 64 rows x 64 columns of mu (and the same 64 columns of s): each lane
+// computes two adjacent columns of a row, the tile goes through shared memory (rows of 65
+// elements, so that the column reads of a warp fall on distinct banks) and is written
+// transposed as bf16 pairs.  The loss is reduced per block (shuffles, then shared memory) and
+// added with one atomic per block.  D and Bp are multiples of 64.
 __global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, int B, int Bp, int D, float lo, float hi,
-                                                __nv_bfloat16* dy, float* loss) {
-  float l = 0.f;
-  const float inv_n = 1.f / ((float)B * (float)D);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Bp * D; i += gridDim.x * blockDim.x) {
-    int r = i / D, d = i % D;
-    float gmu = 0.f, gs = 0.f;
-    if (r < B) {
-      float mu = y[(size_t)r * 2 * D + d], sr = y[(size_t)r * 2 * D + D + d];
-      float s = fminf(fmaxf(sr, lo), hi);
-      float e = a[(size_t)r * D + d] - mu;
-      float iv = expf(-2.f * s);
-      l += (0.5f * e * e * iv + s) * inv_n;
-      gmu = -e * iv * inv_n;
-      gs = (sr > lo && sr < hi) ? (1.f - e * e * iv) * inv_n : 0.f;
-    }
-    dy[(size_t)r * 2 * D + d] = __float2bfloat16_rn(gmu);
-    dy[(size_t)r * 2 * D + D + d] = __float2bfloat16_rn(gs);
-  }
+                                                __nv_bfloat16* dy, __nv_bfloat16* dyt, float* loss) {
+  __shared__ __nv_bfloat16 tm[64][65], ts[64][65];
   __shared__ float red[8];
-  for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  const int r0 = blockIdx.y * 64, d0 = blockIdx.x * 64, x2 = 2 * threadIdx.x;
+  const float inv_n = 1.f / ((float)B * (float)D);
+  float l = 0.f;
+  for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+    const int r = r0 + k, d = d0 + x2;
+    float gm[2] = {0.f, 0.f}, gs[2] = {0.f, 0.f};
+    if (r < B) {
+      const float2 mu = *reinterpret_cast<const float2*>(y + (size_t)r * 2 * D + d);
+      const float2 sr = *reinterpret_cast<const float2*>(y + (size_t)r * 2 * D + D + d);
+      const float* ar = a + (size_t)r * D + d;  // the caller's targets: no alignment assumed
+      const float m2[2] = {mu.x, mu.y}, s2[2] = {sr.x, sr.y}, a2[2] = {ar[0], ar[1]};
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float s = fminf(fmaxf(s2[i], lo), hi);
+        const float e = a2[i] - m2[i];
+        const float iv = expf(-2.f * s);
+        l += (0.5f * e * e * iv + s) * inv_n;
+        gm[i] = -e * iv * inv_n;
+        gs[i] = (s2[i] > lo && s2[i] < hi) ? (1.f - e * e * iv) * inv_n : 0.f;
+      }
+    }
+    const __nv_bfloat162 bm = __floats2bfloat162_rn(gm[0], gm[1]), bs = __floats2bfloat162_rn(gs[0], gs[1]);
+    *reinterpret_cast<__nv_bfloat162*>(dy + (size_t)r * 2 * D + d) = bm;
+    *reinterpret_cast<__nv_bfloat162*>(dy + (size_t)r * 2 * D + D + d) = bs;
+    tm[k][x2] = bm.x;
+    tm[k][x2 + 1] = bm.y;
+    ts[k][x2] = bs.x;
+    ts[k][x2 + 1] = bs.y;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+    const int r = r0 + x2;
+    __nv_bfloat162 vm, vs;
+    vm.x = tm[x2][k];
+    vm.y = tm[x2 + 1][k];
+    vs.x = ts[x2][k];
+    vs.y = ts[x2 + 1][k];
+    *reinterpret_cast<__nv_bfloat162*>(dyt + (size_t)(d0 + k) * Bp + r) = vm;
+    *reinterpret_cast<__nv_bfloat162*>(dyt + (size_t)(D + d0 + k) * Bp + r) = vs;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = l;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
     float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < (int)(blockDim.x * blockDim.y >> 5); ++w) t += red[w];
     if (t != 0.f) atomicAdd(loss, t);
   }
 }
@@ -465,26 +536,37 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows)
 
 size_t gemm_smem(int BN) { return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024; }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool TR = false>
 cudaError_t gemm_launch(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s,
                         int split = 1) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN)) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gemm_smem(BN));
+  if (TR && (ep.out_t == nullptr || ep.ldt % 16 || ep.ldt < M)) return cudaErrorInvalidValue;
+  // the dynamic shared memory opt-in is per device: one bit per device that has it
+  static std::atomic<uint64_t> attr{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!((attr.load() >> dev) & 1u)) {
+    e = cudaFuncSetAttribute(gemm_kernel<BN, EPI, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemm_smem(BN));
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.fetch_or(uint64_t(1) << dev);
   }
   dim3 grid(N / BN, M / BM, split);
-  gemm_kernel<BN, EPI><<<grid, 128, gemm_smem(BN), s>>>(ta, tb, ep, K / split);
+  gemm_kernel<BN, EPI, TR><<<grid, 128, gemm_smem(BN), s>>>(ta, tb, ep, K / split);
   return cudaGetLastError();
 }
 
+// ep.out_t set: the epilogue also writes the transposed copy (EPI_BIAS_GELU, EPI_GELU_BWD)
 template <int EPI>
 cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const EpiArgs& ep, cudaStream_t s) {
   if (M % BM || K % BK || N % 64) return cudaErrorInvalidValue;
+  constexpr bool can_t = EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD;
+  if (ep.out_t && !can_t) return cudaErrorInvalidValue;
+  if (can_t && ep.out_t)
+    return N % 128 == 0 ? gemm_launch<128, EPI, can_t>(A, M, B, N, K, ep, s) : gemm_launch<64, EPI, can_t>(A, M, B, N, K, ep, s);
   if (N % 128 == 0) return gemm_launch<128, EPI>(A, M, B, N, K, ep, s);
   return gemm_launch<64, EPI>(A, M, B, N, K, ep, s);
 }
@@ -647,15 +729,19 @@ extern "C" cf_status cf_mlp_param_count(const cf_mlp* m, int64_t* n) {
   return CF_OK;
 }
 
-static cf_status forward(cf_mlp* m, const float* x, int B, cudaStream_t s) {
+// train: the hidden layers' GEMMs also write H1^T and H2^T [H x Bp], the K-major operands of
+// the weight gradients
+static cf_status forward(cf_mlp* m, const float* x, int B, cudaStream_t s, bool train = false) {
   const int Bp = (B + 127) / 128 * 128;
   int n = Bp * m->kin;
   pack_input<<<(n + 255) / 256, 256, 0, s>>>(x, B, m->fin, Bp, m->kin, m->X0);
   EpiArgs e1{};
   e1.bias = m->w + m->ob1; e1.out_bf16 = m->H1; e1.out_z = m->Z1; e1.ldo = m->H; e1.m_valid = Bp; e1.err = m->err;
+  if (train) { e1.out_t = m->H1t; e1.ldt = Bp; }
   cudaError_t e = gemm<EPI_BIAS_GELU>(m->X0, Bp, m->W1b, m->H, m->kin, e1, s);
   EpiArgs e2 = e1;
   e2.bias = m->w + m->ob2; e2.out_bf16 = m->H2; e2.out_z = m->Z2;
+  if (train) e2.out_t = m->H2t;
   if (e == cudaSuccess) e = gemm<EPI_BIAS_GELU>(m->H1, Bp, m->W2b, m->H, m->H, e2, s);
   EpiArgs e3{};
   e3.bias = m->w + m->ob3; e3.out_f32 = m->Y; e3.ldo = m->O; e3.m_valid = Bp; e3.err = m->err;
@@ -678,8 +764,7 @@ extern "C" cf_status cf_mlp_forward(cf_mlp* m, const float* x, int32_t B, float*
 static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float hi, cudaStream_t s) {
   const int Bp = (B + 127) / 128 * 128, H = m->H, O = m->O, D = O / 2;
   cudaMemsetAsync(m->loss, 0, 4, s);
-  int n = Bp * D;
-  nll_grad<<<std::min((n + 255) / 256, 1216), 256, 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->loss);
+  nll_grad<<<dim3(D / 64, Bp / 64), dim3(32, 8), 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->dYt, m->loss);
   auto colsum = [&](const __nv_bfloat16* gm, int N, float* db) {
     int slices = kColSlices;
     while (2 * slices * N <= kColSlices * (O > H ? O : H) && Bp % (2 * slices) == 0 && Bp / (2 * slices) >= 8)
@@ -692,26 +777,23 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
     transpose_bf16<<<dim3((C + 63) / 64, (R + 63) / 64), tb, 0, s>>>(in, R, C, out);
   };
   cudaError_t e = cudaSuccess;
-  // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 (times gelu'(Z2))
-  T(m->dY, Bp, O, m->dYt);
-  T(m->H2, Bp, H, m->H2t);
+  // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 (times gelu'(Z2)); dY^T comes from
+  // nll_grad and H2^T from the forward pass, dA2^T and dA1^T from the GELU-derivative epilogues
   EpiArgs ew{};
   ew.out_f32 = m->g + m->oW3; ew.ldo = H; ew.m_valid = O; ew.err = m->err;
   e = gemm_f32_splitk(m->dYt, O, m->H2t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
   colsum(m->dY, O, m->g + m->ob3);
   EpiArgs eb{};
   eb.out_bf16 = m->dA2; eb.z = m->Z2; eb.ldo = H; eb.m_valid = Bp; eb.err = m->err;
+  eb.out_t = m->dA2t; eb.ldt = Bp;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dY, Bp, m->W3t, H, O, eb, s);
   // layer 2
-  T(m->dA2, Bp, H, m->dA2t);
-  T(m->H1, Bp, H, m->H1t);
   ew.out_f32 = m->g + m->oW2; ew.ldo = H; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm_f32_splitk(m->dA2t, H, m->H1t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
   colsum(m->dA2, H, m->g + m->ob2);
-  eb.out_bf16 = m->dA1; eb.z = m->Z1;
+  eb.out_bf16 = m->dA1; eb.z = m->Z1; eb.out_t = m->dA1t;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dA2, Bp, m->W2t, H, H, eb, s);
   // layer 1
-  T(m->dA1, Bp, H, m->dA1t);
   T(m->X0, Bp, m->kin, m->X0t);
   ew.out_f32 = m->g + m->oW1; ew.ldo = m->kin; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm_f32_splitk(m->dA1t, H, m->X0t, m->kin, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
@@ -725,7 +807,7 @@ extern "C" cf_status cf_mlp_gradients(cf_mlp* m, const float* x, const float* ta
                                       float logstd_hi, float* grads, float* loss, void* stream) {
   if (!m || !x || !target || B < 1 || B > m->maxB) return mfail(CF_ERR_INVALID_ARGUMENT, "bad mlp arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  cf_status st = forward(m, x, B, s);
+  cf_status st = forward(m, x, B, s, true);
   if (st == CF_OK) st = backward(m, target, B, logstd_lo, logstd_hi, s);
   if (st != CF_OK) return st;
   if (grads) cudaMemcpyAsync(grads, m->g, m->nparam * 4, cudaMemcpyDeviceToDevice, s);
