@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_own_distinct_worlds_and_reduce_timings():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may hold OpenMP threads
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
