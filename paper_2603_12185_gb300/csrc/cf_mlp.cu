@@ -46,6 +46,8 @@ struct EpiArgs {
   int* err;
   __nv_bfloat16* out_t;     // optional [N x ldt] transposed copy of out_bf16 (EPI_BIAS_GELU, EPI_GELU_BWD)
   int ldt;
+  float* colsum;            // optional with out_t, EPI_GELU_BWD: [M / 128 x ldo] column sums of out_bf16
+                            // over each CTA's 128 rows (the bias gradient's partial sums)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     constexpr int kTB = 18;
     __nv_bfloat16* tstage = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<float*>(smem) + 4 * 32 * 20) +
                             warp * (32 * kTB);
+    float* csm = reinterpret_cast<float*>(smem) + 4 * 32 * 20 + 4 * 32 * kTB / 2;  // [4 warps][BN] column sums
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
     const int quad = lane & 3, ro = lane >> 2;
     float* out_f32 = ep.out_f32 + (size_t)blockIdx.z * ep.slice_stride;
@@ -289,17 +292,29 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
         const int row0 = m0 + warp * 32 + 16 * h;
         __nv_bfloat16* dst = ep.out_t + (size_t)(n0 + c + j) * ep.ldt + row0;
         const __nv_bfloat16* src = tstage + 16 * h * kTB + j;
+        float csum = 0.f;  // this half-column's stored values, summed in row order
         if (row0 + 16 <= ep.m_valid) {
           uint32_t w[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            w[k] = (uint32_t)__bfloat16_as_ushort(src[(2 * k) * kTB]) |
-                   ((uint32_t)__bfloat16_as_ushort(src[(2 * k + 1) * kTB]) << 16);
+          for (int k = 0; k < 8; ++k) {
+            const __nv_bfloat16 lo = src[(2 * k) * kTB], hi = src[(2 * k + 1) * kTB];
+            w[k] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            csum += __bfloat162float(lo);
+            csum += __bfloat162float(hi);
+          }
           reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
           reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
         } else {
           for (int t = 0; t < 16; ++t)
-            if (row0 + t < ep.m_valid) dst[t] = src[t * kTB];
+            if (row0 + t < ep.m_valid) {
+              dst[t] = src[t * kTB];
+              csum += __bfloat162float(src[t * kTB]);
+            }
+        }
+        if (EPI == EPI_GELU_BWD && ep.colsum != nullptr) {
+          // both halves of the column (lanes 2j, 2j + 1), kept per warp until the CTA's barrier
+          csum += __shfl_xor_sync(0xffffffffu, csum, 1);
+          if (h == 0) csm[warp * BN + c + j] = csum;
         }
         __syncwarp();
       }
@@ -308,6 +323,12 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  if (TR && EPI == EPI_GELU_BWD && ep.colsum != nullptr && s_ok && warp == 0) {
+    // the four warps' column sums of this CTA's 128 rows, added in warp order
+    const float* csm = reinterpret_cast<const float*>(smem) + 4 * 32 * 20 + 4 * 32 * 18 / 2;
+    for (int col = lane; col < BN; col += 32)
+      ep.colsum[(size_t)blockIdx.y * ep.ldo + n0 + col] = ((csm[col] + csm[BN + col]) + csm[2 * BN + col]) + csm[3 * BN + col];
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -372,11 +393,15 @@ __global__ void transpose_bf16(const __nv_bfloat16* in, int R, int C, __nv_bfloa
 // computes two adjacent columns of a row, the tile goes through shared memory (rows of 65
 // elements, so that the column reads of a warp fall on distinct banks) and is written
 // transposed as bf16 pairs.  The loss is reduced per block (shuffles, then shared memory) and
-// added with one atomic per block.  D and Bp are multiples of 64.
+// added with one atomic per block.  The bias gradient's partial sums: each block also writes
+// the column sums of its 64 rows of the stored (bf16) dL/dy into part[Bp / 64][2D], adding its
+// 8 row groups in order.  D and Bp are multiples of 64.
 __global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, int B, int Bp, int D, float lo, float hi,
-                                                __nv_bfloat16* dy, __nv_bfloat16* dyt, float* loss) {
+                                                __nv_bfloat16* dy, __nv_bfloat16* dyt, float* loss, float* part) {
   __shared__ __nv_bfloat16 tm[64][65], ts[64][65];
   __shared__ float red[8];
+  __shared__ float4 csum[8][32];
+  float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);  // this thread's two mu columns, then two s columns
   const int r0 = blockIdx.y * 64, d0 = blockIdx.x * 64, x2 = 2 * threadIdx.x;
   const float inv_n = 1.f / ((float)B * (float)D);
   float l = 0.f;
@@ -401,12 +426,29 @@ __global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, 
     const __nv_bfloat162 bm = __floats2bfloat162_rn(gm[0], gm[1]), bs = __floats2bfloat162_rn(gs[0], gs[1]);
     *reinterpret_cast<__nv_bfloat162*>(dy + (size_t)r * 2 * D + d) = bm;
     *reinterpret_cast<__nv_bfloat162*>(dy + (size_t)r * 2 * D + D + d) = bs;
+    cs.x += __low2float(bm);
+    cs.y += __high2float(bm);
+    cs.z += __low2float(bs);
+    cs.w += __high2float(bs);
     tm[k][x2] = bm.x;
     tm[k][x2 + 1] = bm.y;
     ts[k][x2] = bs.x;
     ts[k][x2 + 1] = bs.y;
   }
+  csum[threadIdx.y][threadIdx.x] = cs;
   __syncthreads();
+  if (threadIdx.y == 0) {
+    float4 t = csum[0][threadIdx.x];
+    for (int g = 1; g < 8; ++g) {
+      const float4 u = csum[g][threadIdx.x];
+      t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+    }
+    float* pr = part + (size_t)blockIdx.y * 2 * D;
+    pr[d0 + x2] = t.x;
+    pr[d0 + x2 + 1] = t.y;
+    pr[D + d0 + x2] = t.z;
+    pr[D + d0 + x2 + 1] = t.w;
+  }
   for (int k = threadIdx.y; k < 64; k += blockDim.y) {
     const int r = r0 + x2;
     __nv_bfloat162 vm, vs;
@@ -428,41 +470,29 @@ __global__ void __launch_bounds__(256) nll_grad(const float* y, const float* a, 
   }
 }
 
-// Column sums db[n] = sum_r g[r][n] of a bf16 gradient [R x N] (N a multiple of 64, R a multiple
-// of `slices`) in two deterministic passes: CTA (c, s) sums rows of slice s for 64 columns
-// (each lane two adjacent columns, the 8 warps interleaved over the rows, combined in warp order)
-// into part[s][n]; then one thread per column adds the slices in order.  Narrow gradients take
-// more slices (the partial buffer holds kColSlices x the widest layer), so that they too give
-// every SM blocks.
-constexpr int kColSlices = 32;
-__global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16* g, int R, int N, int slices, float* part) {
+// Bias gradients db[n] = sum over the partial sums part[k][n], k = 0 .. slices - 1, in a fixed
+// order (deterministic); the partials are written by nll_grad (one per 64-row tile) and by the
+// GELU-derivative GEMM epilogues (one per 128-row CTA).  N is a multiple of 64.
+__global__ void __launch_bounds__(256) bias_grad_final(const float* part, int N, int slices, float* db) {
+  // 64 columns per block, two adjacent ones per lane; warp w adds partials w, w + 8, ... in
+  // order, then warp 0 adds the 8 warps' sums in order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.x * 64 + 2 * lane;
-  const int rows = R / slices, r0 = blockIdx.y * rows;
-  float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-  for (int r = r0 + warp; r < r0 + rows; r += 8) {
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(g + (size_t)r * N + c0);
-    s0 += __low2float(v);
-    s1 += __high2float(v);
+  float2 t = make_float2(0.f, 0.f);
+  for (int k = warp; k < slices; k += 8) {
+    const float2 v = *reinterpret_cast<const float2*>(part + (size_t)k * N + c0);
+    t.x += v.x;
+    t.y += v.y;
   }
   __shared__ float2 red[8][32];
-  red[warp][lane] = make_float2(s0, s1);
+  red[warp][lane] = t;
   __syncthreads();
   if (warp == 0) {
-    float t0 = 0.f, t1 = 0.f;
-    for (int w = 0; w < 8; ++w) { t0 += red[w][lane].x; t1 += red[w][lane].y; }
-    part[(size_t)blockIdx.y * N + c0] = t0;
-    part[(size_t)blockIdx.y * N + c0 + 1] = t1;
+    float2 u = red[0][lane];
+    for (int w = 1; w < 8; ++w) { u.x += red[w][lane].x; u.y += red[w][lane].y; }
+    db[c0] = u.x;
+    db[c0 + 1] = u.y;
   }
-}
-
-__global__ void bias_grad_final(const float* part, int N, int slices, float* db) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  float s = 0.f;
-  for (int k = 0; k < slices; ++k) s += part[(size_t)k * N + n];
-  db[n] = s;
 }
 
 // Adam on the fp32 master weights; refreshes the bf16 copy (and its transpose when given)
@@ -565,6 +595,7 @@ cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const EpiArg
   if (M % BM || K % BK || N % 64) return cudaErrorInvalidValue;
   constexpr bool can_t = EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD;
   if (ep.out_t && !can_t) return cudaErrorInvalidValue;
+  if (ep.colsum && (EPI != EPI_GELU_BWD || !ep.out_t || ep.ldo != N)) return cudaErrorInvalidValue;
   if (can_t && ep.out_t)
     return N % 128 == 0 ? gemm_launch<128, EPI, can_t>(A, M, B, N, K, ep, s) : gemm_launch<64, EPI, can_t>(A, M, B, N, K, ep, s);
   if (N % 128 == 0) return gemm_launch<128, EPI>(A, M, B, N, K, ep, s);
@@ -619,7 +650,7 @@ struct cf_mlp {
   size_t oW1, ob1, oW2, ob2, oW3, ob3;
   __nv_bfloat16 *W1b, *W2b, *W3b, *W2t, *W3t;
   __nv_bfloat16 *X0, *Z1, *H1, *Z2, *H2, *dY, *dA2, *dA1, *dYt, *H2t, *dA2t, *H1t, *dA1t, *X0t;
-  float *Y, *loss, *colpart, *splitk;
+  float *Y, *loss, *part3, *part2, *part1, *splitk;
   size_t splitk_floats;
   int num_sms;
   int* err;
@@ -641,7 +672,9 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
   size_t o_H2t = take((size_t)Bp * H * 2), o_dA2t = take((size_t)Bp * H * 2), o_H1t = take((size_t)Bp * H * 2);
   size_t o_dA1t = take((size_t)Bp * H * 2), o_X0t = take((size_t)Bp * kin * 2);
   size_t o_Y = take((size_t)Bp * O * 4), o_loss = take(16), o_err = take(16);
-  size_t o_colpart = take((size_t)kColSlices * (O > H ? O : H) * 4);
+  // the bias gradients' partial sums: dY per 64-row tile, dA2 and dA1 per 32-row chunk
+  size_t o_part3 = take((size_t)(Bp / 64) * O * 4), o_part2 = take((size_t)(Bp / 32) * H * 4);
+  size_t o_part1 = take((size_t)(Bp / 32) * H * 4);
   const size_t wmax = std::max((size_t)O * H, std::max((size_t)H * H, (size_t)H * kin));
   size_t o_splitk = take((size_t)kSplitScratch * wmax * 4);
   if (m) {
@@ -659,7 +692,7 @@ static size_t mlp_layout(int fin, int H, int O, int maxB, cf_mlp* m) {
     m->H2t = (__nv_bfloat16*)(b + o_H2t); m->dA2t = (__nv_bfloat16*)(b + o_dA2t); m->H1t = (__nv_bfloat16*)(b + o_H1t);
     m->dA1t = (__nv_bfloat16*)(b + o_dA1t); m->X0t = (__nv_bfloat16*)(b + o_X0t);
     m->Y = (float*)(b + o_Y); m->loss = (float*)(b + o_loss); m->err = (int*)(b + o_err);
-    m->colpart = (float*)(b + o_colpart);
+    m->part3 = (float*)(b + o_part3); m->part2 = (float*)(b + o_part2); m->part1 = (float*)(b + o_part1);
     m->splitk = (float*)(b + o_splitk);
     m->splitk_floats = (size_t)kSplitScratch * wmax;
   }
@@ -764,13 +797,10 @@ extern "C" cf_status cf_mlp_forward(cf_mlp* m, const float* x, int32_t B, float*
 static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float hi, cudaStream_t s) {
   const int Bp = (B + 127) / 128 * 128, H = m->H, O = m->O, D = O / 2;
   cudaMemsetAsync(m->loss, 0, 4, s);
-  nll_grad<<<dim3(D / 64, Bp / 64), dim3(32, 8), 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->dYt, m->loss);
-  auto colsum = [&](const __nv_bfloat16* gm, int N, float* db) {
-    int slices = kColSlices;
-    while (2 * slices * N <= kColSlices * (O > H ? O : H) && Bp % (2 * slices) == 0 && Bp / (2 * slices) >= 8)
-      slices *= 2;
-    bias_grad_part<<<dim3(N / 64, slices), 256, 0, s>>>(gm, Bp, N, slices, m->colpart);
-    bias_grad_final<<<(N + 127) / 128, 128, 0, s>>>(m->colpart, N, slices, db);
+  nll_grad<<<dim3(D / 64, Bp / 64), dim3(32, 8), 0, s>>>(m->Y, target, B, Bp, D, lo, hi, m->dY, m->dYt, m->loss,
+                                                         m->part3);
+  auto colsum = [&](const float* part, int N, int slices, float* db) {
+    bias_grad_final<<<N / 64, 256, 0, s>>>(part, N, slices, db);
   };
   dim3 tb(32, 8);
   auto T = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
@@ -782,22 +812,22 @@ static cf_status backward(cf_mlp* m, const float* target, int B, float lo, float
   EpiArgs ew{};
   ew.out_f32 = m->g + m->oW3; ew.ldo = H; ew.m_valid = O; ew.err = m->err;
   e = gemm_f32_splitk(m->dYt, O, m->H2t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
-  colsum(m->dY, O, m->g + m->ob3);
+  colsum(m->part3, O, Bp / 64, m->g + m->ob3);
   EpiArgs eb{};
   eb.out_bf16 = m->dA2; eb.z = m->Z2; eb.ldo = H; eb.m_valid = Bp; eb.err = m->err;
-  eb.out_t = m->dA2t; eb.ldt = Bp;
+  eb.out_t = m->dA2t; eb.ldt = Bp; eb.colsum = m->part2;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dY, Bp, m->W3t, H, O, eb, s);
   // layer 2
   ew.out_f32 = m->g + m->oW2; ew.ldo = H; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm_f32_splitk(m->dA2t, H, m->H1t, H, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
-  colsum(m->dA2, H, m->g + m->ob2);
-  eb.out_bf16 = m->dA1; eb.z = m->Z1; eb.out_t = m->dA1t;
+  colsum(m->part2, H, Bp / 128, m->g + m->ob2);
+  eb.out_bf16 = m->dA1; eb.z = m->Z1; eb.out_t = m->dA1t; eb.colsum = m->part1;
   if (e == cudaSuccess) e = gemm<EPI_GELU_BWD>(m->dA2, Bp, m->W2t, H, H, eb, s);
   // layer 1
   T(m->X0, Bp, m->kin, m->X0t);
   ew.out_f32 = m->g + m->oW1; ew.ldo = m->kin; ew.m_valid = H;
   if (e == cudaSuccess) e = gemm_f32_splitk(m->dA1t, H, m->X0t, m->kin, Bp, ew, m->splitk, m->splitk_floats, m->num_sms, s);
-  colsum(m->dA1, H, m->g + m->ob1);
+  colsum(m->part1, H, Bp / 128, m->g + m->ob1);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(CF_ERR_CUDA, cudaGetErrorString(e));
   return CF_OK;
