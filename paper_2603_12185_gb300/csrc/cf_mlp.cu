@@ -137,6 +137,13 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
+// The epilogue's shared memory, behind the idle operand ring: per warp a [32][20] float slice,
+// then per warp a [32][kEpiTB] bf16 copy of the slice's outputs, then [4][BN] column sums.
+constexpr int kEpiTB = 18;
+__device__ __forceinline__ float* epi_colsum_smem(uint8_t* smem) {
+  return reinterpret_cast<float*>(smem) + 4 * 32 * 20 + 4 * 32 * kEpiTB / 2;
+}
+
 // TR: also write the transposed copy ep.out_t (EPI_BIAS_GELU, EPI_GELU_BWD); a template
 // parameter, so that the instantiations without it keep the plain epilogue's code
 template <int BN, int EPI, bool TR = false>
@@ -230,10 +237,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     // the slice's bf16 outputs again, for the optional transposed copy: rows of kTB = 18
     // elements (4-byte aligned; the two half-columns a lane pair reads fall on different banks)
     constexpr bool trans = TR && (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD);
-    constexpr int kTB = 18;
+    constexpr int kTB = kEpiTB;
     __nv_bfloat16* tstage = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<float*>(smem) + 4 * 32 * 20) +
                             warp * (32 * kTB);
-    float* csm = reinterpret_cast<float*>(smem) + 4 * 32 * 20 + 4 * 32 * kTB / 2;  // [4 warps][BN] column sums
+    float* csm = epi_colsum_smem(smem);
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
     const int quad = lane & 3, ro = lane >> 2;
     float* out_f32 = ep.out_f32 + (size_t)blockIdx.z * ep.slice_stride;
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   if (TR && EPI == EPI_GELU_BWD && ep.colsum != nullptr && s_ok && warp == 0) {
     // the four warps' column sums of this CTA's 128 rows, added in warp order
-    const float* csm = reinterpret_cast<const float*>(smem) + 4 * 32 * 20 + 4 * 32 * 18 / 2;
+    const float* csm = epi_colsum_smem(smem);
     for (int col = lane; col < BN; col += 32)
       ep.colsum[(size_t)blockIdx.y * ep.ldo + n0 + col] = ((csm[col] + csm[BN + col]) + csm[2 * BN + col]) + csm[3 * BN + col];
   }
