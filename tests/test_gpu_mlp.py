@@ -43,10 +43,13 @@ def test_forward_matches_oracle(B):
     assert _rel(y, yo) < 5e-3
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("B", [384, 300, 16384])
+def test_gradients_match_oracle(B):
+    """384 rows fill three 128-row tiles; 300 leave 84 zero-padded rows in the last (their
+    gradient rows must be zero and add nothing to the weight and bias sums); 16384 is the
+    benchmark's batch."""
     from paper_2603_12185_gb300 import comfree as CF
-    B = 384
-    net = CF.Mlp(FIN, H, O, max_batch=512, seed=5)
+    net = CF.Mlp(FIN, H, O, max_batch=max(B, 512), seed=5)
     x, a = _data(B, 6)
     g, loss = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(a).cuda())
     g = g.cpu().numpy()
