@@ -112,3 +112,31 @@ def test_impedance_features_from_records(cf):
     rec["flags"] = [cf.CONTACT_B_STATIC, 0, 0]
     x = cf.impedance_features(rec, 0.001)
     np.testing.assert_allclose(x, [[-0.5, 0.625, 0.125, 1], [1, 0.1, 0.3, 0], [-1, -0.3, 1.2, 0]], rtol=1e-6)
+
+
+def test_mlp_workspace_covers_its_buffers_without_a_device(cf):
+    """cf_mlp_workspace_bytes validates the layer sizes on the host and returns room for every
+    buffer: parameters, gradients and Adam moments (4 x fp32), the BF16 weights and their
+    transposes, the batch's BF16 activations, gradients and their transposes, the FP32 output,
+    the bias gradients' partial sums (per 64 and per 128 rows) and the split-K scratch."""
+    import ctypes as C
+    L = cf.lib()
+    n = C.c_size_t()
+    for bad in ((0, 256, 1024), (300, 256, 1024), (49, 200, 1024), (49, 256, 1000)):
+        assert cf.STATUS[L.cf_mlp_workspace_bytes(*bad, 1024, C.byref(n))] == "CF_ERR_INVALID_ARGUMENT"
+    assert cf.STATUS[L.cf_mlp_workspace_bytes(49, 256, 1024, 0, C.byref(n))] == "CF_ERR_INVALID_ARGUMENT"
+    fin, H, O = 49, 256, 1024
+    kin = 64
+    npar = H * kin + H + H * H + H + O * H + O
+    sizes = []
+    for B in (1, 300, 16384):
+        assert cf.STATUS[L.cf_mlp_workspace_bytes(fin, H, O, B, C.byref(n))] == "CF_OK"
+        Bp = (B + 127) // 128 * 128
+        floor = (4 * npar * 4                                    # w, g, m, v
+                 + 2 * (H * kin + 2 * H * H + 2 * O * H)          # W1, W2, W3 and W2^T, W3^T in BF16
+                 + 2 * Bp * (2 * kin + 10 * H + 2 * O)           # activations, gradients, transposes
+                 + 4 * Bp * O                                    # Y
+                 + 4 * ((Bp // 64) * O + 2 * (Bp // 32) * H))    # bias-gradient partials
+        assert n.value >= floor, (B, n.value, floor)
+        sizes.append(n.value)
+    assert sizes[0] < sizes[1] < sizes[2]
