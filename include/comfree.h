@@ -307,7 +307,10 @@ cf_status cf_mlp_param_count(const cf_mlp* mlp, int64_t* n);
 /* y[B][out] = MLP(x[B][in]) (device pointers, FP32 in and out) */
 cf_status cf_mlp_forward(cf_mlp* mlp, const float* x, int32_t B, float* y, void* stream);
 /* Gradient of the mean Gaussian negative log-likelihood of target[B][out/2] under the output
- * (log-stds clamped to [lo, hi]); grads[n_params] and loss[1] are device pointers (nullable). */
+ * (log-stds clamped to [lo, hi]); grads[n_params] and loss[1] are device pointers (nullable).
+ * The gradients are bitwise reproducible: every sum runs in a fixed order (split-K slices and
+ * the bias gradients' partial sums are added in order).  The loss adds one partial per block
+ * with an atomic, so its last bits may vary from call to call. */
 cf_status cf_mlp_gradients(cf_mlp* mlp, const float* x, const float* target, int32_t B, float logstd_lo,
                            float logstd_hi, float* grads, float* loss, void* stream);
 /* one Adam step (beta 0.9/0.999, eps 1e-8) on that loss */
