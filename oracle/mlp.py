@@ -6,6 +6,12 @@ float64 numpy.  With ``bf16=True`` every operand the tensor-core path stores in 
 weights, activations, pre-activations, back-propagated gradients) is rounded to BF16 at the same
 points, so the comparison isolates accumulation order; with ``bf16=False`` it is the exact
 function whose gradient the finite-difference pin checks.
+
+Parity unpinned: where the BF16 rounding sits (which intermediates are rounded) mirrors what
+the tensor-core kernels store; no CPU pin fixes it, only the GPU comparison does.  Everything
+else (GELU and its derivative, the layers, the NLL and its clamp, every back-propagation step)
+is pinned in tests/test_mlp_oracle.py, and tests/test_oracle_mutants.py checks that those pins
+catch planted mistakes.
 """
 import math
 
