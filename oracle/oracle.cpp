@@ -30,7 +30,10 @@
  * applies it.
  *
  * Parity pins (tests/test_oracle_pins.py) tie every stage to closed forms, hand-derived
- * worked examples, invariants, brute force or finite differences.
+ * worked examples, invariants, brute force or finite differences; tests/test_oracle_mutants.py
+ * plants mistakes in copies of this file and checks that a pin catches each.  Parity unpinned:
+ * absolute penetration depths against the paper's table (they depend on the readings of the
+ * impedance's units and trace, and on scenes that are not reproducible here).
  */
 #include <algorithm>
 #include <cmath>
