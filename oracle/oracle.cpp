@@ -31,9 +31,9 @@
  *
  * Parity pins (tests/test_oracle_pins.py) tie every stage to closed forms, hand-derived
  * worked examples, invariants, brute force or finite differences; tests/test_oracle_mutants.py
- * plants mistakes in copies of this file and checks that a pin catches each.  Parity unpinned:
- * absolute penetration depths against the paper's table (they depend on the readings of the
- * impedance's units and trace, and on scenes that are not reproducible here).
+ * plants mistakes in copies of this file and checks that a pin catches each.  The paper's
+ * penetration-depth table pins the order of its six impedance settings and, for a resting
+ * sphere, their magnitudes within a third; parity unpinned: the paper's MJWarp-relative claims.
  */
 #include <algorithm>
 #include <cmath>
