@@ -507,6 +507,74 @@ def test_resting_depths_follow_the_papers_depth_table(oracle):
 
 
 # ------------------------------------------------------------------------------------------
+# the paper's qualitative behaviours (Sec. IV-B, IV-C) on the oracle
+# ------------------------------------------------------------------------------------------
+def _trajectory(oracle, d, p, q, v, dt, steps, every):
+    out = []
+    for _ in range(steps // every):
+        q, v, _ = oracle.step(d, p, dt, every, q, v)
+        out.append((q.copy(), v.copy()))
+    return out
+
+
+def test_torsional_friction_decays_a_spin_faster_for_a_larger_coefficient(oracle):
+    """Sec. IV-B: a sphere held to spin about the normal (a vertical hinge through its centre,
+    2 mm into the floor) loses its spin monotonically, faster for the larger mu_tor.  The contact
+    point lies on the hinge axis, so the translational trace is zero; the per-body 1/m
+    impedance (trace_mode 1) is used."""
+    finals = {}
+    for mu_tor in (0.002, 0.01):
+        d = Wd.world([dict(parent=-1, jnt=S.HINGE, pos=(0, 0, 0.048), axis=(0, 0, 1), mass=1.0,
+                           inertia=(1e-3, 1e-3, 1e-3))],
+                     [dict(type=S.PLANE, body=-1, mu=(0.5, mu_tor, 0.0)),
+                      dict(type=S.SPHERE, body=0, size=(0.05, 0, 0), mu=(0.5, mu_tor, 0.0))])
+        p = Wd.params(n_t=4, n_tor=2, n_rol=0, trace_mode=1)
+        w = np.array([v[0] for _, v in _trajectory(oracle, d, p, [0.0], [10.0], DT, 500, 25)])
+        assert np.all(np.diff(w) < 0.0) and w[-1] > 0.0
+        finals[mu_tor] = w[-1]
+    assert finals[0.01] < finals[0.002]
+
+
+def test_rolling_friction_decays_a_roll_faster_for_a_larger_coefficient(oracle):
+    """Sec. IV-B: a capsule rolling without slip along +x slows monotonically, faster for the
+    larger mu_rol."""
+    finals = {}
+    for mu_rol in (0.002, 0.01):
+        d = Wd.world([dict(mass=1.0, inertia=(2e-3, 2e-3, 5e-4))],
+                     [dict(type=S.PLANE, body=-1, mu=(0.8, 0.0, mu_rol)),
+                      dict(type=S.CAPSULE, body=0, size=(0.03, 0.05, 0), mu=(0.8, 0.0, mu_rol))])
+        p = Wd.params(n_t=8, n_tor=2, n_rol=8)
+        R = np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]], float)      # capsule axis along y
+        q0 = np.array([0, 0, 0.028, *S.quat_about((1, 0, 0), np.pi / 2)])
+        v0 = np.array([0.5, 0, 0, *(R.T @ np.array([0, 0.5 / 0.03, 0]))])
+        vx = np.array([v[0] for _, v in _trajectory(oracle, d, p, q0, v0, DT, 1000, 50)])
+        assert np.all(np.diff(vx[2:]) < 0.0) and vx[-1] > 0.0
+        finals[mu_rol] = vx[-1]
+    assert finals[0.01] < finals[0.002]
+
+
+@pytest.mark.parametrize("dt", [0.002, 0.02])
+def test_thrown_cube_slides_to_rest_without_drift(oracle, dt):
+    """Sec. IV-C: a cube thrown onto a plane with v = (2, 0, 0) and omega = (0.1, 0.1, 0.1) slides
+    to rest; its horizontal speed never grows once it slides, and it settles without drift, also
+    at dt = 0.02 s (where it rests deeper: about 17 mm against 2.2 mm at dt = 2 ms)."""
+    d = Wd.world([dict(mass=1.0, inertia=S.box_mass_inertia([0.05] * 3, 1.0)[1])],
+                 [dict(type=S.PLANE, body=-1, mu=(0.5, 0, 0)),
+                  dict(type=S.BOX, body=0, size=(0.05, 0.05, 0.05), mu=(0.5, 0, 0))])
+    p = Wd.params(n_t=4, k_user=0.3, d_user=0.005)
+    steps = int(round(3.0 / dt))
+    tr = _trajectory(oracle, d, p, np.array([0, 0, 0.2, 1, 0, 0, 0.0]), np.array([2.0, 0, 0, 0.1, 0.1, 0.1]), dt,
+                     steps, max(1, steps // 60))
+    speed = np.array([np.hypot(v[0], v[1]) for _, v in tr])
+    z = np.array([q[2] for q, _ in tr])
+    assert speed[-1] < 0.05 * 2.0
+    land = int(np.argmax(z < 0.06))
+    assert np.all(np.diff(speed[land + 1:]) <= 1e-9)
+    # at rest without drift, penetrating (the gap term's g dt^2 deepens the rest at dt = 0.02 s)
+    assert abs(z[-1] - z[-5]) < 1e-4 and (0.045 if dt == 0.002 else 0.03) < z[-1] < 0.05
+
+
+# ------------------------------------------------------------------------------------------
 # invariants
 # ------------------------------------------------------------------------------------------
 def test_sphere_sphere_conserves_momentum(oracle):
