@@ -583,14 +583,12 @@ def run_extras(rank):
     return {k: fn(rank) for k, fn in EXTRAS.items()}
 
 
-def cpu_baseline(nbody, rank, budget_s=40.0, min_steps=100):
-    """The FP64 oracle as it stands, OpenMP over the host cores, on a bounded sample of the timed
-    workload.  For the 256-body headline: the 16 sampled worlds (0, 256, ..., 3840) of the same
-    seeded 4096-world batch at step 800 of the episode, where the GPU's timed window starts
-    (advanced there by the oracle alone, oracle/late_states.py), stepped from there for at least
-    min_steps steps or until the budget is spent.  Other body counts: the same batch's first
-    worlds from their initial state (the sample says so)."""
-    from oracle import oracle as O
+def _oracle_sample(nbody, rank):
+    """The bounded sample of the headline workload that the oracle steps: for 256 bodies the 16
+    sampled worlds (0, 256, ..., 3840) of the seeded 4096-world batch at step 800 of the episode,
+    where the GPU's timed window starts (advanced there by the oracle alone,
+    oracle/late_states.py); other body counts, 16 worlds of the same workload from the initial
+    state.  Returns (scene batch, its step, a description, q, v in FP64)."""
     from paper_2603_12185_gb300 import scenes as S
     late = None
     if nbody == 256 and rank == 0:
@@ -606,10 +604,18 @@ def cpu_baseline(nbody, rank, budget_s=40.0, min_steps=100):
         sb = S.make_pile(16, nbody, seed=R.rank_seed(1000, rank))
         start = 0
         where = f"16 worlds x {nbody} bodies of the same seeded workload from the initial state"
-    nw = sb.nworld
-    runner = O.BatchRunner([sb.world(w) for w in range(nw)], sb.params)
     q = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.q0])
     v = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.v0])
+    return sb, start, where, q, v
+
+
+def cpu_baseline(nbody, rank, budget_s=40.0, min_steps=100):
+    """The FP64 oracle as it stands, OpenMP over the host cores, on the bounded sample of
+    `_oracle_sample`, stepped for at least min_steps steps or until the budget is spent."""
+    from oracle import oracle as O
+    sb, start, where, q, v = _oracle_sample(nbody, rank)
+    nw = sb.nworld
+    runner = O.BatchRunner([sb.world(w) for w in range(nw)], sb.params)
     cores = O.max_threads()
     chunk, done, t_total, contacts = 5, 0, 0.0, 0
     while done < min_steps or t_total < budget_s / 4:
@@ -636,24 +642,8 @@ def reference_arm(args, budget_s=240.0):
     more untimed step measures the step time; if K + W steps of all 16 worlds would exceed
     `budget_s`, each step takes fewer worlds (never fewer than the host's threads)."""
     from oracle import oracle as O
-    from paper_2603_12185_gb300 import scenes as S
     nbody = args.bodies
-    late = None
-    if nbody == 256:
-        from oracle import late_states as LS
-        if os.path.exists(LS.PATH):
-            late = LS
-    if late is not None:
-        sb, _ = late.load()
-        start = late.STEPS
-        where = (f"worlds {late.WORLDS[0]}, {late.WORLDS[1]}, ..., {late.WORLDS[-1]} of the seeded 4096 x {nbody} "
-                 f"batch from their step-{start} state (the start of the GPU's timed window; oracle-advanced)")
-    else:
-        sb = S.make_pile(16, nbody, seed=R.rank_seed(1000, 0))
-        start = 0
-        where = f"16 worlds x {nbody} bodies of the same seeded workload from the initial state"
-    q = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.q0])
-    v = np.concatenate([np.asarray(x, np.float32).astype(np.float64) for x in sb.v0])
+    sb, start, where, q, v = _oracle_sample(nbody, 0)
     cores = O.max_threads()
     runner = O.BatchRunner([sb.world(w) for w in range(sb.nworld)], sb.params)
     t0 = time.perf_counter()
