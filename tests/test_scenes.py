@@ -100,3 +100,17 @@ def test_sphere_and_box_inertia_against_integration():
     m, i = S.box_mass_inertia(np.array(hs), 8.0 * np.prod(hs))
     assert m == pytest.approx(vol, rel=1e-12)
     assert i[0] == pytest.approx(ixx, rel=1e-3) and i[2] == pytest.approx(izz, rel=1e-3)
+
+
+def test_cylinder_and_ellipsoid_inertia_against_integration():
+    r, h = 0.03, 0.05                                  # radius, half length along z
+    vol, ixx, izz = _grid_inertia(lambda x, y, z: x * x + y * y <= r * r, (r, r, h))
+    m, i = S.cylinder_mass_inertia(r, h, 1.0)
+    assert m == pytest.approx(vol, rel=1e-2)
+    assert i[0] == pytest.approx(ixx, rel=1e-2) and i[2] == pytest.approx(izz, rel=1e-2)
+    e = np.array([0.05, 0.03, 0.02])
+    inside = lambda x, y, z: (x / e[0]) ** 2 + (y / e[1]) ** 2 + (z / e[2]) ** 2 <= 1.0
+    vol, ixx, izz = _grid_inertia(inside, tuple(e))
+    m, i = S.ellipsoid_mass_inertia(e, 1.0)
+    assert m == pytest.approx(vol, rel=1e-2)
+    assert i[0] == pytest.approx(ixx, rel=1e-2) and i[2] == pytest.approx(izz, rel=1e-2)
