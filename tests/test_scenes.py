@@ -114,3 +114,38 @@ def test_cylinder_and_ellipsoid_inertia_against_integration():
     m, i = S.ellipsoid_mass_inertia(e, 1.0)
     assert m == pytest.approx(vol, rel=1e-2)
     assert i[0] == pytest.approx(ixx, rel=1e-2) and i[2] == pytest.approx(izz, rel=1e-2)
+
+
+def test_hand_geometry_by_forward_kinematics():
+    """The hand as its generator describes it, read back through the oracle's (separately pinned)
+    forward kinematics: finger f's base at radius 6.5 cm, azimuth pi/4 + f pi/2, height 1.5 cm;
+    its first joint about the vertical, the other three about the horizontal flexion axis, and a
+    positive flexion curls the finger toward the centre; links stacked end to end."""
+    from oracle import oracle as O
+    sb = S.make_hand(1, seed=0)
+    d = sb.world(0)
+    q = np.array(sb.q0[0], float)
+    nq = len(q)
+    q[7:] = 0.0
+    _, _, P = O.dynamics(d, (0, 0, -9.81), q, np.zeros(len(sb.v0[0])))
+    for f in range(4):
+        a = np.pi / 4 + f * np.pi / 2
+        er = np.array([np.cos(a), np.sin(a), 0.0])
+        b0 = 1 + 4 * f
+        np.testing.assert_allclose(P[b0, :3], 0.065 * er + [0, 0, 0.015], atol=1e-12)
+        R0 = P[b0, 3:12].reshape(3, 3)
+        np.testing.assert_allclose(R0 @ d["body_axis"][b0], [0, 0, 1], atol=1e-12)   # abduction: vertical
+        for j in range(1, 4):
+            b = b0 + j
+            R = P[b, 3:12].reshape(3, 3)
+            ax = R @ d["body_axis"][b]
+            assert abs(ax[2]) < 1e-12                                                  # flexion: horizontal
+            L = d["body_pos"][b][2]
+            assert 0.03 <= L <= 0.05
+            np.testing.assert_allclose(P[b, :3], P[b - 1, :3] + P[b - 1, 3:12].reshape(3, 3) @ [0, 0, L], atol=1e-12)
+        tip = lambda PP: PP[b0 + 3, :3] + PP[b0 + 3, 3:12].reshape(3, 3) @ [0, 0, 0.04]
+        qc = q.copy()
+        qc[7 + 4 * f + 1] = 0.5                                                        # flex the second joint
+        _, _, Pc = O.dynamics(d, (0, 0, -9.81), qc, np.zeros(len(sb.v0[0])))
+        assert np.hypot(*tip(Pc)[:2]) < np.hypot(*tip(P)[:2]) - 0.01
+    assert nq == 23
