@@ -140,3 +140,31 @@ def test_mlp_workspace_covers_its_buffers_without_a_device(cf):
         assert n.value >= floor, (B, n.value, floor)
         sizes.append(n.value)
     assert sizes[0] < sizes[1] < sizes[2]
+
+
+def declared_signatures():
+    """{name: number of parameters} of every function include/comfree.h declares."""
+    src = open(os.path.join(ROOT, "include", "comfree.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for name, args in re.findall(r"\b(cf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        args = " ".join(args.split())
+        out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_passes_every_declared_parameter(cf):
+    """The ctypes binding declares, for every entry point of the header, as many arguments as
+    the header's prototype has: a mismatch would shift every later argument of the call."""
+    sigs = declared_signatures()
+    assert len(sigs) >= 19
+    L = cf.lib()
+    missing = []
+    for name, n in sigs.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            missing.append(name)
+            continue
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+    assert not missing, missing
