@@ -168,3 +168,71 @@ def test_binding_passes_every_declared_parameter(cf):
             continue
         assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
     assert not missing, missing
+
+
+def _c_kind(decl):
+    """Kind of one C parameter declaration: ('ptr',), ('float', bytes) or ('int', bytes)."""
+    d = " ".join(decl.replace("const ", " ").split())
+    if "*" in d or "[" in d:          # an array parameter decays to a pointer
+        return ("ptr",)
+    t = d.rsplit(" ", 1)[0] if " " in d else d
+    sizes = {"int32_t": ("int", 4), "int": ("int", 4), "uint32_t": ("int", 4), "int64_t": ("int", 8),
+             "uint64_t": ("int", 8), "size_t": ("int", 8), "float": ("float", 4), "double": ("float", 8),
+             "cf_status": ("int", 4)}  # an enum, passed as a C int
+    return sizes.get(t, ("other", t))
+
+
+def _ctypes_kind(t):
+    import ctypes as C
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return ("ptr",)
+    if t in (C.c_float, C.c_double):
+        return ("float", C.sizeof(t))
+    return ("int", C.sizeof(t))
+
+
+def test_binding_argument_kinds_match_the_header(cf):
+    """Every argument's kind as the binding passes it (pointer, floating point of a width,
+    integer of a width) matches the header's prototype."""
+    src = open(os.path.join(ROOT, "include", "comfree.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    L = cf.lib()
+    checked = 0
+    for name, args in re.findall(r"\b(cf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        args = " ".join(args.split())
+        if args in ("", "void"):
+            continue
+        kinds = [_c_kind(a) for a in args.split(",")]
+        assert all(k[0] != "other" for k in kinds), (name, kinds)
+        got = [_ctypes_kind(t) for t in getattr(L, name).argtypes]
+        assert got == kinds, (name, got, kinds)
+        checked += 1
+    assert checked >= 35
+
+
+def test_binding_return_kinds_match_the_header(cf):
+    """cf_status returns come back as a C int (ctypes' default), strings as char pointers (a
+    default int would truncate the pointer), sizes as size_t, void functions as None."""
+    import ctypes as C
+    src = open(os.path.join(ROOT, "include", "comfree.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    L = cf.lib()
+    seen = 0
+    for ret, name in re.findall(r"(?m)^\s*((?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**)\s*\b(cf_[a-z_0-9]+)\s*\(", src):
+        ret = " ".join(ret.replace("*", " * ").split())
+        rt = getattr(L, name).restype
+        if ret == "cf_status":
+            assert rt is C.c_int, name
+        elif ret == "const char *":
+            assert rt is C.c_char_p, name
+        elif ret == "void":
+            assert rt is None, name
+        elif ret in ("size_t", "int32_t", "int", "float", "double"):
+            want = {"size_t": C.c_size_t, "int32_t": C.c_int32, "int": C.c_int, "float": C.c_float,
+                    "double": C.c_double}[ret]
+            assert rt is not None and C.sizeof(rt) == C.sizeof(want) and \
+                (rt in (C.c_float, C.c_double)) == (want in (C.c_float, C.c_double)), name
+        else:
+            raise AssertionError(f"{name}: unexpected return type {ret}")
+        seen += 1
+    assert seen == len(declared_functions())
