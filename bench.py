@@ -397,6 +397,24 @@ def extra_spheres(rank):
             "world_steps_per_s_500_steps_per_launch": 64 * 500 / (ms500 / 1e3)}
 
 
+def algorithmic_bytes_per_step(sb, controls=False):
+    """Algorithmic HBM bytes of one step of every world of a scene batch (the roofline's
+    numerator): a pile world moves BYTES_PER_BODY per body (q and v read and written, its
+    8-float parameter block read); an articulated world reads and writes its q and v and, when
+    controls are set, reads one torque per hinge."""
+    from paper_2603_12185_gb300 import scenes as S
+    total = 0
+    for w in range(sb.nworld):
+        t = sb.template_of(w)
+        if t.pile:
+            total += BYTES_PER_BODY * len(t.body_parent)
+        else:
+            total += 8 * (len(sb.q0[w]) + len(sb.v0[w]))
+            if controls:
+                total += 4 * int((np.asarray(t.body_jnt) == S.HINGE).sum())
+    return total
+
+
 def extra_mixed(rank):
     """Uneven worlds: 8192 worlds interleaving pile16/pile64/pile256/hand, one launch per step,
     eager and from a CUDA graph of ten launches."""
@@ -411,9 +429,13 @@ def extra_mixed(rank):
     c = b.contact_counts()
     g = b.graph(sb.dt, 1, repeat=10)
     ms_graph = _timed(g.replay, 5) / 10
+    by = algorithmic_bytes_per_step(sb)
+    pk, src = peaks()
+    gbs = by / (ms / 1e3) / 1e9
     return {"world_steps_per_s": 8192 / (ms / 1e3), "ms_per_step": ms,
             "world_steps_per_s_graph": 8192 / (ms_graph / 1e3), "ms_per_step_graph": ms_graph,
-            "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen]}
+            "contacts_per_world": float(c.mean()), "warps_per_world": [int(x) for x in chosen],
+            "bytes_per_step": by, "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "peak_source": src}
 
 
 def extra_impedance(rank):

@@ -19,3 +19,16 @@ def test_reference_arm_times_k_steps_after_w(monkeypatch):
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert "steps 4..6 timed after 3 untimed" in cb["sample"]
+
+
+def test_algorithmic_bytes_of_the_workloads():
+    """The roofline's numerator: 136 B per pile body (q and v read and written, the 8-float
+    parameter block read), q and v of an articulated world read and written (and, with
+    controls, 16 torques of a hand read); the 4096 x 256 headline comes to 142.6 MB."""
+    from paper_2603_12185_gb300 import scenes as S
+    assert bench.BYTES_PER_BODY == 136
+    sb = S.make_mixed(8, seed=0)                      # worlds: pile16, pile64, pile256, hand, twice
+    per_pile = 136 * (16 + 64 + 256)
+    assert bench.algorithmic_bytes_per_step(sb) == 2 * per_pile + 2 * (23 + 22) * 8
+    assert bench.algorithmic_bytes_per_step(sb, controls=True) == 2 * per_pile + 2 * bench.HAND_BYTES
+    assert bench.algorithmic_bytes_per_step(S.make_pile(64, 256, seed=0)) * 64 == 142606336
