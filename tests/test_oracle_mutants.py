@@ -112,6 +112,24 @@ MUTANTS = [
     ("learned impedance: hidden units without their bias",
      "S a(b1[h]);",
      "S a(0.0);"),
+    ("learned impedance: gap feature not scaled by the solimp width",
+     "x[0] = clampv(phi / S(width), S(-1.0), S(1.0));",
+     "x[0] = clampv(phi, S(-1.0), S(1.0));"),
+    ("learned impedance: normal-row feature clamped at 1 instead of 4",
+     "x[2] = clampv(w_n / trace_sum, S(0.0), S(4.0));",
+     "x[2] = clampv(w_n / trace_sum, S(0.0), S(1.0));"),
+    ("learned impedance: static-side flag inverted",
+     "x[3] = S(b_static ? 1.0 : 0.0);",
+     "x[3] = S(b_static ? 0.0 : 1.0);"),
+    ("learned impedance: free-body lever from the body origin instead of the centre of mass",
+     "V3<S> u = mulT(P[b].R, cross(p - P[b].com, n));",
+     "V3<S> u = mulT(P[b].R, cross(p - P[b].x, n));"),
+    ("learned impedance: network output not clamped",
+     "if (prm->trace_mode == 3) mphi *= exp(clampv(impnet_g(prm->impnet, feat), S(-IMP_CLAMP), S(IMP_CLAMP)));",
+     "if (prm->trace_mode == 3) mphi *= exp(impnet_g(prm->impnet, feat));"),
+    ("learned impedance: hidden units linear instead of tanh",
+     "g += S(w2[h]) * tanh(a);",
+     "g += S(w2[h]) * a;"),
     # the contact frame
     ("left-handed contact frame",
      "t2 = cross(n, t1);",
