@@ -1244,20 +1244,20 @@ def test_dual_gradient_matches_finite_differences(oracle):
 def test_batch_runner_equals_single_world_steps(oracle):
     """The OpenMP batch entry point (the timed CPU baseline and the parity runs) steps every world
     exactly as the single-world step does: same bits, any thread count."""
-    sb = S.make_mixed(8, seed=4)
+    sb = S.make_mixed(4, seed=4)                     # a 16-, 64- and 256-body pile and a hand
     q = np.concatenate([np.asarray(x, np.float64) for x in sb.q0])
     v = np.concatenate([np.asarray(x, np.float64) for x in sb.v0])
     outs = []
     for threads in (1, 3):
         runner = oracle.BatchRunner([sb.world(w) for w in range(sb.nworld)], sb.params)
         qb, vb = q.copy(), v.copy()
-        counts = runner.run(qb, vb, sb.dt, 20, nthreads=threads)
+        counts = runner.run(qb, vb, sb.dt, 10, nthreads=threads)
         outs.append((qb, vb, counts))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     qo = vo = 0
     for w in range(sb.nworld):
         nq, nv = len(sb.q0[w]), len(sb.v0[w])
-        qs, vs, nc = oracle.step(sb.world(w), sb.params, sb.dt, 20, sb.q0[w], sb.v0[w])
+        qs, vs, nc = oracle.step(sb.world(w), sb.params, sb.dt, 10, sb.q0[w], sb.v0[w])
         assert np.array_equal(outs[0][0][qo:qo + nq], qs) and np.array_equal(outs[0][1][vo:vo + nv], vs)
         assert outs[0][2][w] == nc
         qo += nq
